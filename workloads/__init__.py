@@ -1,0 +1,27 @@
+"""Seeded synthetic GRAPE problems shaped like the paper's transmon-cavity workloads.
+
+This module only *builds inputs*: Hamiltonian matrices (as scipy CSR), initial
+states, targets, forbidden-state projectors and seeded control amplitudes.  It
+holds none of the method's arithmetic (no propagation, no cost, no gradient),
+so that both the CPU oracle (``oracle/``) and the CUDA path
+(``paper_2304_06200_gb300``) can be fed the same problems without sharing code.
+
+Physical model (Sec. II; benchmark Hamiltonian Eq. (fockH) in Sec. IV.B): in
+the frame rotating with the drives, a transmon ``b`` (anharmonicity alpha) is
+dispersively coupled to a cavity ``a`` (shift chi) and both are driven by
+x/y quadrature controls.  Units: angular frequency in rad/ns (``X/2pi = v GHz``
+means ``X = 2 pi v``), time in ns.
+"""
+
+from .transmon import (  # noqa: F401
+    Problem,
+    build_config,
+    config_names,
+    smooth_controls,
+    haar_unitary,
+    transmon_cavity,
+    two_transmon_cavity,
+    two_level_rabi,
+    random_problem,
+    batch_instances,
+)
