@@ -1,0 +1,185 @@
+/*
+ * grape_hg.h -- C ABI of the GB300 hard-coded-gradient (HG) GRAPE library.
+ *
+ * One evaluation returns the composite GRAPE cost and its gradient with respect
+ * to every piecewise-constant control amplitude (arXiv:2304.06200, Sec. II and
+ * Sec. III).  Propagators exp(-i H_n dt) are never formed: each step applies the
+ * scaled truncated-Taylor action (e^{B}_m)^s, B = -i H_n dt / s (Sec. III.B, Eqs.
+ * (scaling squaring equation), (eBm equation), (eBmpsi)), with (m, s) chosen per
+ * step by the paper's error bound E_A(m, s) <= tau (Eq. (accuracy inequality),
+ * App. C Eq. (overallupperbound)).  The gradient follows the forward-backward
+ * scheme of Sec. III.C / Fig. 1: a forward sweep to psi_N, then a backward sweep
+ * that re-propagates psi and the costate with the adjoint step and accumulates
+ * <costate| dU_n/du_kn |psi_{n-1}> (Eqs. (stgradient), (gategradient),
+ * (C2stgrad)), the derivative being that of the Taylor approximant at frozen
+ * (m, s) (Eq. (auxiliary equation)).
+ *
+ * Cost (all terms optional through their weights):
+ *   C     = w_fid * C1 + w_forbid * C2 + w_amp * C_amp
+ *   C1    = 1 - |g / n|^2,  g = sum_h <phi_T^h | psi_N^h>     Eq. (C1st) / gate form, Sec. III.A
+ *   C2    = 1/(N n) sum_{n'=1..N} sum_h <psi_n'^h|Omega|psi_n'^h>   App. A, Eq. (c2st)
+ *   C_amp = 1/N sum_{k,n} u_kn^2                    amplitude penalty named in Sec. II
+ * with n = n_states columns propagated together as one block.
+ *
+ * Conventions
+ *   - Complex numbers are interleaved (re, im) doubles.
+ *   - State blocks (psi0, target) are dim x n_states, column-major: column h is
+ *     dim contiguous complex numbers.
+ *   - Controls u and gradients are n_controls x n_steps doubles, row-major
+ *     (row k = control channel k, column n = time step n).
+ *   - Every function returns a grape_status; no C++ exception crosses the ABI.
+ *     On failure grape_last_error() returns a thread-local message.
+ *   - Host arrays passed to grape_problem_create are deep-copied: the caller
+ *     keeps ownership.  The problem object owns all device memory it uses.
+ *   - One problem must not be used from two host threads or two streams at once.
+ */
+#ifndef GRAPE_HG_H
+#define GRAPE_HG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GRAPE_ABI_VERSION 1
+
+typedef struct grape_problem grape_problem;
+
+typedef enum {
+  GRAPE_OK = 0,
+  GRAPE_EINVAL = 1,          /* bad argument, shape or pointer                                */
+  GRAPE_ENOMEM = 2,          /* a device or host allocation failed                            */
+  GRAPE_ECUDA = 3,           /* a CUDA runtime call failed (message in grape_last_error)      */
+  GRAPE_ETOL = 4,            /* some step has no (m, s) with E_A(m, s) <= tau (App. C)         */
+  GRAPE_ETIMEOUT = 5,        /* a bounded device wait gave up                                 */
+  GRAPE_ENOTHERMITIAN = 6,   /* H0 or some H_k is not Hermitian                               */
+  GRAPE_ESTATE = 7,          /* call order: grape_grad without a preceding grape_cost         */
+  GRAPE_ENONFINITE = 8       /* a control amplitude is NaN or infinite                       */
+} grape_status;
+
+typedef enum { GRAPE_CSR = 0, GRAPE_DENSE = 1 } grape_format;
+
+/* Arithmetic of the propagation bulk.  Cost, overlaps, gradient sums and the
+ * step norms are FP64 in every mode. */
+typedef enum {
+  GRAPE_FP64 = 0,        /* complex128 throughout                                        */
+  GRAPE_FP32_BULK = 1    /* Taylor increments in complex64, states/costates kept FP64     */
+} grape_precision;
+
+/* One Hermitian operator (H0 or a control H_k), dim x dim.
+ *   fmt == GRAPE_CSR:   rowptr[dim+1] (int64, rowptr[0] == 0), colind[nnz] (int32, 0-based,
+ *                       any order within a row, no duplicates), values[2*nnz] complex.
+ *   fmt == GRAPE_DENSE: values[2*dim*dim] complex, row-major; rowptr/colind ignored.
+ * Zero entries of a dense operator are dropped. */
+typedef struct {
+  int32_t fmt;
+  int64_t nnz;
+  const int64_t* rowptr;
+  const int32_t* colind;
+  const double* values;
+} grape_op;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  alloc
+ * returns a device pointer aligned to 256 bytes or NULL; free releases it.
+ * Both NULL: cudaMalloc / cudaFree. */
+typedef void* (*grape_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*grape_free_fn)(void* ptr, size_t bytes, void* ctx);
+
+typedef struct {
+  int64_t dim;                 /* Hilbert-space dimension d                               */
+  int32_t n_controls;          /* K >= 0 (at most 32)                                      */
+  int32_t n_steps;             /* N >= 1                                                  */
+  int32_t n_states;            /* n, 1 <= n <= dim: columns propagated together           */
+  double dt;                   /* step length (> 0), same time unit as 1/H                */
+  grape_op H0;                 /* drift H_s                                               */
+  const grape_op* Hk;          /* K control operators h_k                                 */
+  const double* psi0;          /* dim x n complex, column-major: initial states psi_0^h   */
+  const double* target;        /* dim x n complex, column-major: phi_T^h = U_T psi_0^h    */
+  const double* omega_diag;    /* dim real: diagonal of the forbidden-state operator, or NULL */
+  double w_fid, w_forbid, w_amp;   /* weights alpha_1..alpha_3 of the composite cost      */
+  double tau;                  /* tolerance of the (m, s) rule, 0 < tau < 1                */
+  int32_t m_max;               /* largest Taylor order considered, 1..60 (0 = 60)          */
+  int32_t ckpt_every;          /* M: psi checkpoint every M steps for the backward sweep;
+                                  0 = automatic, < 0 = no checkpoints (pure re-propagation) */
+  int32_t precision;           /* grape_precision                                         */
+  int32_t cluster;             /* CTAs per column team: 0 = automatic, else 1,2,4,8,16     */
+  int32_t device;              /* CUDA device ordinal                                     */
+  grape_alloc_fn alloc;        /* optional device allocator (see above)                   */
+  grape_free_fn free;
+  void* alloc_ctx;
+} grape_desc;
+
+/* Information about a problem (valid after create; schedule fields after an evaluation). */
+typedef struct {
+  int64_t device_bytes;        /* device memory held by the problem                      */
+  int64_t union_nnz;           /* non-zeros of the union pattern of H0 and all H_k        */
+  int64_t ctrl_entries;        /* stored control entries (sum of nnz(H_k))                 */
+  int32_t sigma;               /* sigma': largest row count of the union pattern (Eq. (sigmapdef)) */
+  int32_t m_cap;               /* largest Taylor order the schedule table can return      */
+  int32_t s_cap;               /* largest scaling factor the schedule table can return    */
+  int32_t cluster;             /* CTAs per column team actually used                      */
+  int32_t ckpt_every;          /* checkpoint spacing actually used (0 = none)             */
+  int32_t smem_bytes;          /* dynamic shared memory per CTA of the sweep kernels       */
+  int64_t total_terms;         /* sum over steps of m_n * s_n for the last evaluation (-1 before) */
+  double max_norm;             /* max_n ||A_n||_1 of the last evaluation (-1 before)       */
+} grape_info;
+
+/* Create a problem (Sec. II: H(t) = H_s + sum_k a_k(t) h_k, piecewise constant over N steps
+ * of length dt).  Validates shapes, Hermiticity and finiteness, builds the union sparsity
+ * pattern, the (m, s) breakpoint table of App. C for the given tau and sigma', and
+ * uploads everything to the device.  On failure *out is set to NULL. */
+grape_status grape_problem_create(const grape_desc* desc, grape_problem** out);
+
+/* Release every resource of the problem (NULL is accepted). */
+void grape_problem_destroy(grape_problem* prob);
+
+/* One full evaluation: cost (forward sweep, Fig. 1(a)) and gradient (backward sweep,
+ * Fig. 1(b)).
+ *   u     n_controls x n_steps controls (row-major), host or device per on_device.
+ *   cost  1 double (host or device); grad n_controls x n_steps doubles or NULL.
+ *   on_device  0: u, cost, grad are host pointers (the call synchronises the stream
+ *              and reports device-side errors); 1: device pointers (asynchronous,
+ *              call grape_sync_status to collect device-side errors).
+ *   stream  cudaStream_t to run on (NULL = legacy default stream). */
+grape_status grape_cost_and_grad(grape_problem* prob, const double* u, double* cost, double* grad,
+                                 int32_t on_device, void* stream);
+
+/* Forward sweep only (Fig. 1(a)): cost, with the state needed by a later grape_grad
+ * (psi_N, checkpoints, g) kept inside the problem. */
+grape_status grape_cost(grape_problem* prob, const double* u, double* cost, int32_t on_device, void* stream);
+
+/* Backward sweep only (Fig. 1(b)) for the controls of the preceding grape_cost call.
+ * GRAPE_ESTATE if no forward sweep has run. */
+grape_status grape_grad(grape_problem* prob, double* grad, int32_t on_device, void* stream);
+
+/* Wait for the problem's pending work on `stream` and return the device error word
+ * (GRAPE_OK, GRAPE_ETOL, GRAPE_ENONFINITE or GRAPE_ETIMEOUT); the word is then cleared. */
+grape_status grape_sync_status(grape_problem* prob, void* stream);
+
+/* Problem information (see grape_info). */
+grape_status grape_problem_info(grape_problem* prob, grape_info* info);
+
+/* Per-step schedule of the last evaluation, copied to host arrays of n_steps entries
+ * each (any may be NULL): Taylor order m_n, scaling factor s_n, and ||A_n||_1. */
+grape_status grape_step_schedule(grape_problem* prob, int32_t* m, int32_t* s, double* norm1);
+
+/* The paper's rule on the host (Sec. III.B; App. C Eq. (overallupperbound)): the smallest
+ * s, then the smallest m <= m_max, with E_A(m, s) <= tau for ||A||_1 = x and sigma' = sigma,
+ * unit roundoff 2^-53 (precision GRAPE_FP64) or 2^-24 (GRAPE_FP32_BULK).
+ * GRAPE_ETOL if no pair with s <= s_max qualifies.  Pure host computation. */
+grape_status grape_select_ms(double x, double tau, int32_t sigma, int32_t precision, int32_t m_max,
+                             int32_t s_max, int32_t* m, int32_t* s);
+
+/* E_A(m, s) itself (App. C Eq. (overallupperbound)); +inf when s R_m(x/s) >= 1. */
+double grape_error_bound(double x, int32_t m, int32_t s, int32_t sigma, int32_t precision);
+
+const char* grape_status_string(grape_status st);
+const char* grape_last_error(void);
+int32_t grape_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRAPE_HG_H */

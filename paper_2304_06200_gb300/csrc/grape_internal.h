@@ -1,0 +1,150 @@
+// Internal declarations shared by the host library and the CUDA kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace grape {
+
+constexpr int kMaxControls = 32;
+constexpr int kMaxTaylor = 60;       // m_max cap (Sec. III.B leaves it open)
+constexpr int kMaxCluster = 16;
+constexpr int kOwnerShift = 20;      // column encoding: bit 31 = entry carries control terms,
+constexpr uint32_t kLocalMask = (1u << kOwnerShift) - 1u;   // bits 20..27 owner CTA, bits 0..19 local row
+constexpr uint32_t kCtrlBit = 1u << 31;
+
+// Device error word values (same numbering as grape_status).
+constexpr int kErrTol = 4;
+constexpr int kErrTimeout = 5;
+constexpr int kErrNonFinite = 8;
+
+// Everything a sweep kernel needs; passed by value.
+struct SweepParams {
+  // problem
+  int dim, K, N, n_states, CL, R;      // CL = CTAs per column team, R = rows per CTA
+  double dt;
+  double w_fid, w_forbid, w_amp;
+  int ckpt_every;                      // 0 = no checkpoints
+  int n_ckpt;                          // number of stored checkpoints
+  int m_cap;
+  // union pattern (global)
+  const int64_t* rowptr;               // dim + 1
+  const uint32_t* colenc;              // nnz, per CL-partition encoding (owner, local, ctrl bit)
+  const double2* h0v;                  // nnz drift values on the union pattern
+  // per-control contribution lists: entries of control k are [cptr[k], cptr[k+1]) sorted by entry
+  const int* cptr;                     // K + 1
+  const int* cidx;                     // global union-entry index
+  const double2* cval;                 // value of h_k at that entry
+  const int* cslice;                   // [(k * CL + rank) * 2 + {0,1}]: range of control k inside rank's rows
+  // controls and schedule
+  const double* u;                     // K x N row-major (device)
+  const int* ms_m;                     // N
+  const int* ms_s;                     // N
+  // states
+  const double2* psi0;                 // d x n column-major
+  const double2* target;               // d x n
+  const double* omega;                 // d or nullptr
+  double2* psiN;                       // d x n
+  double2* ckpt;                       // n_ckpt x n x d
+  // reductions
+  double2* part_g;                     // n_teams * CL
+  double* part_c2;                     // n_teams * CL
+  double* part_grad;                   // (n_teams * CL) x N x K
+  const double2* g_final;              // device scalar g (after the forward finalize)
+  // scratch for buffers that do not fit in shared memory (per CTA slices)
+  double2* scratch;
+  int64_t scratch_stride;              // doubles2 per CTA
+  // shared-memory plan (see make_layout) and scratch offsets (in double2 units) of the
+  // buffers that are not in shared memory
+  int in_smem, m_smem;
+  int64_t scr_vals, scr_W, scr_wslot;
+  int max_nnz_loc;
+  // entry-major control contributions (for assembling H_n on the union pattern)
+  const int* ectr_ptr;                 // nnz + 1
+  const int* ectr_k;
+  const double2* ectr_val;
+  int* err;                            // device error word
+};
+
+struct ScheduleParams {
+  int dim, K, N;
+  double dt;
+  const int64_t* rowptr;
+  const double2* h0v;
+  const int* ectr_ptr;
+  const int* ectr_k;
+  const double2* ectr_val;
+  const double* u;
+  const double* table;                 // s_cap x m_cap breakpoints X[s-1][m-1] (largest feasible x), < 0 = never
+  const double* table_smax;            // s_cap: max over m of X
+  int m_cap, s_cap;
+  int* ms_m;
+  int* ms_s;
+  double* norm1;
+  int* err;
+};
+
+struct FinalizeParams {
+  int n_parts, n_states, N, K;
+  double w_fid, w_forbid, w_amp;
+  const double2* part_g;
+  const double* part_c2;
+  const double* u;
+  double2* g_out;
+  double* cost_out;
+  double* parts_out;                   // [C1, C2, C_amp, |g|]
+};
+
+struct GradReduceParams {
+  int n_parts, N, K;
+  double w_amp;
+  const double* part_grad;
+  const double* u;
+  double* grad;                        // K x N row-major
+};
+
+// Dynamic shared-memory layout of the sweep kernels (byte offsets).  Exchange buffers,
+// per-row states and the local pattern always live in shared memory; the drift-plus-control
+// values (vals), the per-entry gradient accumulators (W) and the first m_smem Horner slots
+// (wslot) live there when they fit, else in the CTA's global scratch slice.
+struct SmemLayout {
+  int xbuf;          // exchange buffers: nchains x 2 x R double2
+  int psi, chi, inc; // R double2 each (chi only in the backward sweep)
+  int vals, W, wslot;
+  int lrow, lcol;    // R + 1 ints, max_nnz_loc uints
+  int total;
+};
+
+__host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
+
+// in_smem bit 0: vals, bit 1: W; m_smem = Horner slots kept in shared memory.
+__host__ __device__ inline SmemLayout make_layout(bool backward, int R, int max_nnz_loc, int in_smem, int m_smem,
+                                                  int cplx_bytes) {
+  SmemLayout L;
+  const int nchains = backward ? 3 : 1;
+  int off = 0;
+  L.xbuf = off; off += align16(nchains * 2 * R * cplx_bytes);
+  L.psi = off;  off += align16(R * 16);
+  L.chi = -1;
+  if (backward) { L.chi = off; off += align16(R * 16); }
+  L.inc = off;  off += align16(R * 16);
+  L.vals = -1; L.W = -1; L.wslot = -1;
+  if (in_smem & 1) { L.vals = off; off += align16(max_nnz_loc * cplx_bytes); }
+  if (backward && (in_smem & 2)) { L.W = off; off += align16(max_nnz_loc * 16); }
+  if (backward && m_smem > 0) { L.wslot = off; off += align16(m_smem * R * cplx_bytes); }
+  L.lrow = off; off += align16((R + 1) * 4);
+  L.lcol = off; off += align16(max_nnz_loc * 4);
+  L.total = off;
+  return L;
+}
+
+// Launchers (grape_kernels.cu).  Return cudaGetLastError() of the launch.
+cudaError_t launch_schedule(const ScheduleParams& p, cudaStream_t st);
+cudaError_t launch_forward(const SweepParams& p, int precision, int smem_bytes, int threads, cudaStream_t st);
+cudaError_t launch_backward(const SweepParams& p, int precision, int smem_bytes, int threads, cudaStream_t st);
+cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t st);
+cudaError_t launch_grad_reduce(const GradReduceParams& p, cudaStream_t st);
+cudaError_t check_nonfinite_u(const double* u, int64_t count, int* err, cudaStream_t st);
+int max_dynamic_smem(int device);
+
+}  // namespace grape

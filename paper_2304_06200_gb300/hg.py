@@ -1,0 +1,253 @@
+"""Python binding of the HG GRAPE C ABI: marshals arrays, owns the problem handle, exposes autograd.
+
+Every step of the evaluation runs in the CUDA library; this module only converts
+operators to CSR arrays, passes pointers and streams, and (optionally) routes the
+library's device allocations through PyTorch's caching allocator so that
+``torch.cuda.max_memory_allocated`` accounts for them.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _abi
+from ._abi import GrapeDesc, GrapeInfo, GrapeOp, check, lib
+
+PRECISIONS = {"fp64": _abi.GRAPE_FP64, "fp32_bulk": _abi.GRAPE_FP32_BULK}
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _csr_arrays(m, dim):
+    """(rowptr int64, colind int32, values interleaved float64) of a scipy sparse or dense matrix."""
+    import scipy.sparse as sp
+
+    csr = sp.csr_matrix(m, dtype=np.complex128)
+    csr.sum_duplicates()
+    if csr.shape != (dim, dim):
+        raise ValueError(f"operator shape {csr.shape} != ({dim}, {dim})")
+    rowptr = np.ascontiguousarray(csr.indptr, dtype=np.int64)
+    col = np.ascontiguousarray(csr.indices, dtype=np.int32)
+    vals = np.ascontiguousarray(csr.data, dtype=np.complex128).view(np.float64)
+    return rowptr, col, vals
+
+
+class _TorchAllocator:
+    """Device allocations through torch's caching allocator (keeps the ctypes callbacks alive)."""
+
+    def __init__(self, device: int):
+        import torch
+
+        self.torch = torch
+        self.device = device
+
+        def _alloc(nbytes, _ctx):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), device=self.device))
+            except Exception:  # out of memory -> NULL -> GRAPE_ENOMEM
+                return None
+
+        def _free(ptr, _nbytes, _ctx):
+            try:
+                torch.cuda.caching_allocator_delete(int(ptr))
+            except Exception:
+                pass
+
+        self.alloc = _abi.ALLOC_FN(_alloc)
+        self.free = _abi.FREE_FN(_free)
+
+
+class GrapeProblem:
+    """One HG GRAPE problem on one GPU (see ``include/grape_hg.h`` for the definition of the cost).
+
+    ``problem`` is any object with the attributes of ``workloads.Problem``: dim, dt,
+    n_steps, H0, Hk (scipy sparse or dense), psi0, target (dim x n complex), omega
+    (dim real or None), w_fid, w_forbid, w_amp, tau.
+    """
+
+    def __init__(self, problem, precision: str = "fp64", ckpt_every: int = 0, cluster: int = 0, device: int = 0,
+                 tau: float | None = None, m_max: int = 0, torch_allocator: bool = True, n_steps: int | None = None):
+        L = lib()
+        self._lib = L
+        self.dim = int(problem.dim)
+        self.K = len(problem.Hk)
+        self.N = int(problem.n_steps if n_steps is None else n_steps)
+        self.n = int(np.asarray(problem.psi0).shape[1])
+        self.device = int(device)
+        self._keep = []
+        ops = [_csr_arrays(problem.H0, self.dim)] + [_csr_arrays(h, self.dim) for h in problem.Hk]
+        self._keep.append(ops)
+
+        def mkop(arrs):
+            rp, ci, va = arrs
+            return GrapeOp(_abi.GRAPE_CSR, int(ci.shape[0]), rp.ctypes.data_as(C.POINTER(C.c_int64)),
+                           ci.ctypes.data_as(C.POINTER(C.c_int32)), _dptr(va))
+
+        hk_arr = (GrapeOp * max(self.K, 1))(*[mkop(o) for o in ops[1:]])
+        psi0 = np.asfortranarray(np.asarray(problem.psi0, dtype=np.complex128))
+        target = np.asfortranarray(np.asarray(problem.target, dtype=np.complex128))
+        psi0_c = np.ascontiguousarray(psi0.T).view(np.float64)      # column h contiguous
+        target_c = np.ascontiguousarray(target.T).view(np.float64)
+        omega = None if problem.omega is None else np.ascontiguousarray(problem.omega, dtype=np.float64)
+        self._keep += [hk_arr, psi0_c, target_c, omega]
+        d = GrapeDesc()
+        d.dim = self.dim
+        d.n_controls = self.K
+        d.n_steps = self.N
+        d.n_states = self.n
+        d.dt = float(problem.dt)
+        d.H0 = mkop(ops[0])
+        d.Hk = C.cast(hk_arr, C.POINTER(GrapeOp))
+        d.psi0 = _dptr(psi0_c)
+        d.target = _dptr(target_c)
+        d.omega_diag = _dptr(omega) if omega is not None else C.POINTER(C.c_double)()
+        d.w_fid, d.w_forbid, d.w_amp = float(problem.w_fid), float(problem.w_forbid), float(problem.w_amp)
+        d.tau = float(problem.tau if tau is None else tau)
+        d.m_max = int(m_max)
+        d.ckpt_every = int(ckpt_every)
+        d.precision = PRECISIONS[precision]
+        d.cluster = int(cluster)
+        d.device = self.device
+        self._alloc = None
+        if torch_allocator:
+            self._alloc = _TorchAllocator(self.device)
+            d.alloc = self._alloc.alloc
+            d.free = self._alloc.free
+        else:
+            d.alloc = _abi.ALLOC_FN()
+            d.free = _abi.FREE_FN()
+        d.alloc_ctx = None
+        handle = C.c_void_p()
+        check(L.grape_problem_create(C.byref(d), C.byref(handle)), "grape_problem_create")
+        self._h = handle
+        self.precision = precision
+
+    # ------------------------------------------------------------------ host-pointer API
+    def cost_and_grad(self, u: np.ndarray, want_grad: bool = True):
+        """(cost, grad) with host arrays; u has shape (K, N)."""
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        if u.shape != (self.K, self.N):
+            raise ValueError(f"u shape {u.shape} != {(self.K, self.N)}")
+        cost = np.zeros(1)
+        grad = np.zeros((self.K, self.N)) if want_grad else None
+        check(self._lib.grape_cost_and_grad(self._h, u.ctypes.data, cost.ctypes.data,
+                                            grad.ctypes.data if want_grad else None, 0, None),
+              "grape_cost_and_grad")
+        return float(cost[0]), grad
+
+    def cost(self, u: np.ndarray) -> float:
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        cost = np.zeros(1)
+        check(self._lib.grape_cost(self._h, u.ctypes.data, cost.ctypes.data, 0, None), "grape_cost")
+        return float(cost[0])
+
+    # ------------------------------------------------------------------ device-pointer API (torch tensors)
+    def cost_and_grad_device(self, u, cost, grad=None, stream=None):
+        """Asynchronous evaluation on device tensors (float64, contiguous) on ``stream`` (default: torch's current)."""
+        import torch
+
+        st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        check(self._lib.grape_cost_and_grad(self._h, u.data_ptr(), cost.data_ptr(),
+                                            grad.data_ptr() if grad is not None else None, 1, st),
+              "grape_cost_and_grad")
+
+    def cost_device(self, u, cost, stream=None):
+        import torch
+
+        st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        check(self._lib.grape_cost(self._h, u.data_ptr(), cost.data_ptr(), 1, st), "grape_cost")
+
+    def grad_device(self, grad, stream=None):
+        import torch
+
+        st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        check(self._lib.grape_grad(self._h, grad.data_ptr(), 1, st), "grape_grad")
+
+    def sync_status(self, stream=None):
+        import torch
+
+        st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        check(self._lib.grape_sync_status(self._h, st), "grape_sync_status")
+
+    # ------------------------------------------------------------------ introspection
+    def info(self) -> dict:
+        inf = GrapeInfo()
+        check(self._lib.grape_problem_info(self._h, C.byref(inf)), "grape_problem_info")
+        return {f: getattr(inf, f) for f, _ in GrapeInfo._fields_}
+
+    def schedule(self):
+        m = np.zeros(self.N, dtype=np.int32)
+        s = np.zeros(self.N, dtype=np.int32)
+        x = np.zeros(self.N, dtype=np.float64)
+        check(self._lib.grape_step_schedule(self._h, m.ctypes.data, s.ctypes.data, x.ctypes.data), "grape_step_schedule")
+        return m, s, x
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.grape_problem_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def select_ms(x: float, tau: float, sigma: int, precision: str = "fp64", m_max: int = 60, s_max: int = 4096):
+    """The library's host-side (m, s) rule (Sec. III.B): returns (m, s) or None when infeasible."""
+    m = C.c_int32()
+    s = C.c_int32()
+    st = lib().grape_select_ms(float(x), float(tau), int(sigma), PRECISIONS[precision], int(m_max), int(s_max),
+                               C.byref(m), C.byref(s))
+    if st == 4:
+        return None
+    check(st, "grape_select_ms")
+    return m.value, s.value
+
+
+def error_bound(x: float, m: int, s: int, sigma: int, precision: str = "fp64") -> float:
+    return lib().grape_error_bound(float(x), int(m), int(s), int(sigma), PRECISIONS[precision])
+
+
+def _make_function():
+    import torch
+
+    class GrapeHG(torch.autograd.Function):
+        """cost = GrapeHG.apply(u, problem): forward sweep in forward(), backward sweep in backward().
+
+        One backward per forward: a second forward on the same problem before the
+        backward overwrites the saved checkpoints.
+        """
+
+        @staticmethod
+        def forward(ctx, u, prob):
+            u = u.detach().to(dtype=torch.float64).contiguous()
+            cost = torch.empty((), dtype=torch.float64, device=u.device)
+            prob.cost_device(u, cost)
+            ctx.prob = prob
+            return cost
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            prob = ctx.prob
+            g = torch.empty((prob.K, prob.N), dtype=torch.float64, device=grad_out.device)
+            prob.grad_device(g)
+            return grad_out * g, None
+
+    return GrapeHG
+
+
+_GRAPE_HG = None
+
+
+def grape_hg():
+    """The ``torch.autograd.Function`` wrapping the HG forward and backward sweeps."""
+    global _GRAPE_HG
+    if _GRAPE_HG is None:
+        _GRAPE_HG = _make_function()
+    return _GRAPE_HG

@@ -1,0 +1,204 @@
+"""GPU parity: the CUDA HG path (through the C ABI) against the CPU FP64 oracle.
+
+Tolerances (FP64 path): relative 1e-10 on the cost, normwise relative 1e-8 on the
+gradient.  The oracle uses the exact exponential, the GPU the truncated-Taylor
+approximant chosen by the paper's bound, so tau is set small enough that the
+approximation error stays below these tolerances (tau <= 1e-12 here).
+"""
+
+import numpy as np
+import pytest
+
+from oracle import cost_and_grad as oracle_cost_and_grad
+from oracle import select_ms as oracle_select
+from workloads import build_config, random_problem
+
+pytestmark = pytest.mark.gpu
+
+COST_RTOL = 1e-10
+GRAD_RTOL = 1e-8
+
+
+def _hg(p, **kw):
+    from paper_2304_06200_gb300 import GrapeProblem
+    return GrapeProblem(p, **kw)
+
+
+def _check(p, u, cost, grad, cost_rtol=COST_RTOL, grad_rtol=GRAD_RTOL, ref=None):
+    r = ref if ref is not None else oracle_cost_and_grad(p, u)
+    assert abs(cost - r.cost) <= cost_rtol * abs(r.cost), (cost, r.cost)
+    gerr = np.linalg.norm(grad - r.grad) / np.linalg.norm(r.grad)
+    assert gerr <= grad_rtol, gerr
+    return r
+
+
+def test_c1_state_transfer_full_size():
+    p = build_config("c1_state_transfer_d30")
+    hg = _hg(p)
+    cost, grad = hg.cost_and_grad(p.u0)
+    _check(p, p.u0, cost, grad)
+
+
+def test_c2_gate_full_size():
+    p = build_config("c2_gate_d80")
+    hg = _hg(p)
+    cost, grad = hg.cost_and_grad(p.u0)
+    r = _check(p, p.u0, cost, grad)
+    # a stronger drive exercises every cost term (C2 becomes sizeable)
+    u = p.u0 * 30
+    cost, grad = hg.cost_and_grad(u)
+    _check(p, u, cost, grad)
+
+
+@pytest.mark.parametrize("dim,K,n,N,cluster", [
+    (2, 1, 1, 3, 1), (7, 2, 3, 5, 1), (33, 3, 2, 9, 2), (65, 2, 4, 6, 4), (130, 4, 3, 7, 8),
+    (257, 3, 2, 5, 16), (40, 5, 1, 11, 16), (97, 1, 5, 4, 0), (31, 0, 2, 3, 0),
+])
+def test_random_ragged_problems(dim, K, n, N, cluster):
+    """Row blocks that do not divide d (ragged last CTA, empty CTAs for d < 16 * R), every team size."""
+    p = random_problem(dim, K, n, N, seed=1000 + dim + K + n + N)
+    hg = _hg(p, cluster=cluster)
+    assert hg.info()["cluster"] == (cluster or hg.info()["cluster"])
+    if K == 0:
+        cost = hg.cost(p.u0)
+        r = oracle_cost_and_grad(p, p.u0)
+        assert abs(cost - r.cost) <= COST_RTOL * abs(r.cost)
+        return
+    cost, grad = hg.cost_and_grad(p.u0)
+    _check(p, p.u0, cost, grad)
+
+
+def test_schedule_follows_the_paper_rule():
+    """(m_n, s_n) on the device equals the oracle's direct rule on the oracle's norms (integers, exact)."""
+    p = build_config("c2_gate_d80", n_steps=200)
+    u = p.u0 * 20
+    hg = _hg(p)
+    hg.cost_and_grad(u)
+    m, s, x = hg.schedule()
+    sigma = hg.info()["sigma"]
+    H0, Hk = p.dense()
+    mism = 0
+    for n in range(p.n_steps):
+        H = H0 + sum(u[k, n] * Hk[k] for k in range(len(Hk)))
+        xn = p.dt * np.max(np.sum(np.abs(H), axis=1))
+        assert x[n] == pytest.approx(xn, rel=1e-13)
+        want = oracle_select(xn, p.tau, sigma)
+        if (m[n], s[n]) != want:
+            mism += 1
+    assert mism == 0
+
+
+def test_gradient_is_derivative_of_the_gpu_cost():
+    """Central differences of the GPU's own cost (schedule unchanged by the perturbation) match its gradient."""
+    p = random_problem(24, 3, 2, 6, seed=77, tau=1e-12)
+    hg = _hg(p)
+    u = p.u0.copy()
+    cost, grad = hg.cost_and_grad(u)
+    m0, s0, _ = hg.schedule()
+    h = 1e-6
+    fd = np.zeros_like(u)
+    for k in range(u.shape[0]):
+        for n in range(u.shape[1]):
+            up = u.copy(); up[k, n] += h
+            um = u.copy(); um[k, n] -= h
+            cp = hg.cost(up)
+            m1, s1, _ = hg.schedule()
+            cm = hg.cost(um)
+            m2, s2, _ = hg.schedule()
+            assert (m1 == m0).all() and (s1 == s0).all() and (m2 == m0).all() and (s2 == s0).all()
+            fd[k, n] = (cp - cm) / (2 * h)
+    assert np.linalg.norm(fd - grad) / np.linalg.norm(grad) < 1e-7
+
+
+def test_repeat_evaluations_are_bitwise_identical():
+    p = build_config("c2_gate_d80", n_steps=50)
+    hg = _hg(p)
+    c1, g1 = hg.cost_and_grad(p.u0)
+    c2, g2 = hg.cost_and_grad(p.u0)
+    assert c1 == c2
+    assert np.array_equal(g1, g2)
+
+
+@pytest.mark.parametrize("ckpt", [-1, 1, 7, 50])
+def test_checkpoint_spacing_does_not_change_the_result(ckpt):
+    p = build_config("c2_gate_d80", n_steps=120)
+    u = p.u0 * 10
+    ref = oracle_cost_and_grad(p, u)
+    hg = _hg(p, ckpt_every=ckpt)
+    cost, grad = hg.cost_and_grad(u)
+    _check(p, u, cost, grad, ref=ref)
+
+
+@pytest.mark.parametrize("cluster", [1, 2, 4, 8, 16])
+def test_team_sizes_agree(cluster):
+    """Same problem split over 1..16 CTAs per column: identical cost and gradient within rounding."""
+    p = build_config("c2_gate_d80", n_steps=40)
+    u = p.u0 * 15
+    ref = oracle_cost_and_grad(p, u)
+    hg = _hg(p, cluster=cluster)
+    cost, grad = hg.cost_and_grad(u)
+    _check(p, u, cost, grad, ref=ref)
+
+
+def test_medium_two_transmon_cavity_parity():
+    """Two transmons x cavity (the d = 4000 system's structure) at d = 4*4*40 = 640, clustered."""
+    from workloads.transmon import _gate_problem, _subspace_two, two_transmon_cavity
+    H0, Hk = two_transmon_cavity(4, 40)
+    dim = 640
+    t1 = np.arange(dim) // 160
+    t2 = (np.arange(dim) // 40) % 4
+    omega = ((t1 == 3) | (t2 == 3)).astype(float)
+    p = _gate_problem("tt4c40", H0, Hk, dim, _subspace_two(4, 40, 4, 1), 1.0, 12, 9, omega, 1.0, 1.0, 1e-2,
+                      1e-12, {})
+    u = p.u0 * 10
+    ref = oracle_cost_and_grad(p, u)
+    for cl in (0, 16):
+        hg = _hg(p, cluster=cl)
+        cost, grad = hg.cost_and_grad(u)
+        _check(p, u, cost, grad, ref=ref)
+
+
+def test_c3_full_dimension_one_step():
+    """The d = 4000, 6-control, 4-state system against the oracle (one step: dense eigh at d = 4000)."""
+    p = build_config("c3_gate_d4000", n_steps=1, tau=1e-12)
+    hg = _hg(p)
+    assert hg.info()["cluster"] > 1
+    cost, grad = hg.cost_and_grad(p.u0)
+    _check(p, p.u0, cost, grad)
+
+
+def test_autograd_function_matches_direct_call():
+    import torch
+    from paper_2304_06200_gb300 import grape_hg
+    p = build_config("c2_gate_d80", n_steps=30)
+    hg = _hg(p)
+    c_ref, g_ref = hg.cost_and_grad(p.u0)
+    u = torch.tensor(p.u0, device="cuda", requires_grad=True)
+    cost = grape_hg().apply(u, hg)
+    (3.0 * cost).backward()
+    assert float(cost) == c_ref
+    np.testing.assert_allclose(u.grad.cpu().numpy(), 3.0 * g_ref, rtol=0, atol=1e-15)
+
+
+def test_error_paths():
+    from paper_2304_06200_gb300 import GrapeError, GrapeProblem
+    p = build_config("c1_state_transfer_d30", n_steps=5)
+    hg = _hg(p)
+    u = p.u0.copy()
+    u[1, 2] = np.nan
+    with pytest.raises(GrapeError) as ei:
+        hg.cost_and_grad(u)
+    assert ei.value.name == "GRAPE_ENONFINITE"
+    with pytest.raises(GrapeError) as ei:
+        hg.cost_and_grad(p.u0 * 1e6)        # ||A||_1 beyond every feasible (m, s)
+    assert ei.value.name == "GRAPE_ETOL"
+    c, g = hg.cost_and_grad(p.u0)           # the problem stays usable after device-side errors
+    assert np.isfinite(c) and np.all(np.isfinite(g))
+    q = build_config("c1_state_transfer_d30", n_steps=5)
+    q.Hk[0] = q.Hk[0] * 1j                  # i (b + b^+) is anti-Hermitian
+    with pytest.raises(GrapeError) as ei:
+        GrapeProblem(q)
+    assert ei.value.name == "GRAPE_ENOTHERMITIAN"
+    fresh = _hg(p)
+    st = fresh._lib.grape_grad(fresh._h, np.zeros((4, 5)).ctypes.data, 0, None)
+    assert st == 7   # GRAPE_ESTATE
