@@ -1,0 +1,498 @@
+#!/usr/bin/env python
+"""HG GRAPE cost+gradient evaluations per second on GB300, with peak HBM against torch full-AD.
+
+One step = one full cost+gradient evaluation (forward sweep, cost, backward sweep,
+gradient) of the workload, inputs resident in HBM.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank evaluates its own
+independent instance of the workload (replicas, weak scaling); rank 0 prints the
+aggregate.  ``--impl reference`` times the CPU oracle (the reference arm) on a
+bounded sample of the same workload on this host's cores.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import warnings
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cost+gradient evals/s & peak HBM: HG kernels vs torch full-AD, 1 GB300"
+DEFAULT_WORKLOAD = "c3_gate_d4000"
+FP64_PEAK_GFLOPS = 1250.0        # GB300 nominal FP64 (non-tensor) rate, all 152 SMs
+L2_FLUSH_BYTES = 256 << 20       # > 129 MB L2
+LAUNCHES_PER_EVAL = 5            # k_schedule, k_forward, k_finalize, k_backward, k_grad_reduce
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fullad", action="store_true")
+    ap.add_argument("--fullad-steps", default="2,4")
+    ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--n-steps", type=int, default=None, help="override the workload's N (profiling a small case)")
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------------ distributed helpers
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def aggregate(local_seconds: float, local_units: int, world: int, reduce_max=None, reduce_sum=None):
+    """Whole-job throughput: units of all ranks / the slowest rank's time (max over ranks)."""
+    t = reduce_max(local_seconds) if reduce_max else local_seconds
+    u = reduce_sum(local_units) if reduce_sum else local_units * world
+    return u / t, t
+
+
+def workload_description(p) -> str:
+    return (f"{p.name}: d={p.dim}, K={p.n_controls} controls, n={p.n_states} states, N={p.n_steps} steps, "
+            f"dt={p.dt} ns, tau={p.tau:g}, weights (fid, forbid, amp)=({p.w_fid}, {p.w_forbid}, {p.w_amp}), "
+            f"seeded smooth controls (RMS 2pi*0.01 rad/ns), complex128")
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ algorithmic work model
+
+def backward_flops(schedule_m, schedule_s, nnz: int, nnz_ctrl_entries: int, dim: int, n: int) -> float:
+    """FP64 flops one k_backward launch must do (complex multiply-add = 8 flops).
+
+    Per substep (s_n of them per step): phase A applies -B to two columns-blocks for m_n terms
+    (psi re-propagation and the Horner costate chain), phase B applies B for m_n - 1 terms and
+    accumulates conj(w_p) x_p on the control entries for m_n terms.  Each Taylor term also
+    scales and accumulates d*n complex numbers (4 flops each).
+    """
+    tot = 0.0
+    for m, s in zip(schedule_m, schedule_s):
+        m = int(m)
+        s = int(s)
+        spmm_terms = 2 * m + (m - 1)
+        tot += s * (spmm_terms * (8.0 * nnz * n + 4.0 * dim * n) + m * 8.0 * nnz_ctrl_entries * n)
+    return tot
+
+
+def forward_flops(schedule_m, schedule_s, nnz: int, dim: int, n: int) -> float:
+    return sum(int(s) * int(m) * (8.0 * nnz * n + 4.0 * dim * n) for m, s in zip(schedule_m, schedule_s))
+
+
+def read_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch recorded from an ncu capture in profiles/ (None if not recorded)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        if line.startswith("traffic_bytes_per_launch:"):
+            try:
+                return float(line.split(":", 1)[1].strip().split()[0])
+            except ValueError:
+                return None
+    return None
+
+
+# ------------------------------------------------------------------ torch full-AD comparator (GPU)
+
+def fullad_taylor_gpu(p, u, sched_m, sched_s, n_steps: int, device: int):
+    """Full automatic differentiation of the same truncated-Taylor propagation in torch (Sec. IV.A, full-AD).
+
+    B_n x = -i dt/s (H0 x + sum_k u_kn H_k x) with cuSPARSE CSR products; autograd records every
+    Taylor term, so memory grows with N * mu (Table I).  Returns (seconds, peak bytes) for n_steps.
+    """
+    import numpy as np
+    import torch
+
+    dev = torch.device("cuda", device)
+
+    def csr(m):
+        m = m.tocsr()
+        return torch.sparse_csr_tensor(torch.tensor(m.indptr, dtype=torch.int64), torch.tensor(m.indices, dtype=torch.int64),
+                                       torch.tensor(m.data, dtype=torch.complex128), size=m.shape).to(dev)
+
+    H0 = csr(p.H0)
+    Hk = [csr(h) for h in p.Hk]
+    psi0 = torch.tensor(np.asarray(p.psi0), dtype=torch.complex128, device=dev)
+    target = torch.tensor(np.asarray(p.target), dtype=torch.complex128, device=dev)
+    om = torch.tensor(np.asarray(p.omega), dtype=torch.float64, device=dev)[:, None] if p.omega is not None else None
+    torch.cuda.synchronize(dev)
+    torch.cuda.reset_peak_memory_stats(dev)
+    base = torch.cuda.memory_allocated(dev)
+    t0 = time.perf_counter()
+    u_t = torch.tensor(np.asarray(u)[:, :n_steps], dtype=torch.float64, device=dev, requires_grad=True)
+    psi = psi0
+    c2 = torch.zeros((), dtype=torch.float64, device=dev)
+    n = psi0.shape[1]
+    for step in range(n_steps):
+        m, s = int(sched_m[step]), int(sched_s[step])
+        uc = u_t[:, step].to(torch.complex128)
+        for _ in range(s):
+            t = psi
+            acc = psi
+            for q in range(1, m + 1):
+                y = torch.sparse.mm(H0, t)
+                for k, h in enumerate(Hk):
+                    y = y + uc[k] * torch.sparse.mm(h, t)
+                t = y * (-1j * p.dt / (s * q))
+                acc = acc + t
+            psi = acc
+        if om is not None:
+            c2 = c2 + torch.sum(om * (psi.real ** 2 + psi.imag ** 2))
+    g = torch.sum(torch.conj(target) * psi)
+    cost = p.w_fid * (1.0 - (g.real ** 2 + g.imag ** 2) / n ** 2) + p.w_forbid * c2 / (n_steps * n) \
+        + p.w_amp * torch.sum(u_t ** 2) / n_steps
+    cost.backward()
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    peak = torch.cuda.max_memory_allocated(dev) - base
+    del u_t, psi, c2, g, cost
+    torch.cuda.empty_cache()
+    return dt, peak
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+
+def oracle_sample(workload: str, seed_offset: int = 0):
+    """Time the CPU oracle on one step of the workload (a bounded sample); returns (seconds, steps)."""
+    from oracle import cost_and_grad
+    from workloads import build_config
+
+    q = build_config(workload, n_steps=1)
+    t0 = time.perf_counter()
+    cost_and_grad(q, q.u0)
+    return time.perf_counter() - t0, 1
+
+
+def oracle_threads() -> int:
+    try:
+        from threadpoolctl import threadpool_info
+        return max((i.get("num_threads", 1) for i in threadpool_info()), default=os.cpu_count() or 1)
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2304_06200_gb300 import GrapeProblem
+    from paper_2304_06200_gb300._abi import lib
+    from workloads import build_config
+
+    lib()
+    p = build_config(args.workload, seed=None if rank == 0 else 1000 + rank, n_steps=args.n_steps)
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats(dev)
+    mem0 = torch.cuda.memory_allocated(dev)
+    hg = GrapeProblem(p, device=local)
+    u = torch.tensor(p.u0, dtype=torch.float64, device=dev)
+    cost = torch.zeros((), dtype=torch.float64, device=dev)
+    grad = torch.zeros((p.n_controls, p.n_steps), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 0)):
+        hg.cost_device(u, cost, stream)
+        hg.grad_device(grad, stream)
+    hg.sync_status(stream)
+    torch.cuda.synchronize()
+    hg_peak = torch.cuda.max_memory_allocated(dev) - mem0
+    info = hg.info()
+    sched_m, sched_s, norms = hg.schedule()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        hg.cost_device(u, cost, stream)
+        ev[i][1].record(stream)
+        hg.grad_device(grad, stream)
+        ev[i][2].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    hg.sync_status(stream)
+    step_ms = [ev[i][0].elapsed_time(ev[i][2]) for i in range(args.steps)]
+    fwd_ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
+    bwd_ms = [ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]
+    local_s = sum(step_ms) / 1e3
+
+    def rmax(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    def rsum(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+        return float(t.item())
+
+    value, tmax = aggregate(local_s, args.steps, world, rmax, rsum)
+
+    # ---- end to end through the host-pointer API (pinned host buffers, H2D + D2H inside the timed region)
+    u_h = torch.tensor(p.u0, dtype=torch.float64).pin_memory()
+    cost_h = torch.zeros(1, dtype=torch.float64).pin_memory()
+    grad_h = torch.zeros((p.n_controls, p.n_steps), dtype=torch.float64).pin_memory()
+    e2e_times = []
+    import ctypes
+    for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = hg._lib.grape_cost_and_grad(hg._h, ctypes.c_void_p(u_h.data_ptr()), ctypes.c_void_p(cost_h.data_ptr()),
+                                         ctypes.c_void_p(grad_h.data_ptr()), 0, None)
+        t1 = time.perf_counter()
+        if st != 0:
+            raise RuntimeError(f"grape_cost_and_grad failed with status {st}")
+        if i > 0:
+            e2e_times.append(t1 - t0)
+    e2e_local = sum(e2e_times)
+    e2e_value = aggregate(e2e_local, len(e2e_times), world, rmax, rsum)[0] if e2e_times else None
+    h2d = p.n_controls * p.n_steps * 8
+    d2h = 8 + p.n_controls * p.n_steps * 8
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (k_backward; FP64-pipe bound)
+    nnz = info["union_nnz"]
+    ctrl_entries = hg_ctrl_entry_count(p)
+    bflops = backward_flops(sched_m, sched_s, nnz, ctrl_entries, p.dim, p.n_states)
+    fflops = forward_flops(sched_m, sched_s, nnz, p.dim, p.n_states)
+    bwd_s = statistics.mean(bwd_ms) / 1e3
+    fwd_s = statistics.mean(fwd_ms) / 1e3
+    achieved = bflops / bwd_s / 1e9
+    traffic = read_traffic("k_backward", args.workload)
+    roofline = {"bound": "alu", "kernel": "k_backward", "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS,
+                "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": traffic,
+                "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (no measured FP64 peak in MEASURED_PEAKS)",
+                "flops_per_launch": bflops, "launch_ms": round(bwd_s * 1e3, 3),
+                "forward": {"kernel": "k_forward", "achieved": round(fflops / fwd_s / 1e9, 2), "launch_ms": round(fwd_s * 1e3, 3),
+                            "frac": round(fflops / fwd_s / 1e9 / FP64_PEAK_GFLOPS, 4)}}
+
+    # ---- torch full-AD comparator (same GPU, same Taylor schedule) for peak HBM
+    peak_hbm = {"hg_bytes": int(hg_peak), "hg_problem_bytes": int(info["device_bytes"])}
+    if not args.no_fullad:
+        try:
+            pts = []
+            for ns in [int(x) for x in args.fullad_steps.split(",") if x]:
+                t_ad, b_ad = fullad_taylor_gpu(p, p.u0, sched_m, sched_s, ns, local)
+                pts.append((ns, t_ad, b_ad))
+            (n1, t1_, b1), (n2, t2_, b2) = pts[0], pts[-1]
+            slope = (b2 - b1) / max(n2 - n1, 1)
+            extrap = b2 + slope * (p.n_steps - n2)
+            peak_hbm.update({
+                "fullad_samples": [{"steps": a, "seconds": round(b, 3), "peak_bytes": int(c)} for a, b, c in pts],
+                "fullad_bytes_extrapolated_full_N": int(extrap),
+                "fullad_fits_in_hbm": bool(extrap < torch.cuda.get_device_properties(dev).total_memory),
+                "fullad_evals_per_s_extrapolated": round(1.0 / (t2_ / n2 * p.n_steps), 6),
+                "ratio_fullad_over_hg": round(extrap / max(hg_peak, 1), 1),
+                "method": "torch autograd through the same truncated-Taylor steps (cuSPARSE CSR products), peak "
+                          "torch.cuda.max_memory_allocated at two reduced N, extrapolated linearly in N"})
+        except Exception as exc:  # the comparator is a reported baseline; report why it is missing
+            peak_hbm["fullad_unavailable"] = f"{type(exc).__name__}: {exc}"[:300]
+
+    # ---- CPU oracle baseline (bounded sample)
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        secs, steps = oracle_sample(args.workload)
+        per_eval = secs / steps * p.n_steps
+        cpu = {"value": 1.0 / per_eval, "unit": "evals/s", "cores": oracle_threads(), "kind": "oracle",
+               "sample": f"oracle (numpy eigh, stored states, divided differences) on {steps} of the "
+                         f"{p.n_steps} steps ({secs:.1f} s), scaled to one full evaluation"}
+
+    secondary = None
+    if not args.no_secondary:
+        secondary = secondary_c2(local)
+
+    out = {
+        "metric": METRIC, "value": round(value, 6), "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(tmax / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_description(p), "parallelism": f"replicas x{world}",
+                   "l2": "flushed before every timed step (256 MB write)", "cluster_ctas_per_column": info["cluster"],
+                   "ckpt_every": info["ckpt_every"], "total_taylor_terms_per_sweep": int(np.sum(sched_m * sched_s)),
+                   "max_norm_A1": round(float(np.max(norms)), 4)},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(e2e_value, 6) if e2e_value else None, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "api": "grape_cost_and_grad with pinned host u/cost/grad"},
+        "gpu_launches": LAUNCHES_PER_EVAL * args.steps,
+        "clocks": clk,
+        "peak_hbm": peak_hbm,
+    }
+    if secondary:
+        out["secondary"] = secondary
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def hg_ctrl_entry_count(p) -> int:
+    """Union-pattern entries that carry at least one control term (where W is accumulated)."""
+    pat = abs(p.Hk[0]).astype(bool)
+    for h in p.Hk[1:]:
+        pat = pat + abs(h).astype(bool)
+    return int(pat.nnz)
+
+
+def secondary_c2(local: int):
+    """The d = 80 gate workload (one CTA per column) for context: evals/s over a few evaluations."""
+    import torch
+    from paper_2304_06200_gb300 import GrapeProblem
+    from workloads import build_config
+
+    p = build_config("c2_gate_d80")
+    dev = torch.device("cuda", local)
+    hg = GrapeProblem(p, device=local)
+    u = torch.tensor(p.u0, dtype=torch.float64, device=dev)
+    cost = torch.zeros((), dtype=torch.float64, device=dev)
+    grad = torch.zeros((p.n_controls, p.n_steps), dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        hg.cost_device(u, cost, st)
+        hg.grad_device(grad, st)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    reps = 10
+    e0.record(st)
+    for _ in range(reps):
+        hg.cost_device(u, cost, st)
+        hg.grad_device(grad, st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    hg.sync_status(st)
+    ms = e0.elapsed_time(e1) / reps
+    return {"workload": workload_description(p), "evals_per_s": round(1e3 / ms, 3), "ms_per_eval": round(ms, 3),
+            "cluster_ctas_per_column": hg.info()["cluster"]}
+
+
+# ------------------------------------------------------------------ reference arm (CPU oracle)
+
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    from workloads import build_config
+
+    p = build_config(args.workload)
+    for _ in range(max(args.warmup, 0)):
+        oracle_sample(args.workload)
+    secs = 0.0
+    steps = 0
+    for _ in range(args.steps):
+        s, n = oracle_sample(args.workload)
+        secs += s
+        steps += n
+    per_eval = secs / steps * p.n_steps
+    value = 1.0 / per_eval
+    cores = oracle_threads()
+    sample = (f"oracle (numpy eigh, stored states, divided differences), each step one of the {p.n_steps} time "
+              f"steps of the workload, scaled to one full evaluation")
+    out = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": max(args.gpus, 1), "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": per_eval * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": workload_description(p), "parallelism": "host cores"},
+           "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main(argv=None):
+    warnings.filterwarnings("ignore", message=".*[Ss]parse.*")
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
