@@ -175,6 +175,32 @@ grape_status grape_select_ms(double x, double tau, int32_t sigma, int32_t precis
 /* E_A(m, s) itself (App. C Eq. (overallupperbound)); +inf when s R_m(x/s) >= 1. */
 double grape_error_bound(double x, int32_t m, int32_t s, int32_t sigma, int32_t precision);
 
+/* Allocation-free propagation of one step (the paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory).  Such callers include code that runs
+ * while a stream is being captured into a CUDA graph (cudaMalloc is not allowed there), real-time
+ * loops that cannot afford cudaMalloc/cudaFree (both can synchronise the whole device), and host
+ * programs that hand out all device memory from their own fixed pool.  The call computes
+ *     psi_out = (e^{B}_m)^s psi_in,   B = -i dt H / s
+ * (the scaled truncated-Taylor action of Sec. III.B) for a dim x n_states block, column-major,
+ * and uses no memory besides the caller's buffers and a 16 MiB array built into the library:
+ *   - rowptr[dim+1] (int64), colind[nnz] (int32), values[2*nnz] (complex): H in CSR, DEVICE
+ *     pointers; column indices outside [0, dim) are ignored.  m in 1..60 and s >= 1 are taken as
+ *     given (grape_select_ms gives the paper's choice).
+ *   - psi_in, psi_out: dim x n_states complex DEVICE arrays (may be the same array).
+ *   - Limit: 3 * dim * n_states <= 349525 (16 MiB / 48 bytes); larger requests return GRAPE_EINVAL
+ *     before anything is launched.
+ *   - It never calls cudaMalloc, cudaFree or any allocating library routine.  The built-in array
+ *     is held on every GPU that loads the library until the process exits.
+ *   - The first call on a device (make that device current) looks up the array's device address;
+ *     make this first call before any stream capture begins.
+ *   - Every call on a device shares the one array: calls whose GPU work overlaps (different
+ *     streams, or different host threads) race and corrupt each other's results.  Serialise them.
+ *     Nothing in the array needs to start at zero; it keeps the last call's contents.
+ *   - Asynchronous on `stream` (NULL = legacy default stream); launch errors are returned. */
+grape_status grape_taylor_step_noalloc(int64_t dim, int32_t n_states, const int64_t* rowptr, const int32_t* colind,
+                                       const double* values, double dt, int32_t m, int32_t s, const double* psi_in,
+                                       double* psi_out, void* stream);
+
 const char* grape_status_string(grape_status st);
 const char* grape_last_error(void);
 int32_t grape_abi_version(void);

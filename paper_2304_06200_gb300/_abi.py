@@ -19,7 +19,7 @@ STATUS = {
 EXPORTED = [
     "grape_problem_create", "grape_problem_destroy", "grape_cost_and_grad", "grape_cost", "grape_grad",
     "grape_sync_status", "grape_problem_info", "grape_step_schedule", "grape_select_ms", "grape_error_bound",
-    "grape_status_string", "grape_last_error", "grape_abi_version",
+    "grape_status_string", "grape_last_error", "grape_abi_version", "grape_taylor_step_noalloc",
 ]
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -84,6 +84,8 @@ def lib(path: str | None = None):
     L.grape_select_ms.restype = C.c_int
     L.grape_error_bound.argtypes = [C.c_double, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
     L.grape_error_bound.restype = C.c_double
+    L.grape_taylor_step_noalloc.argtypes = [C.c_int64, C.c_int32, P, P, P, C.c_double, C.c_int32, C.c_int32, P, P, P]
+    L.grape_taylor_step_noalloc.restype = C.c_int
     L.grape_status_string.argtypes = [C.c_int]
     L.grape_status_string.restype = C.c_char_p
     L.grape_last_error.argtypes = []

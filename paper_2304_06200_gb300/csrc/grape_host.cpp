@@ -126,6 +126,11 @@ bool is_hermitian(const HostCSR& A, int64_t dim) {
 
 }  // namespace
 
+namespace grape {
+// Lets other translation units of the library report a message through grape_last_error().
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace grape
+
 struct grape_problem {
   int device = 0;
   int64_t dim = 0;
