@@ -31,7 +31,7 @@ METRIC = "cost+gradient evals/s & peak HBM: HG kernels vs torch full-AD, 1 GB300
 DEFAULT_WORKLOAD = "c3_gate_d4000"
 FP64_PEAK_GFLOPS = 1250.0        # GB300 nominal FP64 (non-tensor) rate, all 152 SMs
 L2_FLUSH_BYTES = 256 << 20       # > 129 MB L2
-LAUNCHES_PER_EVAL = 5            # k_schedule, k_forward, k_finalize, k_backward, k_grad_reduce
+LAUNCHES_PER_EVAL = 5            # k_schedule, k_forward, k_finalize, k_backward(_split), k_grad_reduce
 
 
 def parse_args(argv=None):
@@ -348,8 +348,9 @@ def run_ours(args):
     bwd_s = statistics.mean(bwd_ms) / 1e3
     fwd_s = statistics.mean(fwd_ms) / 1e3
     achieved = bflops / bwd_s / 1e9
-    traffic = read_traffic("k_backward", args.workload)
-    roofline = {"bound": "alu", "kernel": "k_backward", "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS,
+    traffic = read_traffic("k_backward_split" if info["backward_mode"] == 2 else "k_backward", args.workload)
+    bwd_kernel = "k_backward_split" if info["backward_mode"] == 2 else "k_backward"
+    roofline = {"bound": "alu", "kernel": bwd_kernel, "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS,
                 "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": traffic,
                 "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (no measured FP64 peak in MEASURED_PEAKS)",
                 "flops_per_launch": bflops, "launch_ms": round(bwd_s * 1e3, 3),
@@ -389,14 +390,18 @@ def run_ours(args):
 
     secondary = None
     if not args.no_secondary:
-        secondary = secondary_c2(local)
+        secondary = {"c2_fp64": secondary_run("c2_gate_d80", "fp64", local),
+                     "c2_fp32_bulk": secondary_run("c2_gate_d80", "fp32_bulk", local),
+                     "c3_fp32_bulk": secondary_run(args.workload, "fp32_bulk", local, ref=(float(cost.item()), grad.cpu().numpy()),
+                                                   n_steps=args.n_steps)}
 
     out = {
         "metric": METRIC, "value": round(value, 6), "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(tmax / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_description(p), "parallelism": f"replicas x{world}",
-                   "l2": "flushed before every timed step (256 MB write)", "cluster_ctas_per_column": info["cluster"],
+                   "l2": "flushed before every timed step (256 MB write)", "cluster_ctas_per_column_fwd": info["cluster_forward"],
+                   "cluster_ctas_per_column_bwd": info["cluster"], "backward_teams_per_column": info["backward_mode"],
                    "ckpt_every": info["ckpt_every"], "total_taylor_terms_per_sweep": int(np.sum(sched_m * sched_s)),
                    "max_norm_A1": round(float(np.max(norms)), 4)},
         "roofline": roofline,
@@ -422,26 +427,26 @@ def hg_ctrl_entry_count(p) -> int:
     return int(pat.nnz)
 
 
-def secondary_c2(local: int):
-    """The d = 80 gate workload (one CTA per column) for context: evals/s over a few evaluations."""
+def secondary_run(name: str, precision: str, local: int, ref=None, n_steps=None, reps: int = 3):
+    """Another workload or precision for context: evals/s (CUDA events) and, given an FP64 result of the
+    same problem, the relative difference of cost and gradient to it."""
+    import numpy as np
     import torch
     from paper_2304_06200_gb300 import GrapeProblem
     from workloads import build_config
 
-    p = build_config("c2_gate_d80")
+    p = build_config(name, n_steps=n_steps)
     dev = torch.device("cuda", local)
-    hg = GrapeProblem(p, device=local)
+    hg = GrapeProblem(p, device=local, precision=precision)
     u = torch.tensor(p.u0, dtype=torch.float64, device=dev)
     cost = torch.zeros((), dtype=torch.float64, device=dev)
     grad = torch.zeros((p.n_controls, p.n_steps), dtype=torch.float64, device=dev)
     st = torch.cuda.current_stream(dev)
-    for _ in range(3):
-        hg.cost_device(u, cost, st)
-        hg.grad_device(grad, st)
+    hg.cost_device(u, cost, st)
+    hg.grad_device(grad, st)
+    torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    reps = 10
     e0.record(st)
     for _ in range(reps):
         hg.cost_device(u, cost, st)
@@ -450,8 +455,17 @@ def secondary_c2(local: int):
     torch.cuda.synchronize()
     hg.sync_status(st)
     ms = e0.elapsed_time(e1) / reps
-    return {"workload": workload_description(p), "evals_per_s": round(1e3 / ms, 3), "ms_per_eval": round(ms, 3),
-            "cluster_ctas_per_column": hg.info()["cluster"]}
+    info = hg.info()
+    out = {"workload": workload_description(p), "precision": precision, "evals_per_s": round(1e3 / ms, 4),
+           "ms_per_eval": round(ms, 3), "cluster_fwd": info["cluster_forward"], "cluster_bwd": info["cluster"],
+           "backward_teams_per_column": info["backward_mode"]}
+    if ref is not None:
+        c_ref, g_ref = ref
+        g = grad.cpu().numpy()
+        out["cost_rel_diff_vs_fp64"] = abs(float(cost.item()) - c_ref) / abs(c_ref)
+        out["grad_rel_diff_vs_fp64"] = float(np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref))
+    hg.close()
+    return out
 
 
 # ------------------------------------------------------------------ reference arm (CPU oracle)

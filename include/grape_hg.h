@@ -104,11 +104,14 @@ typedef struct {
   int32_t ckpt_every;          /* M: psi checkpoint every M steps for the backward sweep;
                                   0 = automatic, < 0 = no checkpoints (pure re-propagation) */
   int32_t precision;           /* grape_precision                                         */
-  int32_t cluster;             /* CTAs per column team: 0 = automatic, else 1,2,4,8,16     */
+  int32_t cluster;             /* CTAs per column team: 0 = automatic, else 1..16 (both sweeps) */
   int32_t device;              /* CUDA device ordinal                                     */
   grape_alloc_fn alloc;        /* optional device allocator (see above)                   */
   grape_free_fn free;
   void* alloc_ctx;
+  int32_t backward_mode;       /* 0 = automatic, 1 = one team per column runs both backward
+                                  phases, 2 = two concurrent teams per column (phase A / phase B),
+                                  needs all 2 * n_states teams co-resident                    */
 } grape_desc;
 
 /* Information about a problem (valid after create; schedule fields after an evaluation). */
@@ -119,11 +122,13 @@ typedef struct {
   int32_t sigma;               /* sigma': largest row count of the union pattern (Eq. (sigmapdef)) */
   int32_t m_cap;               /* largest Taylor order the schedule table can return      */
   int32_t s_cap;               /* largest scaling factor the schedule table can return    */
-  int32_t cluster;             /* CTAs per column team actually used                      */
+  int32_t cluster;             /* CTAs per column team of the backward sweep               */
   int32_t ckpt_every;          /* checkpoint spacing actually used (0 = none)             */
   int32_t smem_bytes;          /* dynamic shared memory per CTA of the sweep kernels       */
   int64_t total_terms;         /* sum over steps of m_n * s_n for the last evaluation (-1 before) */
   double max_norm;             /* max_n ||A_n||_1 of the last evaluation (-1 before)       */
+  int32_t backward_mode;       /* 1 = one team per column, 2 = two concurrent teams per column */
+  int32_t cluster_forward;     /* CTAs per column team of the forward sweep                */
 } grape_info;
 
 /* Create a problem (Sec. II: H(t) = H_s + sum_k a_k(t) h_k, piecewise constant over N steps

@@ -39,14 +39,14 @@ class GrapeDesc(C.Structure):
                 ("w_fid", C.c_double), ("w_forbid", C.c_double), ("w_amp", C.c_double),
                 ("tau", C.c_double), ("m_max", C.c_int32), ("ckpt_every", C.c_int32), ("precision", C.c_int32),
                 ("cluster", C.c_int32), ("device", C.c_int32),
-                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p), ("backward_mode", C.c_int32)]
 
 
 class GrapeInfo(C.Structure):
     _fields_ = [("device_bytes", C.c_int64), ("union_nnz", C.c_int64), ("ctrl_entries", C.c_int64),
                 ("sigma", C.c_int32), ("m_cap", C.c_int32), ("s_cap", C.c_int32), ("cluster", C.c_int32),
                 ("ckpt_every", C.c_int32), ("smem_bytes", C.c_int32), ("total_terms", C.c_int64),
-                ("max_norm", C.c_double)]
+                ("max_norm", C.c_double), ("backward_mode", C.c_int32), ("cluster_forward", C.c_int32)]
 
 
 _LIB = None

@@ -131,12 +131,19 @@ namespace grape {
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 }  // namespace grape
 
+// Partition and shared-memory plan of one sweep kernel.
+struct KPlan {
+  int CL = 0, R = 0, mnl = 0, threads = 0, smem = 0, in_smem = 0, m_smem = 0;
+  int64_t stride = 0, scr_vals = 0, scr_W = 0, scr_Wb = 0, scr_wslot = 0;
+  uint32_t* d_colenc = nullptr;
+};
+
 struct grape_problem {
   int device = 0;
   int64_t dim = 0;
   int K = 0, N = 0, n = 0;
   double dt = 0, w_fid = 0, w_forbid = 0, w_amp = 0, tau = 0;
-  int precision = 0, CL = 1, R = 0, ckpt_every = 0, n_ckpt = 0, m_cap = 0, s_cap = 0, sigma = 0;
+  int precision = 0, ckpt_every = 0, n_ckpt = 0, m_cap = 0, s_cap = 0, sigma = 0;
   int64_t nnz = 0, n_ctr = 0;
   bool has_omega = false;
   grape_alloc_fn alloc_fn = nullptr;
@@ -147,12 +154,11 @@ struct grape_problem {
   grape::ScheduleTable table;
   // device buffers
   int64_t* d_rowptr = nullptr;
-  uint32_t* d_colenc = nullptr;
   double2* d_h0v = nullptr;
   int* d_cptr = nullptr;
   int* d_cidx = nullptr;
   double2* d_cval = nullptr;
-  int* d_cslice = nullptr;
+  int* d_cslice = nullptr;   // control slices of the backward partition
   int* d_ectr_ptr = nullptr;
   int* d_ectr_k = nullptr;
   double2* d_ectr_val = nullptr;
@@ -176,9 +182,14 @@ struct grape_problem {
   double* d_grad = nullptr;
   double2* d_scratch = nullptr;
   int* d_err = nullptr;
-  // launch plan
-  int threads = 0, fwd_smem = 0, bwd_smem = 0, fwd_in_smem = 0, bwd_in_smem = 0, m_smem = 0, max_nnz_loc = 0;
-  int64_t scratch_stride = 0, scr_vals = 0, scr_W = 0, scr_wslot = 0;
+  // split backward
+  int bwd_mode = 1;                 // 1 fused, 2 split
+  double2* d_ring = nullptr;
+  int64_t ring_slot = 0;
+  int ring_depth = 2;
+  unsigned* d_flags = nullptr;      // ready[n*CL], done[n*CL]
+  // launch plans of the forward and the backward sweep
+  KPlan fwd, bwd;
   bool forward_done = false;
   bool evaluated = false;
   cudaStream_t last_stream = nullptr;
@@ -306,17 +317,28 @@ grape_status build(grape_problem* P, const grape_desc* d) {
     ectr_ptr[e + 1] = (int)ectr_k.size();
   }
   // ---- (m, s) breakpoint table (App. C)
-  const double uround = grape::unit_roundoff(P->precision);
+  // Both precisions share the FP64 bound's schedule (the FP32-bulk path keeps its states in FP64;
+  // the bound with u = 2^-24 certifies no useful tolerance).
+  const double uround = grape::unit_roundoff(GRAPE_FP64);
   P->table = grape::build_table(P->tau, P->sigma, uround, P->m_cap, 4096, 2000.0);
   if (P->table.x_max < 0.0) return fail(GRAPE_ETOL, "no (m, s) pair satisfies E_A <= tau even for ||A||_1 = 0");
   P->m_cap = P->table.m_cap;
   P->s_cap = P->table.s_cap;
-  // ---- team size: CTAs per column (cost model: FP64 lanes per SM per clock ~1.7, team barrier
-  // ~80 clocks inside one CTA and ~1100 clocks (barrier + remote read latency) across a cluster)
+  // ---- partitions: CTAs per column team (CL) for the forward and the backward sweep.
+  // Cost model per Taylor term and CTA, in SM clocks: a * (entries x chains) + b * (rows x chains)
+  // + team barrier, with a = 4 FMA per complex multiply-add at 1.7 FP64 lanes/clk (FP32: ~100
+  // lanes/clk), b = the FP64 increment of a row, barrier ~80 clk in one CTA and ~1100 clk
+  // (barrier + first remote loads) across a cluster; launches wider than the GPU run in waves.
   const int dev = P->device;
   const int nsm = sm_count(dev);
+  const int cb = P->precision == GRAPE_FP32_BULK ? 8 : 16;   // bytes of one bulk complex number
   const int smem_max = grape::max_dynamic_smem(dev) - 2048;   // static shared memory of the kernels
-  auto plan_for = [&](int CL, int* R_out, int* mnl_out) -> bool {
+  const double a_cost = cb == 16 ? 4.0 / 1.7 : 4.0 / 100.0;   // clocks per complex multiply-add per SM
+  const double b_cost = 2.0 / 1.7;
+  int64_t nnz_ctrl = 0;
+  for (int64_t e = 0; e < nnz; ++e) nnz_ctrl += ectr_ptr[e + 1] > ectr_ptr[e] ? 1 : 0;
+  const double wf = nnz > 0 ? (double)nnz_ctrl / (double)nnz : 0.0;
+  auto rows_entries = [&](int CL, int* R_out, int* mnl_out) -> bool {
     const int64_t R = (dim + CL - 1) / CL;
     if (R >= (1 << 20)) return false;
     int mnl = 0;
@@ -324,76 +346,126 @@ grape_status build(grape_problem* P, const grape_desc* d) {
       const int64_t r0 = std::min<int64_t>((int64_t)r * R, dim), r1 = std::min<int64_t>(r0 + R, dim);
       mnl = std::max<int>(mnl, (int)(rowptr[r1] - rowptr[r0]));
     }
-    const int fixed = grape::make_layout(true, (int)R, mnl, 0, 0, 16).total;
-    if (fixed > smem_max) return false;
     *R_out = (int)R;
-    *mnl_out = mnl;
+    *mnl_out = std::max(mnl, 1);
     return true;
   };
-  int bestCL = 0, bestR = 0, bestMnl = 0;
-  double bestCost = 1e300;
-  const int cands[5] = {1, 2, 4, 8, 16};
-  for (int ci = 0; ci < 5; ++ci) {
-    const int CL = cands[ci];
-    if (d->cluster > 0 && CL != d->cluster) continue;
-    if (CL > 1 && CL > dim) continue;
-    int R = 0, mnl = 0;
-    if (!plan_for(CL, &R, &mnl)) continue;
-    const double work = mnl * 4.0 / 1.7;
-    const double sync = CL == 1 ? 80.0 : 1100.0;
-    const double waves = std::ceil((double)d->n_states * CL / nsm);
-    const double cost = waves * (work + sync);
-    if (cost < bestCost * 0.98) {
-      bestCost = cost;
-      bestCL = CL;
-      bestR = R;
-      bestMnl = mnl;
+  auto threads_for = [](int R) { return (int)std::min<int64_t>(512, std::max<int64_t>(64, ((int64_t)R + 31) / 32 * 32)); };
+  // fixed cost of one dependent Taylor term (barrier, load and multiply-add latency), measured on GB300
+  auto sync_cost = [](int CL) { return CL == 1 ? 1200.0 : 3000.0; };
+  auto waves = [&](int ctas) { return std::ceil((double)ctas / nsm); };
+  // backward shared-memory plan for (R, mnl): which optional buffers fit, Horner slots kept in smem
+  auto bwd_plan = [&](int R, int mnl, int* bin_out, int* msm_out, int* fused_smem, int* split_smem) -> bool {
+    if (grape::make_layout(true, R, mnl, 0, 0, cb).total > smem_max) return false;
+    int bin = 0;
+    if (grape::make_layout(true, R, mnl, 1, 0, cb).total <= smem_max) bin = 1;
+    if (grape::make_layout(true, R, mnl, bin | 2, 0, cb).total <= smem_max) bin |= 2;
+    if (cb == 8 && grape::make_layout(true, R, mnl, bin | 4, 0, cb).total <= smem_max) bin |= 4;
+    const int base = grape::make_layout(true, R, mnl, bin, 0, cb).total;
+    int msm = (int)std::min<int64_t>(P->m_cap, (smem_max - base - 16) / std::max<int64_t>((int64_t)R * cb, 1));
+    msm = std::max(msm, 0);
+    *bin_out = bin;
+    *msm_out = msm;
+    *fused_smem = grape::make_layout(true, R, mnl, bin, msm, cb).total;
+    *split_smem = base;
+    return true;
+  };
+  int mode_req = d->backward_mode;
+  if (mode_req < 0 || mode_req > 2) return fail(GRAPE_EINVAL, "backward_mode must be 0, 1 or 2");
+  // forward
+  {
+    double best = 1e300;
+    for (int CL = 1; CL <= grape::kMaxCluster; ++CL) {
+      if (d->cluster > 0 && CL != d->cluster) continue;
+      if (CL > 1 && CL > dim) continue;
+      int R = 0, mnl = 0;
+      if (!rows_entries(CL, &R, &mnl)) continue;
+      if (grape::make_layout(false, R, mnl, 0, 0, cb).total > smem_max) continue;
+      const double cost = waves(P->n * CL) * (a_cost * mnl + b_cost * R + sync_cost(CL));
+      if (cost < best * 0.98) {
+        best = cost;
+        P->fwd.CL = CL;
+        P->fwd.R = R;
+        P->fwd.mnl = mnl;
+      }
+    }
+    if (P->fwd.CL == 0) return fail(GRAPE_EINVAL, "problem does not fit the forward sweep's shared memory");
+    const int R = P->fwd.R, mnl = P->fwd.mnl;
+    P->fwd.in_smem = grape::make_layout(false, R, mnl, 1, 0, cb).total <= smem_max ? 1 : 0;
+    P->fwd.m_smem = 0;
+    P->fwd.smem = grape::make_layout(false, R, mnl, P->fwd.in_smem, 0, cb).total;
+    P->fwd.threads = threads_for(R);
+  }
+  // backward: one team per column (fused) or two concurrent teams (split) when co-resident
+  {
+    double best = 1e300;
+    for (int CL = 1; CL <= grape::kMaxCluster; ++CL) {
+      if (d->cluster > 0 && CL != d->cluster) continue;
+      if (CL > 1 && CL > dim) continue;
+      int R = 0, mnl = 0, bin = 0, msm = 0, fsm = 0, ssm = 0;
+      if (!rows_entries(CL, &R, &mnl)) continue;
+      if (!bwd_plan(R, mnl, &bin, &msm, &fsm, &ssm)) continue;
+      const int thr = threads_for(R);
+      for (int mode = 1; mode <= 2; ++mode) {
+        if (mode_req != 0 && mode != mode_req) continue;
+        double cost;
+        if (mode == 1) {
+          cost = waves(P->n * CL) * (a_cost * mnl * (3.0 + wf) + b_cost * R * 2.0 + 2.0 * sync_cost(CL));
+        } else {
+          if (grape::split_capacity(P->precision, CL, ssm, thr) < 2 * P->n) continue;
+          cost = std::max(a_cost * mnl * 2.0 + b_cost * R + sync_cost(CL), a_cost * mnl * (1.0 + wf) + sync_cost(CL));
+        }
+        if (cost < best * 0.98) {
+          best = cost;
+          P->bwd_mode = mode;
+          P->bwd.CL = CL;
+          P->bwd.R = R;
+          P->bwd.mnl = mnl;
+          P->bwd.in_smem = bin;
+          P->bwd.m_smem = mode == 1 ? msm : 0;
+          P->bwd.smem = mode == 1 ? fsm : ssm;
+          P->bwd.threads = thr;
+        }
+      }
+    }
+    if (P->bwd.CL == 0) {
+      if (mode_req == 2) return fail(GRAPE_EINVAL, "backward_mode 2: the 2 * n_states teams cannot be co-resident");
+      return fail(GRAPE_EINVAL, "problem does not fit the backward sweep's shared memory");
     }
   }
-  if (bestCL == 0) return fail(GRAPE_EINVAL, "problem does not fit the sweep kernels' shared memory for any team size");
-  P->CL = bestCL;
-  P->R = bestR;
-  P->max_nnz_loc = std::max(bestMnl, 1);
-  const int CL = P->CL, R = P->R;
-  // column encoding for this partition
-  std::vector<uint32_t> colenc(nnz);
-  for (int64_t i = 0; i < dim; ++i)
-    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
-      const int32_t j = ucol[e];
-      const uint32_t owner = (uint32_t)(j / R), local = (uint32_t)(j - (int64_t)owner * R);
-      uint32_t enc = (owner << grape::kOwnerShift) | local;
-      if (ectr_ptr[e + 1] > ectr_ptr[e]) enc |= grape::kCtrlBit;
-      colenc[e] = enc;
-    }
-  std::vector<int> cslice((size_t)std::max(K, 1) * CL * 2, 0);
+  // column encodings (owner CTA, local row, control bit) of both partitions, control slices of the backward one
+  auto encode = [&](int R, std::vector<uint32_t>& enc) {
+    enc.resize(nnz);
+    for (int64_t i = 0; i < dim; ++i)
+      for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        const int32_t j = ucol[e];
+        const uint32_t owner = (uint32_t)(j / R), local = (uint32_t)(j - (int64_t)owner * R);
+        uint32_t x = (owner << grape::kOwnerShift) | local;
+        if (ectr_ptr[e + 1] > ectr_ptr[e]) x |= grape::kCtrlBit;
+        enc[e] = x;
+      }
+  };
+  std::vector<uint32_t> colenc_f, colenc_b;
+  encode(P->fwd.R, colenc_f);
+  encode(P->bwd.R, colenc_b);
+  const int CLb = P->bwd.CL, Rb = P->bwd.R;
+  std::vector<int> cslice((size_t)std::max(K, 1) * CLb * 2, 0);
   for (int k = 0; k < K; ++k)
-    for (int r = 0; r < CL; ++r) {
-      const int64_t r0 = std::min<int64_t>((int64_t)r * R, dim), r1 = std::min<int64_t>(r0 + R, dim);
+    for (int r = 0; r < CLb; ++r) {
+      const int64_t r0 = std::min<int64_t>((int64_t)r * Rb, dim), r1 = std::min<int64_t>(r0 + Rb, dim);
       const auto b = cidx.begin() + cptr[k], e = cidx.begin() + cptr[k + 1];
-      cslice[(k * CL + r) * 2] = (int)(std::lower_bound(b, e, (int)rowptr[r0]) - cidx.begin());
-      cslice[(k * CL + r) * 2 + 1] = (int)(std::lower_bound(b, e, (int)rowptr[r1]) - cidx.begin());
+      cslice[(k * CLb + r) * 2] = (int)(std::lower_bound(b, e, (int)rowptr[r0]) - cidx.begin());
+      cslice[(k * CLb + r) * 2 + 1] = (int)(std::lower_bound(b, e, (int)rowptr[r1]) - cidx.begin());
     }
-  // ---- shared-memory plan
-  const int mnl = P->max_nnz_loc;
-  int fin = 0;
-  if (grape::make_layout(false, R, mnl, 1, 0, 16).total <= smem_max) fin = 1;
-  P->fwd_in_smem = fin;
-  P->fwd_smem = grape::make_layout(false, R, mnl, fin, 0, 16).total;
-  int bin = 0;
-  if (grape::make_layout(true, R, mnl, 1, 0, 16).total <= smem_max) bin = 1;
-  if (grape::make_layout(true, R, mnl, bin | 2, 0, 16).total <= smem_max) bin |= 2;
-  const int base = grape::make_layout(true, R, mnl, bin, 0, 16).total;
-  int m_smem = (int)std::min<int64_t>(P->m_cap, (smem_max - base - 16) / std::max<int64_t>((int64_t)R * 16, 1));
-  m_smem = std::max(m_smem, 0);
-  P->bwd_in_smem = bin;
-  P->m_smem = m_smem;
-  P->bwd_smem = grape::make_layout(true, R, mnl, bin, m_smem, 16).total;
-  P->threads = (int)std::min<int64_t>(1024, std::max<int64_t>(64, ((int64_t)R + 31) / 32 * 32));
-  P->scr_vals = 0;
-  P->scr_W = mnl;
-  P->scr_wslot = 2 * (int64_t)mnl;
-  P->scratch_stride = 2 * (int64_t)mnl + (int64_t)std::max(0, P->m_cap - m_smem) * R;
-  P->scratch_stride = (P->scratch_stride + 15) / 16 * 16;
+  // per-CTA global scratch (buffers that do not fit in shared memory), in double2 units
+  for (KPlan* kp : {&P->fwd, &P->bwd}) {
+    kp->scr_vals = 0;
+    kp->scr_W = kp->mnl;
+    kp->scr_Wb = 2 * (int64_t)kp->mnl;
+    kp->scr_wslot = 3 * (int64_t)kp->mnl;
+    const int wslots = kp == &P->bwd && P->bwd_mode == 1 ? std::max(0, P->m_cap - kp->m_smem) : 0;
+    kp->stride = (3 * (int64_t)kp->mnl + (int64_t)wslots * kp->R + 15) / 16 * 16;
+  }
   // ---- checkpoints
   int M = d->ckpt_every;
   if (M == 0) M = std::min(50, P->N);
@@ -401,10 +473,11 @@ grape_status build(grape_problem* P, const grape_desc* d) {
   P->ckpt_every = M;
   P->n_ckpt = M > 0 ? (P->N - 1) / M : 0;
   // ---- device memory
-  const int parts = P->n * CL;
+  const int parts_f = P->n * P->fwd.CL, parts_b = P->n * P->bwd.CL;
   std::vector<double> tabX(P->table.X), tabS(P->table.smax);
   if ((st = upload(P, &P->d_rowptr, rowptr.data(), rowptr.size()))) return st;
-  if ((st = upload(P, &P->d_colenc, colenc.data(), colenc.size()))) return st;
+  if ((st = upload(P, &P->fwd.d_colenc, colenc_f.data(), colenc_f.size()))) return st;
+  if ((st = upload(P, &P->bwd.d_colenc, colenc_b.data(), colenc_b.size()))) return st;
   if ((st = upload(P, &P->d_h0v, h0v.data(), h0v.size()))) return st;
   if ((st = upload(P, &P->d_cptr, cptr.data(), cptr.size()))) return st;
   if ((st = upload(P, &P->d_cidx, cidx.data(), cidx.size()))) return st;
@@ -428,26 +501,33 @@ grape_status build(grape_problem* P, const grape_desc* d) {
   if ((st = dzeros(P, &P->d_norm1, (size_t)P->N))) return st;
   if ((st = dzeros(P, &P->d_psiN, blk))) return st;
   if ((st = dzeros(P, &P->d_ckpt, (size_t)std::max(P->n_ckpt, 1) * blk))) return st;
-  if ((st = dzeros(P, &P->d_part_g, (size_t)parts))) return st;
-  if ((st = dzeros(P, &P->d_part_c2, (size_t)parts))) return st;
-  if ((st = dzeros(P, &P->d_part_grad, (size_t)parts * P->N * std::max(K, 1)))) return st;
+  if ((st = dzeros(P, &P->d_part_g, (size_t)parts_f))) return st;
+  if ((st = dzeros(P, &P->d_part_c2, (size_t)parts_f))) return st;
+  if ((st = dzeros(P, &P->d_part_grad, (size_t)parts_b * P->N * std::max(K, 1)))) return st;
   if ((st = dzeros(P, &P->d_g, 1))) return st;
   if ((st = dzeros(P, &P->d_cost, 1))) return st;
   if ((st = dzeros(P, &P->d_parts, 4))) return st;
   if ((st = dzeros(P, &P->d_grad, (size_t)std::max(K, 1) * P->N))) return st;
-  if ((st = dzeros(P, &P->d_scratch, (size_t)parts * P->scratch_stride))) return st;
   if ((st = dzeros(P, &P->d_err, 1))) return st;
+  if (P->bwd_mode == 2) {
+    P->ring_slot = (int64_t)(1 + P->m_cap) * dim;
+    if ((st = dzeros(P, &P->d_ring, (size_t)P->n * P->ring_depth * P->ring_slot))) return st;
+    if ((st = dzeros(P, &P->d_flags, (size_t)2 * parts_b))) return st;
+  }
+  const int64_t scr_f = (int64_t)parts_f * P->fwd.stride;
+  const int64_t scr_b = (int64_t)(P->bwd_mode == 2 ? 2 * parts_b : parts_b) * P->bwd.stride;
+  if ((st = dzeros(P, &P->d_scratch, (size_t)std::max(scr_f, scr_b)))) return st;
   return GRAPE_OK;
 }
 
-grape::SweepParams sweep_params(grape_problem* P) {
+grape::SweepParams sweep_params(grape_problem* P, const KPlan& kp) {
   grape::SweepParams p{};
   p.dim = (int)P->dim;
   p.K = P->K;
   p.N = P->N;
   p.n_states = P->n;
-  p.CL = P->CL;
-  p.R = P->R;
+  p.CL = kp.CL;
+  p.R = kp.R;
   p.dt = P->dt;
   p.w_fid = P->w_fid;
   p.w_forbid = P->w_forbid;
@@ -456,7 +536,7 @@ grape::SweepParams sweep_params(grape_problem* P) {
   p.n_ckpt = P->n_ckpt;
   p.m_cap = P->m_cap;
   p.rowptr = P->d_rowptr;
-  p.colenc = P->d_colenc;
+  p.colenc = kp.d_colenc;
   p.h0v = P->d_h0v;
   p.cptr = P->d_cptr;
   p.cidx = P->d_cidx;
@@ -475,11 +555,14 @@ grape::SweepParams sweep_params(grape_problem* P) {
   p.part_grad = P->d_part_grad;
   p.g_final = P->d_g;
   p.scratch = P->d_scratch;
-  p.scratch_stride = P->scratch_stride;
-  p.scr_vals = P->scr_vals;
-  p.scr_W = P->scr_W;
-  p.scr_wslot = P->scr_wslot;
-  p.max_nnz_loc = P->max_nnz_loc;
+  p.scratch_stride = kp.stride;
+  p.scr_vals = kp.scr_vals;
+  p.scr_W = kp.scr_W;
+  p.scr_Wb = kp.scr_Wb;
+  p.scr_wslot = kp.scr_wslot;
+  p.max_nnz_loc = kp.mnl;
+  p.in_smem = kp.in_smem;
+  p.m_smem = kp.m_smem;
   p.ectr_ptr = P->d_ectr_ptr;
   p.ectr_k = P->d_ectr_k;
   p.ectr_val = P->d_ectr_val;
@@ -555,9 +638,9 @@ grape_status grape_problem_create(const grape_desc* d, grape_problem** out) {
   if (!(d->dt > 0.0) || !std::isfinite(d->dt)) return fail(GRAPE_EINVAL, "dt must be finite and > 0");
   if (!(d->tau > 0.0 && d->tau < 1.0)) return fail(GRAPE_EINVAL, "tau must be in (0, 1)");
   if (d->m_max < 0 || d->m_max > grape::kMaxTaylor) return fail(GRAPE_EINVAL, "m_max must be in 0..60");
-  if (d->precision != GRAPE_FP64) return fail(GRAPE_EINVAL, "precision: only GRAPE_FP64 is available in this build");
-  if (!(d->cluster == 0 || d->cluster == 1 || d->cluster == 2 || d->cluster == 4 || d->cluster == 8 || d->cluster == 16))
-    return fail(GRAPE_EINVAL, "cluster must be 0, 1, 2, 4, 8 or 16");
+  if (d->precision != GRAPE_FP64 && d->precision != GRAPE_FP32_BULK)
+    return fail(GRAPE_EINVAL, "precision must be GRAPE_FP64 or GRAPE_FP32_BULK");
+  if (d->cluster < 0 || d->cluster > grape::kMaxCluster) return fail(GRAPE_EINVAL, "cluster must be 0 (automatic) or 1..16");
   if (d->n_controls > 0 && !d->Hk) return fail(GRAPE_EINVAL, "Hk is NULL");
   if (!d->psi0 || !d->target) return fail(GRAPE_EINVAL, "psi0 / target is NULL");
   if ((d->alloc == nullptr) != (d->free == nullptr)) return fail(GRAPE_EINVAL, "alloc and free must both be set or both NULL");
@@ -645,13 +728,11 @@ grape_status run_forward(grape_problem* P, const double* u, bool u_on_device, cu
   sp.norm1 = P->d_norm1;
   sp.err = P->d_err;
   if ((e = grape::launch_schedule(sp, st)) != cudaSuccess) return cuda_fail(e, "launch k_schedule");
-  grape::SweepParams p = sweep_params(P);
-  p.in_smem = P->fwd_in_smem;
-  p.m_smem = 0;
-  if ((e = grape::launch_forward(p, P->precision, P->fwd_smem, P->threads, st)) != cudaSuccess)
+  grape::SweepParams p = sweep_params(P, P->fwd);
+  if ((e = grape::launch_forward(p, P->precision, P->fwd.smem, P->fwd.threads, st)) != cudaSuccess)
     return cuda_fail(e, "launch k_forward");
   grape::FinalizeParams fp{};
-  fp.n_parts = P->n * P->CL;
+  fp.n_parts = P->n * P->fwd.CL;
   fp.n_states = P->n;
   fp.N = P->N;
   fp.K = P->K;
@@ -672,15 +753,26 @@ grape_status run_forward(grape_problem* P, const double* u, bool u_on_device, cu
 
 // Backward sweep (Fig. 1(b)) without host synchronisation; the gradient stays on the device.
 grape_status run_backward(grape_problem* P, cudaStream_t st) {
-  grape::SweepParams p = sweep_params(P);
-  p.in_smem = P->bwd_in_smem;
-  p.m_smem = P->m_smem;
+  grape::SweepParams p = sweep_params(P, P->bwd);
   cudaError_t e;
-  if ((e = grape::launch_backward(p, P->precision, P->bwd_smem, P->threads, st)) != cudaSuccess)
-    return cuda_fail(e, "launch k_backward");
+  if (P->bwd_mode == 2) {
+    p.ring = P->d_ring;
+    p.ring_slot = P->ring_slot;
+    p.ring_depth = P->ring_depth;
+    p.ready = P->d_flags;
+    p.done = P->d_flags + (size_t)P->n * P->bwd.CL;
+    p.spin_limit = 1LL << 24;
+    if ((e = cudaMemsetAsync(P->d_flags, 0, sizeof(unsigned) * 2 * (size_t)P->n * P->bwd.CL, st)) != cudaSuccess)
+      return cuda_fail(e, "cudaMemsetAsync (flags)");
+    if ((e = grape::launch_backward_split(p, P->precision, P->bwd.smem, P->bwd.threads, st)) != cudaSuccess)
+      return cuda_fail(e, "launch k_backward_split");
+  } else {
+    if ((e = grape::launch_backward(p, P->precision, P->bwd.smem, P->bwd.threads, st)) != cudaSuccess)
+      return cuda_fail(e, "launch k_backward");
+  }
   if (P->K > 0) {
     grape::GradReduceParams gp{};
-    gp.n_parts = P->n * P->CL;
+    gp.n_parts = P->n * P->bwd.CL;
     gp.N = P->N;
     gp.K = P->K;
     gp.w_amp = P->w_amp;
@@ -766,11 +858,13 @@ grape_status grape_problem_info(grape_problem* P, grape_info* info) {
   info->sigma = P->sigma;
   info->m_cap = P->m_cap;
   info->s_cap = P->s_cap;
-  info->cluster = P->CL;
+  info->cluster = P->bwd.CL;
+  info->cluster_forward = P->fwd.CL;
   info->ckpt_every = P->ckpt_every;
-  info->smem_bytes = std::max(P->fwd_smem, P->bwd_smem);
+  info->smem_bytes = std::max(P->fwd.smem, P->bwd.smem);
   info->total_terms = -1;
   info->max_norm = -1.0;
+  info->backward_mode = P->bwd_mode;
   if (P->evaluated) {
     DeviceGuard guard(P->device);
     std::vector<int> m(P->N), s(P->N);

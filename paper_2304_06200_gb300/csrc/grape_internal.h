@@ -57,13 +57,20 @@ struct SweepParams {
   // shared-memory plan (see make_layout) and scratch offsets (in double2 units) of the
   // buffers that are not in shared memory
   int in_smem, m_smem;
-  int64_t scr_vals, scr_W, scr_wslot;
+  int64_t scr_vals, scr_W, scr_Wb, scr_wslot;
   int max_nnz_loc;
   // entry-major control contributions (for assembling H_n on the union pattern)
   const int* ectr_ptr;                 // nnz + 1
   const int* ectr_k;
   const double2* ectr_val;
   int* err;                            // device error word
+  // split backward (team A: psi and Horner chains; team B: x chain, W, gradient), see k_backward_split
+  double2* ring;                       // n_states x ring_depth slots of (1 + m_cap) * dim
+  int64_t ring_slot;                   // complex numbers per slot
+  int ring_depth;
+  unsigned* ready;                     // n_states x CL: substeps published by team A's CTA
+  unsigned* done;                      // n_states x CL: substeps consumed by team B's CTA
+  long long spin_limit;                // polls before a wait gives up (sets the timeout error)
 };
 
 struct ScheduleParams {
@@ -108,16 +115,17 @@ struct GradReduceParams {
 // values (vals), the per-entry gradient accumulators (W) and the first m_smem Horner slots
 // (wslot) live there when they fit, else in the CTA's global scratch slice.
 struct SmemLayout {
-  int xbuf;          // exchange buffers: nchains x 2 x R double2
+  int xbuf;          // exchange buffers: nchains x 2 x R bulk complex
   int psi, chi, inc; // R double2 each (chi only in the backward sweep)
-  int vals, W, wslot;
+  int vals, W, Wb, wslot;
   int lrow, lcol;    // R + 1 ints, max_nnz_loc uints
   int total;
 };
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
-// in_smem bit 0: vals, bit 1: W; m_smem = Horner slots kept in shared memory.
+// in_smem bit 0: vals, bit 1: W, bit 2: Wb (FP32-bulk staging of W); m_smem = Horner slots kept in
+// shared memory; cplx_bytes = 16 (FP64 bulk) or 8 (FP32 bulk).
 __host__ __device__ inline SmemLayout make_layout(bool backward, int R, int max_nnz_loc, int in_smem, int m_smem,
                                                   int cplx_bytes) {
   SmemLayout L;
@@ -128,9 +136,10 @@ __host__ __device__ inline SmemLayout make_layout(bool backward, int R, int max_
   L.chi = -1;
   if (backward) { L.chi = off; off += align16(R * 16); }
   L.inc = off;  off += align16(R * 16);
-  L.vals = -1; L.W = -1; L.wslot = -1;
+  L.vals = -1; L.W = -1; L.Wb = -1; L.wslot = -1;
   if (in_smem & 1) { L.vals = off; off += align16(max_nnz_loc * cplx_bytes); }
   if (backward && (in_smem & 2)) { L.W = off; off += align16(max_nnz_loc * 16); }
+  if (backward && cplx_bytes == 8 && (in_smem & 4)) { L.Wb = off; off += align16(max_nnz_loc * 8); }
   if (backward && m_smem > 0) { L.wslot = off; off += align16(m_smem * R * cplx_bytes); }
   L.lrow = off; off += align16((R + 1) * 4);
   L.lcol = off; off += align16(max_nnz_loc * 4);
@@ -142,6 +151,9 @@ __host__ __device__ inline SmemLayout make_layout(bool backward, int R, int max_
 cudaError_t launch_schedule(const ScheduleParams& p, cudaStream_t st);
 cudaError_t launch_forward(const SweepParams& p, int precision, int smem_bytes, int threads, cudaStream_t st);
 cudaError_t launch_backward(const SweepParams& p, int precision, int smem_bytes, int threads, cudaStream_t st);
+cudaError_t launch_backward_split(const SweepParams& p, int precision, int smem_bytes, int threads, cudaStream_t st);
+// Largest number of co-resident clusters (or blocks when CL == 1) of the split backward kernel.
+int split_capacity(int precision, int CL, int smem_bytes, int threads);
 cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t st);
 cudaError_t launch_grad_reduce(const GradReduceParams& p, cudaStream_t st);
 cudaError_t check_nonfinite_u(const double* u, int64_t count, int* err, cudaStream_t st);

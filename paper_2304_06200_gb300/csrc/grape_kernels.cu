@@ -165,50 +165,96 @@ __global__ void __launch_bounds__(256) k_schedule(ScheduleParams p) {
 
 // ------------------------------------------------------------------ sweep helpers
 
+// Bulk (Taylor-term) arithmetic type: double for the FP64 path, float for the FP32-bulk path.
+// States (psi, chi), their increments, the W accumulators and every reduction stay FP64.
+template <typename T> struct CxT;
+template <> struct CxT<double> { using t = double2; };
+template <> struct CxT<float> { using t = float2; };
+template <typename T> using cx = typename CxT<T>::t;
+
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double2 to_d2(const double2 v) { return v; }
+__device__ __forceinline__ double2 to_d2(const float2 v) { return make_double2(v.x, v.y); }
+template <typename T> __device__ __forceinline__ cx<T> from_d2(const double2 v);
+template <> __device__ __forceinline__ double2 from_d2<double>(const double2 v) { return v; }
+template <> __device__ __forceinline__ float2 from_d2<float>(const double2 v) { return make_float2((float)v.x, (float)v.y); }
+template <typename T> __device__ __forceinline__ cx<T> make_cx(T x, T y);
+template <> __device__ __forceinline__ double2 make_cx<double>(double x, double y) { return make_double2(x, y); }
+template <> __device__ __forceinline__ float2 make_cx<float>(float x, float y) { return make_float2(x, y); }
+template <typename C2> __device__ __forceinline__ C2 czero();
+template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.0f, 0.0f); }
+
+template <typename C2>
+__device__ __forceinline__ void cmacT(C2& acc, const C2 a, const C2 b) {  // acc += a b
+  acc.x = fmaT(a.x, b.x, acc.x);
+  acc.x = fmaT(-a.y, b.y, acc.x);
+  acc.y = fmaT(a.x, b.y, acc.y);
+  acc.y = fmaT(a.y, b.x, acc.y);
+}
+
+template <typename C2>
+__device__ __forceinline__ void cmac_conjT(C2& acc, const C2 a, const C2 b) {  // acc += conj(a) b
+  acc.x = fmaT(a.x, b.x, acc.x);
+  acc.x = fmaT(a.y, b.y, acc.x);
+  acc.y = fmaT(a.x, b.y, acc.y);
+  acc.y = fmaT(-a.y, b.x, acc.y);
+}
+
+// One Horner step in bulk precision: chi/(p+1)! - yw (for FP64 in one fused rounding).
+__device__ __forceinline__ double2 horner(const double2 ch, double f, const double2 yw) {
+  return make_double2(fma(ch.x, f, -yw.x), fma(ch.y, f, -yw.y));
+}
+__device__ __forceinline__ float2 horner(const double2 ch, double f, const float2 yw) {
+  return make_float2((float)(ch.x * f) - yw.x, (float)(ch.y * f) - yw.y);
+}
+
+template <typename T>
 struct Carve {
-  double2* xb;        // exchange buffers (local)
+  cx<T>* xb;          // exchange buffers (local)
   double2* psi;
   double2* chi;
   double2* inc;
-  double2* vals;
-  double2* W;
-  double2* wsm;       // Horner slots in shared memory (first m_smem)
-  double2* wgl;       // Horner slots in global scratch (slots >= m_smem)
+  cx<T>* vals;
+  double2* W;         // FP64 accumulators of conj(w_p) x_p per local entry
+  float2* Wb;         // FP32-bulk path: per-substep staging of W in bulk precision
+  cx<T>* wsm;         // Horner slots in shared memory (first m_smem)
+  cx<T>* wgl;         // Horner slots in global scratch (slots >= m_smem)
   int* lrow;
   uint32_t* lcol;
 };
 
-__device__ __forceinline__ Carve carve(unsigned char* smem, const SweepParams& p, bool backward, int part) {
-  const SmemLayout L = make_layout(backward, p.R, p.max_nnz_loc, p.in_smem, p.m_smem, 16);
+template <typename T>
+__device__ __forceinline__ Carve<T> carve(unsigned char* smem, const SweepParams& p, bool backward, int part) {
+  const SmemLayout L = make_layout(backward, p.R, p.max_nnz_loc, p.in_smem, p.m_smem, (int)sizeof(cx<T>));
   double2* scr = p.scratch + (int64_t)part * p.scratch_stride;
-  Carve c;
-  c.xb = reinterpret_cast<double2*>(smem + L.xbuf);
+  Carve<T> c;
+  c.xb = reinterpret_cast<cx<T>*>(smem + L.xbuf);
   c.psi = reinterpret_cast<double2*>(smem + L.psi);
   c.chi = backward ? reinterpret_cast<double2*>(smem + L.chi) : nullptr;
   c.inc = reinterpret_cast<double2*>(smem + L.inc);
-  c.vals = L.vals >= 0 ? reinterpret_cast<double2*>(smem + L.vals) : scr + p.scr_vals;
+  c.vals = L.vals >= 0 ? reinterpret_cast<cx<T>*>(smem + L.vals) : reinterpret_cast<cx<T>*>(scr + p.scr_vals);
   c.W = L.W >= 0 ? reinterpret_cast<double2*>(smem + L.W) : scr + p.scr_W;
-  c.wsm = L.wslot >= 0 ? reinterpret_cast<double2*>(smem + L.wslot) : nullptr;
-  c.wgl = scr + p.scr_wslot;
+  c.Wb = L.Wb >= 0 ? reinterpret_cast<float2*>(smem + L.Wb) : reinterpret_cast<float2*>(scr + p.scr_Wb);
+  c.wsm = L.wslot >= 0 ? reinterpret_cast<cx<T>*>(smem + L.wslot) : nullptr;
+  c.wgl = reinterpret_cast<cx<T>*>(scr + p.scr_wslot);
   c.lrow = reinterpret_cast<int*>(smem + L.lrow);
   c.lcol = reinterpret_cast<uint32_t*>(smem + L.lcol);
   return c;
 }
 
-// Horner slot p of local row i.
-__device__ __forceinline__ double2* wslot_ptr(const Carve& c, int m_smem, int R, int p, int i) {
-  return p < m_smem ? c.wsm + (int64_t)p * R + i : c.wgl + (int64_t)(p - m_smem) * R + i;
-}
-
-// Table of generic pointers to exchange buffer `b` of every CTA of the team.
-template <bool CLUSTER>
+// Table of generic pointers to one exchange buffer of every CTA of the team.
+template <typename T>
 struct XTab {
-  double2* ptr[kMaxCluster];
+  cx<T>* ptr[kMaxCluster];
 };
 
-// Assemble B_n = -i dt H_n / s on the CTA's local entries: vals[e] = (dt/s) * (-i) * (h0 + sum_k u_kn h_k).
-__device__ __forceinline__ void assemble(const SweepParams& p, const Carve& c, int64_t e0, int nnz_loc, int n,
-                                         double scale, const double* s_u) {
+// Assemble B_n = -i dt H_n / s on the CTA's local entries: vals[e] = (dt/s) * (-i) * (h0 + sum_k u_kn h_k),
+// evaluated in FP64 and stored in the bulk precision.
+template <typename T>
+__device__ __forceinline__ void assemble(const SweepParams& p, cx<T>* vals, int64_t e0, int nnz_loc, double scale,
+                                         const double* s_u) {
   for (int e = threadIdx.x; e < nnz_loc; e += blockDim.x) {
     const int64_t ge = e0 + e;
     double2 v = p.h0v[ge];
@@ -218,7 +264,7 @@ __device__ __forceinline__ void assemble(const SweepParams& p, const Carve& c, i
       v.x = fma(uk, hv.x, v.x);
       v.y = fma(uk, hv.y, v.y);
     }
-    c.vals[e] = make_double2(scale * v.y, -scale * v.x);   // -i v
+    vals[e] = from_d2<T>(make_double2(scale * v.y, -scale * v.x));   // -i v
   }
 }
 
@@ -226,8 +272,8 @@ __device__ __forceinline__ void load_controls(const SweepParams& p, int n, doubl
   if (threadIdx.x < p.K) s_u[threadIdx.x] = p.u[(int64_t)threadIdx.x * p.N + n];
 }
 
-template <bool CLUSTER>
-__device__ __forceinline__ double2 xload(const double2* local, const XTab<CLUSTER>& tab, uint32_t enc) {
+template <typename T, bool CLUSTER>
+__device__ __forceinline__ cx<T> xload(const cx<T>* local, const XTab<T>& tab, uint32_t enc) {
   if constexpr (CLUSTER) {
     return tab.ptr[(enc >> kOwnerShift) & 0xFFu][enc & kLocalMask];
   } else {
@@ -235,38 +281,121 @@ __device__ __forceinline__ double2 xload(const double2* local, const XTab<CLUSTE
   }
 }
 
-template <bool CLUSTER>
-__device__ __forceinline__ void sweep_setup(const SweepParams& p, const Carve& c, int r0, int nrows, int64_t e0,
-                                            int nnz_loc) {
-  for (int i = threadIdx.x; i <= nrows; i += blockDim.x) c.lrow[i] = (int)(p.rowptr[r0 + i] - e0);
-  for (int e = threadIdx.x; e < nnz_loc; e += blockDim.x) c.lcol[e] = p.colenc[e0 + e];
+
+// Row products on the local pattern.  FP64: one accumulator per chain (the FP64 pipe is the bound,
+// so no extra instructions).  FP32 (latency bound): entries two at a time, both loads (a remote
+// row costs a distributed-shared-memory round trip) issued before the two multiply-adds, which go
+// to two accumulators.  The trip count is exact either way: no padded multiply-adds.
+template <typename T, bool CLUSTER>
+__device__ __forceinline__ cx<T> row_mv(const cx<T>* __restrict__ vals, const uint32_t* __restrict__ lcol, int ea,
+                                        int eb, const cx<T>* xs, const XTab<T>& tab) {
+  using C2 = cx<T>;
+  if constexpr (sizeof(C2) == 16) {
+    C2 y = czero<C2>();
+    for (int e = ea; e < eb; ++e) cmacT(y, vals[e], xload<T, CLUSTER>(xs, tab, lcol[e]));
+    return y;
+  }
+  C2 y0 = czero<C2>(), y1 = czero<C2>();
+  int e = ea;
+  for (; e + 2 <= eb; e += 2) {
+    const C2 v0 = vals[e], v1 = vals[e + 1];
+    const C2 x0 = xload<T, CLUSTER>(xs, tab, lcol[e]);
+    const C2 x1 = xload<T, CLUSTER>(xs, tab, lcol[e + 1]);
+    cmacT(y0, v0, x0);
+    cmacT(y1, v1, x1);
+  }
+  if (e < eb) cmacT(y0, vals[e], xload<T, CLUSTER>(xs, tab, lcol[e]));
+  y0.x += y1.x;
+  y0.y += y1.y;
+  return y0;
 }
+
+// Two chains through the same matrix row: ya = row . xa, yw = row . xw.
+template <typename T, bool CLUSTER>
+__device__ __forceinline__ void row_mv2(const cx<T>* __restrict__ vals, const uint32_t* __restrict__ lcol, int ea, int eb,
+                                        const cx<T>* xa, const XTab<T>& ta, const cx<T>* xw, const XTab<T>& tw,
+                                        cx<T>& ya, cx<T>& yw) {
+  using C2 = cx<T>;
+  if constexpr (sizeof(C2) == 16) {
+    C2 a = czero<C2>(), w = czero<C2>();
+    for (int e = ea; e < eb; ++e) {
+      const uint32_t enc = lcol[e];
+      const C2 v = vals[e];
+      cmacT(a, v, xload<T, CLUSTER>(xa, ta, enc));
+      cmacT(w, v, xload<T, CLUSTER>(xw, tw, enc));
+    }
+    ya = a;
+    yw = w;
+    return;
+  }
+  C2 a0 = czero<C2>(), a1 = czero<C2>(), w0 = czero<C2>(), w1 = czero<C2>();
+  int e = ea;
+  for (; e + 2 <= eb; e += 2) {
+    const uint32_t c0 = lcol[e], c1 = lcol[e + 1];
+    const C2 v0 = vals[e], v1 = vals[e + 1];
+    const C2 xa0 = xload<T, CLUSTER>(xa, ta, c0), xa1 = xload<T, CLUSTER>(xa, ta, c1);
+    const C2 xw0 = xload<T, CLUSTER>(xw, tw, c0), xw1 = xload<T, CLUSTER>(xw, tw, c1);
+    cmacT(a0, v0, xa0);
+    cmacT(w0, v0, xw0);
+    cmacT(a1, v1, xa1);
+    cmacT(w1, v1, xw1);
+  }
+  if (e < eb) {
+    const uint32_t c0 = lcol[e];
+    const C2 v0 = vals[e];
+    cmacT(a0, v0, xload<T, CLUSTER>(xa, ta, c0));
+    cmacT(w0, v0, xload<T, CLUSTER>(xw, tw, c0));
+  }
+  ya = make_cx<T>(a0.x + a1.x, a0.y + a1.y);
+  yw = make_cx<T>(w0.x + w1.x, w0.y + w1.y);
+}
+
+__device__ __forceinline__ void sweep_setup(const SweepParams& p, int* lrow, uint32_t* lcol, int r0, int nrows,
+                                            int64_t e0, int nnz_loc) {
+  for (int i = threadIdx.x; i <= nrows; i += blockDim.x) lrow[i] = (int)(p.rowptr[r0 + i] - e0);
+  for (int e = threadIdx.x; e < nnz_loc; e += blockDim.x) lcol[e] = p.colenc[e0 + e];
+}
+
+// Everything one CTA of a team needs inside the sweeps.
+template <typename T, bool CLUSTER>
+struct Team {
+  Carve<T> c;
+  XTab<T>* tab;         // shared-memory table per exchange buffer
+  // exchange buffer b (A chain 0,1; Horner chain 2,3; x chain 4,5), contiguous in shared memory
+  __device__ __forceinline__ cx<T>* X(int b) const { return c.xb + b * R; }
+  int r0, nrows, R, rank, CL;
+  int64_t e0;
+  int nnz_loc;
+};
 
 // ------------------------------------------------------------------ forward sweep
 
 // psi_n = (e^{B}_m)^s psi_{n-1} by the recursions b_j = (B/j) b_{j-1} (App. C Eq. (recursive relation 1))
 // and c_l = e^B_m c_{l-1} (Eq. (recursive relation2)); C2 accumulates <psi_n|Omega|psi_n> (App. A).
-template <bool CLUSTER>
-__global__ void __launch_bounds__(1024, 1) k_forward(SweepParams p) {
+// The state psi and the per-substep sum of the terms are FP64; the terms themselves use the bulk type.
+template <typename T, bool CLUSTER>
+__global__ void __launch_bounds__(512, 1) k_forward(SweepParams p) {
+  using C2 = cx<T>;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32];
   __shared__ double s_u[kMaxControls];
-  __shared__ XTab<CLUSTER> tab[2];
+  __shared__ XTab<T> tab[2];
   const int part = blockIdx.x;
   const int team = part / p.CL, rank = part % p.CL;
   const int r0 = min(rank * p.R, p.dim), r1 = min(r0 + p.R, p.dim), nrows = r1 - r0;
   const int64_t e0 = p.rowptr[r0];
   const int nnz_loc = (int)(p.rowptr[r1] - e0);
-  const Carve c = carve(smem, p, false, part);
-  double2* T[2] = {c.xb, c.xb + p.R};
+  const Carve<T> c = carve<T>(smem, p, false, part);
+  C2* const X0 = c.xb;
+  const int R = p.R;
   if constexpr (CLUSTER) {
     cg::cluster_group cl = cg::this_cluster();
     if (threadIdx.x < p.CL) {
-      tab[0].ptr[threadIdx.x] = cl.map_shared_rank(T[0], threadIdx.x);
-      tab[1].ptr[threadIdx.x] = cl.map_shared_rank(T[1], threadIdx.x);
+      tab[0].ptr[threadIdx.x] = cl.map_shared_rank(X0, threadIdx.x);
+      tab[1].ptr[threadIdx.x] = cl.map_shared_rank(X0 + R, threadIdx.x);
     }
   }
-  sweep_setup<CLUSTER>(p, c, r0, nrows, e0, nnz_loc);
+  sweep_setup(p, c.lrow, c.lcol, r0, nrows, e0, nnz_loc);
   const int64_t col0 = (int64_t)team * p.dim + r0;
   for (int i = threadIdx.x; i < nrows; i += blockDim.x) c.psi[i] = p.psi0[col0 + i];
   double c2acc = 0.0;
@@ -276,26 +405,28 @@ __global__ void __launch_bounds__(1024, 1) k_forward(SweepParams p) {
     if (s <= 0 || m <= 0) continue;   // flagged by k_schedule; uniform over the team
     load_controls(p, n, s_u);
     __syncthreads();
-    assemble(p, c, e0, nnz_loc, n, p.dt / s, s_u);
+    assemble<T>(p, c.vals, e0, nnz_loc, p.dt / s, s_u);
     __syncthreads();
     for (int l = 0; l < s; ++l) {
       for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
-        T[0][i] = c.psi[i];
+        X0[i] = from_d2<T>(c.psi[i]);
         c.inc[i] = make_double2(0.0, 0.0);
       }
       team_sync<CLUSTER>();
       for (int q = 1; q <= m; ++q) {
         const int src = (q - 1) & 1, dst = q & 1;
-        const double iq = c_inv_int[q];
+        const T iq = (T)c_inv_int[q];
+        const C2* xs = X0 + src * R;
+        C2* xd = X0 + dst * R;
         for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
-          double2 y = make_double2(0.0, 0.0);
-          const int ea = c.lrow[i], eb = c.lrow[i + 1];
-          for (int e = ea; e < eb; ++e) cmac(y, c.vals[e], xload<CLUSTER>(T[src], tab[src], c.lcol[e]));
-          y = cscale(y, iq);
-          T[dst][i] = y;
+          C2 y = row_mv<T, CLUSTER>(c.vals, c.lcol, c.lrow[i], c.lrow[i + 1], xs, tab[src]);
+          y.x *= iq;
+          y.y *= iq;
+          xd[i] = y;
           double2 a = c.inc[i];
-          a.x += y.x;
-          a.y += y.y;
+          const double2 yd = to_d2(y);
+          a.x += yd.x;
+          a.y += yd.y;
           c.inc[i] = a;
         }
         team_sync<CLUSTER>();
@@ -339,6 +470,423 @@ __global__ void __launch_bounds__(1024, 1) k_forward(SweepParams p) {
   team_sync<CLUSTER>();   // no CTA leaves while a team member may still read its shared memory
 }
 
+// ------------------------------------------------------------------ backward sweep: shared pieces
+//
+// For every step n = N..1 and substep l = s-1..0 (B = -i dt H_n / s, P = e^B_m):
+//   phase A  psi^(l) = P(-B) psi^(l+1) (adjoint re-propagation, Fig. 1(b)) and the Horner chain
+//            w_{m-1} = chi/m!,  w_p = chi/(p+1)! + (-B) w_{p+1},  chi^(l) = w_{-1} = P(-B) chi^(l+1)
+//   phase B  x_0 = psi^(l), x_{p+1} = B x_p, and W_ij += conj(w_p[i]) x_p[j] on control entries
+// so that  sum_l <chi^(l+1)| dP/du_k |psi^(l)> = sum_ij (C_k)_ij W_ij with C_k = -i dt h_k / s,
+// which is the derivative of the approximant (e^B_m)^s at frozen (m, s) (Eq. (auxiliary equation)):
+// dP = sum_q 1/q! sum_{r+p=q-1} B^r C B^p  regrouped as  sum_p <w_p| C |x_p>.
+// chi is the combined costate of C1 and C2 (Eqs. (stgradient), (gategradient), (C2stgrad)):
+//   chi_N = -(w_fid g / n^2) phi_T + (w_forbid/(N n)) Omega psi_N,
+//   chi_{n-1} = U_n^+ chi_n + (w_forbid/(N n)) Omega psi_{n-1}   (n-1 >= 1).
+
+// psi_N and chi_N on the CTA's rows.
+__device__ __forceinline__ void costate_init(const SweepParams& p, double2* psi, double2* chi, int64_t col0, int r0,
+                                             int nrows, double c2w) {
+  const double nS = (double)p.n_states;
+  const double2 g = *p.g_final;
+  const double2 coefA = make_double2(-p.w_fid * g.x / (nS * nS), -p.w_fid * g.y / (nS * nS));
+  for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+    const double2 v = p.psiN[col0 + i];
+    psi[i] = v;
+    double2 ch = cmul(coefA, p.target[col0 + i]);
+    if (c2w != 0.0) {
+      const double w = c2w * p.omega[r0 + i];
+      ch.x = fma(w, v.x, ch.x);
+      ch.y = fma(w, v.y, ch.y);
+    }
+    chi[i] = ch;
+  }
+}
+
+// Phase A of one substep.  wout(p, i, w) stores Horner vector w_p of local row i.
+template <typename T, bool CLUSTER, typename WOut>
+__device__ __forceinline__ void phase_a(Team<T, CLUSTER>& tm, int m, WOut wout) {
+  using C2 = cx<T>;
+  const Carve<T>& c = tm.c;
+  const double fm = c_inv_fact[m];
+  for (int i = threadIdx.x; i < tm.nrows; i += blockDim.x) {
+    tm.X(0)[i] = from_d2<T>(c.psi[i]);
+    c.inc[i] = make_double2(0.0, 0.0);
+    const C2 w0 = from_d2<T>(cscale(c.chi[i], fm));
+    tm.X(2)[i] = w0;
+    wout(m - 1, i, w0);
+  }
+  team_sync<CLUSTER>();
+  for (int q = 1; q <= m; ++q) {
+    const int src = (q - 1) & 1, dst = q & 1;
+    const T iq = (T)c_inv_int[q];
+    const double fq = c_inv_fact[m - q];
+    for (int i = threadIdx.x; i < tm.nrows; i += blockDim.x) {
+      C2 ya, yw;
+      row_mv2<T, CLUSTER>(c.vals, c.lcol, c.lrow[i], c.lrow[i + 1], tm.X(src), tm.tab[src], tm.X(2 + src),
+                          tm.tab[2 + src], ya, yw);
+      ya.x *= -iq;                                   // (-B) a_{q-1} / q
+      ya.y *= -iq;
+      tm.X(dst)[i] = ya;
+      double2 a = c.inc[i];
+      const double2 yad = to_d2(ya);
+      a.x += yad.x;
+      a.y += yad.y;
+      c.inc[i] = a;
+      const double2 ch = c.chi[i];
+      if (q < m) {
+        const C2 w = horner(ch, fq, yw);             // chi/(p+1)! + (-B) w_{p+1}
+        tm.X(2 + dst)[i] = w;
+        wout(m - 1 - q, i, w);
+      } else {
+        const double2 ywd = to_d2(yw);
+        c.chi[i] = make_double2(fma(ch.x, fq, -ywd.x), fma(ch.y, fq, -ywd.y));   // chi^(l) = w_{-1}
+      }
+    }
+    team_sync<CLUSTER>();
+  }
+  for (int i = threadIdx.x; i < tm.nrows; i += blockDim.x) {
+    double2 v = c.psi[i];
+    const double2 a = c.inc[i];
+    v.x += a.x;
+    v.y += a.y;
+    c.psi[i] = v;                                  // psi^(l)
+  }
+}
+
+// Phase B of one substep.  X[4] must hold psi^(l) (own rows) on entry; win(p, i) returns w_p of row i.
+template <typename T, bool CLUSTER, typename WIn>
+__device__ __forceinline__ void phase_b(Team<T, CLUSTER>& tm, int m, WIn win) {
+  using C2 = cx<T>;
+  constexpr bool kStage = sizeof(C2) == 8;      // FP32 bulk: stage W per substep in float
+  const Carve<T>& c = tm.c;
+  // With one row per thread, w_{p+1} is fetched while term p runs (it may come from L2).
+  const bool one_row = tm.nrows <= (int)blockDim.x;
+  C2 wnext = (one_row && (int)threadIdx.x < tm.nrows) ? win(0, threadIdx.x) : czero<C2>();
+  team_sync<CLUSTER>();
+  for (int pp = 0; pp < m; ++pp) {
+    const int src = pp & 1, dst = src ^ 1;
+    const bool more = pp < m - 1;
+    const C2* xs = tm.X(4 + src);
+    for (int i = threadIdx.x; i < tm.nrows; i += blockDim.x) {
+      C2 wp;
+      if (one_row) {
+        wp = wnext;
+        if (more) wnext = win(pp + 1, i);
+      } else {
+        wp = win(pp, i);
+      }
+      C2 y0 = czero<C2>(), y1 = czero<C2>();
+      const int ea = c.lrow[i], eb = c.lrow[i + 1];
+      if constexpr (sizeof(C2) == 16) {   // FP64: one accumulator, exact loop
+        for (int e = ea; e < eb; ++e) {
+          const uint32_t enc = c.lcol[e];
+          const C2 x = xload<T, CLUSTER>(xs, tm.tab[4 + src], enc);
+          if (more) cmacT(y0, c.vals[e], x);
+          if (enc & kCtrlBit) {
+            double2 acc = c.W[e];
+            cmac_conjT(acc, wp, x);
+            c.W[e] = acc;
+          }
+        }
+        if (more) tm.X(4 + dst)[i] = y0;
+        continue;
+      }
+      auto wacc = [&](int e, const C2 x) {
+        if constexpr (kStage) {
+          float2 acc = c.Wb[e];
+          cmac_conjT(acc, wp, x);
+          c.Wb[e] = acc;
+        } else {
+          double2 acc = c.W[e];
+          cmac_conjT(acc, wp, x);
+          c.W[e] = acc;
+        }
+      };
+      int e = ea;
+      for (; e + 2 <= eb; e += 2) {
+        const uint32_t c0 = c.lcol[e], c1 = c.lcol[e + 1];
+        const C2 x0 = xload<T, CLUSTER>(xs, tm.tab[4 + src], c0);
+        const C2 x1 = xload<T, CLUSTER>(xs, tm.tab[4 + src], c1);
+        if (more) {
+          cmacT(y0, c.vals[e], x0);
+          cmacT(y1, c.vals[e + 1], x1);
+        }
+        if (c0 & kCtrlBit) wacc(e, x0);
+        if (c1 & kCtrlBit) wacc(e + 1, x1);
+      }
+      if (e < eb) {
+        const uint32_t c0 = c.lcol[e];
+        const C2 x0 = xload<T, CLUSTER>(xs, tm.tab[4 + src], c0);
+        if (more) cmacT(y0, c.vals[e], x0);
+        if (c0 & kCtrlBit) wacc(e, x0);
+      }
+      if (more) tm.X(4 + dst)[i] = make_cx<T>(y0.x + y1.x, y0.y + y1.y);
+    }
+    if (more) team_sync<CLUSTER>();
+  }
+  if constexpr (kStage) {   // fold the substep's FP32 sums into the FP64 accumulators (same thread owns the row)
+    for (int i = threadIdx.x; i < tm.nrows; i += blockDim.x)
+      for (int e = c.lrow[i]; e < c.lrow[i + 1]; ++e)
+        if (c.lcol[e] & kCtrlBit) {
+          const float2 b = c.Wb[e];
+          double2 a = c.W[e];
+          a.x += b.x;
+          a.y += b.y;
+          c.W[e] = a;
+          c.Wb[e] = make_float2(0.0f, 0.0f);
+        }
+  }
+}
+
+__device__ __forceinline__ void zero_w(const SweepParams& p, double2* W, float2* Wb, int nnz_loc, bool staged) {
+  for (int e = threadIdx.x; e < nnz_loc; e += blockDim.x) {
+    W[e] = make_double2(0.0, 0.0);
+    if (staged) Wb[e] = make_float2(0.0f, 0.0f);
+  }
+}
+
+// Step end on the psi/chi side: checkpoint reset of psi_{n} and the C2 source of chi.
+__device__ __forceinline__ void step_end(const SweepParams& p, double2* psi, double2* chi, int n, int col, int r0,
+                                         int nrows, double c2w) {
+  if (n <= 0) return;
+  if (p.ckpt_every > 0 && n % p.ckpt_every == 0 && n / p.ckpt_every - 1 < p.n_ckpt) {
+    const double2* srcp = p.ckpt + ((int64_t)(n / p.ckpt_every - 1) * p.n_states + col) * p.dim + r0;
+    for (int i = threadIdx.x; i < nrows; i += blockDim.x) psi[i] = srcp[i];
+  }
+  if (c2w != 0.0) {
+    for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+      const double w = c2w * p.omega[r0 + i];
+      const double2 v = psi[i];
+      double2 ch = chi[i];
+      ch.x = fma(w, v.x, ch.x);
+      ch.y = fma(w, v.y, ch.y);
+      chi[i] = ch;
+    }
+  }
+}
+
+// dC/du_kn part = 2 Re sum_ij (C_k)_ij W_ij, C_k = -i (dt/s) h_k: Re(-i h W) = h.x W.y + h.y W.x
+__device__ __forceinline__ void grad_partials(const SweepParams& p, const double2* W, int rank, int out_part, int n,
+                                              int s, int64_t e0, double* red) {
+  const double gscale = 2.0 * p.dt / s;
+  for (int k = 0; k < p.K; ++k) {
+    const int lo = p.cslice[(k * p.CL + rank) * 2], hi = p.cslice[(k * p.CL + rank) * 2 + 1];
+    double acc = 0.0;
+    for (int cc = lo + threadIdx.x; cc < hi; cc += blockDim.x) {
+      const int e = (int)(p.cidx[cc] - e0);
+      const double2 w = W[e];
+      const double2 h = p.cval[cc];
+      acc = fma(h.x, w.y, acc);
+      acc = fma(h.y, w.x, acc);
+    }
+    const double tot = block_sum(acc, red);
+    if (threadIdx.x == 0) p.part_grad[((int64_t)out_part * p.N + n) * p.K + k] = gscale * tot;
+  }
+}
+
+template <typename T, bool CLUSTER>
+__device__ __forceinline__ void team_init(Team<T, CLUSTER>& tm, unsigned char* smem, XTab<T>* tab, const SweepParams& p,
+                                          int part, int rank) {
+  tm.rank = rank;
+  tm.CL = p.CL;
+  tm.R = p.R;
+  tm.r0 = min(rank * p.R, p.dim);
+  const int r1 = min(tm.r0 + p.R, p.dim);
+  tm.nrows = r1 - tm.r0;
+  tm.e0 = p.rowptr[tm.r0];
+  tm.nnz_loc = (int)(p.rowptr[r1] - tm.e0);
+  tm.c = carve<T>(smem, p, true, part);
+  tm.tab = tab;
+  if constexpr (CLUSTER) {
+    cg::cluster_group cl = cg::this_cluster();
+    if (threadIdx.x < p.CL)
+      for (int b = 0; b < 6; ++b) tab[b].ptr[threadIdx.x] = cl.map_shared_rank(tm.X(b), threadIdx.x);
+  }
+  sweep_setup(p, tm.c.lrow, tm.c.lcol, tm.r0, tm.nrows, tm.e0, tm.nnz_loc);
+}
+
+// ------------------------------------------------------------------ backward sweep, one team per column
+
+template <typename T, bool CLUSTER>
+__global__ void __launch_bounds__(512, 1) k_backward(SweepParams p) {
+  using C2 = cx<T>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[32];
+  __shared__ double s_u[kMaxControls];
+  __shared__ XTab<T> tab[6];
+  const int part = blockIdx.x;
+  const int col = part / p.CL, rank = part % p.CL;
+  Team<T, CLUSTER> tm;
+  team_init<T, CLUSTER>(tm, smem, tab, p, part, rank);
+  const Carve<T>& c = tm.c;
+  const int64_t col0 = (int64_t)col * p.dim + tm.r0;
+  const double c2w = (p.omega && p.w_forbid != 0.0) ? p.w_forbid / ((double)p.N * p.n_states) : 0.0;
+  const int R = p.R, m_smem = p.m_smem;
+  costate_init(p, c.psi, c.chi, col0, tm.r0, tm.nrows, c2w);
+  team_sync<CLUSTER>();
+  auto slot = [&](int pp, int i) -> C2* {
+    return pp < m_smem ? c.wsm + (int64_t)pp * R + i : c.wgl + (int64_t)(pp - m_smem) * R + i;
+  };
+  for (int n = p.N - 1; n >= 0; --n) {
+    const int m = p.ms_m[n], s = p.ms_s[n];
+    if (s <= 0 || m <= 0) continue;
+    load_controls(p, n, s_u);
+    __syncthreads();
+    assemble<T>(p, c.vals, tm.e0, tm.nnz_loc, p.dt / s, s_u);
+    zero_w(p, c.W, c.Wb, tm.nnz_loc, sizeof(C2) == 8);
+    __syncthreads();
+    for (int l = s - 1; l >= 0; --l) {
+      phase_a<T, CLUSTER>(tm, m, [&](int pp, int i, C2 w) { *slot(pp, i) = w; });
+      for (int i = threadIdx.x; i < tm.nrows; i += blockDim.x) tm.X(4)[i] = from_d2<T>(c.psi[i]);
+      phase_b<T, CLUSTER>(tm, m, [&](int pp, int i) -> C2 { return *slot(pp, i); });
+    }
+    __syncthreads();
+    step_end(p, c.psi, c.chi, n, col, tm.r0, tm.nrows, c2w);
+    grad_partials(p, c.W, rank, part, n, s, tm.e0, red);
+    __syncthreads();
+  }
+  team_sync<CLUSTER>();
+}
+
+// ------------------------------------------------------------------ backward sweep, two teams per column
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* a) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned* a, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+
+// Thread 0 polls until *flag >= target (wrap-safe), at most `limit` polls.
+__device__ __forceinline__ int wait_geq(const unsigned* flag, unsigned target, long long limit) {
+  for (long long it = 0; it < limit; ++it) {
+    if ((int)(ld_acquire(flag) - target) >= 0) return 1;
+    __nanosleep(128);
+  }
+  return 0;
+}
+
+// Team-uniform AND of one flag per CTA: every CTA of the team takes the same decision, so no CTA
+// leaves a loop that its cluster peers continue (which would strand them at a cluster barrier).
+// Alternating slots make one barrier sufficient.
+template <bool CLUSTER>
+__device__ __forceinline__ int team_all(int mine, int* s_flags, unsigned t, int CL) {
+  int* f = s_flags + (t & 1);
+  if (threadIdx.x == 0) *f = mine;
+  team_sync<CLUSTER>();
+  int all = 1;
+  if constexpr (CLUSTER) {
+    cg::cluster_group cl = cg::this_cluster();
+    for (int r = 0; r < CL; ++r) all &= *cl.map_shared_rank(f, r);
+  } else {
+    all = *f;
+  }
+  return all;
+}
+
+// The backward sweep with its two phases on two teams per column that run concurrently: team A
+// (role 0) runs phase A and publishes, per substep, psi^(l) and the Horner vectors w_p into a ring
+// slot in global memory; team B (role 1) runs phase B one substep behind and computes the per-step
+// gradient partials.  A's CTA r hands rows [r0, r1) to B's CTA r through release/acquire flags
+// (one pair per CTA), so a substep costs no extra team barrier.  Every wait is bounded; a wait that
+// gives up sets the timeout error and both teams leave uniformly.  The arithmetic per row is the
+// same as in k_backward, so the results are identical.
+template <typename T, bool CLUSTER>
+__global__ void __launch_bounds__(512, 1) k_backward_split(SweepParams p) {
+  using C2 = cx<T>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[32];
+  __shared__ double s_u[kMaxControls];
+  __shared__ XTab<T> tab[6];
+  __shared__ int s_flags[2];
+  const int part = blockIdx.x;
+  const int team = part / p.CL, rank = part % p.CL;
+  const int col = team >> 1, role = team & 1;
+  Team<T, CLUSTER> tm;
+  team_init<T, CLUSTER>(tm, smem, tab, p, part, rank);
+  const Carve<T>& c = tm.c;
+  const int64_t col0 = (int64_t)col * p.dim + tm.r0;
+  const int dim = p.dim, r0 = tm.r0;
+  const int64_t slot_c2 = p.ring_slot;                  // bulk-type elements per ring slot
+  C2* ring_col = reinterpret_cast<C2*>(p.ring) + (int64_t)col * p.ring_depth * slot_c2;
+  unsigned* ready = p.ready + col * p.CL + rank;
+  unsigned* done = p.done + col * p.CL + rank;
+  const double c2w = (p.omega && p.w_forbid != 0.0) ? p.w_forbid / ((double)p.N * p.n_states) : 0.0;
+  unsigned t = 0;
+  bool alive = true;
+  if (role == 0) {
+    costate_init(p, c.psi, c.chi, col0, r0, tm.nrows, c2w);
+    team_sync<CLUSTER>();
+    for (int n = p.N - 1; n >= 0 && alive; --n) {
+      const int m = p.ms_m[n], s = p.ms_s[n];
+      if (s <= 0 || m <= 0) continue;
+      load_controls(p, n, s_u);
+      __syncthreads();
+      assemble<T>(p, c.vals, tm.e0, tm.nnz_loc, p.dt / s, s_u);
+      __syncthreads();
+      for (int l = s - 1; l >= 0; --l) {
+        C2* rs = ring_col + (int64_t)(t % (unsigned)p.ring_depth) * slot_c2;
+        if (t >= (unsigned)p.ring_depth) {
+          int ok = 1;
+          if (threadIdx.x == 0) ok = wait_geq(done, t + 1 - (unsigned)p.ring_depth, p.spin_limit);
+          if (!team_all<CLUSTER>(ok, s_flags, t, p.CL)) {
+            if (threadIdx.x == 0) set_error(p.err, kErrTimeout);
+            alive = false;
+            break;
+          }
+        }
+        phase_a<T, CLUSTER>(tm, m, [&](int pp, int i, C2 w) { rs[(int64_t)(1 + pp) * dim + r0 + i] = w; });
+        for (int i = threadIdx.x; i < tm.nrows; i += blockDim.x) rs[r0 + i] = from_d2<T>(c.psi[i]);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          __threadfence();
+          st_release(ready, t + 1);
+        }
+        ++t;
+      }
+      if (!alive) break;
+      __syncthreads();
+      step_end(p, c.psi, c.chi, n, col, r0, tm.nrows, c2w);
+      __syncthreads();
+    }
+  } else {
+    const int partB = col * p.CL + rank;
+    team_sync<CLUSTER>();
+    for (int n = p.N - 1; n >= 0 && alive; --n) {
+      const int m = p.ms_m[n], s = p.ms_s[n];
+      if (s <= 0 || m <= 0) continue;
+      load_controls(p, n, s_u);
+      __syncthreads();
+      assemble<T>(p, c.vals, tm.e0, tm.nnz_loc, p.dt / s, s_u);
+      zero_w(p, c.W, c.Wb, tm.nnz_loc, sizeof(C2) == 8);
+      __syncthreads();
+      for (int l = s - 1; l >= 0; --l) {
+        const C2* rs = ring_col + (int64_t)(t % (unsigned)p.ring_depth) * slot_c2;
+        int ok = 1;
+        if (threadIdx.x == 0) ok = wait_geq(ready, t + 1, p.spin_limit);
+        if (!team_all<CLUSTER>(ok, s_flags, t, p.CL)) {
+          if (threadIdx.x == 0) set_error(p.err, kErrTimeout);
+          alive = false;
+          break;
+        }
+        for (int i = threadIdx.x; i < tm.nrows; i += blockDim.x) tm.X(4)[i] = __ldcg(rs + r0 + i);
+        phase_b<T, CLUSTER>(tm, m, [&](int pp, int i) -> C2 { return __ldcg(rs + (int64_t)(1 + pp) * dim + r0 + i); });
+        __syncthreads();
+        if (threadIdx.x == 0) st_release(done, t + 1);
+        ++t;
+      }
+      if (!alive) break;
+      __syncthreads();
+      grad_partials(p, c.W, rank, partB, n, s, tm.e0, red);
+      __syncthreads();
+    }
+  }
+  team_sync<CLUSTER>();
+}
+
 // ------------------------------------------------------------------ finalize (one block)
 
 __global__ void __launch_bounds__(256) k_finalize(FinalizeParams p) {
@@ -368,172 +916,6 @@ __global__ void __launch_bounds__(256) k_finalize(FinalizeParams p) {
       p.parts_out[3] = sqrt(gx * gx + gy * gy);
     }
   }
-}
-
-// ------------------------------------------------------------------ backward sweep
-
-// For every step n = N..1 and substep l = s-1..0 (B = -i dt H_n / s, P = e^B_m):
-//   phase A  psi^(l) = P(-B) psi^(l+1) (adjoint re-propagation, Fig. 1(b)) and the Horner chain
-//            w_{m-1} = chi/m!,  w_p = chi/(p+1)! + (-B) w_{p+1},  chi^(l) = w_{-1} = P(-B) chi^(l+1)
-//   phase B  x_0 = psi^(l), x_{p+1} = B x_p, and W_ij += conj(w_p[i]) x_p[j] on control entries
-// so that  sum_l <chi^(l+1)| dP/du_k |psi^(l)> = sum_ij (C_k)_ij W_ij with C_k = -i dt h_k / s,
-// which is the derivative of the approximant (e^B_m)^s at frozen (m, s) (Eq. (auxiliary equation)):
-// dP = sum_q 1/q! sum_{r+p=q-1} B^r C B^p  regrouped as  sum_p <w_p| C |x_p>.
-// chi is the combined costate of C1 and C2 (Eqs. (stgradient), (gategradient), (C2stgrad)):
-//   chi_N = -(w_fid g / n^2) phi_T + (w_forbid/(N n)) Omega psi_N,
-//   chi_{n-1} = U_n^+ chi_n + (w_forbid/(N n)) Omega psi_{n-1}   (n-1 >= 1).
-template <bool CLUSTER>
-__global__ void __launch_bounds__(1024, 1) k_backward(SweepParams p) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double red[32];
-  __shared__ double s_u[kMaxControls];
-  __shared__ XTab<CLUSTER> tab[6];
-  const int part = blockIdx.x;
-  const int team = part / p.CL, rank = part % p.CL;
-  const int r0 = min(rank * p.R, p.dim), r1 = min(r0 + p.R, p.dim), nrows = r1 - r0;
-  const int64_t e0 = p.rowptr[r0];
-  const int nnz_loc = (int)(p.rowptr[r1] - e0);
-  const Carve c = carve(smem, p, true, part);
-  const int R = p.R;
-  // exchange buffers: A (psi chain) 0,1; W (Horner chain) 2,3; X (x chain) 4,5
-  double2* X[6] = {c.xb, c.xb + R, c.xb + 2 * R, c.xb + 3 * R, c.xb + 4 * R, c.xb + 5 * R};
-  if constexpr (CLUSTER) {
-    cg::cluster_group cl = cg::this_cluster();
-    if (threadIdx.x < p.CL)
-      for (int b = 0; b < 6; ++b) tab[b].ptr[threadIdx.x] = cl.map_shared_rank(X[b], threadIdx.x);
-  }
-  sweep_setup<CLUSTER>(p, c, r0, nrows, e0, nnz_loc);
-  const int64_t col0 = (int64_t)team * p.dim + r0;
-  const double nS = (double)p.n_states;
-  const double2 g = *p.g_final;
-  const double2 coefA = make_double2(-p.w_fid * g.x / (nS * nS), -p.w_fid * g.y / (nS * nS));
-  const double c2w = (p.omega && p.w_forbid != 0.0) ? p.w_forbid / ((double)p.N * nS) : 0.0;
-  for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
-    const double2 v = p.psiN[col0 + i];
-    c.psi[i] = v;
-    double2 ch = cmul(coefA, p.target[col0 + i]);
-    if (c2w != 0.0) {
-      const double w = c2w * p.omega[r0 + i];
-      ch.x = fma(w, v.x, ch.x);
-      ch.y = fma(w, v.y, ch.y);
-    }
-    c.chi[i] = ch;
-  }
-  team_sync<CLUSTER>();
-  for (int n = p.N - 1; n >= 0; --n) {
-    const int m = p.ms_m[n], s = p.ms_s[n];
-    if (s <= 0 || m <= 0) continue;
-    load_controls(p, n, s_u);
-    __syncthreads();
-    assemble(p, c, e0, nnz_loc, n, p.dt / s, s_u);
-    for (int e = threadIdx.x; e < nnz_loc; e += blockDim.x) c.W[e] = make_double2(0.0, 0.0);
-    __syncthreads();
-    for (int l = s - 1; l >= 0; --l) {
-      // ---------------- phase A: psi and Horner chains with -B
-      const double fm = c_inv_fact[m];
-      for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
-        X[0][i] = c.psi[i];
-        c.inc[i] = make_double2(0.0, 0.0);
-        const double2 w0 = cscale(c.chi[i], fm);
-        X[2][i] = w0;
-        *wslot_ptr(c, p.m_smem, R, m - 1, i) = w0;
-      }
-      team_sync<CLUSTER>();
-      for (int q = 1; q <= m; ++q) {
-        const int src = (q - 1) & 1, dst = q & 1;
-        const double iq = c_inv_int[q];
-        const double fq = c_inv_fact[m - q];
-        for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
-          double2 ya = make_double2(0.0, 0.0), yw = make_double2(0.0, 0.0);
-          const int ea = c.lrow[i], eb = c.lrow[i + 1];
-          for (int e = ea; e < eb; ++e) {
-            const uint32_t enc = c.lcol[e];
-            const double2 v = c.vals[e];
-            cmac(ya, v, xload<CLUSTER>(X[src], tab[src], enc));
-            cmac(yw, v, xload<CLUSTER>(X[2 + src], tab[2 + src], enc));
-          }
-          ya = cscale(ya, -iq);                       // (-B) a_{q-1} / q
-          X[dst][i] = ya;
-          double2 a = c.inc[i];
-          a.x += ya.x;
-          a.y += ya.y;
-          c.inc[i] = a;
-          const double2 ch = c.chi[i];
-          const double2 w = make_double2(fma(ch.x, fq, -yw.x), fma(ch.y, fq, -yw.y));   // chi/(p+1)! + (-B) w_{p+1}
-          X[2 + dst][i] = w;
-          if (q < m) *wslot_ptr(c, p.m_smem, R, m - 1 - q, i) = w;
-          else c.chi[i] = w;                           // chi^(l) = w_{-1}
-        }
-        team_sync<CLUSTER>();
-      }
-      // ---------------- phase B: x chain with B, accumulate W on control entries
-      for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
-        double2 v = c.psi[i];
-        const double2 a = c.inc[i];
-        v.x += a.x;
-        v.y += a.y;
-        c.psi[i] = v;                                  // psi^(l)
-        X[4][i] = v;
-      }
-      team_sync<CLUSTER>();
-      for (int pp = 0; pp < m; ++pp) {
-        const int src = pp & 1, dst = src ^ 1;
-        const bool more = pp < m - 1;
-        for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
-          const double2 wp = *wslot_ptr(c, p.m_smem, R, pp, i);
-          double2 y = make_double2(0.0, 0.0);
-          const int ea = c.lrow[i], eb = c.lrow[i + 1];
-          for (int e = ea; e < eb; ++e) {
-            const uint32_t enc = c.lcol[e];
-            const double2 x = xload<CLUSTER>(X[4 + src], tab[4 + src], enc);
-            if (more) cmac(y, c.vals[e], x);
-            if (enc & kCtrlBit) {
-              double2 acc = c.W[e];
-              cmac_conj(acc, wp, x);
-              c.W[e] = acc;
-            }
-          }
-          if (more) X[4 + dst][i] = y;
-        }
-        if (more) team_sync<CLUSTER>();
-      }
-    }
-    // ---------------- step end: psi ~ psi_n (0-based state index n), costate source, gradient
-    __syncthreads();
-    if (n > 0) {
-      if (p.ckpt_every > 0 && n % p.ckpt_every == 0 && n / p.ckpt_every - 1 < p.n_ckpt) {
-        const double2* srcp = p.ckpt + ((int64_t)(n / p.ckpt_every - 1) * p.n_states + team) * p.dim + r0;
-        for (int i = threadIdx.x; i < nrows; i += blockDim.x) c.psi[i] = srcp[i];
-      }
-      if (c2w != 0.0) {
-        for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
-          const double w = c2w * p.omega[r0 + i];
-          const double2 v = c.psi[i];
-          double2 ch = c.chi[i];
-          ch.x = fma(w, v.x, ch.x);
-          ch.y = fma(w, v.y, ch.y);
-          c.chi[i] = ch;
-        }
-      }
-    }
-    // dC/du_kn part = 2 Re sum_ij (C_k)_ij W_ij, C_k = -i (dt/s) h_k: Re(-i h W) = h.x W.y + h.y W.x
-    const double gscale = 2.0 * p.dt / s;
-    for (int k = 0; k < p.K; ++k) {
-      const int lo = p.cslice[(k * p.CL + rank) * 2], hi = p.cslice[(k * p.CL + rank) * 2 + 1];
-      double acc = 0.0;
-      for (int cc = lo + threadIdx.x; cc < hi; cc += blockDim.x) {
-        const int e = (int)(p.cidx[cc] - e0);
-        const double2 w = c.W[e];
-        const double2 h = p.cval[cc];
-        acc = fma(h.x, w.y, acc);
-        acc = fma(h.y, w.x, acc);
-      }
-      const double tot = block_sum(acc, red);
-      if (threadIdx.x == 0) p.part_grad[((int64_t)part * p.N + n) * p.K + k] = gscale * tot;
-    }
-    __syncthreads();
-  }
-  team_sync<CLUSTER>();
 }
 
 // ------------------------------------------------------------------ gradient reduce
@@ -597,15 +979,104 @@ static cudaError_t launch_sweep(KernelT kern, const SweepParams& p, int smem_byt
 }
 
 cudaError_t launch_forward(const SweepParams& p, int precision, int smem_bytes, int threads, cudaStream_t st) {
-  (void)precision;
-  if (p.CL > 1) return launch_sweep(k_forward<true>, p, smem_bytes, threads, st);
-  return launch_sweep(k_forward<false>, p, smem_bytes, threads, st);
+  if (precision == 1) {
+    if (p.CL > 1) return launch_sweep(k_forward<float, true>, p, smem_bytes, threads, st);
+    return launch_sweep(k_forward<float, false>, p, smem_bytes, threads, st);
+  }
+  if (p.CL > 1) return launch_sweep(k_forward<double, true>, p, smem_bytes, threads, st);
+  return launch_sweep(k_forward<double, false>, p, smem_bytes, threads, st);
 }
 
 cudaError_t launch_backward(const SweepParams& p, int precision, int smem_bytes, int threads, cudaStream_t st) {
-  (void)precision;
-  if (p.CL > 1) return launch_sweep(k_backward<true>, p, smem_bytes, threads, st);
-  return launch_sweep(k_backward<false>, p, smem_bytes, threads, st);
+  if (precision == 1) {
+    if (p.CL > 1) return launch_sweep(k_backward<float, true>, p, smem_bytes, threads, st);
+    return launch_sweep(k_backward<float, false>, p, smem_bytes, threads, st);
+  }
+  if (p.CL > 1) return launch_sweep(k_backward<double, true>, p, smem_bytes, threads, st);
+  return launch_sweep(k_backward<double, false>, p, smem_bytes, threads, st);
+}
+
+template <typename KernelT>
+static cudaError_t launch_split(KernelT kern, const SweepParams& p, int smem_bytes, int threads, cudaStream_t st) {
+  cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  if (r != cudaSuccess) return r;
+  if (p.CL > 8) {
+    r = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (r != cudaSuccess) return r;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * p.n_states * p.CL);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem_bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  int na = 0;
+  attr[na].id = cudaLaunchAttributeCooperative;   // both teams of a column must be co-resident
+  attr[na].val.cooperative = 1;
+  ++na;
+  if (p.CL > 1) {
+    attr[na].id = cudaLaunchAttributeClusterDimension;
+    attr[na].val.clusterDim.x = p.CL;
+    attr[na].val.clusterDim.y = 1;
+    attr[na].val.clusterDim.z = 1;
+    ++na;
+  }
+  cfg.attrs = attr;
+  cfg.numAttrs = na;
+  r = cudaLaunchKernelEx(&cfg, kern, p);
+  if (r != cudaSuccess) return r;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backward_split(const SweepParams& p, int precision, int smem_bytes, int threads, cudaStream_t st) {
+  cudaError_t e = ensure_constants();
+  if (e != cudaSuccess) return e;
+  if (precision == 1) {
+    if (p.CL > 1) return launch_split(k_backward_split<float, true>, p, smem_bytes, threads, st);
+    return launch_split(k_backward_split<float, false>, p, smem_bytes, threads, st);
+  }
+  if (p.CL > 1) return launch_split(k_backward_split<double, true>, p, smem_bytes, threads, st);
+  return launch_split(k_backward_split<double, false>, p, smem_bytes, threads, st);
+}
+
+template <typename KernelT>
+static int capacity_of(KernelT kern, int CL, int smem_bytes, int threads) {
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) != cudaSuccess) return 0;
+  if (CL > 1) {
+    if (CL > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) return 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem_bytes;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) return 0;
+    return n;
+  }
+  int per_sm = 0, dev = 0, nsm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem_bytes) != cudaSuccess) return 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return per_sm * nsm;
+}
+
+int split_capacity(int precision, int CL, int smem_bytes, int threads) {
+  cudaGetLastError();
+  int r;
+  if (precision == 1)
+    r = CL > 1 ? capacity_of(k_backward_split<float, true>, CL, smem_bytes, threads)
+               : capacity_of(k_backward_split<float, false>, CL, smem_bytes, threads);
+  else
+    r = CL > 1 ? capacity_of(k_backward_split<double, true>, CL, smem_bytes, threads)
+               : capacity_of(k_backward_split<double, false>, CL, smem_bytes, threads);
+  cudaGetLastError();
+  return r;
 }
 
 cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t st) {

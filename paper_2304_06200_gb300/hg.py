@@ -70,7 +70,8 @@ class GrapeProblem:
     """
 
     def __init__(self, problem, precision: str = "fp64", ckpt_every: int = 0, cluster: int = 0, device: int = 0,
-                 tau: float | None = None, m_max: int = 0, torch_allocator: bool = True, n_steps: int | None = None):
+                 tau: float | None = None, m_max: int = 0, torch_allocator: bool = True, n_steps: int | None = None,
+                 backward_mode: int = 0):
         L = lib()
         self._lib = L
         self.dim = int(problem.dim)
@@ -121,6 +122,7 @@ class GrapeProblem:
             d.alloc = _abi.ALLOC_FN()
             d.free = _abi.FREE_FN()
         d.alloc_ctx = None
+        d.backward_mode = int(backward_mode)
         handle = C.c_void_p()
         check(L.grape_problem_create(C.byref(d), C.byref(handle)), "grape_problem_create")
         self._h = handle

@@ -140,6 +140,24 @@ def test_team_sizes_agree(cluster):
     _check(p, u, cost, grad, ref=ref)
 
 
+@pytest.mark.parametrize("name,N,cluster,drive", [("c2_gate_d80", 60, 0, 10.0), ("c2_gate_d80", 30, 4, 20.0),
+                                                 ("c1_state_transfer_d30", 40, 16, 5.0),
+                                                 ("c2_gate_d80", 25, 12, 10.0), ("c1_state_transfer_d30", 20, 7, 3.0)])
+def test_split_and_fused_backward_agree_bitwise(name, N, cluster, drive):
+    """Two concurrent teams per column (phase A / phase B) give exactly the one-team result."""
+    p = build_config(name, n_steps=N)
+    u = p.u0 * drive
+    fused = _hg(p, cluster=cluster, backward_mode=1)
+    split = _hg(p, cluster=cluster, backward_mode=2)
+    assert fused.info()["backward_mode"] == 1 and split.info()["backward_mode"] == 2
+    c1, g1 = fused.cost_and_grad(u)
+    c2, g2 = split.cost_and_grad(u)
+    assert c1 == c2
+    assert np.array_equal(g1, g2)
+    c3, g3 = split.cost_and_grad(u)          # the ring flags restart at zero every launch
+    assert c3 == c2 and np.array_equal(g3, g2)
+
+
 def test_medium_two_transmon_cavity_parity():
     """Two transmons x cavity (the d = 4000 system's structure) at d = 4*4*40 = 640, clustered."""
     from workloads.transmon import _gate_problem, _subspace_two, two_transmon_cavity
@@ -202,3 +220,33 @@ def test_error_paths():
     fresh = _hg(p)
     st = fresh._lib.grape_grad(fresh._h, np.zeros((4, 5)).ctypes.data, 0, None)
     assert st == 7   # GRAPE_ESTATE
+
+
+# ---------------------------------------------------------------- FP32-bulk path (Taylor terms in complex64)
+
+FP32_RTOL = 1e-5
+
+
+@pytest.mark.parametrize("name,N", [("c1_state_transfer_d30", None), ("c2_gate_d80", None)])
+def test_fp32_bulk_parity_full_size(name, N):
+    """FP32 increments, FP64 states/overlaps/gradient sums: relative 1e-5 on cost and gradient."""
+    p = build_config(name, n_steps=N)
+    hg = _hg(p, precision="fp32_bulk")
+    cost, grad = hg.cost_and_grad(p.u0)
+    _check(p, p.u0, cost, grad, cost_rtol=FP32_RTOL, grad_rtol=FP32_RTOL)
+
+
+@pytest.mark.parametrize("dim,K,n,N,cluster", [(130, 4, 3, 40, 0), (257, 3, 2, 12, 16), (65, 2, 5, 9, 5)])
+def test_fp32_bulk_parity_random(dim, K, n, N, cluster):
+    p = random_problem(dim, K, n, N, seed=2000 + dim)
+    hg = _hg(p, precision="fp32_bulk", cluster=cluster)
+    cost, grad = hg.cost_and_grad(p.u0)
+    _check(p, p.u0, cost, grad, cost_rtol=FP32_RTOL, grad_rtol=FP32_RTOL)
+
+
+def test_fp32_bulk_split_and_fused_agree_bitwise():
+    p = build_config("c2_gate_d80", n_steps=40)
+    u = p.u0 * 10
+    a = _hg(p, precision="fp32_bulk", backward_mode=1).cost_and_grad(u)
+    b = _hg(p, precision="fp32_bulk", backward_mode=2).cost_and_grad(u)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1])
