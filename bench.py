@@ -47,6 +47,10 @@ def parse_args(argv=None):
     ap.add_argument("--fullad-steps", default="2,4")
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--n-steps", type=int, default=None, help="override the workload's N (profiling a small case)")
+    ap.add_argument("--batch", action="store_true", help="also measure the 64-instance batch (one graph launch)")
+    ap.add_argument("--autotune", action="store_true", help="autotune every batch member (slower set-up)")
+    ap.add_argument("--m-sweep", action="store_true", help="also sweep the checkpoint spacing M over {50, 200, 1000}")
+    ap.add_argument("--c4", action="store_true", help="also run the d = 16000 workload in FP32 bulk and FP64")
     return ap.parse_args(argv)
 
 
@@ -395,6 +399,14 @@ def run_ours(args):
                      "c3_fp32_bulk": secondary_run(args.workload, "fp32_bulk", local, ref=(float(cost.item()), grad.cpu().numpy()),
                                                    n_steps=args.n_steps)}
 
+    extra = {}
+    if args.m_sweep:
+        extra["checkpoint_sweep"] = checkpoint_sweep(args.workload, local, args.n_steps)
+    if args.c4:
+        extra["c4"] = c4_compare(local)
+    if args.batch:
+        extra["c5_batch"] = batch_compare(local, args.autotune)
+
     out = {
         "metric": METRIC, "value": round(value, 6), "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(tmax / args.steps * 1e3, 3), "higher_is_better": True,
@@ -414,6 +426,7 @@ def run_ours(args):
     }
     if secondary:
         out["secondary"] = secondary
+    out.update(extra)
     print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -466,6 +479,146 @@ def secondary_run(name: str, precision: str, local: int, ref=None, n_steps=None,
         out["grad_rel_diff_vs_fp64"] = float(np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref))
     hg.close()
     return out
+
+
+def _timed_eval(hg, u, cost, grad, reps=1):
+    import torch
+    hg.cost_and_grad_device(u, cost, grad)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        hg.cost_and_grad_device(u, cost, grad)
+    e1.record()
+    torch.cuda.synchronize()
+    hg.sync_status()
+    return e0.elapsed_time(e1) / reps
+
+
+def checkpoint_sweep(name, local, n_steps=None):
+    """Checkpoint spacing M in {50, 200, 1000}: evals/s and peak HBM of the HG evaluation."""
+    import torch
+    from paper_2304_06200_gb300 import GrapeProblem
+    from workloads import build_config
+
+    p = build_config(name, n_steps=n_steps)
+    dev = torch.device("cuda", local)
+    out = []
+    for M in (50, 200, 1000):
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats(dev)
+        m0 = torch.cuda.memory_allocated(dev)
+        hg = GrapeProblem(p, device=local, ckpt_every=M)
+        u = torch.tensor(p.u0, dtype=torch.float64, device=dev)
+        cost = torch.zeros((), dtype=torch.float64, device=dev)
+        grad = torch.zeros_like(u)
+        ms = _timed_eval(hg, u, cost, grad)
+        peak = torch.cuda.max_memory_allocated(dev) - m0
+        out.append({"M": M, "evals_per_s": round(1e3 / ms, 4), "peak_bytes": int(peak), "cost": float(cost.item()),
+                    "grad_norm": float(torch.linalg.norm(grad).item())})
+        hg.close()
+        del u, cost, grad
+    return out
+
+
+def c4_compare(local):
+    """d = 16000, 16 states, N = 4000: FP32 bulk against the plain FP64 kernels (same problem)."""
+    import numpy as np
+    import torch
+    from paper_2304_06200_gb300 import GrapeProblem
+    from workloads import build_config
+
+    p = build_config("c4_gate_d16000")
+    dev = torch.device("cuda", local)
+    res = {}
+    ref = None
+    for prec in ("fp64", "fp32_bulk"):
+        hg = GrapeProblem(p, device=local, precision=prec)
+        u = torch.tensor(p.u0, dtype=torch.float64, device=dev)
+        cost = torch.zeros((), dtype=torch.float64, device=dev)
+        grad = torch.zeros_like(u)
+        ms = _timed_eval(hg, u, cost, grad)
+        inf = hg.info()
+        r = {"evals_per_s": round(1e3 / ms, 5), "ms_per_eval": round(ms, 1), "cluster_fwd": inf["cluster_forward"],
+             "cluster_bwd": inf["cluster"], "backward_teams_per_column": inf["backward_mode"],
+             "taylor_terms_per_sweep": inf["total_terms"], "device_bytes": inf["device_bytes"]}
+        g = grad.cpu().numpy()
+        if ref is None:
+            ref = (float(cost.item()), g)
+        else:
+            r["cost_rel_diff_vs_fp64"] = abs(float(cost.item()) - ref[0]) / abs(ref[0])
+            r["grad_rel_diff_vs_fp64"] = float(np.linalg.norm(g - ref[1]) / np.linalg.norm(ref[1]))
+        res[prec] = r
+        hg.close()
+    res["workload"] = workload_description(p)
+    res["speedup_fp32_bulk_over_fp64"] = round(res["fp64"]["ms_per_eval"] / res["fp32_bulk"]["ms_per_eval"], 2)
+    return res
+
+
+def batch_compare(local, tune=False):
+    """64 uneven instances: one graph launch (FP32 bulk) against the same 64 one at a time (plain FP64)."""
+    import numpy as np
+    import torch
+    from paper_2304_06200_gb300 import GrapeBatch, GrapeProblem, autotune
+    from workloads import batch_instances
+
+    insts = batch_instances()
+    dev = torch.device("cuda", local)
+    t0 = time.perf_counter()
+    members = []
+    tune_report = []
+    for p in insts:
+        if tune:
+            hg, rep = autotune(p, precision="fp32_bulk", device=local, probe_steps=32, m_caps=(0, 30),
+                               clusters=[0, 1, 4, 8, 16])
+            tune_report.append({"name": p.name, "cluster": rep["cluster"], "m_max": rep["m_max"]})
+        else:
+            hg = GrapeProblem(p, device=local, precision="fp32_bulk", backward_mode=1)
+        members.append(hg)
+    batch = GrapeBatch(members, n_streams=16)
+    setup_s = time.perf_counter() - t0
+    us = [torch.tensor(p.u0, dtype=torch.float64, device=dev) for p in insts]
+    grads = [torch.zeros_like(u) for u in us]
+    costs = torch.zeros(len(insts), dtype=torch.float64, device=dev)
+    batch.cost_and_grad_device(us, costs, grads)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record()
+    for _ in range(reps):
+        batch.cost_and_grad_device(us, costs, grads)
+    e1.record()
+    torch.cuda.synchronize()
+    for m in members:
+        m.sync_status()
+    batch_ms = e0.elapsed_time(e1) / reps
+    cb = costs.cpu().numpy()
+    gb = [g.cpu().numpy() for g in grads]
+    batch.close()
+    for m in members:
+        m.close()
+    # the same 64, one at a time, plain FP64 kernels
+    seq_ms = 0.0
+    cerr, gerr = 0.0, 0.0
+    for i, p in enumerate(insts):
+        hg = GrapeProblem(p, device=local, precision="fp64")
+        cost = torch.zeros((), dtype=torch.float64, device=dev)
+        ms = _timed_eval(hg, us[i], cost, grads[i])
+        seq_ms += ms
+        c = float(cost.item())
+        g = grads[i].cpu().numpy()
+        cerr = max(cerr, abs(cb[i] - c) / abs(c))
+        gerr = max(gerr, float(np.linalg.norm(gb[i] - g) / np.linalg.norm(g)))
+        hg.close()
+    dims = sorted({p.dim for p in insts})
+    return {"instances": len(insts), "dims": dims, "counts": {d: sum(p.dim == d for p in insts) for d in dims},
+            "batch_ms_per_eval_of_all": round(batch_ms, 2), "batch_evals_per_s": round(len(insts) * 1e3 / batch_ms, 3),
+            "sequential_fp64_ms": round(seq_ms, 1), "sequential_fp64_evals_per_s": round(len(insts) * 1e3 / seq_ms, 3),
+            "speedup": round(seq_ms / batch_ms, 2), "max_cost_rel_diff_vs_fp64": cerr,
+            "max_grad_rel_diff_vs_fp64": gerr, "setup_s": round(setup_s, 1), "autotuned": tune,
+            "tune": tune_report[:8]}
 
 
 # ------------------------------------------------------------------ reference arm (CPU oracle)

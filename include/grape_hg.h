@@ -112,6 +112,10 @@ typedef struct {
   int32_t backward_mode;       /* 0 = automatic, 1 = one team per column runs both backward
                                   phases, 2 = two concurrent teams per column (phase A / phase B),
                                   needs all 2 * n_states teams co-resident                    */
+  double bulk_norm_cap;        /* > 0: the (m, s) rule only considers s >= ||A||_1 / cap, i.e.
+                                  ||B||_1 <= cap, which bounds the largest Taylor term (reduces
+                                  FP32-bulk rounding); 0 = default (2.0 for GRAPE_FP32_BULK, no
+                                  cap for GRAPE_FP64, i.e. the paper's rule unchanged)            */
 } grape_desc;
 
 /* Information about a problem (valid after create; schedule fields after an evaluation). */
@@ -179,6 +183,23 @@ grape_status grape_select_ms(double x, double tau, int32_t sigma, int32_t precis
 
 /* E_A(m, s) itself (App. C Eq. (overallupperbound)); +inf when s R_m(x/s) >= 1. */
 double grape_error_bound(double x, int32_t m, int32_t s, int32_t sigma, int32_t precision);
+
+/* ---- Batches: many independent problems evaluated by one CUDA-graph launch.
+ * grape_batch_create records, once, every member's evaluation (forward sweep, cost, backward sweep,
+ * gradient) into one CUDA graph whose branches run on n_streams concurrent lanes (0 = 8), members
+ * assigned longest first; a launch of the graph then evaluates all members with their kernels
+ * running side by side, so that many small column teams fill the GPU.  Members must be distinct
+ * problems on one device created with backward_mode = 1 (the two-team sweep waits on its partner
+ * team and must not share the GPU with unrelated kernels).  The batch does not own the problems:
+ * destroy the batch before them.  This realises the paper's per-instance HG evaluation (Sec. III)
+ * for many instances at once; the paper itself treats one instance at a time. */
+typedef struct grape_batch grape_batch;
+grape_status grape_batch_create(grape_problem* const* probs, int32_t count, int32_t n_streams, grape_batch** out);
+void grape_batch_destroy(grape_batch* batch);
+/* u[i]: member i's controls (K_i x N_i), costs[count], grads[i] (K_i x N_i, the array may be NULL or
+ * hold NULLs).  on_device selects host or device pointers as in grape_cost_and_grad. */
+grape_status grape_batch_cost_and_grad(grape_batch* batch, const double* const* u, double* costs,
+                                       double* const* grads, int32_t on_device, void* stream);
 
 /* Allocation-free propagation of one step (the paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory).  Such callers include code that runs

@@ -6,5 +6,5 @@ binding.  There is no CPU fallback: if the library cannot be built or loaded,
 every entry point raises.
 """
 
-from .hg import GrapeProblem, error_bound, grape_hg, select_ms  # noqa: F401
+from .hg import GrapeBatch, GrapeProblem, autotune, error_bound, grape_hg, select_ms  # noqa: F401
 from ._abi import GrapeError, EXPORTED  # noqa: F401

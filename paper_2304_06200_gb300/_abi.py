@@ -20,6 +20,7 @@ EXPORTED = [
     "grape_problem_create", "grape_problem_destroy", "grape_cost_and_grad", "grape_cost", "grape_grad",
     "grape_sync_status", "grape_problem_info", "grape_step_schedule", "grape_select_ms", "grape_error_bound",
     "grape_status_string", "grape_last_error", "grape_abi_version", "grape_taylor_step_noalloc",
+    "grape_batch_create", "grape_batch_destroy", "grape_batch_cost_and_grad",
 ]
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -39,7 +40,8 @@ class GrapeDesc(C.Structure):
                 ("w_fid", C.c_double), ("w_forbid", C.c_double), ("w_amp", C.c_double),
                 ("tau", C.c_double), ("m_max", C.c_int32), ("ckpt_every", C.c_int32), ("precision", C.c_int32),
                 ("cluster", C.c_int32), ("device", C.c_int32),
-                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p), ("backward_mode", C.c_int32)]
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p), ("backward_mode", C.c_int32),
+                ("bulk_norm_cap", C.c_double)]
 
 
 class GrapeInfo(C.Structure):
@@ -86,6 +88,12 @@ def lib(path: str | None = None):
     L.grape_error_bound.restype = C.c_double
     L.grape_taylor_step_noalloc.argtypes = [C.c_int64, C.c_int32, P, P, P, C.c_double, C.c_int32, C.c_int32, P, P, P]
     L.grape_taylor_step_noalloc.restype = C.c_int
+    L.grape_batch_create.argtypes = [C.POINTER(P), C.c_int32, C.c_int32, C.POINTER(P)]
+    L.grape_batch_create.restype = C.c_int
+    L.grape_batch_destroy.argtypes = [P]
+    L.grape_batch_destroy.restype = None
+    L.grape_batch_cost_and_grad.argtypes = [P, C.POINTER(P), P, C.POINTER(P), C.c_int32, P]
+    L.grape_batch_cost_and_grad.restype = C.c_int
     L.grape_status_string.argtypes = [C.c_int]
     L.grape_status_string.restype = C.c_char_p
     L.grape_last_error.argtypes = []

@@ -86,7 +86,7 @@ static double breakpoint(int m, int s, int sigma, double u, double tau) {
   return lo;
 }
 
-ScheduleTable build_table(double tau, int sigma, double u, int m_max, int s_limit, double x_enough) {
+ScheduleTable build_table(double tau, int sigma, double u, int m_max, int s_limit, double x_enough, int s_min_rows) {
   ScheduleTable t;
   t.m_cap = m_max;
   double best = -1.0;
@@ -102,6 +102,7 @@ ScheduleTable build_table(double tau, int sigma, double u, int m_max, int s_limi
     t.smax.push_back(smax);
     t.s_cap = s;
     if (smax > best) { best = smax; best_s = s; since_best = 0; } else { ++since_best; }
+    if (s < s_min_rows) continue;
     if (best >= x_enough) break;
     // Past the peak, rounding dominates and larger s only shrinks the feasible range.
     if (best_s > 0 && since_best >= 16 && s >= 2 * best_s) break;

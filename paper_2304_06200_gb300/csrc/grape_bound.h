@@ -20,7 +20,7 @@ struct ScheduleTable {
   std::vector<double> smax;
 };
 
-ScheduleTable build_table(double tau, int sigma, double u, int m_max, int s_limit, double x_enough);
+ScheduleTable build_table(double tau, int sigma, double u, int m_max, int s_limit, double x_enough, int s_min_rows = 1);
 bool table_lookup(const ScheduleTable& t, double x, int* m_out, int* s_out);
 
 }  // namespace grape

@@ -143,6 +143,7 @@ struct grape_problem {
   int64_t dim = 0;
   int K = 0, N = 0, n = 0;
   double dt = 0, w_fid = 0, w_forbid = 0, w_amp = 0, tau = 0;
+  double b_cap = 0;   // cap on ||B||_1 = ||A||_1 / s in the schedule (0 = the paper's rule unchanged)
   int precision = 0, ckpt_every = 0, n_ckpt = 0, m_cap = 0, s_cap = 0, sigma = 0;
   int64_t nnz = 0, n_ctr = 0;
   bool has_omega = false;
@@ -320,7 +321,7 @@ grape_status build(grape_problem* P, const grape_desc* d) {
   // Both precisions share the FP64 bound's schedule (the FP32-bulk path keeps its states in FP64;
   // the bound with u = 2^-24 certifies no useful tolerance).
   const double uround = grape::unit_roundoff(GRAPE_FP64);
-  P->table = grape::build_table(P->tau, P->sigma, uround, P->m_cap, 4096, 2000.0);
+  P->table = grape::build_table(P->tau, P->sigma, uround, P->m_cap, 4096, 2000.0, P->b_cap > 0.0 ? 128 : 1);
   if (P->table.x_max < 0.0) return fail(GRAPE_ETOL, "no (m, s) pair satisfies E_A <= tau even for ||A||_1 = 0");
   P->m_cap = P->table.m_cap;
   P->s_cap = P->table.s_cap;
@@ -642,6 +643,7 @@ grape_status grape_problem_create(const grape_desc* d, grape_problem** out) {
     return fail(GRAPE_EINVAL, "precision must be GRAPE_FP64 or GRAPE_FP32_BULK");
   if (d->cluster < 0 || d->cluster > grape::kMaxCluster) return fail(GRAPE_EINVAL, "cluster must be 0 (automatic) or 1..16");
   if (d->n_controls > 0 && !d->Hk) return fail(GRAPE_EINVAL, "Hk is NULL");
+  if (d->bulk_norm_cap < 0.0 || !std::isfinite(d->bulk_norm_cap)) return fail(GRAPE_EINVAL, "bulk_norm_cap must be >= 0");
   if (!d->psi0 || !d->target) return fail(GRAPE_EINVAL, "psi0 / target is NULL");
   if ((d->alloc == nullptr) != (d->free == nullptr)) return fail(GRAPE_EINVAL, "alloc and free must both be set or both NULL");
   const double ws[3] = {d->w_fid, d->w_forbid, d->w_amp};
@@ -669,6 +671,7 @@ grape_status grape_problem_create(const grape_desc* d, grape_problem** out) {
   P->tau = d->tau;
   P->precision = d->precision;
   P->m_cap = d->m_max == 0 ? grape::kMaxTaylor : d->m_max;
+  P->b_cap = d->bulk_norm_cap > 0.0 ? d->bulk_norm_cap : (d->precision == GRAPE_FP32_BULK ? 2.0 : 0.0);
   P->alloc_fn = d->alloc;
   P->free_fn = d->free;
   P->alloc_ctx = d->alloc_ctx;
@@ -723,6 +726,7 @@ grape_status run_forward(grape_problem* P, const double* u, bool u_on_device, cu
   sp.table_smax = P->d_table_smax;
   sp.m_cap = P->m_cap;
   sp.s_cap = P->s_cap;
+  sp.b_cap = P->b_cap;
   sp.ms_m = P->d_ms_m;
   sp.ms_s = P->d_ms_s;
   sp.norm1 = P->d_norm1;
@@ -840,6 +844,218 @@ grape_status grape_cost_and_grad(grape_problem* P, const double* u, double* cost
                             "cudaMemcpyAsync (grad)")))
     return s;
   if (!on_device) return read_error_word(P, st);
+  return GRAPE_OK;
+}
+
+// ------------------------------------------------------------------ batches
+
+}  // extern "C"
+
+struct grape_batch {
+  int device = 0;
+  int count = 0;
+  std::vector<grape_problem*> probs;
+  std::vector<int64_t> u_off, g_off;
+  int64_t u_total = 0, g_total = 0;
+  double* d_u = nullptr;
+  double* d_cost = nullptr;
+  double* d_grad = nullptr;
+  std::vector<void*> owned;                 // cudaMalloc'ed staging buffers
+  cudaStream_t origin = nullptr;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<int> order;                   // longest first
+  std::vector<int> lane;                    // stream of each problem
+  void release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (auto e : events) cudaEventDestroy(e);
+    for (auto s : streams) cudaStreamDestroy(s);
+    if (origin) cudaStreamDestroy(origin);
+    for (void* p : owned) cudaFree(p);
+    exec = nullptr;
+    graph = nullptr;
+    events.clear();
+    streams.clear();
+    origin = nullptr;
+    owned.clear();
+  }
+};
+
+namespace {
+
+grape_status batch_build(grape_batch* B, int n_streams) {
+  cudaError_t e;
+  const int count = B->count;
+  // staging buffers (fixed addresses referenced by the graph)
+  B->u_off.resize(count);
+  B->g_off.resize(count);
+  for (int i = 0; i < count; ++i) {
+    B->u_off[i] = B->u_total;
+    B->g_off[i] = B->g_total;
+    B->u_total += (int64_t)B->probs[i]->K * B->probs[i]->N;
+    B->g_total += (int64_t)B->probs[i]->K * B->probs[i]->N;
+  }
+  void* ptr = nullptr;
+  const size_t bytes[3] = {(size_t)std::max<int64_t>(B->u_total, 1) * 8, (size_t)count * 8,
+                           (size_t)std::max<int64_t>(B->g_total, 1) * 8};
+  double** dst[3] = {&B->d_u, &B->d_cost, &B->d_grad};
+  for (int k = 0; k < 3; ++k) {
+    if ((e = cudaMalloc(&ptr, bytes[k])) != cudaSuccess) return cuda_fail(e, "cudaMalloc (batch staging)");
+    B->owned.push_back(ptr);
+    *dst[k] = static_cast<double*>(ptr);
+    if ((e = cudaMemset(ptr, 0, bytes[k])) != cudaSuccess) return cuda_fail(e, "cudaMemset (batch staging)");
+  }
+  // longest-first order, greedy assignment to the least loaded stream
+  std::vector<double> work(count);
+  for (int i = 0; i < count; ++i) {
+    const grape_problem* P = B->probs[i];
+    work[i] = (double)P->N * (double)P->nnz * (double)P->n;
+  }
+  B->order.resize(count);
+  std::iota(B->order.begin(), B->order.end(), 0);
+  std::stable_sort(B->order.begin(), B->order.end(), [&](int a, int b) { return work[a] > work[b]; });
+  n_streams = std::max(1, std::min(n_streams, count));
+  std::vector<double> load(n_streams, 0.0);
+  B->lane.assign(count, 0);
+  for (int i : B->order) {
+    const int j = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    B->lane[i] = j;
+    load[j] += work[i];
+  }
+  if ((e = cudaStreamCreateWithFlags(&B->origin, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+  B->streams.resize(n_streams);
+  for (auto& s : B->streams)
+    if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+  B->events.resize(n_streams + 1);
+  for (auto& ev : B->events)
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+  // one warm evaluation per problem outside the capture (first launches set kernel attributes and
+  // constants, which are not stream work)
+  for (int i = 0; i < count; ++i) {
+    grape_problem* P = B->probs[i];
+    grape_status s = run_forward(P, B->d_u + B->u_off[i], true, B->origin);
+    if (s) return s;
+    if ((s = run_backward(P, B->origin))) return s;
+  }
+  if ((e = cudaStreamSynchronize(B->origin)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  for (int i = 0; i < count; ++i) cudaMemset(B->probs[i]->d_err, 0, sizeof(int));
+  // capture: fork onto the lanes, every problem's sequence on its lane, join back
+  if ((e = cudaStreamBeginCapture(B->origin, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+    return cuda_fail(e, "cudaStreamBeginCapture");
+  grape_status st = GRAPE_OK;
+  cudaEventRecord(B->events[n_streams], B->origin);
+  for (auto s : B->streams) cudaStreamWaitEvent(s, B->events[n_streams], 0);
+  for (int i : B->order) {
+    grape_problem* P = B->probs[i];
+    cudaStream_t s = B->streams[B->lane[i]];
+    if ((st = run_forward(P, B->d_u + B->u_off[i], true, s))) break;
+    if ((st = run_backward(P, s))) break;
+    if ((e = cudaMemcpyAsync(B->d_cost + i, P->d_cost, sizeof(double), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
+      st = cuda_fail(e, "cudaMemcpyAsync (batch cost)");
+      break;
+    }
+    if (P->K > 0 && (e = cudaMemcpyAsync(B->d_grad + B->g_off[i], P->d_grad, (size_t)P->K * P->N * sizeof(double),
+                                         cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
+      st = cuda_fail(e, "cudaMemcpyAsync (batch grad)");
+      break;
+    }
+  }
+  for (int j = 0; j < n_streams; ++j) {
+    cudaEventRecord(B->events[j], B->streams[j]);
+    cudaStreamWaitEvent(B->origin, B->events[j], 0);
+  }
+  e = cudaStreamEndCapture(B->origin, &B->graph);
+  if (st) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  if ((e = cudaGraphInstantiate(&B->exec, B->graph, 0)) != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  return GRAPE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+grape_status grape_batch_create(grape_problem* const* probs, int32_t count, int32_t n_streams, grape_batch** out) {
+  if (!out) return fail(GRAPE_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!probs || count < 1) return fail(GRAPE_EINVAL, "need at least one problem");
+  for (int i = 0; i < count; ++i) {
+    if (!probs[i]) return fail(GRAPE_EINVAL, "NULL problem in batch");
+    if (probs[i]->device != probs[0]->device) return fail(GRAPE_EINVAL, "batch problems must share one device");
+    if (probs[i]->bwd_mode != 1)
+      return fail(GRAPE_EINVAL, "batch members must use backward_mode 1 (two-team sweeps wait on each other and must "
+                                "not share the GPU with concurrent kernels)");
+    for (int j = 0; j < i; ++j)
+      if (probs[j] == probs[i]) return fail(GRAPE_EINVAL, "a problem appears twice in the batch");
+  }
+  DeviceGuard guard(probs[0]->device);
+  if (!guard.ok) return fail(GRAPE_ECUDA, "cudaSetDevice failed");
+  grape_batch* B = new (std::nothrow) grape_batch();
+  if (!B) return fail(GRAPE_ENOMEM, "host allocation failed");
+  B->device = probs[0]->device;
+  B->count = count;
+  B->probs.assign(probs, probs + count);
+  grape_status st;
+  try {
+    st = batch_build(B, n_streams <= 0 ? 8 : n_streams);
+  } catch (...) {
+    st = fail(GRAPE_ENOMEM, "host allocation failed");
+  }
+  if (st) {
+    B->release();
+    delete B;
+    return st;
+  }
+  *out = B;
+  return GRAPE_OK;
+}
+
+void grape_batch_destroy(grape_batch* B) {
+  if (!B) return;
+  DeviceGuard guard(B->device);
+  cudaDeviceSynchronize();
+  B->release();
+  delete B;
+}
+
+grape_status grape_batch_cost_and_grad(grape_batch* B, const double* const* u, double* costs, double* const* grads,
+                                       int32_t on_device, void* stream) {
+  if (!B || !u || !costs) return fail(GRAPE_EINVAL, "NULL argument");
+  DeviceGuard guard(B->device);
+  if (!guard.ok) return fail(GRAPE_ECUDA, "cudaSetDevice failed");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  cudaError_t e;
+  for (int i = 0; i < B->count; ++i) {
+    const grape_problem* P = B->probs[i];
+    const size_t n = (size_t)P->K * P->N;
+    if (n == 0) continue;
+    if (!u[i]) return fail(GRAPE_EINVAL, "NULL control array in batch");
+    if ((e = cudaMemcpyAsync(B->d_u + B->u_off[i], u[i], n * 8, kin, st)) != cudaSuccess)
+      return cuda_fail(e, "cudaMemcpyAsync (batch u)");
+  }
+  if ((e = cudaGraphLaunch(B->exec, st)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+  if ((e = cudaMemcpyAsync(costs, B->d_cost, (size_t)B->count * 8, kout, st)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemcpyAsync (batch costs)");
+  if (grads) {
+    for (int i = 0; i < B->count; ++i) {
+      const grape_problem* P = B->probs[i];
+      const size_t n = (size_t)P->K * P->N;
+      if (n == 0 || !grads[i]) continue;
+      if ((e = cudaMemcpyAsync(grads[i], B->d_grad + B->g_off[i], n * 8, kout, st)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync (batch grad)");
+    }
+  }
+  if (!on_device) {
+    for (int i = 0; i < B->count; ++i) {
+      grape_status s = read_error_word(B->probs[i], st);
+      if (s) return s;
+    }
+  }
   return GRAPE_OK;
 }
 

@@ -85,6 +85,7 @@ struct ScheduleParams {
   const double* table;                 // s_cap x m_cap breakpoints X[s-1][m-1] (largest feasible x), < 0 = never
   const double* table_smax;            // s_cap: max over m of X
   int m_cap, s_cap;
+  double b_cap;                        // > 0: only pairs with ||B||_1 = x / s <= b_cap (FP32-bulk schedule)
   int* ms_m;
   int* ms_s;
   double* norm1;

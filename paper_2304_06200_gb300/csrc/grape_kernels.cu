@@ -148,7 +148,9 @@ __global__ void __launch_bounds__(256) k_schedule(ScheduleParams p) {
       if (!(x <= 1e300)) {
         set_error(p.err, kErrNonFinite);
       } else {
-        for (int si = 1; si <= p.s_cap && s == 0; ++si) {
+        int s0 = 1;
+        if (p.b_cap > 0.0) s0 = min(max(1, (int)ceil(x / p.b_cap)), p.s_cap);
+        for (int si = s0; si <= p.s_cap && s == 0; ++si) {
           if (p.table_smax[si - 1] >= x) {
             for (int mi = 1; mi <= p.m_cap; ++mi)
               if (p.table[(int64_t)(si - 1) * p.m_cap + (mi - 1)] >= x) { m = mi; s = si; break; }

@@ -71,7 +71,7 @@ class GrapeProblem:
 
     def __init__(self, problem, precision: str = "fp64", ckpt_every: int = 0, cluster: int = 0, device: int = 0,
                  tau: float | None = None, m_max: int = 0, torch_allocator: bool = True, n_steps: int | None = None,
-                 backward_mode: int = 0):
+                 backward_mode: int = 0, bulk_norm_cap: float = 0.0):
         L = lib()
         self._lib = L
         self.dim = int(problem.dim)
@@ -123,6 +123,7 @@ class GrapeProblem:
             d.free = _abi.FREE_FN()
         d.alloc_ctx = None
         d.backward_mode = int(backward_mode)
+        d.bulk_norm_cap = float(bulk_norm_cap)
         handle = C.c_void_p()
         check(L.grape_problem_create(C.byref(d), C.byref(handle)), "grape_problem_create")
         self._h = handle
@@ -198,6 +199,105 @@ class GrapeProblem:
             self.close()
         except Exception:
             pass
+
+
+class GrapeBatch:
+    """Many independent problems evaluated by one CUDA-graph launch (``grape_batch_create``).
+
+    The members must be ``GrapeProblem`` objects created with ``backward_mode=1``; the batch keeps
+    references to them so they outlive it.
+    """
+
+    def __init__(self, problems, n_streams: int = 8):
+        L = lib()
+        self._lib = L
+        self.problems = list(problems)
+        handles = (C.c_void_p * len(self.problems))(*[p._h.value for p in self.problems])
+        h = C.c_void_p()
+        check(L.grape_batch_create(handles, len(self.problems), int(n_streams), C.byref(h)), "grape_batch_create")
+        self._h = h
+
+    def cost_and_grad(self, us):
+        """Host arrays: list of (K_i, N_i) controls -> (costs array, list of gradients)."""
+        us = [np.ascontiguousarray(u, dtype=np.float64) for u in us]
+        grads = [np.zeros_like(u) for u in us]
+        costs = np.zeros(len(us))
+        up = (C.c_void_p * len(us))(*[u.ctypes.data for u in us])
+        gp = (C.c_void_p * len(us))(*[g.ctypes.data for g in grads])
+        check(self._lib.grape_batch_cost_and_grad(self._h, up, costs.ctypes.data, gp, 0, None), "grape_batch_cost_and_grad")
+        return costs, grads
+
+    def cost_and_grad_device(self, us, costs, grads, stream=None):
+        """Device tensors: list of (K_i, N_i) float64 controls, costs (count,), list of gradient tensors."""
+        import torch
+
+        st = (stream or torch.cuda.current_stream(self.problems[0].device)).cuda_stream
+        up = (C.c_void_p * len(us))(*[u.data_ptr() for u in us])
+        gp = (C.c_void_p * len(us))(*[g.data_ptr() for g in grads])
+        check(self._lib.grape_batch_cost_and_grad(self._h, up, costs.data_ptr(), gp, 1, st), "grape_batch_cost_and_grad")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.grape_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(problem, precision: str = "fp64", device: int = 0, probe_steps: int = 48, backward_mode: int = 1,
+             clusters=None, m_caps=(0, 30, 20), repeats: int = 2):
+    """Pick the team size (CTAs per column) and Taylor-order cap with the fastest measured evaluation.
+
+    Each candidate is timed (CUDA events, after one warm-up) on the first ``probe_steps`` steps of the
+    problem; the winner is returned as ``(GrapeProblem for the full problem, report)``.  Candidates
+    whose descriptor is rejected (shared memory, co-residency) are skipped.  The Taylor-order cap
+    changes the (m, s) the paper's rule returns (a smaller cap forces more substeps), never the
+    tolerance.
+    """
+    import torch
+
+    if clusters is None:
+        clusters = [0] + [c for c in (1, 2, 4, 8, 12, 16) if c <= problem.dim]
+    N = problem.n_steps
+    ns = min(N, probe_steps)
+    u = torch.tensor(np.asarray(problem.u0)[:, :ns], dtype=torch.float64, device=f"cuda:{device}")
+    cost = torch.zeros((), dtype=torch.float64, device=u.device)
+    grad = torch.zeros_like(u)
+    report = []
+    best = None
+    for cl in clusters:
+        for mc in m_caps:
+            try:
+                hg = GrapeProblem(problem, precision=precision, cluster=cl, device=device, m_max=mc, n_steps=ns,
+                                  backward_mode=backward_mode)
+            except Exception as exc:  # rejected configuration
+                report.append({"cluster": cl, "m_max": mc, "skipped": str(exc)[:80]})
+                continue
+            hg.cost_and_grad_device(u, cost, grad)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(repeats):
+                hg.cost_and_grad_device(u, cost, grad)
+            e1.record()
+            torch.cuda.synchronize()
+            hg.sync_status()
+            ms = e0.elapsed_time(e1) / repeats
+            inf = hg.info()
+            report.append({"cluster": cl, "m_max": mc, "ms": ms, "cluster_used": inf["cluster"],
+                           "terms": inf["total_terms"]})
+            if best is None or ms < best[0]:
+                best = (ms, cl, mc)
+            hg.close()
+    if best is None:
+        raise RuntimeError("autotune: no candidate configuration was accepted")
+    _, cl, mc = best
+    full = GrapeProblem(problem, precision=precision, cluster=cl, device=device, m_max=mc, backward_mode=backward_mode)
+    return full, {"cluster": cl, "m_max": mc, "candidates": report}
 
 
 def select_ms(x: float, tau: float, sigma: int, precision: str = "fp64", m_max: int = 60, s_max: int = 4096):

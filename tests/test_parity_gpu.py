@@ -250,3 +250,57 @@ def test_fp32_bulk_split_and_fused_agree_bitwise():
     a = _hg(p, precision="fp32_bulk", backward_mode=1).cost_and_grad(u)
     b = _hg(p, precision="fp32_bulk", backward_mode=2).cost_and_grad(u)
     assert a[0] == b[0] and np.array_equal(a[1], b[1])
+
+
+# ---------------------------------------------------------------- batches (one CUDA-graph launch for many problems)
+
+def _small_batch(precision):
+    from paper_2304_06200_gb300 import GrapeProblem
+    from workloads.transmon import _gate_problem, _subspace_one, transmon_cavity
+    probs, raw = [], []
+    specs = [(3, 10, 1, 4, 37), (4, 20, 8, 3, 61), (4, 60, 2, 2, 45), (3, 10, 5, 4, 90), (4, 20, 3, 4, 23),
+             (4, 60, 7, 3, 30)]
+    for i, (nt, nc, n, K, N) in enumerate(specs):
+        H0, Hk = transmon_cavity(nt, nc)
+        dim = nt * nc
+        omega = np.array([1.0 if (j // nc) == nt - 1 else 0.0 for j in range(dim)])
+        p = _gate_problem(f"b{i}", H0, Hk[:K], dim, _subspace_one(nt, nc, n), 1.0, N, 7000 + i, omega, 1.0, 1.0,
+                          1e-2, 1e-12, {})
+        p.u0 = p.u0 * 10
+        raw.append(p)
+        probs.append(GrapeProblem(p, precision=precision, backward_mode=1))
+    return raw, probs
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
+def test_batch_graph_matches_individual_evaluations(precision):
+    from paper_2304_06200_gb300 import GrapeBatch
+    raw, probs = _small_batch(precision)
+    singles = [hg.cost_and_grad(p.u0) for p, hg in zip(raw, probs)]
+    batch = GrapeBatch(probs, n_streams=3)
+    for _ in range(2):                                # the graph is launched repeatedly
+        costs, grads = batch.cost_and_grad([p.u0 for p in raw])
+        for (c, g), cb, gb in zip(singles, costs, grads):
+            assert c == cb
+            assert np.array_equal(g, gb)
+    if precision == "fp64":                           # and the batch is right, not just consistent
+        for p, cb, gb in zip(raw[:2], costs[:2], grads[:2]):
+            _check(p, p.u0, cb, gb)
+    batch.close()
+
+
+def test_batch_rejects_two_team_members():
+    from paper_2304_06200_gb300 import GrapeBatch, GrapeError
+    p = build_config("c1_state_transfer_d30", n_steps=10)
+    hg = _hg(p, backward_mode=2)
+    with pytest.raises(GrapeError):
+        GrapeBatch([hg])
+
+
+def test_autotune_returns_a_correct_problem():
+    from paper_2304_06200_gb300 import autotune
+    p = build_config("c2_gate_d80", n_steps=40)
+    hg, rep = autotune(p, clusters=[0, 1, 2], m_caps=(0, 20), probe_steps=8)
+    assert any("ms" in r for r in rep["candidates"])
+    cost, grad = hg.cost_and_grad(p.u0)
+    _check(p, p.u0, cost, grad)
