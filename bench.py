@@ -17,6 +17,8 @@ from __future__ import annotations
 import argparse
 import json
 import warnings
+
+import numpy as np
 import os
 import statistics
 import subprocess
@@ -51,6 +53,8 @@ def parse_args(argv=None):
     ap.add_argument("--autotune", action="store_true", help="autotune every batch member (slower set-up)")
     ap.add_argument("--m-sweep", action="store_true", help="also sweep the checkpoint spacing M over {50, 200, 1000}")
     ap.add_argument("--c4", action="store_true", help="also run the d = 16000 workload in FP32 bulk and FP64")
+    ap.add_argument("--dense", action="store_true", help="also run the dense d = 2048 variant on the tensor cores")
+    ap.add_argument("--dense-steps", type=int, default=20)
     return ap.parse_args(argv)
 
 
@@ -406,6 +410,8 @@ def run_ours(args):
         extra["c4"] = c4_compare(local)
     if args.batch:
         extra["c5_batch"] = batch_compare(local, args.autotune)
+    if args.dense:
+        extra["dense_d2048_tc"] = dense_compare(local, args.dense_steps)
 
     out = {
         "metric": METRIC, "value": round(value, 6), "unit": "evals/s", "n_gpus": world, "steps": args.steps,
@@ -553,6 +559,65 @@ def c4_compare(local):
         hg.close()
     res["workload"] = workload_description(p)
     res["speedup_fp32_bulk_over_fp64"] = round(res["fp64"]["ms_per_eval"] / res["fp32_bulk"]["ms_per_eval"], 2)
+    return res
+
+
+def dense_problem_d2048(n_steps):
+    """Transmon (8 levels) x cavity (256 levels), d = 2048, stored dense, 16 states, dt = 0.5 ns."""
+    from workloads.transmon import _gate_problem, _subspace_two, transmon_cavity
+
+    H0, Hk = transmon_cavity(8, 256)
+    dim = 2048
+    omega = np.array([1.0 if (j // 256) == 7 else 0.0 for j in range(dim)])
+    idx = [t * 256 + c for t in (0, 1) for c in range(8)]
+    return _gate_problem("dense_d2048", H0.toarray(), [h.toarray() for h in Hk], dim, idx, 0.5, n_steps, 4, omega,
+                         1.0, 1.0, 1e-2, 1e-10, {"stored": "dense"})
+
+
+def dense_compare(local, n_steps):
+    """Dense d = 2048 on tcgen05 (FP16 hi/lo, FP32 accumulation) against the FP64 kernels on the same problem."""
+    import torch
+    from paper_2304_06200_gb300 import GrapeProblem
+
+    p = dense_problem_d2048(n_steps)
+    dev = torch.device("cuda", local)
+    res = {"workload": workload_description(p) + ", H stored dense"}
+    ref = None
+    for prec in ("fp64", "tc_fp16"):
+        hg = GrapeProblem(p, device=local, precision=prec)
+        u = torch.tensor(p.u0, dtype=torch.float64, device=dev)
+        cost = torch.zeros((), dtype=torch.float64, device=dev)
+        grad = torch.zeros_like(u)
+        hg.cost_device(u, cost)
+        hg.grad_device(grad)
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        hg.cost_device(u, cost)
+        e[1].record()
+        hg.grad_device(grad)
+        e[2].record()
+        torch.cuda.synchronize()
+        hg.sync_status()
+        inf = hg.info()
+        fwd_ms, bwd_ms = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+        r = {"ms_per_eval": round(fwd_ms + bwd_ms, 2), "fwd_ms": round(fwd_ms, 2), "bwd_ms": round(bwd_ms, 2),
+             "taylor_terms_per_sweep": inf["total_terms"]}
+        g = grad.cpu().numpy()
+        if ref is None:
+            ref = (float(cost.item()), g)
+        else:
+            r["cost_rel_diff_vs_fp64"] = abs(float(cost.item()) - ref[0]) / abs(ref[0])
+            r["grad_rel_diff_vs_fp64"] = float(np.linalg.norm(g - ref[1]) / np.linalg.norm(ref[1]))
+            # tensor work actually issued per forward product: 2 operators x 3 hi/lo products x 2 d^2 N_real
+            nreal = ((2 * p.n_states + 15) // 16) * 16
+            flops = inf["total_terms"] * 2 * 3 * 2.0 * p.dim * p.dim * nreal
+            r["forward_tensor_tflops"] = round(flops / (fwd_ms / 1e3) / 1e12, 2)
+            r["forward_us_per_term"] = round(fwd_ms * 1e3 / inf["total_terms"], 2)
+            r["operator_bytes_per_term"] = 4 * p.dim * p.dim * 2
+            r["forward_l2_gbs"] = round(r["operator_bytes_per_term"] * inf["total_terms"] / (fwd_ms / 1e3) / 1e9, 1)
+        res[prec] = r
+        hg.close()
     return res
 
 

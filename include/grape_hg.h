@@ -65,7 +65,10 @@ typedef enum { GRAPE_CSR = 0, GRAPE_DENSE = 1 } grape_format;
  * step norms are FP64 in every mode. */
 typedef enum {
   GRAPE_FP64 = 0,        /* complex128 throughout                                        */
-  GRAPE_FP32_BULK = 1    /* Taylor increments in complex64, states/costates kept FP64     */
+  GRAPE_FP32_BULK = 1,   /* Taylor increments in complex64, states/costates kept FP64     */
+  GRAPE_TC_FP16 = 2      /* dense operator: every Taylor product is a real-split GEMM on the
+                            tensor cores (FP16 hi/lo operands, FP32 accumulation); states,
+                            costates and reductions FP64.  Needs dim % 128 == 0, n_states <= 16. */
 } grape_precision;
 
 /* One Hermitian operator (H0 or a control H_k), dim x dim.

@@ -8,7 +8,7 @@ import os
 from .build import LIB, build_library
 
 GRAPE_CSR, GRAPE_DENSE = 0, 1
-GRAPE_FP64, GRAPE_FP32_BULK = 0, 1
+GRAPE_FP64, GRAPE_FP32_BULK, GRAPE_TC_FP16 = 0, 1, 2
 
 STATUS = {
     0: "GRAPE_OK", 1: "GRAPE_EINVAL", 2: "GRAPE_ENOMEM", 3: "GRAPE_ECUDA", 4: "GRAPE_ETOL",

@@ -1,0 +1,687 @@
+// Dense-operator variant of the HG evaluation on the 5th-generation tensor cores (tcgen05).
+//
+// When H is stored dense, one Taylor term y = B x for a block of n columns is a complex GEMM
+// (B: d x d, x: d x n).  With B = Br + i Bi and x = xr + i xi the product splits into real GEMMs
+//     D1 = Br [xr | xi],   D2 = Bi [xr | xi],   yr = D1(xr) - D2(xi),   yi = D1(xi) + D2(xr)
+// run on tcgen05.mma (kind::f16, FP32 accumulation in tensor memory).  FP16 keeps 11 significant
+// bits, so both operands are split into a high and a low FP16 part (v = hi + lo), and three
+// products hi*hi + hi*lo + lo*hi recover about 22 bits; states, costates, W accumulators and all
+// reductions stay FP64 as in the FP32-bulk path.  The chain (forward terms, the adjoint
+// re-propagation, the Horner costate chain and the x chain of the backward sweep) is the same as in
+// grape_kernels.cu; here it is driven from the host, one tensor-core product per Taylor term.
+//
+// Kernel k_dense_apply: grid (KS, d / 128), clusters of KS CTAs split the K (= d) dimension; each
+// CTA streams its 128-row slab of the four operator matrices and the matching X columns through a
+// two-stage cp.async pipeline into shared memory (K-major, no-swizzle core-matrix layout: 8 rows x
+// 16 bytes per core matrix, K-adjacent core matrices 128 bytes apart, 8-row groups 1024 bytes
+// apart), one thread issues the MMAs, and the K-split partials are summed deterministically through
+// distributed shared memory by rank 0 of the cluster.
+#include <cuda_fp16.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "grape_internal.h"
+#include "grape_dense.h"
+
+namespace grape {
+
+namespace {
+
+constexpr int kTM = 128;        // rows per CTA (MMA M)
+constexpr int kKC = 64;         // K chunk per pipeline stage
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: K-major, no swizzle, LBO = K-direction core-matrix stride,
+// SBO = 8-row-group stride, version 1 (sm_100 family).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+               : "memory");
+}
+
+// Bounded wait for the completion of phase `parity` of an mbarrier; returns 0 on timeout.
+__device__ __forceinline__ int mbar_wait(uint64_t* mbar, uint32_t parity, long long limit) {
+  uint32_t done = 0;
+  for (long long it = 0; it < limit && !done; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.b32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(parity)
+        : "memory");
+  }
+  return (int)done;
+}
+
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
+}
+
+// byte offset of (row r, k) inside a K-major no-swizzle tile with kcores core matrices along K
+__device__ __forceinline__ int core_off(int r, int k, int kcores) {
+  return (r >> 3) * (kcores * 128) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+struct ApplyArgs {
+  const __half* op[4];     // Br_hi, Br_lo, Bi_hi, Bi_lo: d x d row-major (K contiguous)
+  const __half* xh;        // X high parts: ncols_real x d (row c = real column c, K contiguous)
+  const __half* xl;        // X low parts
+  float2* y;               // output: d x ncols complex, column-major (column h contiguous)
+  int d, ncols, nreal;     // nreal = 2 * ncols padded to a multiple of 16 (MMA N)
+  float alpha;             // y = alpha * B x
+  int* err;
+};
+
+// Tile bytes: four operator tiles (128 x 64 fp16 = 16 KB each) + X hi/lo tiles (nreal x 64 fp16).
+__host__ __device__ inline int stage_bytes(int nreal) { return 4 * 16384 + 2 * nreal * 128; }
+
+__global__ void __launch_bounds__(kThreads, 1) k_dense_apply(ApplyArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_ok;
+  const int tid = threadIdx.x;
+  const int ks = blockIdx.x, KS = gridDim.x;
+  const int row0 = blockIdx.y * kTM;
+  const int Kc = a.d / KS;                      // this CTA's K range [ks * Kc, (ks + 1) * Kc)
+  const int nchunks = Kc / kKC;
+  const int nreal = a.nreal;
+  const int SB = stage_bytes(nreal);
+  unsigned char* stage[2] = {smem, smem + SB};
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+    s_ok = 1;
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (tid < 32) {   // 128 TMEM columns: D1 at column 0, D2 at column 64 (N <= 64)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  auto load_chunk = [&](int c, unsigned char* st) {
+    const int k0 = ks * Kc + c * kKC;
+    // operator tiles: 128 rows x 8 sixteen-byte pieces each
+    for (int idx = tid; idx < 4 * kTM * 8; idx += kThreads) {
+      const int mat = idx / (kTM * 8), rem = idx % (kTM * 8), r = rem / 8, piece = rem % 8;
+      const __half* g = a.op[mat] + (int64_t)(row0 + r) * a.d + k0 + piece * 8;
+      cp_async16(st + mat * 16384 + core_off(r, piece * 8, 8), g);
+    }
+    // X tiles: nreal rows (real columns) x 8 pieces, hi then lo; padded rows read column 0 (ignored)
+    for (int idx = tid; idx < 2 * nreal * 8; idx += kThreads) {
+      const int part = idx / (nreal * 8), rem = idx % (nreal * 8), r = rem / 8, piece = rem % 8;
+      const int rr = r < 2 * a.ncols ? r : 0;
+      const __half* g = (part == 0 ? a.xh : a.xl) + (int64_t)rr * a.d + k0 + piece * 8;
+      cp_async16(st + 4 * 16384 + part * nreal * 128 + core_off(r, piece * 8, 8), g);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+
+  // idesc: D f32, A/B f16, both K-major, N = nreal, M = 128
+  const uint32_t idesc = (1u << 4) | ((uint32_t)(nreal >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
+  uint32_t phase[2] = {0u, 0u};
+  int ok = 1;
+  load_chunk(0, stage[0]);
+  for (int c = 0; c < nchunks; ++c) {
+    const int sc = c & 1;
+    if (c + 1 < nchunks) {
+      const int sn = (c + 1) & 1;
+      if (c >= 1) {   // the MMAs of chunk c-1 read stage sn: wait before overwriting it
+        if (!mbar_wait(&mbar[sn], phase[sn], 1LL << 26)) ok = 0;
+        phase[sn] ^= 1u;
+      }
+      load_chunk(c + 1, stage[sn]);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sbase = smem_u32(stage[sc]);
+      const uint32_t xh = sbase + 4 * 16384, xl = xh + nreal * 128;
+      for (int kk = 0; kk < kKC / 16; ++kk) {
+        const uint32_t ko = kk * 256;   // 16 K = two core matrices along K
+        const uint64_t bh = smem_desc(xh + ko, 128, 1024), bl = smem_desc(xl + ko, 128, 1024);
+        const uint64_t arh = smem_desc(sbase + 0 * 16384 + ko, 128, 1024);
+        const uint64_t arl = smem_desc(sbase + 1 * 16384 + ko, 128, 1024);
+        const uint64_t aih = smem_desc(sbase + 2 * 16384 + ko, 128, 1024);
+        const uint64_t ail = smem_desc(sbase + 3 * 16384 + ko, 128, 1024);
+        const uint32_t first = (c == 0 && kk == 0) ? 0u : 1u;
+        mma_f16(tmem, arh, bh, idesc, first);
+        mma_f16(tmem, arh, bl, idesc, 1u);
+        mma_f16(tmem, arl, bh, idesc, 1u);
+        mma_f16(tmem + 64, aih, bh, idesc, first);
+        mma_f16(tmem + 64, aih, bl, idesc, 1u);
+        mma_f16(tmem + 64, ail, bh, idesc, 1u);
+      }
+      mma_commit(&mbar[sc]);
+    }
+  }
+  // wait for the last chunk's MMAs (the earlier ones completed before it: MMAs complete in order)
+  {
+    const int sl = (nchunks - 1) & 1;
+    if (!mbar_wait(&mbar[sl], phase[sl], 1LL << 26)) ok = 0;
+  }
+  if (!ok) {
+    s_ok = 0;
+    atomicCAS(a.err, 0, kErrTimeout);
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  // epilogue: warp w (0..3) owns rows 32w..32w+31; D1/D2 columns -> complex partial sums in smem
+  float* part = reinterpret_cast<float*>(smem);   // 128 rows x (2 * ncols) floats (stages are free now)
+  const int warp = tid >> 5, lane = tid & 31;
+  const int ncols = a.ncols;
+  if (warp < 4) {
+    const int row = 32 * warp + lane;
+    for (int cc = 0; cc < nreal; cc += 16) {   // 16 real columns = 8 complex columns per chunk
+      uint32_t r1[16], r2[16];
+      const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + cc;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r1[0]), "=r"(r1[1]), "=r"(r1[2]), "=r"(r1[3]), "=r"(r1[4]), "=r"(r1[5]), "=r"(r1[6]), "=r"(r1[7]),
+            "=r"(r1[8]), "=r"(r1[9]), "=r"(r1[10]), "=r"(r1[11]), "=r"(r1[12]), "=r"(r1[13]), "=r"(r1[14]),
+            "=r"(r1[15])
+          : "r"(ta));
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r2[0]), "=r"(r2[1]), "=r"(r2[2]), "=r"(r2[3]), "=r"(r2[4]), "=r"(r2[5]), "=r"(r2[6]), "=r"(r2[7]),
+            "=r"(r2[8]), "=r"(r2[9]), "=r"(r2[10]), "=r"(r2[11]), "=r"(r2[12]), "=r"(r2[13]), "=r"(r2[14]),
+            "=r"(r2[15])
+          : "r"(ta + 64));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int h = cc / 2 + j;
+        if (h < ncols) {
+          const float d1r = __uint_as_float(r1[2 * j]), d1i = __uint_as_float(r1[2 * j + 1]);
+          const float d2r = __uint_as_float(r2[2 * j]), d2i = __uint_as_float(r2[2 * j + 1]);
+          part[row * 2 * ncols + 2 * h] = d1r - d2i;       // yr = Br xr - Bi xi
+          part[row * 2 * ncols + 2 * h + 1] = d1i + d2r;   // yi = Br xi + Bi xr
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  // deterministic K-split reduction over the cluster: rank 0 sums ranks 0..KS-1 in order
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+  if (ks == 0) {
+    for (int idx = tid; idx < kTM * ncols; idx += kThreads) {
+      const int row = idx / ncols, h = idx % ncols;
+      float sr = 0.f, si = 0.f;
+      for (int r = 0; r < KS; ++r) {
+        const float* pr;
+        asm volatile("mapa.u64 %0, %1, %2;" : "=l"(pr) : "l"(part), "r"(r));
+        sr += pr[row * 2 * ncols + 2 * h];
+        si += pr[row * 2 * ncols + 2 * h + 1];
+      }
+      a.y[(int64_t)h * a.d + row0 + row] = make_float2(a.alpha * sr, a.alpha * si);
+    }
+  }
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+  if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+}
+
+// ------------------------------------------------------------------ elementwise chain kernels
+
+__device__ __forceinline__ void split_f16(float v, __half& hi, __half& lo) {
+  hi = __float2half_rn(v);
+  lo = __float2half_rn(v - __half2float(hi));
+}
+
+// X (real columns 2h, 2h+1 of block `blk`) <- split of a complex FP64 (scaled) or FP32 block
+__global__ void k_split_d(const double2* __restrict__ v, double scale, int d, int ncols, int col_off, __half* xh,
+                          __half* xl) {
+  const int64_t total = (int64_t)d * ncols;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int h = (int)(i / d), r = (int)(i % d);
+    const double2 z = v[i];
+    __half a, b;
+    split_f16((float)(z.x * scale), a, b);
+    xh[(int64_t)(2 * (h + col_off)) * d + r] = a;
+    xl[(int64_t)(2 * (h + col_off)) * d + r] = b;
+    split_f16((float)(z.y * scale), a, b);
+    xh[(int64_t)(2 * (h + col_off) + 1) * d + r] = a;
+    xl[(int64_t)(2 * (h + col_off) + 1) * d + r] = b;
+  }
+}
+
+// forward term: x_q = y (already scaled by 1/q), inc += y, X <- split(y)
+__global__ void k_fwd_term(const float2* __restrict__ y, double2* inc, int d, int ncols, __half* xh, __half* xl) {
+  const int64_t total = (int64_t)d * ncols;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int h = (int)(i / d), r = (int)(i % d);
+    const float2 z = y[i];
+    double2 a = inc[i];
+    a.x += z.x;
+    a.y += z.y;
+    inc[i] = a;
+    __half p, q;
+    split_f16(z.x, p, q);
+    xh[(int64_t)(2 * h) * d + r] = p;
+    xl[(int64_t)(2 * h) * d + r] = q;
+    split_f16(z.y, p, q);
+    xh[(int64_t)(2 * h + 1) * d + r] = p;
+    xl[(int64_t)(2 * h + 1) * d + r] = q;
+  }
+}
+
+__global__ void k_axpy_d(double2* a, const double2* __restrict__ b, int64_t total) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    double2 v = a[i];
+    const double2 w = b[i];
+    v.x += w.x;
+    v.y += w.y;
+    a[i] = v;
+  }
+}
+
+// phase A term q: y holds (B [a | w]) for the psi chain (columns 0..n-1) and the Horner chain (n..2n-1).
+//   a_q = -y_a / q (inc += a_q), w_{m-1-q} = chi/(m-q)! - y_w  (q < m), chi^(l) = chi - y_w (q == m)
+__global__ void k_phase_a_term(const float2* __restrict__ y, double2* inc, double2* chi, float2* wslot, int d, int n,
+                               int q, int m, double iq, double fq, __half* xh, __half* xl) {
+  const int64_t total = (int64_t)d * n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int h = (int)(i / d), r = (int)(i % d);
+    const float2 ya = y[i];
+    const float2 yw = y[total + i];
+    const float ar = (float)(-iq) * ya.x, ai = (float)(-iq) * ya.y;
+    double2 a = inc[i];
+    a.x += ar;
+    a.y += ai;
+    inc[i] = a;
+    __half p, s2;
+    split_f16(ar, p, s2);
+    xh[(int64_t)(2 * h) * d + r] = p;
+    xl[(int64_t)(2 * h) * d + r] = s2;
+    split_f16(ai, p, s2);
+    xh[(int64_t)(2 * h + 1) * d + r] = p;
+    xl[(int64_t)(2 * h + 1) * d + r] = s2;
+    const double2 ch = chi[i];
+    if (q < m) {
+      const float wr = (float)(ch.x * fq) - yw.x, wi = (float)(ch.y * fq) - yw.y;
+      wslot[(int64_t)(m - 1 - q) * total + i] = make_float2(wr, wi);
+      split_f16(wr, p, s2);
+      xh[(int64_t)(2 * (h + n)) * d + r] = p;
+      xl[(int64_t)(2 * (h + n)) * d + r] = s2;
+      split_f16(wi, p, s2);
+      xh[(int64_t)(2 * (h + n) + 1) * d + r] = p;
+      xl[(int64_t)(2 * (h + n) + 1) * d + r] = s2;
+    } else {
+      chi[i] = make_double2(ch.x - yw.x, ch.y - yw.y);
+    }
+  }
+}
+
+// phase A start: X <- [split(psi) | split(chi / m!)], w_{m-1} = chi / m!, inc = 0
+__global__ void k_phase_a_start(const double2* __restrict__ psi, const double2* __restrict__ chi, double2* inc,
+                                float2* wslot, int d, int n, int m, double fm, __half* xh, __half* xl) {
+  const int64_t total = (int64_t)d * n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int h = (int)(i / d), r = (int)(i % d);
+    const double2 v = psi[i];
+    __half p, s2;
+    split_f16((float)v.x, p, s2);
+    xh[(int64_t)(2 * h) * d + r] = p;
+    xl[(int64_t)(2 * h) * d + r] = s2;
+    split_f16((float)v.y, p, s2);
+    xh[(int64_t)(2 * h + 1) * d + r] = p;
+    xl[(int64_t)(2 * h + 1) * d + r] = s2;
+    inc[i] = make_double2(0.0, 0.0);
+    const double2 ch = chi[i];
+    const float wr = (float)(ch.x * fm), wi = (float)(ch.y * fm);
+    wslot[(int64_t)(m - 1) * total + i] = make_float2(wr, wi);
+    split_f16(wr, p, s2);
+    xh[(int64_t)(2 * (h + n)) * d + r] = p;
+    xl[(int64_t)(2 * (h + n)) * d + r] = s2;
+    split_f16(wi, p, s2);
+    xh[(int64_t)(2 * (h + n) + 1) * d + r] = p;
+    xl[(int64_t)(2 * (h + n) + 1) * d + r] = s2;
+  }
+}
+
+// phase B: xcur <- y (the next x_p, FP32) and X <- split(y)
+__global__ void k_phase_b_term(const float2* __restrict__ y, float2* xcur, int d, int n, __half* xh, __half* xl) {
+  const int64_t total = (int64_t)d * n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int h = (int)(i / d), r = (int)(i % d);
+    const float2 z = y[i];
+    xcur[i] = z;
+    __half p, s2;
+    split_f16(z.x, p, s2);
+    xh[(int64_t)(2 * h) * d + r] = p;
+    xl[(int64_t)(2 * h) * d + r] = s2;
+    split_f16(z.y, p, s2);
+    xh[(int64_t)(2 * h + 1) * d + r] = p;
+    xl[(int64_t)(2 * h + 1) * d + r] = s2;
+  }
+}
+
+__global__ void k_psi_to_f32(const double2* __restrict__ psi, float2* xcur, int64_t total) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+    xcur[i] = make_float2((float)psi[i].x, (float)psi[i].y);
+}
+
+// W[ce] += sum_h conj(w_p[row, h]) x_p[col, h] over the control-carrying entries (FP32 products, FP64 sum)
+__global__ void k_w_accum(const float2* __restrict__ wp, const float2* __restrict__ xp, const int* __restrict__ ce_row,
+                          const int* __restrict__ ce_col, double2* W, int nce, int d, int n) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nce; c += gridDim.x * blockDim.x) {
+    const int r = ce_row[c], j = ce_col[c];
+    float ar = 0.f, ai = 0.f;
+    for (int h = 0; h < n; ++h) {
+      const float2 w = wp[(int64_t)h * d + r];
+      const float2 x = xp[(int64_t)h * d + j];
+      ar = fmaf(w.x, x.x, ar);
+      ar = fmaf(w.y, x.y, ar);
+      ai = fmaf(w.x, x.y, ai);
+      ai = fmaf(-w.y, x.x, ai);
+    }
+    double2 acc = W[c];
+    acc.x += ar;
+    acc.y += ai;
+    W[c] = acc;
+  }
+}
+
+// dense operator of step n: B = -i (dt/s) (H0 + sum_k u_kn H_k) on the union pattern, split into the
+// FP16 hi/lo parts of Br = (dt/s) Im H and Bi = -(dt/s) Re H (entries off the pattern stay zero)
+__global__ void k_dense_assemble(const int64_t* __restrict__ rowptr, const int* __restrict__ ucol,
+                                 const double2* __restrict__ h0v, const int* __restrict__ ectr_ptr,
+                                 const int* __restrict__ ectr_k, const double2* __restrict__ ectr_val,
+                                 const double* __restrict__ u, int N, int n, double scale, int d, __half* brh,
+                                 __half* brl, __half* bih, __half* bil) {
+  for (int i = blockIdx.x; i < d; i += gridDim.x) {
+    for (int64_t e = rowptr[i] + threadIdx.x; e < rowptr[i + 1]; e += blockDim.x) {
+      double2 v = h0v[e];
+      for (int c = ectr_ptr[e]; c < ectr_ptr[e + 1]; ++c) {
+        const double uk = u[(int64_t)ectr_k[c] * N + n];
+        v.x = fma(uk, ectr_val[c].x, v.x);
+        v.y = fma(uk, ectr_val[c].y, v.y);
+      }
+      const int64_t o = (int64_t)i * d + ucol[e];
+      __half p, q;
+      split_f16((float)(scale * v.y), p, q);
+      brh[o] = p;
+      brl[o] = q;
+      split_f16((float)(-scale * v.x), p, q);
+      bih[o] = p;
+      bil[o] = q;
+    }
+  }
+}
+
+// per-step C2 contribution and the forward's g / C2 partials (single block, deterministic)
+__global__ void k_c2_add(const double2* __restrict__ psi, const double* __restrict__ omega, int64_t total, int d,
+                         double* c2acc) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
+    const double2 v = psi[i];
+    s = fma(omega[i % d], v.x * v.x + v.y * v.y, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    *c2acc += t;
+  }
+}
+
+__global__ void k_overlap(const double2* __restrict__ psi, const double2* __restrict__ target, int64_t total,
+                          double2* g_out) {
+  __shared__ double rx[32], ry[32];
+  double sx = 0.0, sy = 0.0;
+  for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
+    const double2 t = target[i], v = psi[i];
+    sx = fma(t.x, v.x, fma(t.y, v.y, sx));
+    sy = fma(t.x, v.y, fma(-t.y, v.x, sy));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    rx[threadIdx.x >> 5] = sx;
+    ry[threadIdx.x >> 5] = sy;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tx = 0.0, ty = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      tx += rx[w];
+      ty += ry[w];
+    }
+    *g_out = make_double2(tx, ty);
+  }
+}
+
+// chi_N = -(w_fid g / n^2) phi_T + c2w Omega psi_N
+__global__ void k_costate_init(const double2* __restrict__ psi, const double2* __restrict__ target,
+                               const double* omega, const double2* __restrict__ g, double w_fid, double c2w, int n,
+                               int d, double2* chi) {
+  const int64_t total = (int64_t)d * n;
+  const double nS = (double)n;
+  const double2 gg = *g;
+  const double ax = -w_fid * gg.x / (nS * nS), ay = -w_fid * gg.y / (nS * nS);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 t = target[i];
+    double2 ch = make_double2(ax * t.x - ay * t.y, ax * t.y + ay * t.x);
+    if (omega && c2w != 0.0) {
+      const double w = c2w * omega[i % d];
+      ch.x = fma(w, psi[i].x, ch.x);
+      ch.y = fma(w, psi[i].y, ch.y);
+    }
+    chi[i] = ch;
+  }
+}
+
+__global__ void k_chi_source(const double2* __restrict__ psi, const double* __restrict__ omega, double c2w, int64_t total,
+                             int d, double2* chi) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const double w = c2w * omega[i % d];
+    double2 ch = chi[i];
+    ch.x = fma(w, psi[i].x, ch.x);
+    ch.y = fma(w, psi[i].y, ch.y);
+    chi[i] = ch;
+  }
+}
+
+// G[n][k] = 2 (dt/s) sum_{contributions of control k} (h.x W.y + h.y W.x), one block per control
+__global__ void k_dense_grad(const int* __restrict__ cptr, const int* __restrict__ cce, const double2* __restrict__ cval,
+                             const double2* __restrict__ W, double gscale, int n_step, int K, double* part_grad) {
+  __shared__ double red[32];
+  const int k = blockIdx.x;
+  double acc = 0.0;
+  for (int c = cptr[k] + threadIdx.x; c < cptr[k + 1]; c += blockDim.x) {
+    const double2 w = W[cce[c]];
+    acc = fma(cval[c].x, w.y, acc);
+    acc = fma(cval[c].y, w.x, acc);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    part_grad[(int64_t)n_step * K + k] = gscale * t;
+  }
+}
+
+int ew_grid(int64_t total) {
+  int64_t g = (total + 255) / 256;
+  if (g > 2048) g = 2048;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+int dense_apply_smem(int nreal) { return 2 * stage_bytes(nreal); }
+
+// y = alpha * B x for the first `ncols` complex columns held in X (real columns 2h, 2h+1).
+static cudaError_t apply(const DenseCtx& c, int ncols, float alpha, float2* y, cudaStream_t st) {
+  ApplyArgs a{};
+  a.op[0] = c.brh;
+  a.op[1] = c.brl;
+  a.op[2] = c.bih;
+  a.op[3] = c.bil;
+  a.xh = c.xh;
+  a.xl = c.xl;
+  a.y = y;
+  a.d = c.d;
+  a.ncols = ncols;
+  a.nreal = ((2 * ncols + 15) / 16) * 16;
+  a.alpha = alpha;
+  a.err = c.err;
+  const int smem = dense_apply_smem(a.nreal);
+  cudaError_t e = cudaFuncSetAttribute(k_dense_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(c.ksplit, c.d / kTM);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = c.ksplit;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, k_dense_apply, a);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+#define DCHK(x)                            \
+  do {                                     \
+    cudaError_t _e = (x);                  \
+    if (_e != cudaSuccess) return _e;      \
+    _e = cudaGetLastError();               \
+    if (_e != cudaSuccess) return _e;      \
+  } while (0)
+
+cudaError_t dense_forward(const DenseCtx& c, const int* m_host, const int* s_host, cudaStream_t st) {
+  const int d = c.d, n = c.n;
+  const int64_t tot = (int64_t)d * n;
+  const int g = ew_grid(tot);
+  DCHK(cudaMemcpyAsync(c.psi, c.psi0, tot * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  DCHK(cudaMemsetAsync(c.c2acc, 0, sizeof(double), st));
+  for (int step = 0; step < c.N; ++step) {
+    const int m = m_host[step], s = s_host[step];
+    if (m <= 0 || s <= 0) continue;
+    k_dense_assemble<<<std::min(d, 2048), 256, 0, st>>>(c.rowptr, c.ucol, c.h0v, c.ectr_ptr, c.ectr_k, c.ectr_val,
+                                                       c.u, c.N, step, c.dt / s, d, c.brh, c.brl, c.bih, c.bil);
+    DCHK(cudaGetLastError());
+    for (int l = 0; l < s; ++l) {
+      k_split_d<<<g, 256, 0, st>>>(c.psi, 1.0, d, n, 0, c.xh, c.xl);
+      DCHK(cudaMemsetAsync(c.inc, 0, tot * sizeof(double2), st));
+      for (int q = 1; q <= m; ++q) {
+        DCHK(apply(c, n, 1.0f / q, c.y, st));
+        k_fwd_term<<<g, 256, 0, st>>>(c.y, c.inc, d, n, c.xh, c.xl);
+        DCHK(cudaGetLastError());
+      }
+      k_axpy_d<<<g, 256, 0, st>>>(c.psi, c.inc, tot);
+      DCHK(cudaGetLastError());
+    }
+    if (c.omega) {
+      k_c2_add<<<1, 1024, 0, st>>>(c.psi, c.omega, tot, d, c.c2acc);
+      DCHK(cudaGetLastError());
+    }
+    if (c.ckpt_every > 0 && (step + 1) % c.ckpt_every == 0 && (step + 1) / c.ckpt_every - 1 < c.n_ckpt)
+      DCHK(cudaMemcpyAsync(c.ckpt + (int64_t)((step + 1) / c.ckpt_every - 1) * tot, c.psi, tot * sizeof(double2),
+                           cudaMemcpyDeviceToDevice, st));
+  }
+  DCHK(cudaMemcpyAsync(c.psiN, c.psi, tot * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  k_overlap<<<1, 1024, 0, st>>>(c.psi, c.target, tot, c.part_g);
+  DCHK(cudaGetLastError());
+  DCHK(cudaMemcpyAsync(c.part_c2, c.c2acc, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return cudaSuccess;
+}
+
+cudaError_t dense_backward(const DenseCtx& c, const int* m_host, const int* s_host, cudaStream_t st) {
+  const int d = c.d, n = c.n;
+  const int64_t tot = (int64_t)d * n;
+  const int g = ew_grid(tot);
+  const double c2w = (c.omega && c.w_forbid != 0.0) ? c.w_forbid / ((double)c.N * n) : 0.0;
+  DCHK(cudaMemcpyAsync(c.psi, c.psiN, tot * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  k_costate_init<<<g, 256, 0, st>>>(c.psiN, c.target, c.omega, c.g_final, c.w_fid, c2w, n, d, c.chi);
+  DCHK(cudaGetLastError());
+  for (int step = c.N - 1; step >= 0; --step) {
+    const int m = m_host[step], s = s_host[step];
+    if (m <= 0 || s <= 0) continue;
+    k_dense_assemble<<<std::min(d, 2048), 256, 0, st>>>(c.rowptr, c.ucol, c.h0v, c.ectr_ptr, c.ectr_k, c.ectr_val,
+                                                       c.u, c.N, step, c.dt / s, d, c.brh, c.brl, c.bih, c.bil);
+    DCHK(cudaGetLastError());
+    DCHK(cudaMemsetAsync(c.W, 0, (size_t)std::max(c.nce, 1) * sizeof(double2), st));
+    for (int l = s - 1; l >= 0; --l) {
+      // phase A: [psi | Horner] chains with -B
+      k_phase_a_start<<<g, 256, 0, st>>>(c.psi, c.chi, c.inc, c.wslot, d, n, m, c.inv_fact[m], c.xh, c.xl);
+      DCHK(cudaGetLastError());
+      for (int q = 1; q <= m; ++q) {
+        DCHK(apply(c, 2 * n, 1.0f, c.y, st));
+        k_phase_a_term<<<g, 256, 0, st>>>(c.y, c.inc, c.chi, c.wslot, d, n, q, m, 1.0 / q, c.inv_fact[m - q], c.xh,
+                                         c.xl);
+        DCHK(cudaGetLastError());
+      }
+      k_axpy_d<<<g, 256, 0, st>>>(c.psi, c.inc, tot);   // psi^(l)
+      DCHK(cudaGetLastError());
+      // phase B: x chain with B, W accumulation on control entries
+      k_psi_to_f32<<<g, 256, 0, st>>>(c.psi, c.xcur, tot);
+      k_split_d<<<g, 256, 0, st>>>(c.psi, 1.0, d, n, 0, c.xh, c.xl);
+      DCHK(cudaGetLastError());
+      for (int p = 0; p < m; ++p) {
+        if (c.nce > 0) {
+          k_w_accum<<<ew_grid(c.nce), 256, 0, st>>>(c.wslot + (int64_t)p * tot, c.xcur, c.ce_row, c.ce_col, c.W, c.nce,
+                                                    d, n);
+          DCHK(cudaGetLastError());
+        }
+        if (p < m - 1) {
+          DCHK(apply(c, n, 1.0f, c.y, st));
+          k_phase_b_term<<<g, 256, 0, st>>>(c.y, c.xcur, d, n, c.xh, c.xl);
+          DCHK(cudaGetLastError());
+        }
+      }
+    }
+    if (step > 0) {
+      if (c.ckpt_every > 0 && step % c.ckpt_every == 0 && step / c.ckpt_every - 1 < c.n_ckpt)
+        DCHK(cudaMemcpyAsync(c.psi, c.ckpt + (int64_t)(step / c.ckpt_every - 1) * tot, tot * sizeof(double2),
+                             cudaMemcpyDeviceToDevice, st));
+      if (c2w != 0.0) {
+        k_chi_source<<<g, 256, 0, st>>>(c.psi, c.omega, c2w, tot, d, c.chi);
+        DCHK(cudaGetLastError());
+      }
+    }
+    if (c.K > 0) {
+      k_dense_grad<<<c.K, 256, 0, st>>>(c.cptr, c.cce, c.cval, c.W, 2.0 * c.dt / s, step, c.K, c.part_grad);
+      DCHK(cudaGetLastError());
+    }
+  }
+  return cudaSuccess;
+}
+
+}  // namespace grape

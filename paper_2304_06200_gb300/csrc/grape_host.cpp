@@ -12,6 +12,7 @@
 
 #include "../../include/grape_hg.h"
 #include "grape_bound.h"
+#include "grape_dense.h"
 #include "grape_internal.h"
 
 using cplx = std::complex<double>;
@@ -191,6 +192,10 @@ struct grape_problem {
   unsigned* d_flags = nullptr;      // ready[n*CL], done[n*CL]
   // launch plans of the forward and the backward sweep
   KPlan fwd, bwd;
+  // dense tensor-core mode
+  bool dense = false;
+  grape::DenseCtx dctx{};
+  std::vector<int> m_host, s_host;
   bool forward_done = false;
   bool evaluated = false;
   cudaStream_t last_stream = nullptr;
@@ -246,6 +251,136 @@ int sm_count(int dev) {
   int v = 0;
   if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
   return std::max(v, 1);
+}
+
+// Device buffers of the dense tensor-core mode (GRAPE_TC_FP16).
+grape_status build_dense(grape_problem* P, const grape_desc* d, const std::vector<int64_t>& rowptr,
+                         const std::vector<int32_t>& ucol, const std::vector<double2>& h0v, const std::vector<int>& cptr,
+                         const std::vector<int>& cidx, const std::vector<double2>& cval, const std::vector<int>& ectr_ptr,
+                         const std::vector<int>& ectr_k, const std::vector<double2>& ectr_val) {
+  grape_status st;
+  const int64_t dim = P->dim;
+  const int n = P->n, K = P->K, N = P->N;
+  P->dense = true;
+  P->fwd.CL = P->bwd.CL = 1;   // one partial per reduction
+  P->bwd_mode = 1;
+  int M = d->ckpt_every;
+  if (M == 0) M = std::min(50, N);
+  if (M < 0) M = 0;
+  P->ckpt_every = M;
+  P->n_ckpt = M > 0 ? (N - 1) / M : 0;
+  // control-carrying entries and the map from control contributions to them
+  std::vector<int> ce_of(rowptr.back(), -1), ce_row, ce_col, cce(cidx.size());
+  for (int64_t i = 0; i < dim; ++i)
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e)
+      if (ectr_ptr[e + 1] > ectr_ptr[e]) {
+        ce_of[e] = (int)ce_row.size();
+        ce_row.push_back((int)i);
+        ce_col.push_back(ucol[e]);
+      }
+  for (size_t c = 0; c < cidx.size(); ++c) cce[c] = ce_of[cidx[c]];
+  grape::DenseCtx& c = P->dctx;
+  c.d = (int)dim;
+  c.n = n;
+  c.N = N;
+  c.K = K;
+  c.ksplit = 8;
+  while (c.ksplit > 1 && (dim / c.ksplit < 64 || (dim / c.ksplit) % 64 != 0)) c.ksplit /= 2;
+  c.dt = P->dt;
+  c.w_fid = P->w_fid;
+  c.w_forbid = P->w_forbid;
+  c.ckpt_every = P->ckpt_every;
+  c.n_ckpt = P->n_ckpt;
+  c.inv_fact[0] = 1.0;
+  for (int q = 1; q < 62; ++q) c.inv_fact[q] = c.inv_fact[q - 1] / q;
+  c.nce = (int)ce_row.size();
+  const size_t dd = (size_t)dim * dim, blk = (size_t)dim * n;
+  __half* hp[4];
+  for (int k = 0; k < 4; ++k)
+    if ((st = dzeros(P, &hp[k], dd))) return st;
+  c.brh = hp[0];
+  c.brl = hp[1];
+  c.bih = hp[2];
+  c.bil = hp[3];
+  __half *xh, *xl;
+  if ((st = dzeros(P, &xh, (size_t)4 * n * dim))) return st;
+  if ((st = dzeros(P, &xl, (size_t)4 * n * dim))) return st;
+  c.xh = xh;
+  c.xl = xl;
+  float2* y;
+  if ((st = dzeros(P, &y, 2 * blk))) return st;
+  c.y = y;
+  double2 *psi, *chi, *inc;
+  if ((st = dzeros(P, &psi, blk)) || (st = dzeros(P, &chi, blk)) || (st = dzeros(P, &inc, blk))) return st;
+  c.psi = psi;
+  c.chi = chi;
+  c.inc = inc;
+  float2 *ws, *xc;
+  if ((st = dzeros(P, &ws, (size_t)P->m_cap * blk)) || (st = dzeros(P, &xc, blk))) return st;
+  c.wslot = ws;
+  c.xcur = xc;
+  double2* W;
+  if ((st = dzeros(P, &W, (size_t)std::max(c.nce, 1)))) return st;
+  c.W = W;
+  int *d_cer, *d_cec, *d_cce, *d_ucol;
+  if ((st = upload(P, &d_cer, ce_row.data(), std::max<size_t>(ce_row.size(), 1)))) return st;
+  if ((st = upload(P, &d_cec, ce_col.data(), std::max<size_t>(ce_col.size(), 1)))) return st;
+  if ((st = upload(P, &d_cce, cce.data(), std::max<size_t>(cce.size(), 1)))) return st;
+  if ((st = upload(P, &d_ucol, ucol.data(), ucol.size()))) return st;
+  c.ce_row = d_cer;
+  c.ce_col = d_cec;
+  c.cce = d_cce;
+  c.ucol = d_ucol;
+  std::vector<double> tabX(P->table.X), tabS(P->table.smax);
+  if ((st = upload(P, &P->d_rowptr, rowptr.data(), rowptr.size()))) return st;
+  if ((st = upload(P, &P->d_h0v, h0v.data(), h0v.size()))) return st;
+  if ((st = upload(P, &P->d_cptr, cptr.data(), cptr.size()))) return st;
+  if ((st = upload(P, &P->d_cidx, cidx.data(), std::max<size_t>(cidx.size(), 1)))) return st;
+  if ((st = upload(P, &P->d_cval, cval.data(), std::max<size_t>(cval.size(), 1)))) return st;
+  if ((st = upload(P, &P->d_ectr_ptr, ectr_ptr.data(), ectr_ptr.size()))) return st;
+  if ((st = upload(P, &P->d_ectr_k, ectr_k.data(), std::max<size_t>(ectr_k.size(), 1)))) return st;
+  if ((st = upload(P, &P->d_ectr_val, ectr_val.data(), std::max<size_t>(ectr_val.size(), 1)))) return st;
+  if ((st = upload(P, &P->d_table, tabX.data(), tabX.size()))) return st;
+  if ((st = upload(P, &P->d_table_smax, tabS.data(), tabS.size()))) return st;
+  if ((st = upload(P, &P->d_psi0, reinterpret_cast<const double2*>(d->psi0), blk))) return st;
+  if ((st = upload(P, &P->d_target, reinterpret_cast<const double2*>(d->target), blk))) return st;
+  if (d->omega_diag) {
+    P->has_omega = true;
+    if ((st = upload(P, &P->d_omega, d->omega_diag, (size_t)dim))) return st;
+  }
+  if ((st = dzeros(P, &P->d_u, (size_t)K * N))) return st;
+  if ((st = dzeros(P, &P->d_ms_m, (size_t)N)) || (st = dzeros(P, &P->d_ms_s, (size_t)N)) ||
+      (st = dzeros(P, &P->d_norm1, (size_t)N)))
+    return st;
+  if ((st = dzeros(P, &P->d_psiN, blk)) || (st = dzeros(P, &P->d_ckpt, (size_t)std::max(P->n_ckpt, 1) * blk))) return st;
+  if ((st = dzeros(P, &P->d_part_g, 1)) || (st = dzeros(P, &P->d_part_c2, 1))) return st;
+  if ((st = dzeros(P, &P->d_part_grad, (size_t)N * std::max(K, 1)))) return st;
+  if ((st = dzeros(P, &P->d_g, 1)) || (st = dzeros(P, &P->d_cost, 1)) || (st = dzeros(P, &P->d_parts, 4))) return st;
+  if ((st = dzeros(P, &P->d_grad, (size_t)std::max(K, 1) * N)) || (st = dzeros(P, &P->d_err, 1))) return st;
+  double* c2acc;
+  if ((st = dzeros(P, &c2acc, 1))) return st;
+  c.c2acc = c2acc;
+  c.rowptr = P->d_rowptr;
+  c.h0v = P->d_h0v;
+  c.ectr_ptr = P->d_ectr_ptr;
+  c.ectr_k = P->d_ectr_k;
+  c.ectr_val = P->d_ectr_val;
+  c.u = P->d_u;
+  c.psi0 = P->d_psi0;
+  c.target = P->d_target;
+  c.omega = P->has_omega ? P->d_omega : nullptr;
+  c.psiN = P->d_psiN;
+  c.ckpt = P->d_ckpt;
+  c.part_g = P->d_part_g;
+  c.part_c2 = P->d_part_c2;
+  c.g_final = P->d_g;
+  c.part_grad = P->d_part_grad;
+  c.cptr = P->d_cptr;
+  c.cval = P->d_cval;
+  c.err = P->d_err;
+  P->m_host.assign(N, 0);
+  P->s_host.assign(N, 0);
+  return GRAPE_OK;
 }
 
 grape_status build(grape_problem* P, const grape_desc* d) {
@@ -325,6 +460,7 @@ grape_status build(grape_problem* P, const grape_desc* d) {
   if (P->table.x_max < 0.0) return fail(GRAPE_ETOL, "no (m, s) pair satisfies E_A <= tau even for ||A||_1 = 0");
   P->m_cap = P->table.m_cap;
   P->s_cap = P->table.s_cap;
+  if (P->precision == GRAPE_TC_FP16) return build_dense(P, d, rowptr, ucol, h0v, cptr, cidx, cval, ectr_ptr, ectr_k, ectr_val);
   // ---- partitions: CTAs per column team (CL) for the forward and the backward sweep.
   // Cost model per Taylor term and CTA, in SM clocks: a * (entries x chains) + b * (rows x chains)
   // + team barrier, with a = 4 FMA per complex multiply-add at 1.7 FP64 lanes/clk (FP32: ~100
@@ -639,8 +775,10 @@ grape_status grape_problem_create(const grape_desc* d, grape_problem** out) {
   if (!(d->dt > 0.0) || !std::isfinite(d->dt)) return fail(GRAPE_EINVAL, "dt must be finite and > 0");
   if (!(d->tau > 0.0 && d->tau < 1.0)) return fail(GRAPE_EINVAL, "tau must be in (0, 1)");
   if (d->m_max < 0 || d->m_max > grape::kMaxTaylor) return fail(GRAPE_EINVAL, "m_max must be in 0..60");
-  if (d->precision != GRAPE_FP64 && d->precision != GRAPE_FP32_BULK)
-    return fail(GRAPE_EINVAL, "precision must be GRAPE_FP64 or GRAPE_FP32_BULK");
+  if (d->precision != GRAPE_FP64 && d->precision != GRAPE_FP32_BULK && d->precision != GRAPE_TC_FP16)
+    return fail(GRAPE_EINVAL, "precision must be GRAPE_FP64, GRAPE_FP32_BULK or GRAPE_TC_FP16");
+  if (d->precision == GRAPE_TC_FP16 && (d->dim % 128 != 0 || d->n_states > 16))
+    return fail(GRAPE_EINVAL, "GRAPE_TC_FP16 needs dim % 128 == 0 and n_states <= 16");
   if (d->cluster < 0 || d->cluster > grape::kMaxCluster) return fail(GRAPE_EINVAL, "cluster must be 0 (automatic) or 1..16");
   if (d->n_controls > 0 && !d->Hk) return fail(GRAPE_EINVAL, "Hk is NULL");
   if (d->bulk_norm_cap < 0.0 || !std::isfinite(d->bulk_norm_cap)) return fail(GRAPE_EINVAL, "bulk_norm_cap must be >= 0");
@@ -671,7 +809,7 @@ grape_status grape_problem_create(const grape_desc* d, grape_problem** out) {
   P->tau = d->tau;
   P->precision = d->precision;
   P->m_cap = d->m_max == 0 ? grape::kMaxTaylor : d->m_max;
-  P->b_cap = d->bulk_norm_cap > 0.0 ? d->bulk_norm_cap : (d->precision == GRAPE_FP32_BULK ? 2.0 : 0.0);
+  P->b_cap = d->bulk_norm_cap > 0.0 ? d->bulk_norm_cap : (d->precision != GRAPE_FP64 ? 2.0 : 0.0);
   P->alloc_fn = d->alloc;
   P->free_fn = d->free;
   P->alloc_ctx = d->alloc_ctx;
@@ -726,12 +864,39 @@ grape_status run_forward(grape_problem* P, const double* u, bool u_on_device, cu
   sp.table_smax = P->d_table_smax;
   sp.m_cap = P->m_cap;
   sp.s_cap = P->s_cap;
-  sp.b_cap = P->b_cap;
   sp.ms_m = P->d_ms_m;
   sp.ms_s = P->d_ms_s;
   sp.norm1 = P->d_norm1;
   sp.err = P->d_err;
+  sp.b_cap = P->b_cap;
   if ((e = grape::launch_schedule(sp, st)) != cudaSuccess) return cuda_fail(e, "launch k_schedule");
+  if (P->dense) {
+    // the host drives one tensor-core product per Taylor term: it needs the schedule
+    if ((e = cudaMemcpyAsync(P->m_host.data(), P->d_ms_m, P->N * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(P->s_host.data(), P->d_ms_s, P->N * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      return cuda_fail(e, "schedule download");
+    if ((e = grape::dense_forward(P->dctx, P->m_host.data(), P->s_host.data(), st)) != cudaSuccess)
+      return cuda_fail(e, "dense forward sweep");
+    grape::FinalizeParams fp{};
+    fp.n_parts = 1;
+    fp.n_states = P->n;
+    fp.N = P->N;
+    fp.K = P->K;
+    fp.w_fid = P->w_fid;
+    fp.w_forbid = P->w_forbid;
+    fp.w_amp = P->w_amp;
+    fp.part_g = P->d_part_g;
+    fp.part_c2 = P->d_part_c2;
+    fp.u = P->d_u;
+    fp.g_out = P->d_g;
+    fp.cost_out = P->d_cost;
+    fp.parts_out = P->d_parts;
+    if ((e = grape::launch_finalize(fp, st)) != cudaSuccess) return cuda_fail(e, "launch k_finalize");
+    P->forward_done = true;
+    P->evaluated = true;
+    return GRAPE_OK;
+  }
   grape::SweepParams p = sweep_params(P, P->fwd);
   if ((e = grape::launch_forward(p, P->precision, P->fwd.smem, P->fwd.threads, st)) != cudaSuccess)
     return cuda_fail(e, "launch k_forward");
@@ -759,7 +924,10 @@ grape_status run_forward(grape_problem* P, const double* u, bool u_on_device, cu
 grape_status run_backward(grape_problem* P, cudaStream_t st) {
   grape::SweepParams p = sweep_params(P, P->bwd);
   cudaError_t e;
-  if (P->bwd_mode == 2) {
+  if (P->dense) {
+    if ((e = grape::dense_backward(P->dctx, P->m_host.data(), P->s_host.data(), st)) != cudaSuccess)
+      return cuda_fail(e, "dense backward sweep");
+  } else if (P->bwd_mode == 2) {
     p.ring = P->d_ring;
     p.ring_slot = P->ring_slot;
     p.ring_depth = P->ring_depth;
@@ -776,7 +944,7 @@ grape_status run_backward(grape_problem* P, cudaStream_t st) {
   }
   if (P->K > 0) {
     grape::GradReduceParams gp{};
-    gp.n_parts = P->n * P->bwd.CL;
+    gp.n_parts = P->dense ? 1 : P->n * P->bwd.CL;
     gp.N = P->N;
     gp.K = P->K;
     gp.w_amp = P->w_amp;
@@ -985,6 +1153,7 @@ grape_status grape_batch_create(grape_problem* const* probs, int32_t count, int3
   for (int i = 0; i < count; ++i) {
     if (!probs[i]) return fail(GRAPE_EINVAL, "NULL problem in batch");
     if (probs[i]->device != probs[0]->device) return fail(GRAPE_EINVAL, "batch problems must share one device");
+    if (probs[i]->dense) return fail(GRAPE_EINVAL, "GRAPE_TC_FP16 problems are driven from the host and cannot join a batch");
     if (probs[i]->bwd_mode != 1)
       return fail(GRAPE_EINVAL, "batch members must use backward_mode 1 (two-team sweeps wait on each other and must "
                                 "not share the GPU with concurrent kernels)");

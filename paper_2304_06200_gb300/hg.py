@@ -15,7 +15,7 @@ import numpy as np
 from . import _abi
 from ._abi import GrapeDesc, GrapeInfo, GrapeOp, check, lib
 
-PRECISIONS = {"fp64": _abi.GRAPE_FP64, "fp32_bulk": _abi.GRAPE_FP32_BULK}
+PRECISIONS = {"fp64": _abi.GRAPE_FP64, "fp32_bulk": _abi.GRAPE_FP32_BULK, "tc_fp16": _abi.GRAPE_TC_FP16}
 
 
 def _dptr(a: np.ndarray):

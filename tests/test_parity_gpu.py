@@ -304,3 +304,39 @@ def test_autotune_returns_a_correct_problem():
     assert any("ms" in r for r in rep["candidates"])
     cost, grad = hg.cost_and_grad(p.u0)
     _check(p, p.u0, cost, grad)
+
+
+# ---------------------------------------------------------------- dense operator on tensor cores (tcgen05)
+
+TC_RTOL = 1e-5
+
+
+def _dense_problem(n_t, n_c, n, N, seed, drive=10.0):
+    from workloads.transmon import _gate_problem, _subspace_one, transmon_cavity
+    H0, Hk = transmon_cavity(n_t, n_c)
+    dim = n_t * n_c
+    omega = np.array([1.0 if (j // n_c) == n_t - 1 else 0.0 for j in range(dim)])
+    p = _gate_problem(f"dense{dim}", H0, Hk, dim, _subspace_one(n_t, n_c, n), 0.5, N, seed, omega, 1.0, 1.0, 1e-2,
+                      1e-12, {})
+    p.u0 = p.u0 * drive
+    return p
+
+
+@pytest.mark.parametrize("n_t,n_c,n,N", [(4, 32, 4, 5), (8, 32, 8, 4), (8, 16, 3, 6)])
+def test_tensor_core_dense_path_parity(n_t, n_c, n, N):
+    """Dense H: every Taylor product on tcgen05 (FP16 hi/lo, FP32 accumulation), FP64 states."""
+    p = _dense_problem(n_t, n_c, n, N, seed=800 + n_t * n_c)
+    hg = _hg(p, precision="tc_fp16")
+    cost, grad = hg.cost_and_grad(p.u0)
+    _check(p, p.u0, cost, grad, cost_rtol=TC_RTOL, grad_rtol=TC_RTOL)
+    c2, g2 = hg.cost_and_grad(p.u0)        # repeatable (deterministic cluster reduction)
+    assert c2 == cost and np.array_equal(g2, grad)
+
+
+def test_tensor_core_dense_d2048_matches_fp64_path():
+    """d = 2048 (transmon 8 x cavity 256): tensor-core dense path against the FP64 sparse kernels."""
+    p = _dense_problem(8, 256, 16, 3, seed=4242, drive=5.0)
+    c64, g64 = _hg(p, precision="fp64").cost_and_grad(p.u0)
+    ctc, gtc = _hg(p, precision="tc_fp16").cost_and_grad(p.u0)
+    assert abs(ctc - c64) <= TC_RTOL * abs(c64)
+    assert np.linalg.norm(gtc - g64) / np.linalg.norm(g64) <= TC_RTOL
