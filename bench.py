@@ -55,6 +55,7 @@ def parse_args(argv=None):
     ap.add_argument("--c4", action="store_true", help="also run the d = 16000 workload in FP32 bulk and FP64")
     ap.add_argument("--dense", action="store_true", help="also run the dense d = 2048 variant on the tensor cores")
     ap.add_argument("--dense-steps", type=int, default=20)
+    ap.add_argument("--backward-mode", type=int, default=0, help="0 auto, 1 one team per column, 2 two teams")
     return ap.parse_args(argv)
 
 
@@ -268,7 +269,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     torch.cuda.reset_peak_memory_stats(dev)
     mem0 = torch.cuda.memory_allocated(dev)
-    hg = GrapeProblem(p, device=local)
+    hg = GrapeProblem(p, device=local, backward_mode=args.backward_mode)
     u = torch.tensor(p.u0, dtype=torch.float64, device=dev)
     cost = torch.zeros((), dtype=torch.float64, device=dev)
     grad = torch.zeros((p.n_controls, p.n_steps), dtype=torch.float64, device=dev)

@@ -219,8 +219,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_apply(ApplyArgs a) {
         if (h < ncols) {
           const float d1r = __uint_as_float(r1[2 * j]), d1i = __uint_as_float(r1[2 * j + 1]);
           const float d2r = __uint_as_float(r2[2 * j]), d2i = __uint_as_float(r2[2 * j + 1]);
-          part[row * 2 * ncols + 2 * h] = d1r - d2i;       // yr = Br xr - Bi xi
-          part[row * 2 * ncols + 2 * h + 1] = d1i + d2r;   // yi = Br xi + Bi xr
+          part[(2 * h) * kTM + row] = d1r - d2i;       // yr = Br xr - Bi xi
+          part[(2 * h + 1) * kTM + row] = d1i + d2r;   // yi = Br xi + Bi xr
         }
       }
     }
@@ -229,14 +229,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_apply(ApplyArgs a) {
   // deterministic K-split reduction over the cluster: rank 0 sums ranks 0..KS-1 in order
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
   if (ks == 0) {
+    const float* parts[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      parts[r] = part;
+      if (r < KS) asm volatile("mapa.u64 %0, %1, %2;" : "=l"(parts[r]) : "l"(part), "r"(r));
+    }
     for (int idx = tid; idx < kTM * ncols; idx += kThreads) {
-      const int row = idx / ncols, h = idx % ncols;
+      const int row = idx % kTM, h = idx / kTM;   // consecutive threads: consecutive rows
+      float vr[8], vi[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        if (r < KS) {
+          vr[r] = parts[r][(2 * h) * kTM + row];
+          vi[r] = parts[r][(2 * h + 1) * kTM + row];
+        }
+      }
       float sr = 0.f, si = 0.f;
-      for (int r = 0; r < KS; ++r) {
-        const float* pr;
-        asm volatile("mapa.u64 %0, %1, %2;" : "=l"(pr) : "l"(part), "r"(r));
-        sr += pr[row * 2 * ncols + 2 * h];
-        si += pr[row * 2 * ncols + 2 * h + 1];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        if (r < KS) {
+          sr += vr[r];
+          si += vi[r];
+        }
       }
       a.y[(int64_t)h * a.d + row0 + row] = make_float2(a.alpha * sr, a.alpha * si);
     }
@@ -558,8 +573,7 @@ static cudaError_t apply(const DenseCtx& c, int ncols, float alpha, float2* y, c
   a.alpha = alpha;
   a.err = c.err;
   const int smem = dense_apply_smem(a.nreal);
-  cudaError_t e = cudaFuncSetAttribute(k_dense_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(c.ksplit, c.d / kTM);
   cfg.blockDim = dim3(kThreads);
@@ -584,6 +598,38 @@ static cudaError_t apply(const DenseCtx& c, int ncols, float alpha, float2* y, c
     _e = cudaGetLastError();               \
     if (_e != cudaSuccess) return _e;      \
   } while (0)
+
+// Kernel attributes are process-wide settings: set them once (outside any stream capture).
+cudaError_t dense_prepare() {
+  return cudaFuncSetAttribute(k_dense_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, dense_apply_smem(64));
+}
+
+// K-split (cluster size) for dimension d: the largest of 8, 4, 2, 1 whose d/128 clusters can all be
+// resident at once (a cluster left for a second wave doubles the time of every product) and whose
+// K range per CTA is a whole number of 64-wide chunks.
+int dense_choose_ksplit(int d) {
+  for (int ks = 8; ks >= 1; ks /= 2) {
+    if (d % ks != 0 || (d / ks) % kKC != 0) continue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ks, d / kTM);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = dense_apply_smem(64);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = ks;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int active = 0;
+    if (cudaOccupancyMaxActiveClusters(&active, k_dense_apply, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (active >= d / kTM) return ks;
+  }
+  return 1;
+}
 
 cudaError_t dense_forward(const DenseCtx& c, const int* m_host, const int* s_host, cudaStream_t st) {
   const int d = c.d, n = c.n;

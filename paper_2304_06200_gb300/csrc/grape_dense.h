@@ -44,6 +44,8 @@ struct DenseCtx {
 };
 
 int dense_apply_smem(int nreal);
+cudaError_t dense_prepare();
+int dense_choose_ksplit(int d);
 cudaError_t dense_forward(const DenseCtx& c, const int* m_host, const int* s_host, cudaStream_t st);
 cudaError_t dense_backward(const DenseCtx& c, const int* m_host, const int* s_host, cudaStream_t st);
 

@@ -196,6 +196,10 @@ struct grape_problem {
   bool dense = false;
   grape::DenseCtx dctx{};
   std::vector<int> m_host, s_host;
+  // CUDA graphs of the dense sweeps, valid for the schedule they were recorded with
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t fwd_exec = nullptr, bwd_exec = nullptr;
+  std::vector<int> fwd_sched, bwd_sched;
   bool forward_done = false;
   bool evaluated = false;
   cudaStream_t last_stream = nullptr;
@@ -216,6 +220,11 @@ struct grape_problem {
     return p;
   }
   void release() {
+    if (fwd_exec) cudaGraphExecDestroy(fwd_exec);
+    if (bwd_exec) cudaGraphExecDestroy(bwd_exec);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    fwd_exec = bwd_exec = nullptr;
+    cap_stream = nullptr;
     for (auto& a : allocations) {
       if (free_fn) free_fn(a.first, a.second, alloc_ctx);
       else cudaFree(a.first);
@@ -284,8 +293,7 @@ grape_status build_dense(grape_problem* P, const grape_desc* d, const std::vecto
   c.n = n;
   c.N = N;
   c.K = K;
-  c.ksplit = 8;
-  while (c.ksplit > 1 && (dim / c.ksplit < 64 || (dim / c.ksplit) % 64 != 0)) c.ksplit /= 2;
+  c.ksplit = 1;   // chosen below, after the kernel attributes are set
   c.dt = P->dt;
   c.w_fid = P->w_fid;
   c.w_forbid = P->w_forbid;
@@ -380,7 +388,41 @@ grape_status build_dense(grape_problem* P, const grape_desc* d, const std::vecto
   c.err = P->d_err;
   P->m_host.assign(N, 0);
   P->s_host.assign(N, 0);
+  cudaError_t e = grape::dense_prepare();
+  if (e != cudaSuccess) return cuda_fail(e, "dense kernel attributes");
+  c.ksplit = grape::dense_choose_ksplit((int)dim);
+  if ((e = cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(e, "cudaStreamCreate");
   return GRAPE_OK;
+}
+
+// Record `body` (a sequence of launches on one stream) into a CUDA graph on the problem's capture
+// stream, unless `exec` already holds a graph recorded for the same schedule; then launch it on st.
+template <typename Body>
+cudaError_t run_recorded(grape_problem* P, cudaGraphExec_t* exec, std::vector<int>* sched, cudaStream_t st, Body body) {
+  std::vector<int> key(P->m_host);
+  key.insert(key.end(), P->s_host.begin(), P->s_host.end());
+  cudaError_t e;
+  if (!*exec || *sched != key) {
+    if (*exec) {
+      cudaGraphExecDestroy(*exec);
+      *exec = nullptr;
+    }
+    if ((e = cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+    const cudaError_t be = body(P->cap_stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(P->cap_stream, &g);
+    if (be != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return be;
+    }
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return e;
+    *sched = key;
+  }
+  return cudaGraphLaunch(*exec, st);
 }
 
 grape_status build(grape_problem* P, const grape_desc* d) {
@@ -876,8 +918,10 @@ grape_status run_forward(grape_problem* P, const double* u, bool u_on_device, cu
         (e = cudaMemcpyAsync(P->s_host.data(), P->d_ms_s, P->N * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
       return cuda_fail(e, "schedule download");
-    if ((e = grape::dense_forward(P->dctx, P->m_host.data(), P->s_host.data(), st)) != cudaSuccess)
-      return cuda_fail(e, "dense forward sweep");
+    e = run_recorded(P, &P->fwd_exec, &P->fwd_sched, st, [&](cudaStream_t cs) {
+      return grape::dense_forward(P->dctx, P->m_host.data(), P->s_host.data(), cs);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "dense forward sweep");
     grape::FinalizeParams fp{};
     fp.n_parts = 1;
     fp.n_states = P->n;
@@ -925,8 +969,10 @@ grape_status run_backward(grape_problem* P, cudaStream_t st) {
   grape::SweepParams p = sweep_params(P, P->bwd);
   cudaError_t e;
   if (P->dense) {
-    if ((e = grape::dense_backward(P->dctx, P->m_host.data(), P->s_host.data(), st)) != cudaSuccess)
-      return cuda_fail(e, "dense backward sweep");
+    e = run_recorded(P, &P->bwd_exec, &P->bwd_sched, st, [&](cudaStream_t cs) {
+      return grape::dense_backward(P->dctx, P->m_host.data(), P->s_host.data(), cs);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "dense backward sweep");
   } else if (P->bwd_mode == 2) {
     p.ring = P->d_ring;
     p.ring_slot = P->ring_slot;
