@@ -30,16 +30,20 @@ def cost_and_grad_fullad(problem, u):
     if problem.omega is not None:
         om = torch.tensor(np.asarray(problem.omega), dtype=torch.float64)[:, None]
     c2 = torch.zeros((), dtype=torch.float64)
+    c3 = torch.zeros((), dtype=torch.float64)
     for step in range(N):
         H = H0 + torch.einsum("k,kij->ij", u_t[:, step].to(torch.complex128), Hk)
         U = torch.linalg.matrix_exp(-1j * problem.dt * H)
         psi = U @ psi
         if om is not None:
             c2 = c2 + torch.sum(om * (psi.real ** 2 + psi.imag ** 2))
+        gk = torch.sum(torch.conj(target) * psi)
+        c3 = c3 + gk.real ** 2 + gk.imag ** 2
     g = torch.sum(torch.conj(target) * psi)
     C1 = 1.0 - (g.real ** 2 + g.imag ** 2) / n ** 2
     C2 = c2 / (N * n)
     Camp = torch.sum(u_t ** 2) / N
-    cost = problem.w_fid * C1 + problem.w_forbid * C2 + problem.w_amp * Camp
+    C3 = 1.0 - c3 / (N * n ** 2)
+    cost = problem.w_fid * C1 + problem.w_forbid * C2 + problem.w_amp * Camp + getattr(problem, "w_tint", 0.0) * C3
     cost.backward()
     return float(cost.detach()), u_t.grad.detach().numpy().copy()

@@ -13,10 +13,11 @@ CUDA path is compared with.  It is deliberately slow and obvious:
 
 Cost (Sec. II composite cost, with the readings listed in the design notes):
 
-    C   = w_fid * C1 + w_forbid * C2 + w_amp * C_amp
+    C   = w_fid * C1 + w_forbid * C2 + w_amp * C_amp + w_tint * C3
     C1  = 1 - |g / n|^2,      g = sum_h <phi_T^h | psi_N^h>          (Eq. (C1st); gate form Sec. III.A)
     C2  = 1/(N n) sum_{n'=1..N} sum_h <psi_n'^h | Omega | psi_n'^h>   (App. A, Eq. (c2st))
     C_amp = 1/N sum_{k,n} u_kn^2                                      (Sec. II "maximal power" penalty)
+    C3  = 1 - 1/(N n^2) sum_{n'=1..N} |g_n'|^2,  g_n' = sum_h <phi_T^h|psi_n'^h>   (App. A, C3st / C3g)
 
 Gradient (Eqs. (stgradient), (gategradient), (C2stgrad)):
 
@@ -24,8 +25,10 @@ Gradient (Eqs. (stgradient), (gategradient), (C2stgrad)):
     dC2/du_kn =  (2/(N n)) Re[ sum_h <Phi_n^h | dU_n/du_kn | psi_{n-1}^h> ]
     dC_amp/du_kn = 2 u_kn / N
 
-with phi_n = U_{n+1}^+ phi_{n+1}, phi_N = phi_T, and Phi_n = U_{n+1}^+ Phi_{n+1} + Omega psi_n,
-Phi_N = Omega psi_N.
+    dC3/du_kn = -(2/(N n^2)) Re[ sum_h <Phi_T,n^h | dU_n/du_kn | psi_{n-1}^h> ]     (App. A, Eq. (state time gradient))
+
+with phi_n = U_{n+1}^+ phi_{n+1}, phi_N = phi_T; Phi_n = U_{n+1}^+ Phi_{n+1} + Omega psi_n,
+Phi_N = Omega psi_N; Phi_T,n = U_{n+1}^+ Phi_T,n+1 + phi_T g_n, Phi_T,N = phi_T g_N (App. A).
 """
 
 from __future__ import annotations
@@ -115,8 +118,11 @@ def _cost_parts(problem, u, psi):
     else:
         C2 = 0.0
     Camp = float(np.sum(np.asarray(u) ** 2)) / N
-    cost = problem.w_fid * C1 + problem.w_forbid * C2 + problem.w_amp * Camp
-    return cost, {"C1": C1, "C2": C2, "C_amp": Camp, "g": g}
+    gs = np.array([np.sum(np.conj(target) * psi[k]) for k in range(1, N + 1)])
+    C3 = 1.0 - float(np.sum(np.abs(gs) ** 2)) / (N * n ** 2)
+    w_tint = getattr(problem, "w_tint", 0.0)
+    cost = problem.w_fid * C1 + problem.w_forbid * C2 + problem.w_amp * Camp + w_tint * C3
+    return cost, {"C1": C1, "C2": C2, "C_amp": Camp, "C3": C3, "g": g, "g_steps": gs}
 
 
 def cost_only(problem, u) -> float:
@@ -139,10 +145,15 @@ def cost_and_grad(problem, u) -> OracleResult:
     use_c2 = problem.omega is not None and problem.w_forbid != 0.0
     om = np.asarray(problem.omega, dtype=np.float64)[:, None] if problem.omega is not None else None
 
+    w_tint = getattr(problem, "w_tint", 0.0)
+    use_c3 = w_tint != 0.0
+    gs = parts["g_steps"]
     dC1 = np.zeros((K, N))
     dC2 = np.zeros((K, N))
+    dC3 = np.zeros((K, N))
     phi = target.copy()                       # phi_N^h = U_T psi_0^h  (gate) / phi_T (state)
     Phi = om * psi[N] if use_c2 else None     # Phi_N^h = Omega psi_N^h (App. A)
+    PhiT = target * gs[N - 1] if use_c3 else None   # Phi_T,N^h = phi_T^h g_N (App. A)
     for step in range(N, 0, -1):              # descending n, as in Fig. 1(b)
         U, lam, V = steps[step - 1]
         for k in range(K):
@@ -151,8 +162,14 @@ def cost_and_grad(problem, u) -> OracleResult:
             dC1[k, step - 1] = -(2.0 / n ** 2) * np.real(np.conj(g) * np.sum(np.conj(phi) * dpsi))
             if use_c2:
                 dC2[k, step - 1] = (2.0 / (N * n)) * np.real(np.sum(np.conj(Phi) * dpsi))
+            if use_c3:
+                dC3[k, step - 1] = -(2.0 / (N * n ** 2)) * np.real(np.sum(np.conj(PhiT) * dpsi))
         phi = U.conj().T @ phi                            # phi_{n-1} = U_n^+ phi_n
         if use_c2 and step - 1 >= 1:
             Phi = U.conj().T @ Phi + om * psi[step - 1]    # Phi_{n-1} = U_n^+ Phi_n + Omega psi_{n-1}
+        if use_c3 and step - 1 >= 1:
+            PhiT = U.conj().T @ PhiT + target * gs[step - 2]   # Phi_T,n-1 = U_n^+ Phi_T,n + phi_T g_{n-1}
     grad = problem.w_fid * dC1 + (problem.w_forbid * dC2 if use_c2 else 0.0) + problem.w_amp * 2.0 * u / N
+    if use_c3:
+        grad = grad + w_tint * dC3
     return OracleResult(cost=cost, grad=grad, parts=parts, psi_N=psi[N])

@@ -240,3 +240,30 @@ def test_norm_conservation_of_oracle_states():
     p = build_config("c2_gate_d80", n_steps=30)
     psi, _ = forward_states(p, p.u0)
     np.testing.assert_allclose(np.linalg.norm(psi[-1], axis=0), 1.0, atol=1e-13)
+
+
+# ---------------------------------------------------------------- time-integrated infidelity C3 (App. A)
+
+def test_time_integrated_infidelity_rabi_closed_form():
+    """H = u sigma_x, target |e>: |<e|psi_n>|^2 = sin^2(n u dt), C3 = 1 - 1/N sum_n sin^2(n u dt),
+    dC3/du_n = -1/N sum_{n'>=n} dt sin(2 n' u dt) (all H_n commute)."""
+    N, dt, uv = 9, 0.27, 0.6
+    p = two_level_rabi(N, dt)
+    p.w_fid, p.w_forbid, p.w_amp, p.w_tint = 0.0, 0.0, 0.0, 1.0
+    r = cost_and_grad(p, _const_u(N, uv))
+    ns = np.arange(1, N + 1)
+    assert r.cost == pytest.approx(1 - np.mean(np.sin(ns * uv * dt) ** 2), abs=1e-14)
+    expect = -np.array([np.sum(dt * np.sin(2 * ns[n - 1:] * uv * dt)) for n in ns]) / N
+    np.testing.assert_allclose(r.grad[0], expect, atol=1e-13)
+
+
+@pytest.mark.parametrize("gate", [True, False])
+def test_time_integrated_infidelity_gradient_fd_and_fullad(gate):
+    p = random_problem(6, 2, 2, 5, seed=61, gate=gate)
+    p.w_tint = 0.8
+    r = cost_and_grad(p, p.u0)
+    G = _fd_grad(p, p.u0)
+    assert np.linalg.norm(r.grad - G) / np.linalg.norm(G) < 1e-8
+    c_ad, g_ad = cost_and_grad_fullad(p, p.u0)
+    assert r.cost == pytest.approx(c_ad, rel=1e-12)
+    assert np.linalg.norm(r.grad - g_ad) / np.linalg.norm(g_ad) < 1e-9

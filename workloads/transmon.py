@@ -39,6 +39,7 @@ class Problem:
     w_fid: float = 1.0
     w_forbid: float = 0.0
     w_amp: float = 0.0
+    w_tint: float = 0.0            # weight of the time-integrated infidelity C3 (App. A)
     u0: np.ndarray | None = None   # (K, N) float64 seeded controls
     tau: float = 1e-12
     meta: dict = field(default_factory=dict)
