@@ -19,6 +19,7 @@
  *   C1    = 1 - |g / n|^2,  g = sum_h <phi_T^h | psi_N^h>     Eq. (C1st) / gate form, Sec. III.A
  *   C2    = 1/(N n) sum_{n'=1..N} sum_h <psi_n'^h|Omega|psi_n'^h>   App. A, Eq. (c2st)
  *   C_amp = 1/N sum_{k,n} u_kn^2                    amplitude penalty named in Sec. II
+ *   C3    = 1 - 1/(N n^2) sum_n' |g_n'|^2          time-integrated infidelity, App. A (weight w_tint)
  * with n = n_states columns propagated together as one block.
  *
  * Conventions
@@ -119,6 +120,9 @@ typedef struct {
                                   ||B||_1 <= cap, which bounds the largest Taylor term (reduces
                                   FP32-bulk rounding); 0 = default (2.0 for GRAPE_FP32_BULK, no
                                   cap for GRAPE_FP64, i.e. the paper's rule unchanged)            */
+  double w_tint;               /* weight alpha_4 of the time-integrated infidelity
+                                  C3 = 1 - 1/(N n^2) sum_{n'=1..N} |sum_h <phi_T^h|psi_n'^h>|^2
+                                  (App. A, C3st / C3g; 0 = off)                                 */
 } grape_desc;
 
 /* Information about a problem (valid after create; schedule fields after an evaluation). */

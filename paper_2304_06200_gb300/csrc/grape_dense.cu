@@ -495,14 +495,18 @@ __global__ void k_overlap(const double2* __restrict__ psi, const double2* __rest
   }
 }
 
-// chi_N = -(w_fid g / n^2) phi_T + c2w Omega psi_N
+// chi_N = -(w_fid g / n^2) phi_T - (w_tint g_N / (N n^2)) phi_T + c2w Omega psi_N
 __global__ void k_costate_init(const double2* __restrict__ psi, const double2* __restrict__ target,
                                const double* omega, const double2* __restrict__ g, double w_fid, double c2w, int n,
-                               int d, double2* chi) {
+                               int d, double2* chi, const double2* __restrict__ gN, double c3w) {
   const int64_t total = (int64_t)d * n;
   const double nS = (double)n;
   const double2 gg = *g;
-  const double ax = -w_fid * gg.x / (nS * nS), ay = -w_fid * gg.y / (nS * nS);
+  double ax = -w_fid * gg.x / (nS * nS), ay = -w_fid * gg.y / (nS * nS);
+  if (c3w != 0.0) {
+    ax = fma(c3w, gN->x, ax);
+    ay = fma(c3w, gN->y, ay);
+  }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const double2 t = target[i];
     double2 ch = make_double2(ax * t.x - ay * t.y, ax * t.y + ay * t.x);
@@ -515,13 +519,23 @@ __global__ void k_costate_init(const double2* __restrict__ psi, const double2* _
   }
 }
 
+// chi += c2w Omega psi_n + c3w g_n phi_T (the C2 and C3 sources of state psi_n, App. A)
 __global__ void k_chi_source(const double2* __restrict__ psi, const double* __restrict__ omega, double c2w, int64_t total,
-                             int d, double2* chi) {
+                             int d, double2* chi, const double2* __restrict__ target, const double2* __restrict__ gn,
+                             double c3w) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const double w = c2w * omega[i % d];
     double2 ch = chi[i];
-    ch.x = fma(w, psi[i].x, ch.x);
-    ch.y = fma(w, psi[i].y, ch.y);
+    if (c2w != 0.0) {
+      const double w = c2w * omega[i % d];
+      ch.x = fma(w, psi[i].x, ch.x);
+      ch.y = fma(w, psi[i].y, ch.y);
+    }
+    if (c3w != 0.0) {
+      const double cx = c3w * gn->x, cy = c3w * gn->y;
+      const double2 t = target[i];
+      ch.x += cx * t.x - cy * t.y;
+      ch.y += cx * t.y + cy * t.x;
+    }
     chi[i] = ch;
   }
 }
@@ -658,6 +672,10 @@ cudaError_t dense_forward(const DenseCtx& c, const int* m_host, const int* s_hos
       k_c2_add<<<1, 1024, 0, st>>>(c.psi, c.omega, tot, d, c.c2acc);
       DCHK(cudaGetLastError());
     }
+    if (c.w_tint != 0.0) {
+      k_overlap<<<1, 1024, 0, st>>>(c.psi, c.target, tot, c.part_g3 + step);
+      DCHK(cudaGetLastError());
+    }
     if (c.ckpt_every > 0 && (step + 1) % c.ckpt_every == 0 && (step + 1) / c.ckpt_every - 1 < c.n_ckpt)
       DCHK(cudaMemcpyAsync(c.ckpt + (int64_t)((step + 1) / c.ckpt_every - 1) * tot, c.psi, tot * sizeof(double2),
                            cudaMemcpyDeviceToDevice, st));
@@ -674,8 +692,10 @@ cudaError_t dense_backward(const DenseCtx& c, const int* m_host, const int* s_ho
   const int64_t tot = (int64_t)d * n;
   const int g = ew_grid(tot);
   const double c2w = (c.omega && c.w_forbid != 0.0) ? c.w_forbid / ((double)c.N * n) : 0.0;
+  const double c3w = c.w_tint != 0.0 ? -c.w_tint / ((double)c.N * n * n) : 0.0;
   DCHK(cudaMemcpyAsync(c.psi, c.psiN, tot * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-  k_costate_init<<<g, 256, 0, st>>>(c.psiN, c.target, c.omega, c.g_final, c.w_fid, c2w, n, d, c.chi);
+  k_costate_init<<<g, 256, 0, st>>>(c.psiN, c.target, c.omega, c.g_final, c.w_fid, c2w, n, d, c.chi, c.g3 + (c.N - 1),
+                                    c3w);
   DCHK(cudaGetLastError());
   for (int step = c.N - 1; step >= 0; --step) {
     const int m = m_host[step], s = s_host[step];
@@ -717,8 +737,8 @@ cudaError_t dense_backward(const DenseCtx& c, const int* m_host, const int* s_ho
       if (c.ckpt_every > 0 && step % c.ckpt_every == 0 && step / c.ckpt_every - 1 < c.n_ckpt)
         DCHK(cudaMemcpyAsync(c.psi, c.ckpt + (int64_t)(step / c.ckpt_every - 1) * tot, tot * sizeof(double2),
                              cudaMemcpyDeviceToDevice, st));
-      if (c2w != 0.0) {
-        k_chi_source<<<g, 256, 0, st>>>(c.psi, c.omega, c2w, tot, d, c.chi);
+      if (c2w != 0.0 || c3w != 0.0) {
+        k_chi_source<<<g, 256, 0, st>>>(c.psi, c.omega, c2w, tot, d, c.chi, c.target, c.g3 + (step - 1), c3w);
         DCHK(cudaGetLastError());
       }
     }

@@ -10,7 +10,7 @@ namespace grape {
 
 struct DenseCtx {
   int d, n, N, K, ksplit;
-  double dt, w_fid, w_forbid;
+  double dt, w_fid, w_forbid, w_tint;
   int ckpt_every, n_ckpt;
   double inv_fact[62];
   // operator of the current step (FP16 hi/lo of Br and Bi, d x d row-major) and work blocks
@@ -39,6 +39,8 @@ struct DenseCtx {
   double* part_c2;          // 1
   double* c2acc;            // 1
   const double2* g_final;
+  double2* part_g3;         // N per-step overlaps (C3) written by the forward sweep
+  const double2* g3;        // N, after the finalize
   double* part_grad;        // N x K
   int* err;
 };

@@ -145,6 +145,7 @@ struct grape_problem {
   int K = 0, N = 0, n = 0;
   double dt = 0, w_fid = 0, w_forbid = 0, w_amp = 0, tau = 0;
   double b_cap = 0;   // cap on ||B||_1 = ||A||_1 / s in the schedule (0 = the paper's rule unchanged)
+  double w_tint = 0;  // weight of the time-integrated infidelity C3
   int precision = 0, ckpt_every = 0, n_ckpt = 0, m_cap = 0, s_cap = 0, sigma = 0;
   int64_t nnz = 0, n_ctr = 0;
   bool has_omega = false;
@@ -179,6 +180,8 @@ struct grape_problem {
   double* d_part_c2 = nullptr;
   double* d_part_grad = nullptr;
   double2* d_g = nullptr;
+  double2* d_part_g3 = nullptr;   // per-step overlap partials (C3)
+  double2* d_g3 = nullptr;
   double* d_cost = nullptr;
   double* d_parts = nullptr;
   double* d_grad = nullptr;
@@ -363,7 +366,8 @@ grape_status build_dense(grape_problem* P, const grape_desc* d, const std::vecto
   if ((st = dzeros(P, &P->d_psiN, blk)) || (st = dzeros(P, &P->d_ckpt, (size_t)std::max(P->n_ckpt, 1) * blk))) return st;
   if ((st = dzeros(P, &P->d_part_g, 1)) || (st = dzeros(P, &P->d_part_c2, 1))) return st;
   if ((st = dzeros(P, &P->d_part_grad, (size_t)N * std::max(K, 1)))) return st;
-  if ((st = dzeros(P, &P->d_g, 1)) || (st = dzeros(P, &P->d_cost, 1)) || (st = dzeros(P, &P->d_parts, 4))) return st;
+  if ((st = dzeros(P, &P->d_g, 1)) || (st = dzeros(P, &P->d_cost, 1)) || (st = dzeros(P, &P->d_parts, 5))) return st;
+  if ((st = dzeros(P, &P->d_part_g3, (size_t)N)) || (st = dzeros(P, &P->d_g3, (size_t)N))) return st;
   if ((st = dzeros(P, &P->d_grad, (size_t)std::max(K, 1) * N)) || (st = dzeros(P, &P->d_err, 1))) return st;
   double* c2acc;
   if ((st = dzeros(P, &c2acc, 1))) return st;
@@ -382,6 +386,9 @@ grape_status build_dense(grape_problem* P, const grape_desc* d, const std::vecto
   c.part_g = P->d_part_g;
   c.part_c2 = P->d_part_c2;
   c.g_final = P->d_g;
+  c.w_tint = P->w_tint;
+  c.part_g3 = P->d_part_g3;
+  c.g3 = P->d_g3;
   c.part_grad = P->d_part_grad;
   c.cptr = P->d_cptr;
   c.cval = P->d_cval;
@@ -685,9 +692,10 @@ grape_status build(grape_problem* P, const grape_desc* d) {
   if ((st = dzeros(P, &P->d_part_grad, (size_t)parts_b * P->N * std::max(K, 1)))) return st;
   if ((st = dzeros(P, &P->d_g, 1))) return st;
   if ((st = dzeros(P, &P->d_cost, 1))) return st;
-  if ((st = dzeros(P, &P->d_parts, 4))) return st;
+  if ((st = dzeros(P, &P->d_parts, 5))) return st;
   if ((st = dzeros(P, &P->d_grad, (size_t)std::max(K, 1) * P->N))) return st;
   if ((st = dzeros(P, &P->d_err, 1))) return st;
+  if ((st = dzeros(P, &P->d_part_g3, (size_t)parts_f * P->N)) || (st = dzeros(P, &P->d_g3, (size_t)P->N))) return st;
   if (P->bwd_mode == 2) {
     P->ring_slot = (int64_t)(1 + P->m_cap) * dim;
     if ((st = dzeros(P, &P->d_ring, (size_t)P->n * P->ring_depth * P->ring_slot))) return st;
@@ -711,6 +719,9 @@ grape::SweepParams sweep_params(grape_problem* P, const KPlan& kp) {
   p.w_fid = P->w_fid;
   p.w_forbid = P->w_forbid;
   p.w_amp = P->w_amp;
+  p.w_tint = P->w_tint;
+  p.part_g3 = P->d_part_g3;
+  p.g3 = P->d_g3;
   p.ckpt_every = P->ckpt_every;
   p.n_ckpt = P->n_ckpt;
   p.m_cap = P->m_cap;
@@ -826,7 +837,7 @@ grape_status grape_problem_create(const grape_desc* d, grape_problem** out) {
   if (d->bulk_norm_cap < 0.0 || !std::isfinite(d->bulk_norm_cap)) return fail(GRAPE_EINVAL, "bulk_norm_cap must be >= 0");
   if (!d->psi0 || !d->target) return fail(GRAPE_EINVAL, "psi0 / target is NULL");
   if ((d->alloc == nullptr) != (d->free == nullptr)) return fail(GRAPE_EINVAL, "alloc and free must both be set or both NULL");
-  const double ws[3] = {d->w_fid, d->w_forbid, d->w_amp};
+  const double ws[4] = {d->w_fid, d->w_forbid, d->w_amp, d->w_tint};
   for (double w : ws)
     if (!std::isfinite(w)) return fail(GRAPE_EINVAL, "weights must be finite");
   const size_t blk = (size_t)d->dim * d->n_states * 2;
@@ -848,6 +859,7 @@ grape_status grape_problem_create(const grape_desc* d, grape_problem** out) {
   P->w_fid = d->w_fid;
   P->w_forbid = d->w_forbid;
   P->w_amp = d->w_amp;
+  P->w_tint = d->w_tint;
   P->tau = d->tau;
   P->precision = d->precision;
   P->m_cap = d->m_max == 0 ? grape::kMaxTaylor : d->m_max;
@@ -930,6 +942,9 @@ grape_status run_forward(grape_problem* P, const double* u, bool u_on_device, cu
     fp.w_fid = P->w_fid;
     fp.w_forbid = P->w_forbid;
     fp.w_amp = P->w_amp;
+    fp.w_tint = P->w_tint;
+    fp.part_g3 = P->w_tint != 0.0 ? P->d_part_g3 : nullptr;
+    fp.g3_out = P->d_g3;
     fp.part_g = P->d_part_g;
     fp.part_c2 = P->d_part_c2;
     fp.u = P->d_u;
@@ -952,6 +967,9 @@ grape_status run_forward(grape_problem* P, const double* u, bool u_on_device, cu
   fp.w_fid = P->w_fid;
   fp.w_forbid = P->w_forbid;
   fp.w_amp = P->w_amp;
+  fp.w_tint = P->w_tint;
+  fp.part_g3 = P->w_tint != 0.0 ? P->d_part_g3 : nullptr;
+  fp.g3_out = P->d_g3;
   fp.part_g = P->d_part_g;
   fp.part_c2 = P->d_part_c2;
   fp.u = P->d_u;

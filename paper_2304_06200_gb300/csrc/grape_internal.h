@@ -23,7 +23,7 @@ struct SweepParams {
   // problem
   int dim, K, N, n_states, CL, R;      // CL = CTAs per column team, R = rows per CTA
   double dt;
-  double w_fid, w_forbid, w_amp;
+  double w_fid, w_forbid, w_amp, w_tint;
   int ckpt_every;                      // 0 = no checkpoints
   int n_ckpt;                          // number of stored checkpoints
   int m_cap;
@@ -51,6 +51,8 @@ struct SweepParams {
   double* part_c2;                     // n_teams * CL
   double* part_grad;                   // (n_teams * CL) x N x K
   const double2* g_final;              // device scalar g (after the forward finalize)
+  double2* part_g3;                    // (n_teams * CL) x N: per-step overlap partials (C3)
+  const double2* g3;                   // N per-step overlaps g_n (after the finalize)
   // scratch for buffers that do not fit in shared memory (per CTA slices)
   double2* scratch;
   int64_t scratch_stride;              // doubles2 per CTA
@@ -94,13 +96,15 @@ struct ScheduleParams {
 
 struct FinalizeParams {
   int n_parts, n_states, N, K;
-  double w_fid, w_forbid, w_amp;
+  double w_fid, w_forbid, w_amp, w_tint;
+  const double2* part_g3;              // n_parts x N (C3), or nullptr
+  double2* g3_out;                     // N
   const double2* part_g;
   const double* part_c2;
   const double* u;
   double2* g_out;
   double* cost_out;
-  double* parts_out;                   // [C1, C2, C_amp, |g|]
+  double* parts_out;                   // [C1, C2, C_amp, |g|, C3]
 };
 
 struct GradReduceParams {

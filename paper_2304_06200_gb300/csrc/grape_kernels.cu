@@ -448,6 +448,13 @@ __global__ void __launch_bounds__(512, 1) k_forward(SweepParams p) {
         c2acc = fma(p.omega[r0 + i], v.x * v.x + v.y * v.y, c2acc);
       }
     }
+    if (p.w_tint != 0.0) {   // per-step overlap partial for C3 (App. A)
+      double2 gl = make_double2(0.0, 0.0);
+      for (int i = threadIdx.x; i < nrows; i += blockDim.x) cmac_conj(gl, p.target[col0 + i], c.psi[i]);
+      const double gx = block_sum(gl.x, red);
+      const double gy = block_sum(gl.y, red);
+      if (threadIdx.x == 0) p.part_g3[(int64_t)part * p.N + n] = make_double2(gx, gy);
+    }
     if (p.ckpt_every > 0 && (n + 1) % p.ckpt_every == 0) {
       const int slot = (n + 1) / p.ckpt_every - 1;
       if (slot < p.n_ckpt) {
@@ -490,7 +497,13 @@ __device__ __forceinline__ void costate_init(const SweepParams& p, double2* psi,
                                              int nrows, double c2w) {
   const double nS = (double)p.n_states;
   const double2 g = *p.g_final;
-  const double2 coefA = make_double2(-p.w_fid * g.x / (nS * nS), -p.w_fid * g.y / (nS * nS));
+  double2 coefA = make_double2(-p.w_fid * g.x / (nS * nS), -p.w_fid * g.y / (nS * nS));
+  if (p.w_tint != 0.0) {   // C3 source of the last state: -(w_tint / (N n^2)) g_N phi_T
+    const double c3w = -p.w_tint / ((double)p.N * nS * nS);
+    const double2 gN = p.g3[p.N - 1];
+    coefA.x = fma(c3w, gN.x, coefA.x);
+    coefA.y = fma(c3w, gN.y, coefA.y);
+  }
   for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
     const double2 v = p.psiN[col0 + i];
     psi[i] = v;
@@ -651,6 +664,20 @@ __device__ __forceinline__ void zero_w(const SweepParams& p, double2* W, float2*
 __device__ __forceinline__ void step_end(const SweepParams& p, double2* psi, double2* chi, int n, int col, int r0,
                                          int nrows, double c2w) {
   if (n <= 0) return;
+  if (p.w_tint != 0.0) {   // C3 source: -(w_tint / (N n^2)) g_n phi_T for the state psi_n (App. A recursion)
+    const double nS = (double)p.n_states;
+    const double c3w = -p.w_tint / ((double)p.N * nS * nS);
+    const double2 gn = p.g3[n - 1];
+    const double2 cf = make_double2(c3w * gn.x, c3w * gn.y);
+    const double2* tg = p.target + (int64_t)col * p.dim + r0;
+    for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+      const double2 t = tg[i];
+      double2 ch = chi[i];
+      ch.x += cf.x * t.x - cf.y * t.y;
+      ch.y += cf.x * t.y + cf.y * t.x;
+      chi[i] = ch;
+    }
+  }
   if (p.ckpt_every > 0 && n % p.ckpt_every == 0 && n / p.ckpt_every - 1 < p.n_ckpt) {
     const double2* srcp = p.ckpt + ((int64_t)(n / p.ckpt_every - 1) * p.n_states + col) * p.dim + r0;
     for (int i = threadIdx.x; i < nrows; i += blockDim.x) psi[i] = srcp[i];
@@ -900,22 +927,38 @@ __global__ void __launch_bounds__(256) k_finalize(FinalizeParams p) {
     c2 += p.part_c2[i];
   }
   for (int64_t i = threadIdx.x; i < (int64_t)p.K * p.N; i += blockDim.x) a2 = fma(p.u[i], p.u[i], a2);
+  double g3sq = 0.0;
+  if (p.part_g3) {   // per-step overlaps g_n (C3): fixed-order sums over the partials
+    for (int n = threadIdx.x; n < p.N; n += blockDim.x) {
+      double sx = 0.0, sy = 0.0;
+      for (int i = 0; i < p.n_parts; ++i) {
+        const double2 v = p.part_g3[(int64_t)i * p.N + n];
+        sx += v.x;
+        sy += v.y;
+      }
+      p.g3_out[n] = make_double2(sx, sy);
+      g3sq = fma(sx, sx, fma(sy, sy, g3sq));
+    }
+  }
   gx = block_sum(gx, red);
   gy = block_sum(gy, red);
   c2 = block_sum(c2, red);
   a2 = block_sum(a2, red);
+  g3sq = block_sum(g3sq, red);
   if (threadIdx.x == 0) {
     const double n = (double)p.n_states;
     const double C1 = 1.0 - (gx * gx + gy * gy) / (n * n);
     const double C2 = c2 / ((double)p.N * n);
     const double Ca = a2 / (double)p.N;
+    const double C3 = p.part_g3 ? 1.0 - g3sq / ((double)p.N * n * n) : 0.0;
     *p.g_out = make_double2(gx, gy);
-    *p.cost_out = p.w_fid * C1 + p.w_forbid * C2 + p.w_amp * Ca;
+    *p.cost_out = p.w_fid * C1 + p.w_forbid * C2 + p.w_amp * Ca + (p.part_g3 ? p.w_tint * C3 : 0.0);
     if (p.parts_out) {
       p.parts_out[0] = C1;
       p.parts_out[1] = C2;
       p.parts_out[2] = Ca;
       p.parts_out[3] = sqrt(gx * gx + gy * gy);
+      p.parts_out[4] = C3;
     }
   }
 }

@@ -124,6 +124,7 @@ class GrapeProblem:
         d.alloc_ctx = None
         d.backward_mode = int(backward_mode)
         d.bulk_norm_cap = float(bulk_norm_cap)
+        d.w_tint = float(getattr(problem, "w_tint", 0.0))
         handle = C.c_void_p()
         check(L.grape_problem_create(C.byref(d), C.byref(handle)), "grape_problem_create")
         self._h = handle

@@ -340,3 +340,33 @@ def test_tensor_core_dense_d2048_matches_fp64_path():
     ctc, gtc = _hg(p, precision="tc_fp16").cost_and_grad(p.u0)
     assert abs(ctc - c64) <= TC_RTOL * abs(c64)
     assert np.linalg.norm(gtc - g64) / np.linalg.norm(g64) <= TC_RTOL
+
+
+# ---------------------------------------------------------------- time-integrated infidelity C3 (App. A)
+
+@pytest.mark.parametrize("name,N,drive", [("c2_gate_d80", 150, 20.0), ("c1_state_transfer_d30", None, 1.0)])
+def test_time_integrated_infidelity_parity(name, N, drive):
+    p = build_config(name, n_steps=N)
+    p.w_tint = 0.7
+    u = p.u0 * drive
+    ref = oracle_cost_and_grad(p, u)
+    assert ref.parts["C3"] > 0.1
+    for mode in (1, 2):
+        hg = _hg(p, backward_mode=mode)
+        cost, grad = hg.cost_and_grad(u)
+        _check(p, u, cost, grad, ref=ref)
+
+
+def test_time_integrated_infidelity_random_and_reduced_precision():
+    p = random_problem(130, 3, 3, 9, seed=3131)
+    p.w_tint = 1.3
+    ref = oracle_cost_and_grad(p, p.u0)
+    cost, grad = _hg(p, cluster=4).cost_and_grad(p.u0)
+    _check(p, p.u0, cost, grad, ref=ref)
+    cost, grad = _hg(p, precision="fp32_bulk").cost_and_grad(p.u0)
+    _check(p, p.u0, cost, grad, cost_rtol=FP32_RTOL, grad_rtol=FP32_RTOL, ref=ref)
+    q = _dense_problem(4, 32, 4, 5, seed=77)
+    q.w_tint = 0.9
+    refq = oracle_cost_and_grad(q, q.u0)
+    cost, grad = _hg(q, precision="tc_fp16").cost_and_grad(q.u0)
+    _check(q, q.u0, cost, grad, cost_rtol=TC_RTOL, grad_rtol=TC_RTOL, ref=refq)
