@@ -170,6 +170,15 @@ grape_status grape_cost(grape_problem* prob, const double* u, double* cost, int3
  * GRAPE_ESTATE if no forward sweep has run. */
 grape_status grape_grad(grape_problem* prob, double* grad, int32_t on_device, void* stream);
 
+/* GRAPE by steepest descent (Sec. II: a <- a - eta grad C): n_iter iterations, each a full
+ * evaluation (forward sweep, cost, backward sweep, gradient) followed by the update, recorded once
+ * into a CUDA graph (on the first call and whenever eta changes) and launched n_iter times.
+ *   u      K x N controls: initial values in, final values out (host or device per on_device).
+ *   costs  n_iter doubles: the cost at the start of each iteration.
+ * Not available for GRAPE_TC_FP16 problems (their sweeps are driven from the host). */
+grape_status grape_optimize(grape_problem* prob, double* u, int32_t n_iter, double eta, double* costs,
+                            int32_t on_device, void* stream);
+
 /* Wait for the problem's pending work on `stream` and return the device error word
  * (GRAPE_OK, GRAPE_ETOL, GRAPE_ENONFINITE or GRAPE_ETIMEOUT); the word is then cleared. */
 grape_status grape_sync_status(grape_problem* prob, void* stream);

@@ -20,7 +20,7 @@ EXPORTED = [
     "grape_problem_create", "grape_problem_destroy", "grape_cost_and_grad", "grape_cost", "grape_grad",
     "grape_sync_status", "grape_problem_info", "grape_step_schedule", "grape_select_ms", "grape_error_bound",
     "grape_status_string", "grape_last_error", "grape_abi_version", "grape_taylor_step_noalloc",
-    "grape_batch_create", "grape_batch_destroy", "grape_batch_cost_and_grad",
+    "grape_batch_create", "grape_batch_destroy", "grape_batch_cost_and_grad", "grape_optimize",
 ]
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -94,6 +94,8 @@ def lib(path: str | None = None):
     L.grape_batch_destroy.restype = None
     L.grape_batch_cost_and_grad.argtypes = [P, C.POINTER(P), P, C.POINTER(P), C.c_int32, P]
     L.grape_batch_cost_and_grad.restype = C.c_int
+    L.grape_optimize.argtypes = [P, P, C.c_int32, C.c_double, P, C.c_int32, P]
+    L.grape_optimize.restype = C.c_int
     L.grape_status_string.argtypes = [C.c_int]
     L.grape_status_string.restype = C.c_char_p
     L.grape_last_error.argtypes = []

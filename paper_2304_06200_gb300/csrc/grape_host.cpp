@@ -199,6 +199,12 @@ struct grape_problem {
   bool dense = false;
   grape::DenseCtx dctx{};
   std::vector<int> m_host, s_host;
+  // steepest-descent iteration recorded as a CUDA graph (grape_optimize)
+  cudaGraphExec_t opt_exec = nullptr;
+  double opt_eta = 0.0;
+  double* d_costs = nullptr;
+  int d_costs_cap = 0;
+  int* d_counter = nullptr;
   // CUDA graphs of the dense sweeps, valid for the schedule they were recorded with
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t fwd_exec = nullptr, bwd_exec = nullptr;
@@ -223,6 +229,8 @@ struct grape_problem {
     return p;
   }
   void release() {
+    if (opt_exec) cudaGraphExecDestroy(opt_exec);
+    opt_exec = nullptr;
     if (fwd_exec) cudaGraphExecDestroy(fwd_exec);
     if (bwd_exec) cudaGraphExecDestroy(bwd_exec);
     if (cap_stream) cudaStreamDestroy(cap_stream);
@@ -900,7 +908,7 @@ namespace {
 grape_status run_forward(grape_problem* P, const double* u, bool u_on_device, cudaStream_t st) {
   const size_t ubytes = (size_t)P->K * P->N * sizeof(double);
   cudaError_t e = cudaSuccess;
-  if (ubytes)
+  if (ubytes && u != P->d_u)
     e = cudaMemcpyAsync(P->d_u, u, ubytes, u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync (u)");
   grape::ScheduleParams sp{};
@@ -1289,6 +1297,82 @@ grape_status grape_batch_cost_and_grad(grape_batch* B, const double* const* u, d
       if (s) return s;
     }
   }
+  return GRAPE_OK;
+}
+
+grape_status grape_optimize(grape_problem* P, double* u, int32_t n_iter, double eta, double* costs, int32_t on_device,
+                            void* stream) {
+  if (!P || (!u && P->K > 0) || !costs || n_iter < 1) return fail(GRAPE_EINVAL, "bad argument");
+  if (!(eta > 0.0) || !std::isfinite(eta)) return fail(GRAPE_EINVAL, "eta must be finite and > 0");
+  if (P->dense) return fail(GRAPE_EINVAL, "GRAPE_TC_FP16 problems are driven from the host and cannot be recorded");
+  DeviceGuard guard(P->device);
+  if (!guard.ok) return fail(GRAPE_ECUDA, "cudaSetDevice failed");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  P->last_stream = st;
+  cudaError_t e;
+  const size_t ubytes = (size_t)P->K * P->N * sizeof(double);
+  if (P->d_costs_cap < n_iter) {
+    if (P->d_costs && (e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    // an optimizer-owned buffer, grown on demand (recording refers to it, so the graph is recorded again)
+    void* pc = P->dalloc((size_t)n_iter * sizeof(double));
+    if (!pc) return fail(GRAPE_ENOMEM, "device allocation failed");
+    P->d_costs = static_cast<double*>(pc);
+    P->d_costs_cap = n_iter;
+    if (P->opt_exec) {
+      cudaGraphExecDestroy(P->opt_exec);
+      P->opt_exec = nullptr;
+    }
+  }
+  if (!P->d_counter) {
+    void* pc = P->dalloc(sizeof(int));
+    if (!pc) return fail(GRAPE_ENOMEM, "device allocation failed");
+    P->d_counter = static_cast<int*>(pc);
+  }
+  if (ubytes && (e = cudaMemcpyAsync(P->d_u, u, ubytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                     st)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemcpyAsync (u)");
+  if ((e = cudaMemsetAsync(P->d_counter, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  if (!P->opt_exec || P->opt_eta != eta) {
+    if (P->opt_exec) {
+      cudaGraphExecDestroy(P->opt_exec);
+      P->opt_exec = nullptr;
+    }
+    // one evaluation outside the capture sets kernel attributes and constants (not stream work)
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    cudaStream_t cs = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+    grape_status s2 = run_forward(P, P->d_u, true, cs);
+    if (!s2) s2 = run_backward(P, cs);
+    if (!s2 && (e = cudaStreamSynchronize(cs)) != cudaSuccess) s2 = cuda_fail(e, "cudaStreamSynchronize");
+    cudaGraph_t g = nullptr;
+    if (!s2 && (e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      s2 = cuda_fail(e, "cudaStreamBeginCapture");
+    if (!s2) {
+      s2 = run_forward(P, P->d_u, true, cs);
+      if (!s2) s2 = run_backward(P, cs);
+      if (!s2 && (e = grape::launch_sd_update(P->d_u, P->d_grad, (int64_t)P->K * P->N, eta, P->d_cost, P->d_costs,
+                                              P->d_counter, P->d_costs_cap, cs)) != cudaSuccess)
+        s2 = cuda_fail(e, "launch k_sd_update");
+      const cudaError_t ee = cudaStreamEndCapture(cs, &g);
+      if (!s2 && ee != cudaSuccess) s2 = cuda_fail(ee, "cudaStreamEndCapture");
+    }
+    if (!s2 && (e = cudaGraphInstantiate(&P->opt_exec, g, 0)) != cudaSuccess) s2 = cuda_fail(e, "cudaGraphInstantiate");
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (s2) return s2;
+    P->opt_eta = eta;
+  }
+  // the stored sweep state belongs to the last evaluated iterate, not to the updated controls
+  P->forward_done = false;
+  for (int it = 0; it < n_iter; ++it)
+    if ((e = cudaGraphLaunch(P->opt_exec, st)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+  if (ubytes && (e = cudaMemcpyAsync(u, P->d_u, ubytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                     st)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemcpyAsync (u out)");
+  if ((e = cudaMemcpyAsync(costs, P->d_costs, (size_t)n_iter * sizeof(double),
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemcpyAsync (costs)");
+  if (!on_device) return read_error_word(P, st);
   return GRAPE_OK;
 }
 

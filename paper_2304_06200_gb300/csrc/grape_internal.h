@@ -162,6 +162,8 @@ int split_capacity(int precision, int CL, int smem_bytes, int threads);
 cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t st);
 cudaError_t launch_grad_reduce(const GradReduceParams& p, cudaStream_t st);
 cudaError_t check_nonfinite_u(const double* u, int64_t count, int* err, cudaStream_t st);
+cudaError_t launch_sd_update(double* u, const double* grad, int64_t count, double eta, const double* cost, double* costs,
+                             int* counter, int max_count, cudaStream_t st);
 int max_dynamic_smem(int device);
 
 }  // namespace grape

@@ -975,6 +975,29 @@ __global__ void k_grad_reduce(GradReduceParams p) {
   }
 }
 
+// One steepest-descent update a <- a - eta grad C (Sec. II), recording the cost of the evaluation
+// that produced `grad` in costs[*counter] and advancing the counter.  The update is evaluated as
+// u - (eta * g) with separate roundings (no contraction), so a host can reproduce it exactly.
+__global__ void k_sd_update(double* u, const double* __restrict__ grad, int64_t count, double eta,
+                            const double* __restrict__ cost, double* costs, int* counter, int max_count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    u[i] = __dsub_rn(u[i], __dmul_rn(eta, grad[i]));
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int c = *counter;
+    if (c < max_count) costs[c] = *cost;
+    *counter = c + 1;
+  }
+}
+
+cudaError_t launch_sd_update(double* u, const double* grad, int64_t count, double eta, const double* cost, double* costs,
+                             int* counter, int max_count, cudaStream_t st) {
+  int grid = (int)((count + 255) / 256);
+  if (grid < 1) grid = 1;
+  if (grid > 1024) grid = 1024;
+  k_sd_update<<<grid, 256, 0, st>>>(u, grad, count, eta, cost, costs, counter, max_count);
+  return cudaGetLastError();
+}
+
 __global__ void k_check_finite(const double* u, int64_t count, int* err) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
     if (!isfinite(u[i])) set_error(err, kErrNonFinite);

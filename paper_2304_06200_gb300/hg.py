@@ -177,6 +177,14 @@ class GrapeProblem:
         st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
         check(self._lib.grape_sync_status(self._h, st), "grape_sync_status")
 
+    def optimize(self, u: np.ndarray, n_iter: int, eta: float):
+        """Steepest descent (one recorded CUDA graph per iteration): returns (final u, costs per iteration)."""
+        u = np.array(u, dtype=np.float64, order="C", copy=True)
+        costs = np.zeros(int(n_iter))
+        check(self._lib.grape_optimize(self._h, u.ctypes.data, int(n_iter), float(eta), costs.ctypes.data, 0, None),
+              "grape_optimize")
+        return u, costs
+
     # ------------------------------------------------------------------ introspection
     def info(self) -> dict:
         inf = GrapeInfo()

@@ -370,3 +370,50 @@ def test_time_integrated_infidelity_random_and_reduced_precision():
     refq = oracle_cost_and_grad(q, q.u0)
     cost, grad = _hg(q, precision="tc_fp16").cost_and_grad(q.u0)
     _check(q, q.u0, cost, grad, cost_rtol=TC_RTOL, grad_rtol=TC_RTOL, ref=refq)
+
+
+def _oracle_descent(p, u, eta, n_iter):
+    """Steepest descent a <- a - eta grad C (Sec. II) driven by the oracle's exact gradient."""
+    costs = []
+    for _ in range(n_iter):
+        r = oracle_cost_and_grad(p, u)
+        costs.append(r.cost)
+        u = u - eta * r.grad
+    return u, np.array(costs)
+
+
+@pytest.mark.parametrize("backward_mode", [0, 1])
+def test_steepest_descent_graph(backward_mode):
+    """grape_optimize: first iterate bitwise equal to one host-driven step, trajectory against the oracle."""
+    p = build_config("c1_state_transfer_d30", n_steps=40)
+    hg = _hg(p, backward_mode=backward_mode)
+    eta = 0.02
+    c0, g0 = hg.cost_and_grad(p.u0)
+    u1, costs = hg.optimize(p.u0, 1, eta)
+    assert costs[0] == c0
+    assert np.array_equal(u1, np.subtract(p.u0, np.multiply(eta, g0)))
+    u5, costs5 = hg.optimize(p.u0, 5, eta)
+    ref_u, ref_c = _oracle_descent(p, np.array(p.u0), eta, 5)
+    assert np.allclose(costs5, ref_c, rtol=1e-9, atol=0), (costs5, ref_c)
+    assert np.linalg.norm(u5 - ref_u) <= 1e-8 * np.linalg.norm(ref_u)
+    # more iterations replay the same recorded graph; the cost decreases for this step size
+    _, costs30 = hg.optimize(p.u0, 30, eta)
+    assert np.array_equal(costs30[:5], costs5)
+    assert np.all(np.diff(costs30) < 0), costs30
+    # a changed step size records the iteration again
+    u1b, _ = hg.optimize(p.u0, 1, 2 * eta)
+    assert np.array_equal(u1b, np.subtract(p.u0, np.multiply(2 * eta, g0)))
+    # a normal evaluation after the optimizer sees the controls it is given
+    c0b, g0b = hg.cost_and_grad(p.u0)
+    assert c0b == c0 and np.array_equal(g0b, g0)
+
+
+def test_steepest_descent_rejects_bad_arguments():
+    from paper_2304_06200_gb300 import GrapeError
+    p = build_config("c1_state_transfer_d30", n_steps=10)
+    hg = _hg(p)
+    for bad in (0.0, -1.0, float("nan"), float("inf")):
+        with pytest.raises(GrapeError):
+            hg.optimize(p.u0, 3, bad)
+    with pytest.raises(GrapeError):
+        hg.optimize(p.u0, 0, 0.01)
