@@ -417,3 +417,22 @@ def test_steepest_descent_rejects_bad_arguments():
             hg.optimize(p.u0, 3, bad)
     with pytest.raises(GrapeError):
         hg.optimize(p.u0, 0, 0.01)
+
+
+@pytest.mark.parametrize("family,size,N,dt,drive", [
+    ("h2", 4, 30, 0.5, 3.0), ("h2", 6, 8, 0.5, 3.0),
+    ("h3", 6, 30, 0.2, 3.0), ("h3", 9, 6, 0.2, 3.0),
+    ("h4", 8, 30, 0.05, 3.0), ("h4", 14, 6, 0.05, 3.0),
+])
+def test_hamiltonian_families_parity(family, size, N, dt, drive):
+    """Three transmons (H_2), qubit chain (H_3) and fluxonium pair (H_4): FP64 and FP32-bulk paths vs the oracle."""
+    from workloads import fluxonium_problem, hadamard3_problem, qubit_chain_problem
+    build = {"h2": hadamard3_problem, "h3": qubit_chain_problem, "h4": fluxonium_problem}[family]
+    p = build(size, N, dt, seed=40 + size)
+    p.tau = 1e-12
+    u = p.u0 * drive
+    r = oracle_cost_and_grad(p, u)
+    cost, grad = _hg(p).cost_and_grad(u)
+    _check(p, u, cost, grad, ref=r)
+    cost, grad = _hg(p, precision="fp32_bulk").cost_and_grad(u)
+    _check(p, u, cost, grad, cost_rtol=FP32_RTOL, grad_rtol=FP32_RTOL, ref=r)

@@ -10,7 +10,9 @@ Physical model (Sec. II; benchmark Hamiltonian Eq. (fockH) in Sec. IV.B): in
 the frame rotating with the drives, a transmon ``b`` (anharmonicity alpha) is
 dispersively coupled to a cavity ``a`` (shift chi) and both are driven by
 x/y quadrature controls.  Units: angular frequency in rad/ns (``X/2pi = v GHz``
-means ``X = 2 pi v``), time in ns.
+means ``X = 2 pi v``), time in ns.  ``families`` adds the paper's other
+Hamiltonians: three coupled transmons (H_2), a qubit chain (H_3) and a coupled
+fluxonium pair (H_4).
 """
 
 from .transmon import (  # noqa: F401
@@ -24,4 +26,12 @@ from .transmon import (  # noqa: F401
     two_level_rabi,
     random_problem,
     batch_instances,
+)
+from .families import (  # noqa: F401
+    three_transmons,
+    hadamard3_problem,
+    qubit_chain,
+    qubit_chain_problem,
+    fluxonium_pair,
+    fluxonium_problem,
 )
