@@ -55,6 +55,8 @@ def parse_args(argv=None):
     ap.add_argument("--c4", action="store_true", help="also run the d = 16000 workload in FP32 bulk and FP64")
     ap.add_argument("--dense", action="store_true", help="also run the dense d = 2048 variant on the tensor cores")
     ap.add_argument("--dense-steps", type=int, default=20)
+    ap.add_argument("--eig", action="store_true",
+                    help="also compare the eigendecomposition propagator (App. F) with the Taylor kernels")
     ap.add_argument("--backward-mode", type=int, default=0, help="0 auto, 1 one team per column, 2 two teams")
     return ap.parse_args(argv)
 
@@ -413,6 +415,8 @@ def run_ours(args):
         extra["c5_batch"] = batch_compare(local, args.autotune)
     if args.dense:
         extra["dense_d2048_tc"] = dense_compare(local, args.dense_steps)
+    if args.eig:
+        extra["eig_vs_taylor"] = eig_compare(local)
 
     out = {
         "metric": METRIC, "value": round(value, 6), "unit": "evals/s", "n_gpus": world, "steps": args.steps,
@@ -620,6 +624,67 @@ def dense_compare(local, n_steps):
         res[prec] = r
         hg.close()
     return res
+
+
+def _timed_eval(hg, p, u0, dev, reps=3):
+    """Median forward / backward milliseconds of one evaluation (CUDA events), plus its cost and gradient."""
+    import torch
+    u = torch.tensor(u0, dtype=torch.float64, device=dev)
+    cost = torch.zeros((), dtype=torch.float64, device=dev)
+    grad = torch.zeros_like(u)
+    hg.cost_device(u, cost)
+    hg.grad_device(grad)
+    torch.cuda.synchronize()
+    f, b = [], []
+    for _ in range(reps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        hg.cost_device(u, cost)
+        e[1].record()
+        hg.grad_device(grad)
+        e[2].record()
+        torch.cuda.synchronize()
+        f.append(e[0].elapsed_time(e[1]))
+        b.append(e[1].elapsed_time(e[2]))
+    hg.sync_status()
+    fwd, bwd = float(np.median(f)), float(np.median(b))
+    return {"ms_per_eval": round(fwd + bwd, 3), "fwd_ms": round(fwd, 3), "bwd_ms": round(bwd, 3)}, \
+        float(cost.item()), grad.cpu().numpy()
+
+
+def eig_compare(local):
+    """Eigendecomposition propagators (App. F) against the Taylor kernels (Sec. III.B), both FP64.
+
+    Two workloads: the d = 80 transmon-cavity gate (8 columns, sparse H, N = 1000) and a dense
+    random d = 96 full-rank gate (96 columns, every matrix element non-zero, N = 500).
+    """
+    import torch
+    from paper_2304_06200_gb300 import GrapeProblem
+    from workloads import build_config, random_problem
+
+    dev = torch.device("cuda", local)
+    out = {}
+    cases = [("c2_gate_d80", build_config("c2_gate_d80"), 1.0),
+             ("dense_random_d96_full_gate", random_problem(96, 4, 96, 500, seed=96, dt=0.3, density=1.0, tau=1e-10),
+              1.0)]
+    for name, p, scale in cases:
+        u0 = p.u0 * scale
+        res = {"workload": workload_description(p)}
+        ref = None
+        for prop in ("taylor", "eig"):
+            hg = GrapeProblem(p, device=local, propagator=prop)
+            r, c, g = _timed_eval(hg, p, u0, dev)
+            if prop == "taylor":
+                r["taylor_terms_per_sweep"] = hg.info()["total_terms"]
+                ref = (c, g)
+            else:
+                r["cost_rel_diff_vs_taylor"] = abs(c - ref[0]) / abs(ref[0])
+                r["grad_rel_diff_vs_taylor"] = float(np.linalg.norm(g - ref[1]) / np.linalg.norm(ref[1]))
+            res[prop] = r
+            hg.close()
+        res["speedup_eig_over_taylor"] = round(res["taylor"]["ms_per_eval"] / res["eig"]["ms_per_eval"], 2)
+        out[name] = res
+    return out
 
 
 def batch_compare(local, tune=False):

@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-#define GRAPE_ABI_VERSION 1
+#define GRAPE_ABI_VERSION 2
 
 typedef struct grape_problem grape_problem;
 
@@ -71,6 +71,17 @@ typedef enum {
                             tensor cores (FP16 hi/lo operands, FP32 accumulation); states,
                             costates and reductions FP64.  Needs dim % 128 == 0, n_states <= 16. */
 } grape_precision;
+
+/* How each step's propagator exp(-i H_n dt) acts.
+ *   GRAPE_PROP_TAYLOR: truncated Taylor series with scaling and squaring, (m, s) by the bound
+ *                      E_A(m, s) <= tau (Sec. III.B, App. C); sparse operators, any dim.
+ *   GRAPE_PROP_EIG:    Hermitian eigendecomposition per step, U_n = V diag(exp(-i lambda dt)) V^+,
+ *                      and the propagator derivative from the divided differences of exp on the
+ *                      spectrum (App. F).  Exact up to rounding; operators treated as dense;
+ *                      needs GRAPE_FP64 and dim <= 96 (the step matrix lives in shared memory);
+ *                      tau, m_max, ckpt_every, cluster and backward_mode are ignored.  Memory
+ *                      grows with N d^2 (three d x d blocks per step). */
+typedef enum { GRAPE_PROP_TAYLOR = 0, GRAPE_PROP_EIG = 1 } grape_propagator;
 
 /* One Hermitian operator (H0 or a control H_k), dim x dim.
  *   fmt == GRAPE_CSR:   rowptr[dim+1] (int64, rowptr[0] == 0), colind[nnz] (int32, 0-based,
@@ -123,6 +134,7 @@ typedef struct {
   double w_tint;               /* weight alpha_4 of the time-integrated infidelity
                                   C3 = 1 - 1/(N n^2) sum_{n'=1..N} |sum_h <phi_T^h|psi_n'^h>|^2
                                   (App. A, C3st / C3g; 0 = off)                                 */
+  int32_t propagator;          /* grape_propagator (0 = Taylor)                               */
 } grape_desc;
 
 /* Information about a problem (valid after create; schedule fields after an evaluation). */
@@ -140,6 +152,7 @@ typedef struct {
   double max_norm;             /* max_n ||A_n||_1 of the last evaluation (-1 before)       */
   int32_t backward_mode;       /* 1 = one team per column, 2 = two concurrent teams per column */
   int32_t cluster_forward;     /* CTAs per column team of the forward sweep                */
+  int32_t propagator;          /* grape_propagator of the problem                          */
 } grape_info;
 
 /* Create a problem (Sec. II: H(t) = H_s + sum_k a_k(t) h_k, piecewise constant over N steps

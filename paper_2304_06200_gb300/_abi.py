@@ -9,6 +9,7 @@ from .build import LIB, build_library
 
 GRAPE_CSR, GRAPE_DENSE = 0, 1
 GRAPE_FP64, GRAPE_FP32_BULK, GRAPE_TC_FP16 = 0, 1, 2
+GRAPE_PROP_TAYLOR, GRAPE_PROP_EIG = 0, 1
 
 STATUS = {
     0: "GRAPE_OK", 1: "GRAPE_EINVAL", 2: "GRAPE_ENOMEM", 3: "GRAPE_ECUDA", 4: "GRAPE_ETOL",
@@ -41,14 +42,15 @@ class GrapeDesc(C.Structure):
                 ("tau", C.c_double), ("m_max", C.c_int32), ("ckpt_every", C.c_int32), ("precision", C.c_int32),
                 ("cluster", C.c_int32), ("device", C.c_int32),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p), ("backward_mode", C.c_int32),
-                ("bulk_norm_cap", C.c_double), ("w_tint", C.c_double)]
+                ("bulk_norm_cap", C.c_double), ("w_tint", C.c_double), ("propagator", C.c_int32)]
 
 
 class GrapeInfo(C.Structure):
     _fields_ = [("device_bytes", C.c_int64), ("union_nnz", C.c_int64), ("ctrl_entries", C.c_int64),
                 ("sigma", C.c_int32), ("m_cap", C.c_int32), ("s_cap", C.c_int32), ("cluster", C.c_int32),
                 ("ckpt_every", C.c_int32), ("smem_bytes", C.c_int32), ("total_terms", C.c_int64),
-                ("max_norm", C.c_double), ("backward_mode", C.c_int32), ("cluster_forward", C.c_int32)]
+                ("max_norm", C.c_double), ("backward_mode", C.c_int32), ("cluster_forward", C.c_int32),
+                ("propagator", C.c_int32)]
 
 
 _LIB = None

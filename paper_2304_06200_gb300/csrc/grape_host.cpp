@@ -13,6 +13,7 @@
 #include "../../include/grape_hg.h"
 #include "grape_bound.h"
 #include "grape_dense.h"
+#include "grape_eig.h"
 #include "grape_internal.h"
 
 using cplx = std::complex<double>;
@@ -195,6 +196,9 @@ struct grape_problem {
   unsigned* d_flags = nullptr;      // ready[n*CL], done[n*CL]
   // launch plans of the forward and the backward sweep
   KPlan fwd, bwd;
+  // eigendecomposition propagators (App. F)
+  bool eig = false;
+  grape::EigCtx ectx{};
   // dense tensor-core mode
   bool dense = false;
   grape::DenseCtx dctx{};
@@ -411,6 +415,83 @@ grape_status build_dense(grape_problem* P, const grape_desc* d, const std::vecto
   return GRAPE_OK;
 }
 
+// Device buffers of the eigendecomposition propagator (App. F): dense operators, per-step
+// eigenpairs and propagators, the stored state and costate histories.
+grape_status build_eig(grape_problem* P, const grape_desc* d, const std::vector<HostCSR>& ops) {
+  grape_status st;
+  const int64_t dim = P->dim;
+  const int n = P->n, K = P->K, N = P->N;
+  P->eig = true;
+  P->fwd.CL = P->bwd.CL = 1;
+  P->bwd_mode = 1;
+  P->ckpt_every = 0;
+  P->n_ckpt = 0;
+  P->m_cap = P->s_cap = 0;
+  const size_t dd = (size_t)dim * dim, blk = (size_t)dim * n;
+  std::vector<double2> dense((size_t)(K + 1) * dd, make_double2(0.0, 0.0));
+  for (int k = 0; k <= K; ++k)
+    for (int64_t i = 0; i < dim; ++i)
+      for (int64_t e = ops[k].rowptr[i]; e < ops[k].rowptr[i + 1]; ++e) {
+        const cplx v = ops[k].val[e];
+        dense[(size_t)k * dd + (size_t)i * dim + ops[k].col[e]] = make_double2(v.real(), v.imag());
+      }
+  grape::EigCtx& c = P->ectx;
+  c.d = (int)dim;
+  c.n = n;
+  c.N = N;
+  c.K = K;
+  c.dt = P->dt;
+  c.w_fid = P->w_fid;
+  c.w_forbid = P->w_forbid;
+  c.w_tint = P->w_tint;
+  double2* ops_d;
+  if ((st = upload(P, &ops_d, dense.data(), dense.size()))) return st;
+  c.H0 = ops_d;
+  c.Hk = ops_d + dd;
+  double *lam, *htau;
+  double2 *V, *Vt, *U, *ph, *ch, *xs;
+  if ((st = dzeros(P, &lam, (size_t)N * dim)) || (st = dzeros(P, &htau, (size_t)N * dim))) return st;
+  if ((st = dzeros(P, &V, (size_t)N * dd)) || (st = dzeros(P, &Vt, (size_t)N * dd)) || (st = dzeros(P, &U, (size_t)N * dd)))
+    return st;
+  if ((st = dzeros(P, &ph, (size_t)(N + 1) * blk)) || (st = dzeros(P, &ch, (size_t)(N + 1) * blk)) ||
+      (st = dzeros(P, &xs, (size_t)N * 2 * blk)))
+    return st;
+  c.lam = lam;
+  c.htau = htau;
+  c.V = V;
+  c.Vt = Vt;
+  c.U = U;
+  c.psi_hist = ph;
+  c.chi_hist = ch;
+  c.xs = xs;
+  if ((st = upload(P, &P->d_psi0, reinterpret_cast<const double2*>(d->psi0), blk))) return st;
+  if ((st = upload(P, &P->d_target, reinterpret_cast<const double2*>(d->target), blk))) return st;
+  if (d->omega_diag) {
+    P->has_omega = true;
+    if ((st = upload(P, &P->d_omega, d->omega_diag, (size_t)dim))) return st;
+  }
+  if ((st = dzeros(P, &P->d_u, (size_t)std::max(K, 1) * N))) return st;
+  if ((st = dzeros(P, &P->d_part_g, (size_t)n)) || (st = dzeros(P, &P->d_part_c2, (size_t)n))) return st;
+  if ((st = dzeros(P, &P->d_part_grad, (size_t)N * std::max(K, 1)))) return st;
+  if ((st = dzeros(P, &P->d_g, 1)) || (st = dzeros(P, &P->d_cost, 1)) || (st = dzeros(P, &P->d_parts, 5))) return st;
+  if ((st = dzeros(P, &P->d_part_g3, (size_t)n * N)) || (st = dzeros(P, &P->d_g3, (size_t)N))) return st;
+  if ((st = dzeros(P, &P->d_grad, (size_t)std::max(K, 1) * N)) || (st = dzeros(P, &P->d_err, 1))) return st;
+  c.psi0 = P->d_psi0;
+  c.target = P->d_target;
+  c.omega = P->has_omega ? P->d_omega : nullptr;
+  c.u = P->d_u;
+  c.part_g = P->d_part_g;
+  c.part_c2 = P->d_part_c2;
+  c.part_g3 = P->w_tint != 0.0 ? P->d_part_g3 : nullptr;
+  c.g_final = P->d_g;
+  c.g3 = P->d_g3;
+  c.part_grad = P->d_part_grad;
+  c.err = P->d_err;
+  const cudaError_t e = grape::eig_prepare((int)dim, K);
+  if (e != cudaSuccess) return cuda_fail(e, "eigendecomposition kernel attributes");
+  return GRAPE_OK;
+}
+
 // Record `body` (a sequence of launches on one stream) into a CUDA graph on the problem's capture
 // stream, unless `exec` already holds a graph recorded for the same schedule; then launch it on st.
 template <typename Body>
@@ -509,6 +590,7 @@ grape_status build(grape_problem* P, const grape_desc* d) {
     }
     ectr_ptr[e + 1] = (int)ectr_k.size();
   }
+  if (d->propagator == GRAPE_PROP_EIG) return build_eig(P, d, ops);
   // ---- (m, s) breakpoint table (App. C)
   // Both precisions share the FP64 bound's schedule (the FP32-bulk path keeps its states in FP64;
   // the bound with u = 2^-24 certifies no useful tolerance).
@@ -780,6 +862,7 @@ grape_status read_error_word(grape_problem* P, cudaStream_t st) {
       case grape::kErrTol: return fail(GRAPE_ETOL, "a step has no (m, s) with E_A(m, s) <= tau");
       case grape::kErrNonFinite: return fail(GRAPE_ENONFINITE, "a control amplitude or step norm is not finite");
       case grape::kErrTimeout: return fail(GRAPE_ETIMEOUT, "a bounded device wait gave up");
+      case grape::kErrEig: return fail(GRAPE_ETOL, "the tridiagonal QL iteration of a step did not converge");
       default: return fail(GRAPE_ECUDA, "unknown device error word");
     }
   }
@@ -840,6 +923,10 @@ grape_status grape_problem_create(const grape_desc* d, grape_problem** out) {
     return fail(GRAPE_EINVAL, "precision must be GRAPE_FP64, GRAPE_FP32_BULK or GRAPE_TC_FP16");
   if (d->precision == GRAPE_TC_FP16 && (d->dim % 128 != 0 || d->n_states > 16))
     return fail(GRAPE_EINVAL, "GRAPE_TC_FP16 needs dim % 128 == 0 and n_states <= 16");
+  if (d->propagator != GRAPE_PROP_TAYLOR && d->propagator != GRAPE_PROP_EIG)
+    return fail(GRAPE_EINVAL, "propagator must be GRAPE_PROP_TAYLOR or GRAPE_PROP_EIG");
+  if (d->propagator == GRAPE_PROP_EIG && (d->precision != GRAPE_FP64 || d->dim > grape::kEigMaxDim))
+    return fail(GRAPE_EINVAL, "GRAPE_PROP_EIG needs GRAPE_FP64 and dim <= 96");
   if (d->cluster < 0 || d->cluster > grape::kMaxCluster) return fail(GRAPE_EINVAL, "cluster must be 0 (automatic) or 1..16");
   if (d->n_controls > 0 && !d->Hk) return fail(GRAPE_EINVAL, "Hk is NULL");
   if (d->bulk_norm_cap < 0.0 || !std::isfinite(d->bulk_norm_cap)) return fail(GRAPE_EINVAL, "bulk_norm_cap must be >= 0");
@@ -911,6 +998,32 @@ grape_status run_forward(grape_problem* P, const double* u, bool u_on_device, cu
   if (ubytes && u != P->d_u)
     e = cudaMemcpyAsync(P->d_u, u, ubytes, u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync (u)");
+  if (P->eig) {
+    if ((e = grape::check_nonfinite_u(P->d_u, (int64_t)P->K * P->N, P->d_err, st)) != cudaSuccess)
+      return cuda_fail(e, "launch k_check_finite");
+    if ((e = grape::eig_forward(P->ectx, st)) != cudaSuccess) return cuda_fail(e, "eigendecomposition forward sweep");
+    grape::FinalizeParams fp{};
+    fp.n_parts = P->n;
+    fp.n_states = P->n;
+    fp.N = P->N;
+    fp.K = P->K;
+    fp.w_fid = P->w_fid;
+    fp.w_forbid = P->w_forbid;
+    fp.w_amp = P->w_amp;
+    fp.w_tint = P->w_tint;
+    fp.part_g3 = P->w_tint != 0.0 ? P->d_part_g3 : nullptr;
+    fp.g3_out = P->d_g3;
+    fp.part_g = P->d_part_g;
+    fp.part_c2 = P->d_part_c2;
+    fp.u = P->d_u;
+    fp.g_out = P->d_g;
+    fp.cost_out = P->d_cost;
+    fp.parts_out = P->d_parts;
+    if ((e = grape::launch_finalize(fp, st)) != cudaSuccess) return cuda_fail(e, "launch k_finalize");
+    P->forward_done = true;
+    P->evaluated = true;
+    return GRAPE_OK;
+  }
   grape::ScheduleParams sp{};
   sp.dim = (int)P->dim;
   sp.K = P->K;
@@ -994,7 +1107,9 @@ grape_status run_forward(grape_problem* P, const double* u, bool u_on_device, cu
 grape_status run_backward(grape_problem* P, cudaStream_t st) {
   grape::SweepParams p = sweep_params(P, P->bwd);
   cudaError_t e;
-  if (P->dense) {
+  if (P->eig) {
+    if ((e = grape::eig_backward(P->ectx, st)) != cudaSuccess) return cuda_fail(e, "eigendecomposition backward sweep");
+  } else if (P->dense) {
     e = run_recorded(P, &P->bwd_exec, &P->bwd_sched, st, [&](cudaStream_t cs) {
       return grape::dense_backward(P->dctx, P->m_host.data(), P->s_host.data(), cs);
     });
@@ -1016,7 +1131,7 @@ grape_status run_backward(grape_problem* P, cudaStream_t st) {
   }
   if (P->K > 0) {
     grape::GradReduceParams gp{};
-    gp.n_parts = P->dense ? 1 : P->n * P->bwd.CL;
+    gp.n_parts = (P->dense || P->eig) ? 1 : P->n * P->bwd.CL;
     gp.N = P->N;
     gp.K = P->K;
     gp.w_amp = P->w_amp;
@@ -1398,7 +1513,8 @@ grape_status grape_problem_info(grape_problem* P, grape_info* info) {
   info->total_terms = -1;
   info->max_norm = -1.0;
   info->backward_mode = P->bwd_mode;
-  if (P->evaluated) {
+  info->propagator = P->eig ? GRAPE_PROP_EIG : GRAPE_PROP_TAYLOR;
+  if (P->evaluated && !P->eig) {
     DeviceGuard guard(P->device);
     std::vector<int> m(P->N), s(P->N);
     std::vector<double> x(P->N);
@@ -1421,6 +1537,7 @@ grape_status grape_problem_info(grape_problem* P, grape_info* info) {
 
 grape_status grape_step_schedule(grape_problem* P, int32_t* m, int32_t* s, double* norm1) {
   if (!P) return fail(GRAPE_EINVAL, "NULL problem");
+  if (P->eig) return fail(GRAPE_EINVAL, "GRAPE_PROP_EIG problems have no Taylor schedule");
   if (!P->evaluated) return fail(GRAPE_ESTATE, "no evaluation has run");
   DeviceGuard guard(P->device);
   cudaError_t e = cudaStreamSynchronize(P->last_stream);

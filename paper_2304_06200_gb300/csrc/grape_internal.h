@@ -17,6 +17,7 @@ constexpr uint32_t kCtrlBit = 1u << 31;
 constexpr int kErrTol = 4;
 constexpr int kErrTimeout = 5;
 constexpr int kErrNonFinite = 8;
+constexpr int kErrEig = 9;
 
 // Everything a sweep kernel needs; passed by value.
 struct SweepParams {

@@ -16,6 +16,7 @@ from . import _abi
 from ._abi import GrapeDesc, GrapeInfo, GrapeOp, check, lib
 
 PRECISIONS = {"fp64": _abi.GRAPE_FP64, "fp32_bulk": _abi.GRAPE_FP32_BULK, "tc_fp16": _abi.GRAPE_TC_FP16}
+PROPAGATORS = {"taylor": _abi.GRAPE_PROP_TAYLOR, "eig": _abi.GRAPE_PROP_EIG}
 
 
 def _dptr(a: np.ndarray):
@@ -71,7 +72,7 @@ class GrapeProblem:
 
     def __init__(self, problem, precision: str = "fp64", ckpt_every: int = 0, cluster: int = 0, device: int = 0,
                  tau: float | None = None, m_max: int = 0, torch_allocator: bool = True, n_steps: int | None = None,
-                 backward_mode: int = 0, bulk_norm_cap: float = 0.0):
+                 backward_mode: int = 0, bulk_norm_cap: float = 0.0, propagator: str = "taylor"):
         L = lib()
         self._lib = L
         self.dim = int(problem.dim)
@@ -125,10 +126,12 @@ class GrapeProblem:
         d.backward_mode = int(backward_mode)
         d.bulk_norm_cap = float(bulk_norm_cap)
         d.w_tint = float(getattr(problem, "w_tint", 0.0))
+        d.propagator = PROPAGATORS[propagator]
         handle = C.c_void_p()
         check(L.grape_problem_create(C.byref(d), C.byref(handle)), "grape_problem_create")
         self._h = handle
         self.precision = precision
+        self.propagator = propagator
 
     # ------------------------------------------------------------------ host-pointer API
     def cost_and_grad(self, u: np.ndarray, want_grad: bool = True):

@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol(L):
     assert sorted(EXPORTED) == declared
     for name in declared:
         assert hasattr(L, name), name
-    assert L.grape_abi_version() == 1
+    assert L.grape_abi_version() == 2
 
 
 def test_status_strings(L):
@@ -86,5 +86,23 @@ def test_create_rejects_bad_descriptors_before_touching_the_device(L):
     d.dim = 0
     assert L.grape_problem_create(C.byref(d), C.byref(h)) == 1
     d.dim, d.n_steps, d.n_states, d.dt, d.tau = 4, 3, 5, 0.1, 1e-8   # n_states > dim
+    assert L.grape_problem_create(C.byref(d), C.byref(h)) == 1
+    assert not h.value
+
+
+def test_create_rejects_bad_propagator_choices(L):
+    """The eigendecomposition propagator (App. F) is FP64-only and bounded by the shared-memory step matrix."""
+    from paper_2304_06200_gb300._abi import GRAPE_FP32_BULK, GRAPE_PROP_EIG, GrapeDesc
+    h = C.c_void_p()
+    d = GrapeDesc()
+    d.dim, d.n_steps, d.n_states, d.dt, d.tau = 4, 3, 1, 0.1, 1e-8
+    d.propagator = 2
+    assert L.grape_problem_create(C.byref(d), C.byref(h)) == 1
+    d.propagator = GRAPE_PROP_EIG
+    d.precision = GRAPE_FP32_BULK
+    assert L.grape_problem_create(C.byref(d), C.byref(h)) == 1
+    assert b"GRAPE_PROP_EIG" in L.grape_last_error()
+    d.precision = 0
+    d.dim = 97
     assert L.grape_problem_create(C.byref(d), C.byref(h)) == 1
     assert not h.value

@@ -436,3 +436,87 @@ def test_hamiltonian_families_parity(family, size, N, dt, drive):
     _check(p, u, cost, grad, ref=r)
     cost, grad = _hg(p, precision="fp32_bulk").cost_and_grad(u)
     _check(p, u, cost, grad, cost_rtol=FP32_RTOL, grad_rtol=FP32_RTOL, ref=r)
+
+
+# ---------------------------------------------------------------- eigendecomposition propagator (App. F)
+
+EIG_COST_RTOL = 1e-11
+EIG_GRAD_RTOL = 1e-9
+
+
+@pytest.mark.parametrize("dim,K,n,N,density", [
+    (1, 1, 1, 4, 0.0), (2, 1, 1, 5, 0.0), (3, 2, 2, 6, 0.0), (33, 3, 5, 7, 0.3), (64, 2, 64, 3, 0.5),
+    (65, 4, 3, 9, 0.2), (96, 3, 7, 5, 1.0), (31, 0, 2, 3, 0.0),
+])
+def test_eig_propagator_random_problems(dim, K, n, N, density):
+    """Ragged and dense random problems, a full-rank gate (n = d), one-dimensional and control-free cases."""
+    p = random_problem(dim, K, n, N, seed=2000 + dim + K + n + N, density=density)
+    hg = _hg(p, propagator="eig")
+    assert hg.info()["propagator"] == 1
+    r = oracle_cost_and_grad(p, p.u0)
+    if K == 0:
+        assert abs(hg.cost(p.u0) - r.cost) <= EIG_COST_RTOL * abs(r.cost)
+        return
+    cost, grad = hg.cost_and_grad(p.u0)
+    _check(p, p.u0, cost, grad, cost_rtol=EIG_COST_RTOL, grad_rtol=EIG_GRAD_RTOL, ref=r)
+
+
+@pytest.mark.parametrize("name,N,tint", [("c1_state_transfer_d30", 200, 0.0), ("c2_gate_d80", 150, 0.0),
+                                         ("c2_gate_d80", 60, 0.7)])
+def test_eig_propagator_workloads(name, N, tint):
+    p = build_config(name, n_steps=N)
+    p.w_tint = tint
+    u = p.u0 * 20
+    r = oracle_cost_and_grad(p, u)
+    cost, grad = _hg(p, propagator="eig").cost_and_grad(u)
+    _check(p, u, cost, grad, cost_rtol=EIG_COST_RTOL, grad_rtol=EIG_GRAD_RTOL, ref=r)
+
+
+def test_eig_propagator_degenerate_spectra():
+    """Zero drift and zero controls: every eigenvalue coincides (Phi_ij -> e^{D_i}, App. F limit)."""
+    import scipy.sparse as sp
+    from workloads import Problem, haar_unitary
+    d, N = 12, 4
+    H0 = sp.csr_matrix(np.diag(np.repeat([0.0, 1.0, 1.0, 2.5], 3)).astype(np.complex128))
+    rng = np.random.default_rng(3)
+    Hk = []
+    for _ in range(2):
+        a = rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))
+        Hk.append(sp.csr_matrix(0.5 * (a + a.conj().T)))
+    psi0 = haar_unitary(d, 4)[:, :3]
+    p = Problem(name="degenerate", dim=d, dt=0.4, n_steps=N, H0=H0, Hk=Hk, psi0=psi0,
+                target=psi0 @ haar_unitary(3, 5), omega=None, w_fid=1.0, w_amp=0.1, u0=np.zeros((2, N)))
+    hg = _hg(p, propagator="eig")
+    for u in (np.zeros((2, N)), 0.3 * rng.standard_normal((2, N))):
+        cost, grad = hg.cost_and_grad(u)
+        _check(p, u, cost, grad, cost_rtol=EIG_COST_RTOL, grad_rtol=EIG_GRAD_RTOL)
+
+
+def test_eig_and_taylor_propagators_agree_on_a_three_transmon_gate():
+    from workloads import hadamard3_problem
+    p = hadamard3_problem(4, 40, 0.5, seed=7)
+    u = p.u0 * 5
+    c_t, g_t = _hg(p, tau=1e-12).cost_and_grad(u)
+    c_e, g_e = _hg(p, propagator="eig").cost_and_grad(u)
+    assert abs(c_t - c_e) <= 1e-10 * abs(c_e)
+    assert np.linalg.norm(g_t - g_e) <= 1e-8 * np.linalg.norm(g_e)
+
+
+def test_eig_propagator_optimizer_and_errors():
+    from paper_2304_06200_gb300 import GrapeError
+    p = build_config("c1_state_transfer_d30", n_steps=40)
+    hg = _hg(p, propagator="eig")
+    c0, g0 = hg.cost_and_grad(p.u0)
+    u1, costs = hg.optimize(p.u0, 3, 0.02)
+    assert costs[0] == c0
+    ref_u, ref_c = _oracle_descent(p, np.array(p.u0), 0.02, 3)
+    assert np.allclose(costs, ref_c, rtol=1e-11, atol=0)
+    assert np.linalg.norm(u1 - ref_u) <= 1e-9 * np.linalg.norm(ref_u)
+    bad = np.array(p.u0)
+    bad[1, 7] = np.nan
+    with pytest.raises(GrapeError):
+        hg.cost_and_grad(bad)
+    with pytest.raises(GrapeError):
+        hg.schedule()
+    c1, _ = hg.cost_and_grad(p.u0)     # the problem stays usable after a reported error
+    assert c1 == c0
