@@ -55,6 +55,8 @@ def parse_args(argv=None):
     ap.add_argument("--c4", action="store_true", help="also run the d = 16000 workload in FP32 bulk and FP64")
     ap.add_argument("--dense", action="store_true", help="also run the dense d = 2048 variant on the tensor cores")
     ap.add_argument("--dense-steps", type=int, default=20)
+    ap.add_argument("--extras-only", action="store_true",
+                    help="skip the main measurement and print only the requested comparisons (for profiling them)")
     ap.add_argument("--eig", action="store_true",
                     help="also compare the eigendecomposition propagator (App. F) with the Taylor kernels")
     ap.add_argument("--backward-mode", type=int, default=0, help="0 auto, 1 one team per column, 2 two teams")
@@ -267,6 +269,14 @@ def run_ours(args):
     from workloads import build_config
 
     lib()
+    if args.extras_only:
+        extra = {}
+        if args.eig:
+            extra["eig_vs_taylor"] = eig_compare(local)
+        if args.dense:
+            extra["dense_d2048_tc"] = dense_compare(local, args.dense_steps)
+        print(json.dumps({"extras": extra}), flush=True)
+        return
     p = build_config(args.workload, seed=None if rank == 0 else 1000 + rank, n_steps=args.n_steps)
     torch.cuda.synchronize()
     torch.cuda.reset_peak_memory_stats(dev)

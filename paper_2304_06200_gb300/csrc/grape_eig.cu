@@ -8,9 +8,11 @@
 //     Phi_ij = (e^{D_i} - e^{D_j}) / (D_i - D_j),  Phi_ii = e^{D_i},  D_i = -i lambda_i dt,
 // evaluated without cancellation as exp((D_i + D_j)/2) sin(theta)/theta, theta = (lambda_i - lambda_j) dt/2.
 //
-// Kernels (all launched with 256 threads):
-//   k_eig_step      one CTA per step: H_n, Householder reduction to real tridiagonal form, implicit
-//                   QL on the tridiagonal (one warp), back-transformation, U_n = V diag(e) V^+
+// Kernels:
+//   k_eig_tridiag   one CTA per step: H_n and its Householder reduction to tridiagonal form
+//   k_eig_ql        one thread per step: implicit QL on the real tridiagonal, rotations recorded
+//   k_eig_rotate    one thread per row of a step: the recorded rotations applied to the identity
+//   k_eig_vectors   one CTA per step: back-transformation to the eigenvectors, U_n = V diag(e) V^+
 //   k_eig_forward   one CTA per column: psi_n = U_n psi_{n-1} (Eq. (statepropagation)), overlaps
 //   k_eig_backward  one CTA per column: chi_{n-1} = U_n^+ chi_n + step sources (combined costate)
 //   k_eig_grad      one CTA per step: G_kn = 2 Re sum_h <chi_n^h| dU_n/du_kn |psi_{n-1}^h>
@@ -18,6 +20,10 @@
 // two sweeps are the sequential part (one d x d matrix-vector product per step and column).
 #include "grape_eig.h"
 #include "grape_internal.h"
+
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
 
 namespace grape {
 namespace {
@@ -72,118 +78,25 @@ __device__ double2 block_all_sum2(double2 v, double* red) {
   return t;
 }
 
-struct StepLayout {
-  int lda;            // leading dimension (d + 1) of the d x d blocks
-  size_t a, z, v, p, w, ph, ad, ed, red, bytes;
-};
+// Shared-memory layout of the reduction and back-transformation kernels: one complex d x d block
+// with leading dimension d + 1 and three complex d-vectors.
+__host__ __device__ inline size_t block_bytes(int d) { return (size_t)16 * d * (d + 1) + (size_t)16 * 3 * d + 8 * 2 * kWarps; }
 
-__host__ __device__ inline StepLayout step_layout(int d) {
-  StepLayout L;
-  L.lda = d + 1;
-  size_t off = 0;
-  L.a = off;  off += (size_t)16 * d * L.lda;    // complex A, later the eigenvector block Y
-  L.z = off;  off += (size_t)8 * d * L.lda;     // real Z (eigenvectors of the tridiagonal)
-  off = (off + 15) & ~(size_t)15;
-  L.v = off;  off += (size_t)16 * d;
-  L.p = off;  off += (size_t)16 * d;
-  L.w = off;  off += (size_t)16 * d;
-  L.ph = off; off += (size_t)16 * d;
-  L.ad = off; off += (size_t)8 * d;
-  L.ed = off; off += (size_t)8 * d;
-  L.red = off; off += (size_t)8 * 2 * kWarps;
-  L.bytes = off;
-  return L;
-}
-
-// Implicit QL with Wilkinson-type shifts on the real symmetric tridiagonal (a, e), e[i] coupling
-// rows i and i+1, accumulating the plane rotations into the columns of Z (textbook algorithm for
-// symmetric tridiagonal eigenproblems).  Run by one warp: every lane evaluates the same scalar
-// recurrence, lane 0 alone stores a and e (followed by __syncwarp), and each lane rotates its own
-// rows of Z.  Gives up after 60 iterations for one eigenvalue and sets kErrEig.
-__device__ void tridiagonal_ql(double* a, double* e, double* Z, int d, int lda, int* err) {
-  const int lane = threadIdx.x & 31;
-  for (int l = 0; l < d; ++l) {
-    int iter = 0;
-    for (;;) {
-      int m = l;
-      for (; m < d - 1; ++m) {
-        const double dd = fabs(a[m]) + fabs(a[m + 1]);
-        if (fabs(e[m]) + dd == dd) break;
-      }
-      if (m == l) break;
-      if (++iter > 60) {
-        if (lane == 0) atomicCAS(err, 0, kErrEig);
-        break;
-      }
-      double g = (a[l + 1] - a[l]) / (2.0 * e[l]);
-      double r = hypot(g, 1.0);
-      g = a[m] - a[l] + e[l] / (g + copysign(r, g));
-      double s = 1.0, c = 1.0, shift = 0.0;
-      bool split = false;
-      for (int i = m - 1; i >= l; --i) {
-        const double f = s * e[i], b = c * e[i];
-        r = hypot(f, g);
-        if (lane == 0) e[i + 1] = r;
-        if (r == 0.0) {   // underflow: the off-diagonal element splits the matrix here
-          const double ai1 = a[i + 1] - shift;
-          __syncwarp();
-          if (lane == 0) {
-            a[i + 1] = ai1;
-            e[m] = 0.0;
-          }
-          __syncwarp();
-          split = true;
-          break;
-        }
-        s = f / r;
-        c = g / r;
-        g = a[i + 1] - shift;
-        r = (a[i] - g) * s + 2.0 * c * b;
-        shift = s * r;
-        const double ai1 = g + shift;
-        g = c * r - b;
-        for (int row = lane; row < d; row += 32) {
-          double* zr = Z + (size_t)row * lda;
-          const double z1 = zr[i + 1], z0 = zr[i];
-          zr[i + 1] = s * z0 + c * z1;
-          zr[i] = c * z0 - s * z1;
-        }
-        __syncwarp();
-        if (lane == 0) a[i + 1] = ai1;
-        __syncwarp();
-      }
-      if (split) continue;
-      const double al = a[l] - shift;
-      __syncwarp();
-      if (lane == 0) {
-        a[l] = al;
-        e[l] = g;
-        e[m] = 0.0;
-      }
-      __syncwarp();
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kT, 1) k_eig_step(EigCtx p) {
+// Householder reduction of H_n = H0 + sum_k u_kn H_k (Sec. II) to tridiagonal form, one CTA per step.
+// H_k = I - tau v v^+ maps column k below the diagonal onto alpha e_1; the trailing block B becomes
+// H_k B H_k = B - v w^+ - w v^+ with p = tau B v, w = p - (tau/2)(v^+ p) v.  Writes the diagonal,
+// the super-diagonal t_i = T_{i,i+1}, the vectors v_k (into the step's slice of U) and tau_k.
+__global__ void __launch_bounds__(kT) k_eig_tridiag(EigCtx p) {
   extern __shared__ __align__(16) unsigned char sm[];
-  const int d = p.d, step = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const StepLayout L = step_layout(d);
-  const int lda = L.lda;
-  double2* A = reinterpret_cast<double2*>(sm + L.a);
-  double* Z = reinterpret_cast<double*>(sm + L.z);
-  double2* vv = reinterpret_cast<double2*>(sm + L.v);
-  double2* pv = reinterpret_cast<double2*>(sm + L.p);
-  double2* wv = reinterpret_cast<double2*>(sm + L.w);
-  double2* ph = reinterpret_cast<double2*>(sm + L.ph);
-  double* ad = reinterpret_cast<double*>(sm + L.ad);
-  double* ed = reinterpret_cast<double*>(sm + L.ed);
-  double* red = reinterpret_cast<double*>(sm + L.red);
+  const int d = p.d, step = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, lda = d + 1;
+  double2* A = reinterpret_cast<double2*>(sm);
+  double2* vv = A + (size_t)d * lda;
+  double2* pv = vv + d;
+  double2* wv = pv + d;
+  double* red = reinterpret_cast<double*>(wv + d);
   const size_t dd = (size_t)d * d;
-  double2* hv = p.U + (size_t)step * dd;      // Householder vectors of this step (row k: v_k)
+  double2* hv = p.U + (size_t)step * dd;
   double* htau = p.htau + (size_t)step * d;
-
-  // H_n = H0 + sum_k u_kn H_k (Sec. II)
   for (int idx = tid; idx < d * d; idx += kT) {
     double2 h = p.H0[idx];
     for (int k = 0; k < p.K; ++k) {
@@ -195,10 +108,6 @@ __global__ void __launch_bounds__(kT, 1) k_eig_step(EigCtx p) {
     A[(idx / d) * lda + idx % d] = h;
   }
   __syncthreads();
-
-  // Householder reduction: H_k = I - tau v v^+ maps column k below the diagonal onto alpha e_1;
-  // the trailing block B becomes H_k B H_k = B - v w^+ - w v^+ with p = tau B v,
-  // w = p - (tau/2)(v^+ p) v.
   for (int k = 0; k + 2 < d; ++k) {
     const int n1 = d - k - 1;
     double2 part = make_double2(0.0, 0.0);
@@ -254,30 +163,135 @@ __global__ void __launch_bounds__(kT, 1) k_eig_step(EigCtx p) {
     }
     __syncthreads();
   }
+  for (int i = tid; i < d; i += kT) {
+    p.tri_a[(size_t)step * d + i] = A[i * lda + i].x;
+    p.tri_t[(size_t)step * d + i] = i + 1 < d ? A[i * lda + i + 1] : make_double2(0.0, 0.0);
+  }
+}
 
-  // Real tridiagonal T_r = P^+ T P with the diagonal phases P_{i+1} = P_i conj(t_i)/|t_i|.
-  if (tid == 0) {
-    ph[0] = make_double2(1.0, 0.0);
-    for (int i = 0; i + 1 < d; ++i) {
-      const double2 t = A[i * lda + i + 1];
-      const double at = hypot(t.x, t.y);
-      ed[i] = at;
-      ph[i + 1] = at > 0.0 ? c_mul(ph[i], make_double2(t.x / at, -t.y / at)) : ph[i];
+// Implicit QL with Wilkinson-type shifts on the real symmetric tridiagonal T_r = P^+ T P
+// (P diagonal phases, P_{i+1} = P_i conj(t_i)/|t_i|), one thread per step: GB300 retires a warp's
+// FP64 instruction only every few tens of clocks per SM sub-partition, so the sequential scalar
+// recurrence runs with 32 steps side by side in the lanes of a warp.  The plane rotations are
+// recorded (index, c, s) for k_eig_rotate; the eigenvalues go to lam.  At most 60 iterations per
+// eigenvalue and p.rot_cap rotations per step; past either limit kErrEig is set.
+__global__ void __launch_bounds__(32) k_eig_ql(EigCtx p) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int d = p.d, lane = threadIdx.x, step = blockIdx.x * 32 + lane;
+  if (step >= p.N) return;   // no block-wide synchronisation in this kernel
+  double* a = reinterpret_cast<double*>(sm) + lane;   // a[i * 32]
+  double* e = a + 32 * d;                              // e[i * 32]
+  const double* ta = p.tri_a + (size_t)step * d;
+  const double2* tt = p.tri_t + (size_t)step * d;
+  double2* ph = p.phase + (size_t)step * d;
+  double2 phi = make_double2(1.0, 0.0);
+  for (int i = 0; i < d; ++i) {
+    a[i * 32] = ta[i];
+    ph[i] = phi;
+    double at = 0.0;
+    if (i + 1 < d) {
+      const double2 t = tt[i];
+      at = hypot(t.x, t.y);
+      if (at > 0.0) phi = c_mul(phi, make_double2(t.x / at, -t.y / at));
     }
-    ed[d - 1] = 0.0;
+    e[i * 32] = at;
   }
-  for (int i = tid; i < d; i += kT) ad[i] = A[i * lda + i].x;
-  for (int idx = tid; idx < d * d; idx += kT) Z[(idx / d) * lda + idx % d] = (idx / d == idx % d) ? 1.0 : 0.0;
-  __syncthreads();
-  if (warp == 0) tridiagonal_ql(ad, ed, Z, d, lda, p.err);
-  __syncthreads();
+  const int cap = p.rot_cap;
+  int* ri = p.rot_i + (size_t)step * cap;
+  double2* rcs = p.rot_cs + (size_t)step * cap;
+  int nrot = 0;
+  bool failed = false;
+  for (int l = 0; l < d; ++l) {
+    int iter = 0;
+    for (;;) {
+      int m = l;
+      for (; m < d - 1; ++m) {
+        const double dd = fabs(a[m * 32]) + fabs(a[(m + 1) * 32]);
+        if (fabs(e[m * 32]) + dd == dd) break;
+      }
+      if (m == l) break;
+      if (++iter > 60) {
+        failed = true;
+        break;
+      }
+      double g = (a[(l + 1) * 32] - a[l * 32]) / (2.0 * e[l * 32]);
+      double r = hypot(g, 1.0);
+      g = a[m * 32] - a[l * 32] + e[l * 32] / (g + copysign(r, g));
+      double s = 1.0, c = 1.0, shift = 0.0;
+      bool split = false;
+      for (int i = m - 1; i >= l; --i) {
+        const double f = s * e[i * 32], b = c * e[i * 32];
+        const double r2 = fma(f, f, g * g);   // entries of H dt are far from the overflow range
+        if (r2 == 0.0) {   // underflow: the off-diagonal element splits the matrix here
+          e[(i + 1) * 32] = 0.0;
+          a[(i + 1) * 32] -= shift;
+          e[m * 32] = 0.0;
+          split = true;
+          break;
+        }
+        const double ir = rsqrt(r2);
+        r = r2 * ir;
+        e[(i + 1) * 32] = r;
+        s = f * ir;
+        c = g * ir;
+        g = a[(i + 1) * 32] - shift;
+        r = (a[i * 32] - g) * s + 2.0 * c * b;
+        shift = s * r;
+        a[(i + 1) * 32] = g + shift;
+        g = c * r - b;
+        if (nrot < cap) {
+          ri[nrot] = i;
+          rcs[nrot] = make_double2(c, s);
+        }
+        ++nrot;
+      }
+      if (split) continue;
+      a[l * 32] -= shift;
+      e[l * 32] = g;
+      e[m * 32] = 0.0;
+    }
+  }
+  if (failed || nrot > cap) atomicCAS(p.err, 0, kErrEig);
+  p.rot_n[step] = nrot < cap ? nrot : cap;
+  for (int i = 0; i < d; ++i) p.lam[(size_t)step * d + i] = a[i * 32];
+}
 
-  // Eigenvectors of H_n: Y = H_0 H_1 ... H_{d-3} P Z, applied right to left.
-  for (int idx = tid; idx < d * d; idx += kT) {
-    const int i = idx / d, c = idx % d;
-    const double z = Z[i * lda + c];
-    A[i * lda + c] = make_double2(ph[i].x * z, ph[i].y * z);
+// Eigenvectors of T_r: Z = I G_1 G_2 ..., every thread rotating its own row of Z (the rows are
+// independent), then Y = P Z written to the step's slice of V.
+__global__ void __launch_bounds__(128) k_eig_rotate(EigCtx p) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int d = p.d, step = blockIdx.x, row = threadIdx.x;
+  if (row >= d) return;   // no block-wide synchronisation in this kernel
+  double* z = reinterpret_cast<double*>(sm) + (size_t)row * (d + 1);
+  for (int c = 0; c < d; ++c) z[c] = c == row ? 1.0 : 0.0;
+  const int n = p.rot_n[step];
+  const int* ri = p.rot_i + (size_t)step * p.rot_cap;
+  const double2* rcs = p.rot_cs + (size_t)step * p.rot_cap;
+  for (int r = 0; r < n; ++r) {
+    const int i = ri[r];
+    const double2 cs = rcs[r];
+    const double z0 = z[i], z1 = z[i + 1];
+    z[i + 1] = fma(cs.y, z0, cs.x * z1);
+    z[i] = fma(cs.x, z0, -cs.y * z1);
   }
+  const double2 ph = p.phase[(size_t)step * d + row];
+  double2* y = p.V + (size_t)step * d * d + (size_t)row * d;
+  for (int c = 0; c < d; ++c) y[c] = make_double2(ph.x * z[c], ph.y * z[c]);
+}
+
+// Back-transformation V_n = H_0 H_1 ... H_{d-3} Y (right to left), the transposed copy, and
+// U_n = V_n diag(exp(-i lambda dt)) V_n^+ written over the step's Householder vectors.
+__global__ void __launch_bounds__(kT) k_eig_vectors(EigCtx p) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int d = p.d, step = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, lda = d + 1;
+  double2* A = reinterpret_cast<double2*>(sm);
+  double2* vv = A + (size_t)d * lda;
+  double2* pv = vv + d;
+  const size_t dd = (size_t)d * d;
+  const double2* hv = p.U + (size_t)step * dd;
+  const double* htau = p.htau + (size_t)step * d;
+  double2* V = p.V + (size_t)step * dd;
+  for (int idx = tid; idx < d * d; idx += kT) A[(idx / d) * lda + idx % d] = V[idx];
   __syncthreads();
   for (int k = d - 3; k >= 0; --k) {
     const double tau = htau[k];
@@ -300,15 +314,11 @@ __global__ void __launch_bounds__(kT, 1) k_eig_step(EigCtx p) {
     }
     __syncthreads();
   }
-
-  // Outputs: eigenvalues, eigenvectors (and their transpose), U_n = Y diag(exp(-i lambda dt)) Y^+.
-  double* lam = p.lam + (size_t)step * d;
-  double2* V = p.V + (size_t)step * dd;
+  const double* lam = p.lam + (size_t)step * d;
   double2* Vt = p.Vt + (size_t)step * dd;
   for (int i = tid; i < d; i += kT) {
-    lam[i] = ad[i];
     double sn, cs;
-    sincos(ad[i] * p.dt, &sn, &cs);
+    sincos(lam[i] * p.dt, &sn, &cs);
     pv[i] = make_double2(cs, -sn);
   }
   for (int idx = tid; idx < d * d; idx += kT) {
@@ -317,37 +327,77 @@ __global__ void __launch_bounds__(kT, 1) k_eig_step(EigCtx p) {
     V[idx] = y;
     Vt[(size_t)c * d + i] = y;
   }
-  __syncthreads();   // every read of hv is done: the step's slice of U may be overwritten
+  __syncthreads();   // every read of the Householder vectors is done
   double2* U = p.U + (size_t)step * dd;
-  for (int idx = tid; idx < d * d; idx += kT) {
-    const int i = idx / d, j = idx % d;
+  constexpr int kJ = 4;   // entries U_ij, j = j0 .. j0 + 3, per thread share the product Y_il e_l
+  const int nj = (d + kJ - 1) / kJ;
+  for (int w = tid; w < d * nj; w += kT) {
+    const int i = w / nj, j0 = (w % nj) * kJ;
     const double2* yi = A + i * lda;
-    const double2* yj = A + j * lda;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int l = 0; l < d; ++l) c_fma(acc, c_mul(yi[l], pv[l]), c_conj(yj[l]));
-    U[idx] = acc;
+    double2 acc[kJ];
+#pragma unroll
+    for (int q = 0; q < kJ; ++q) acc[q] = make_double2(0.0, 0.0);
+    for (int l = 0; l < d; ++l) {
+      const double2 a = c_mul(yi[l], pv[l]);
+#pragma unroll
+      for (int q = 0; q < kJ; ++q)
+        if (j0 + q < d) c_fma(acc[q], a, c_conj(A[(j0 + q) * lda + l]));
+    }
+#pragma unroll
+    for (int q = 0; q < kJ; ++q)
+      if (j0 + q < d) U[(size_t)i * d + j0 + q] = acc[q];
   }
 }
 
-// Forward sweep of one column h: psi_s = U_s psi_{s-1}; overlaps and the C2 / C3 accumulations.
+// Rows [row_begin(q), row_begin(q + 1)) of a column belong to CTA q of the column's cluster.
+__device__ __forceinline__ int row_begin(int q, int d, int cl) { return (int)((int64_t)q * d / cl); }
+
+__device__ __forceinline__ int row_owner(int i, int d, int cl) {
+  int q = (int)((int64_t)i * cl / d);
+  while (q + 1 < cl && row_begin(q + 1, d, cl) <= i) ++q;
+  while (q > 0 && row_begin(q, d, cl) > i) --q;
+  return q;
+}
+
+// The rows computed by the other CTAs of the cluster, read from their copy of `buf` (same offset).
+template <bool CLUSTER>
+__device__ __forceinline__ void exchange_rows(double2* buf, int d, int cl, int rank, int r0, int r1) {
+  if constexpr (CLUSTER) {
+    cg::cluster_group cluster = cg::this_cluster();
+    cluster.sync();   // every CTA's own rows of buf are written
+    for (int i = threadIdx.x; i < d; i += kT) {
+      if (i >= r0 && i < r1) continue;
+      buf[i] = *cluster.map_shared_rank(buf + i, row_owner(i, d, cl));
+    }
+  }
+  __syncthreads();
+}
+
+// Forward sweep of column h = blockIdx.x / CL, rows split over a cluster of CL CTAs:
+// psi_s = U_s psi_{s-1} (Eq. (statepropagation)); overlaps and the C2 / C3 accumulations per CTA.
+// Double-buffered: a CTA rewrites a buffer two steps after it was read remotely, and the
+// cluster barrier of the step in between orders the two.
+template <bool CLUSTER>
 __global__ void __launch_bounds__(kT) k_eig_forward(EigCtx p) {
   extern __shared__ __align__(16) unsigned char sm[];
-  const int d = p.d, h = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  double2* cur = reinterpret_cast<double2*>(sm);
-  double2* nxt = cur + d;
-  double* red = reinterpret_cast<double*>(nxt + d);
+  const int d = p.d, cl = p.sweep_cl, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int h = blockIdx.x / cl, rank = blockIdx.x % cl, part = h * cl + rank;
+  const int r0 = row_begin(rank, d, cl), r1 = row_begin(rank + 1, d, cl);
+  double2* buf0 = reinterpret_cast<double2*>(sm);
+  double2* buf1 = buf0 + d;
+  double* red = reinterpret_cast<double*>(buf1 + d);
   const size_t dd = (size_t)d * d, col = (size_t)h * d, slab = (size_t)p.n * d;
   const double2* tgt = p.target + col;
-  for (int i = tid; i < d; i += kT) {
-    cur[i] = p.psi0[col + i];
-    p.psi_hist[col + i] = cur[i];
-  }
+  for (int i = tid; i < d; i += kT) buf0[i] = p.psi0[col + i];
+  for (int i = r0 + tid; i < r1; i += kT) p.psi_hist[col + i] = p.psi0[col + i];
   __syncthreads();
   double c2 = 0.0;
   for (int s = 0; s < p.N; ++s) {
+    const double2* cur = (s & 1) ? buf1 : buf0;
+    double2* nxt = (s & 1) ? buf0 : buf1;
     const double2* Us = p.U + (size_t)s * dd;
     double2* hist = p.psi_hist + (size_t)(s + 1) * slab + col;
-    for (int i = warp; i < d; i += kWarps) {
+    for (int i = r0 + warp; i < r1; i += kWarps) {
       const double2* urow = Us + (size_t)i * d;
       double2 acc = make_double2(0.0, 0.0);
       for (int j = lane; j < d; j += 32) c_fma(acc, urow[j], cur[j]);
@@ -358,37 +408,39 @@ __global__ void __launch_bounds__(kT) k_eig_forward(EigCtx p) {
         if (p.omega) c2 = fma(p.omega[i], fma(acc.x, acc.x, acc.y * acc.y), c2);
       }
     }
-    __syncthreads();
+    exchange_rows<CLUSTER>(nxt, d, cl, rank, r0, r1);
     if (p.part_g3) {
       double2 g = make_double2(0.0, 0.0);
-      for (int i = tid; i < d; i += kT) c_fma_conj(g, tgt[i], nxt[i]);
+      for (int i = r0 + tid; i < r1; i += kT) c_fma_conj(g, tgt[i], nxt[i]);
       g = block_all_sum2(g, red);
-      if (tid == 0) p.part_g3[(size_t)h * p.N + s] = g;
+      if (tid == 0) p.part_g3[(size_t)part * p.N + s] = g;
     }
-    double2* t = cur;
-    cur = nxt;
-    nxt = t;
   }
+  const double2* fin = (p.N & 1) ? buf1 : buf0;
   double2 g = make_double2(0.0, 0.0);
-  for (int i = tid; i < d; i += kT) c_fma_conj(g, tgt[i], cur[i]);
+  for (int i = r0 + tid; i < r1; i += kT) c_fma_conj(g, tgt[i], fin[i]);
   g = block_all_sum2(g, red);
   const double c2s = block_all_sum2(make_double2(c2, 0.0), red).x;
   if (tid == 0) {
-    p.part_g[h] = g;
-    p.part_c2[h] = c2s;
+    p.part_g[part] = g;
+    p.part_c2[part] = c2s;
   }
+  if constexpr (CLUSTER) cg::this_cluster().sync();   // no CTA leaves while its rows may still be read
 }
 
-// Backward sweep of one column h: the combined costate
+// Backward sweep of column h (rows split over the cluster as in the forward sweep): the combined costate
 //   chi_N = -(w_fid g / n^2) phi_T + (w_forbid/(N n)) Omega psi_N - (w_tint/(N n^2)) g_N phi_T,
 //   chi_{s-1} = U_s^+ chi_s + (w_forbid/(N n)) Omega psi_{s-1} - (w_tint/(N n^2)) g_{s-1} phi_T.
+template <bool CLUSTER>
 __global__ void __launch_bounds__(kT) k_eig_backward(EigCtx p) {
   extern __shared__ __align__(16) unsigned char sm[];
-  const int d = p.d, h = blockIdx.x, tid = threadIdx.x;
-  const int parts = kT / d < 1 ? 1 : kT / d;
-  double2* cur = reinterpret_cast<double2*>(sm);
-  double2* nxt = cur + d;
-  double2* tmp = nxt + d;   // parts x d partial products
+  const int d = p.d, cl = p.sweep_cl, tid = threadIdx.x;
+  const int h = blockIdx.x / cl, rank = blockIdx.x % cl;
+  const int r0 = row_begin(rank, d, cl), r1 = row_begin(rank + 1, d, cl), nr = r1 - r0;
+  const int parts = nr > 0 ? (kT / nr < 1 ? 1 : (kT / nr > d ? d : kT / nr)) : 1;
+  double2* buf0 = reinterpret_cast<double2*>(sm);
+  double2* buf1 = buf0 + d;
+  double2* tmp = buf1 + d;   // parts x nr partial products
   const size_t dd = (size_t)d * d, col = (size_t)h * d, slab = (size_t)p.n * d;
   const double2* tgt = p.target + col;
   const double nS = (double)p.n, Nd = (double)p.N;
@@ -410,30 +462,34 @@ __global__ void __launch_bounds__(kT) k_eig_backward(EigCtx p) {
         ch.x = fma(w, psiN[i].x, ch.x);
         ch.y = fma(w, psiN[i].y, ch.y);
       }
-      cur[i] = ch;
-      hist[i] = ch;
+      buf0[i] = ch;
+      if (i >= r0 && i < r1) hist[i] = ch;
     }
   }
   __syncthreads();
   for (int s = p.N; s >= 2; --s) {
+    const int it = p.N - s;
+    const double2* cur = (it & 1) ? buf1 : buf0;
+    double2* nxt = (it & 1) ? buf0 : buf1;
     const double2* Us = p.U + (size_t)(s - 1) * dd;
-    for (int t = tid; t < parts * d; t += kT) {
-      const int i = t % d, q = t / d;
+    for (int t = tid; t < parts * nr; t += kT) {
+      const int i = r0 + t % nr, q = t / nr;
       const int j0 = (int)((int64_t)q * d / parts), j1 = (int)((int64_t)(q + 1) * d / parts);
       double2 acc = make_double2(0.0, 0.0);
       for (int j = j0; j < j1; ++j) c_fma_conj(acc, Us[(size_t)j * d + i], cur[j]);
-      tmp[(size_t)q * d + i] = acc;
+      tmp[t] = acc;
     }
     __syncthreads();
     const double2* psi = p.psi_hist + (size_t)(s - 1) * slab + col;
     double2* hist = p.chi_hist + (size_t)(s - 1) * slab + col;
     double2 c3 = make_double2(0.0, 0.0);
     if (c3w != 0.0) c3 = make_double2(c3w * p.g3[s - 2].x, c3w * p.g3[s - 2].y);
-    for (int i = tid; i < d; i += kT) {
-      double2 y = tmp[i];
+    for (int li = tid; li < nr; li += kT) {
+      const int i = r0 + li;
+      double2 y = tmp[li];
       for (int q = 1; q < parts; ++q) {
-        y.x += tmp[(size_t)q * d + i].x;
-        y.y += tmp[(size_t)q * d + i].y;
+        y.x += tmp[(size_t)q * nr + li].x;
+        y.y += tmp[(size_t)q * nr + li].y;
       }
       if (c2w != 0.0) {
         const double w = c2w * p.omega[i];
@@ -444,20 +500,36 @@ __global__ void __launch_bounds__(kT) k_eig_backward(EigCtx p) {
       nxt[i] = y;
       hist[i] = y;
     }
-    __syncthreads();
-    double2* t = cur;
-    cur = nxt;
-    nxt = t;
+    exchange_rows<CLUSTER>(nxt, d, cl, rank, r0, r1);
   }
+  if constexpr (CLUSTER) cg::this_cluster().sync();
 }
 
-__device__ __forceinline__ double2 divided_difference(double li, double lj, double dt) {
-  // exp((D_i + D_j)/2) sin(theta)/theta, D = -i lambda dt, theta = (lambda_i - lambda_j) dt / 2
-  const double th = 0.5 * (li - lj) * dt;
-  const double sinc = fabs(th) < 1e-4 ? 1.0 - th * th * (1.0 / 6.0) : sin(th) / th;
-  double sn, cs;
-  sincos(0.5 * (li + lj) * dt, &sn, &cs);
-  return make_double2(cs * sinc, -sn * sinc);
+// sin(x)/x: the Taylor series of sin(x)/x through x^12 for |x| < 1/4 (remainder below 1e-20),
+// else the ratio itself.
+__device__ __forceinline__ double sinc_of(double x, double sin_x) {
+  if (fabs(x) < 0.25) {
+    const double x2 = x * x;
+    double t = 1.0 / 6227020800.0;           // 1/13!
+    t = fma(t, x2, -1.0 / 39916800.0);       // 1/11!
+    t = fma(t, x2, 1.0 / 362880.0);          // 1/9!
+    t = fma(t, x2, -1.0 / 5040.0);           // 1/7!
+    t = fma(t, x2, 1.0 / 120.0);             // 1/5!
+    t = fma(t, x2, -1.0 / 6.0);              // 1/3!
+    return fma(t, x2, 1.0);
+  }
+  return sin_x / x;
+}
+
+// Phi_ij = exp((D_i + D_j)/2) sin(theta)/theta with D = -i lambda dt and theta = alpha_i - alpha_j,
+// alpha = lambda dt / 2, from the per-eigenvalue cos/sin of alpha: exp((D_i + D_j)/2) = h_i h_j with
+// h = (cos alpha, -sin alpha), sin(theta) = s_i c_j - c_i s_j (used only where |theta| >= 1/4).
+__device__ __forceinline__ double2 divided_difference(double ai, double aj, double ci, double si, double cj,
+                                                      double sj) {
+  const double th = ai - aj;
+  const double sinc = sinc_of(th, fma(si, cj, -ci * sj));
+  const double2 hh = c_mul(make_double2(ci, -si), make_double2(cj, -sj));
+  return make_double2(hh.x * sinc, hh.y * sinc);
 }
 
 // Gradient of step s + 1 (block s):  with psi' = V^+ psi_s and chi' = V^+ chi_{s+1} (V = V_{s+1}),
@@ -472,6 +544,9 @@ __global__ void __launch_bounds__(kT, 1) k_eig_grad(EigCtx p) {
   double2* Q = reinterpret_cast<double2*>(sm);
   double2* cw = Q + (size_t)d * ldq;                       // kWarps x d
   double* acck = reinterpret_cast<double*>(cw + (size_t)kWarps * d);   // kWarps x K
+  double* ha = acck + kWarps * (K > 0 ? K : 1);                        // alpha_i = lambda_i dt / 2
+  double* hc = ha + d;                                                 // cos alpha_i
+  double* hs = hc + d;                                                 // sin alpha_i
   const size_t dd = (size_t)d * d, slab = (size_t)n * d;
   const double2* V = p.V + (size_t)s * dd;
   const double2* Vt = p.Vt + (size_t)s * dd;
@@ -492,12 +567,17 @@ __global__ void __launch_bounds__(kT, 1) k_eig_grad(EigCtx p) {
     xc[idx] = b;
   }
   for (int i = tid; i < kWarps * K; i += kT) acck[i] = 0.0;
+  for (int i = tid; i < d; i += kT) {
+    const double al = 0.5 * lam[i] * p.dt;
+    ha[i] = al;
+    sincos(al, &hs[i], &hc[i]);
+  }
   __syncthreads();
   for (int idx = tid; idx < d * d; idx += kT) {
     const int i = idx / d, j = idx % d;
     double2 m = make_double2(0.0, 0.0);
     for (int h = 0; h < n; ++h) c_fma_conj(m, xc[(size_t)h * d + i], xp[(size_t)h * d + j]);
-    Q[i * ldq + j] = c_mul(divided_difference(lam[i], lam[j], p.dt), m);
+    Q[i * ldq + j] = c_mul(divided_difference(ha[i], ha[j], hc[i], hs[i], hc[j], hs[j]), m);
   }
   __syncthreads();
   double2* c = cw + (size_t)warp * d;
@@ -545,37 +625,68 @@ __global__ void __launch_bounds__(kT, 1) k_eig_grad(EigCtx p) {
 }
 
 size_t forward_smem(int d) { return (size_t)16 * 2 * d + 8 * 2 * kWarps; }
-size_t backward_smem(int d) {
-  const int parts = kT / d < 1 ? 1 : kT / d;
-  return (size_t)16 * (2 + parts) * d;
-}
+size_t backward_smem(int d) { return (size_t)16 * (2 * d + kT); }
 
 }  // namespace
 
-int eig_step_smem(int d) { return (int)step_layout(d).bytes; }
+int eig_step_smem(int d) { return (int)block_bytes(d); }
+
+int eig_ql_smem(int d) { return 8 * 2 * 32 * d; }
+
+int eig_rotate_smem(int d) { return 8 * d * (d + 1); }
 
 int eig_grad_smem(int d, int K) {
-  return (int)((size_t)16 * d * (d + 1) + (size_t)16 * kWarps * d + (size_t)8 * kWarps * (K > 0 ? K : 1));
+  return (int)((size_t)16 * d * (d + 1) + (size_t)16 * kWarps * d + (size_t)8 * kWarps * (K > 0 ? K : 1) +
+               (size_t)8 * 3 * d);
 }
 
 cudaError_t eig_prepare(int d, int K) {
-  cudaError_t e = cudaFuncSetAttribute(k_eig_step, cudaFuncAttributeMaxDynamicSharedMemorySize, eig_step_smem(d));
+  cudaError_t e = cudaFuncSetAttribute(k_eig_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, eig_step_smem(d));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_eig_vectors, cudaFuncAttributeMaxDynamicSharedMemorySize, eig_step_smem(d));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eig_ql, cudaFuncAttributeMaxDynamicSharedMemorySize, eig_ql_smem(d));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_eig_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize, eig_rotate_smem(d));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_eig_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, eig_grad_smem(d, K));
   return e;
 }
 
+template <typename KernelT>
+cudaError_t launch_sweep_kernel(KernelT kern, const EigCtx& c, size_t smem, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(c.n * c.sweep_cl);
+  cfg.blockDim = dim3(kT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  if (c.sweep_cl > 1) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = c.sweep_cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, kern, c);
+}
+
 cudaError_t eig_forward(const EigCtx& c, cudaStream_t st) {
-  k_eig_step<<<c.N, kT, eig_step_smem(c.d), st>>>(c);
+  k_eig_tridiag<<<c.N, kT, eig_step_smem(c.d), st>>>(c);
+  k_eig_ql<<<(c.N + 31) / 32, 32, eig_ql_smem(c.d), st>>>(c);
+  k_eig_rotate<<<c.N, (c.d + 31) / 32 * 32, eig_rotate_smem(c.d), st>>>(c);
+  k_eig_vectors<<<c.N, kT, eig_step_smem(c.d), st>>>(c);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_eig_forward<<<c.n, kT, forward_smem(c.d), st>>>(c);
-  return cudaGetLastError();
+  const size_t smem = forward_smem(c.d);
+  return c.sweep_cl > 1 ? launch_sweep_kernel(k_eig_forward<true>, c, smem, st)
+                        : launch_sweep_kernel(k_eig_forward<false>, c, smem, st);
 }
 
 cudaError_t eig_backward(const EigCtx& c, cudaStream_t st) {
-  k_eig_backward<<<c.n, kT, backward_smem(c.d), st>>>(c);
-  cudaError_t e = cudaGetLastError();
+  const size_t smem = backward_smem(c.d);
+  cudaError_t e = c.sweep_cl > 1 ? launch_sweep_kernel(k_eig_backward<true>, c, smem, st)
+                                 : launch_sweep_kernel(k_eig_backward<false>, c, smem, st);
   if (e != cudaSuccess || c.K == 0) return e;
   k_eig_grad<<<c.N, kT, eig_grad_smem(c.d, c.K), st>>>(c);
   return cudaGetLastError();

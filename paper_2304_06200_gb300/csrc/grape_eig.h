@@ -11,6 +11,7 @@ constexpr int kEigMaxDim = 96;   // the step matrix and its eigenvector block li
 
 struct EigCtx {
   int d, n, N, K;
+  int sweep_cl;           // CTAs per column (one cluster) in the forward and backward sweeps
   double dt, w_fid, w_forbid, w_tint;
   const double2* H0;      // d x d dense drift, row-major
   const double2* Hk;      // K x d x d dense controls, row-major (Hermitian)
@@ -20,6 +21,13 @@ struct EigCtx {
   double2* Vt;            // N x d x d transposed copy (Vt_n[c][i] = V_n[i][c])
   double2* U;             // N x d x d step propagators (Householder vectors of the step until they are replaced)
   double* htau;           // N x d Householder scalars
+  double* tri_a;          // N x d diagonal of the tridiagonal form
+  double2* tri_t;         // N x d super-diagonal t_i = T_{i,i+1} (complex)
+  double2* phase;         // N x d diagonal phases that make the tridiagonal real
+  int rot_cap;            // recorded plane rotations per step (capacity)
+  int* rot_i;             // N x rot_cap rotation index i (columns i, i+1)
+  double2* rot_cs;        // N x rot_cap (c, s)
+  int* rot_n;             // N rotations recorded
   const double2* psi0;    // d x n column-major
   const double2* target;  // d x n column-major
   const double* omega;    // d or nullptr
@@ -36,6 +44,8 @@ struct EigCtx {
 };
 
 int eig_step_smem(int d);
+int eig_ql_smem(int d);
+int eig_rotate_smem(int d);
 int eig_grad_smem(int d, int K);
 cudaError_t eig_prepare(int d, int K);
 cudaError_t eig_forward(const EigCtx& c, cudaStream_t st);

@@ -422,7 +422,6 @@ grape_status build_eig(grape_problem* P, const grape_desc* d, const std::vector<
   const int64_t dim = P->dim;
   const int n = P->n, K = P->K, N = P->N;
   P->eig = true;
-  P->fwd.CL = P->bwd.CL = 1;
   P->bwd_mode = 1;
   P->ckpt_every = 0;
   P->n_ckpt = 0;
@@ -436,6 +435,13 @@ grape_status build_eig(grape_problem* P, const grape_desc* d, const std::vector<
         dense[(size_t)k * dd + (size_t)i * dim + ops[k].col[e]] = make_double2(v.real(), v.imag());
       }
   grape::EigCtx& c = P->ectx;
+  // CTAs per column in the sweeps: about ten rows each, at most 8 (portable cluster), and no more
+  // than the SMs can hold at once for all n columns
+  int cl = (int)std::min<int64_t>(8, std::max<int64_t>(1, dim / 10));
+  const int nsm = sm_count(P->device);
+  while (cl > 1 && (int64_t)n * cl > nsm) --cl;
+  c.sweep_cl = cl;
+  P->fwd.CL = P->bwd.CL = cl;
   c.d = (int)dim;
   c.n = n;
   c.N = N;
@@ -456,6 +462,22 @@ grape_status build_eig(grape_problem* P, const grape_desc* d, const std::vector<
   if ((st = dzeros(P, &ph, (size_t)(N + 1) * blk)) || (st = dzeros(P, &ch, (size_t)(N + 1) * blk)) ||
       (st = dzeros(P, &xs, (size_t)N * 2 * blk)))
     return st;
+  // QL rotations: about d^2 for a whole tridiagonal eigenproblem (1-2 shifted sweeps per eigenvalue
+  // over the unreduced part); four times that before the step reports kErrEig
+  c.rot_cap = (int)(4 * dd + 64);
+  double *tri_a;
+  double2 *tri_t, *phase, *rot_cs;
+  int *rot_i, *rot_n;
+  if ((st = dzeros(P, &tri_a, (size_t)N * dim)) || (st = dzeros(P, &tri_t, (size_t)N * dim)) ||
+      (st = dzeros(P, &phase, (size_t)N * dim)) || (st = dzeros(P, &rot_cs, (size_t)N * c.rot_cap)) ||
+      (st = dzeros(P, &rot_i, (size_t)N * c.rot_cap)) || (st = dzeros(P, &rot_n, (size_t)N)))
+    return st;
+  c.tri_a = tri_a;
+  c.tri_t = tri_t;
+  c.phase = phase;
+  c.rot_cs = rot_cs;
+  c.rot_i = rot_i;
+  c.rot_n = rot_n;
   c.lam = lam;
   c.htau = htau;
   c.V = V;
@@ -471,10 +493,11 @@ grape_status build_eig(grape_problem* P, const grape_desc* d, const std::vector<
     if ((st = upload(P, &P->d_omega, d->omega_diag, (size_t)dim))) return st;
   }
   if ((st = dzeros(P, &P->d_u, (size_t)std::max(K, 1) * N))) return st;
-  if ((st = dzeros(P, &P->d_part_g, (size_t)n)) || (st = dzeros(P, &P->d_part_c2, (size_t)n))) return st;
+  const size_t parts = (size_t)n * cl;
+  if ((st = dzeros(P, &P->d_part_g, parts)) || (st = dzeros(P, &P->d_part_c2, parts))) return st;
   if ((st = dzeros(P, &P->d_part_grad, (size_t)N * std::max(K, 1)))) return st;
   if ((st = dzeros(P, &P->d_g, 1)) || (st = dzeros(P, &P->d_cost, 1)) || (st = dzeros(P, &P->d_parts, 5))) return st;
-  if ((st = dzeros(P, &P->d_part_g3, (size_t)n * N)) || (st = dzeros(P, &P->d_g3, (size_t)N))) return st;
+  if ((st = dzeros(P, &P->d_part_g3, parts * N)) || (st = dzeros(P, &P->d_g3, (size_t)N))) return st;
   if ((st = dzeros(P, &P->d_grad, (size_t)std::max(K, 1) * N)) || (st = dzeros(P, &P->d_err, 1))) return st;
   c.psi0 = P->d_psi0;
   c.target = P->d_target;
@@ -1003,7 +1026,7 @@ grape_status run_forward(grape_problem* P, const double* u, bool u_on_device, cu
       return cuda_fail(e, "launch k_check_finite");
     if ((e = grape::eig_forward(P->ectx, st)) != cudaSuccess) return cuda_fail(e, "eigendecomposition forward sweep");
     grape::FinalizeParams fp{};
-    fp.n_parts = P->n;
+    fp.n_parts = P->n * P->ectx.sweep_cl;
     fp.n_states = P->n;
     fp.N = P->N;
     fp.K = P->K;
