@@ -30,6 +30,7 @@ namespace {
 
 constexpr int kT = 256;
 constexpr int kWarps = kT / 32;
+constexpr int kQlLanes = 8;   // steps per warp in k_eig_ql (the rest of the warp idles)
 
 __device__ __forceinline__ double2 c_mul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -79,8 +80,10 @@ __device__ double2 block_all_sum2(double2 v, double* red) {
 }
 
 // Shared-memory layout of the reduction and back-transformation kernels: one complex d x d block
-// with leading dimension d + 1 and three complex d-vectors.
-__host__ __device__ inline size_t block_bytes(int d) { return (size_t)16 * d * (d + 1) + (size_t)16 * 3 * d + 8 * 2 * kWarps; }
+// with leading dimension d + 1, three complex d-vectors and kT complex partial sums.
+__host__ __device__ inline size_t block_bytes(int d) {
+  return (size_t)16 * d * (d + 1) + (size_t)16 * 3 * d + (size_t)16 * kT + 8 * 2 * kWarps;
+}
 
 // Householder reduction of H_n = H0 + sum_k u_kn H_k (Sec. II) to tridiagonal form, one CTA per step.
 // H_k = I - tau v v^+ maps column k below the diagonal onto alpha e_1; the trailing block B becomes
@@ -88,12 +91,13 @@ __host__ __device__ inline size_t block_bytes(int d) { return (size_t)16 * d * (
 // the super-diagonal t_i = T_{i,i+1}, the vectors v_k (into the step's slice of U) and tau_k.
 __global__ void __launch_bounds__(kT) k_eig_tridiag(EigCtx p) {
   extern __shared__ __align__(16) unsigned char sm[];
-  const int d = p.d, step = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, lda = d + 1;
+  const int d = p.d, step = blockIdx.x, tid = threadIdx.x, lda = d + 1;
   double2* A = reinterpret_cast<double2*>(sm);
   double2* vv = A + (size_t)d * lda;
   double2* pv = vv + d;
   double2* wv = pv + d;
-  double* red = reinterpret_cast<double*>(wv + d);
+  double2* tmp = wv + d;   // kT partial sums
+  double* red = reinterpret_cast<double*>(tmp + kT);
   const size_t dd = (size_t)d * d;
   double2* hv = p.U + (size_t)step * dd;
   double* htau = p.htau + (size_t)step * d;
@@ -134,12 +138,24 @@ __global__ void __launch_bounds__(kT) k_eig_tridiag(EigCtx p) {
         hv[(size_t)k * d + i] = vi;
       }
       __syncthreads();
-      for (int i = warp; i < n1; i += kWarps) {
-        const double2* brow = A + (k + 1 + i) * lda + (k + 1);
-        double2 acc = make_double2(0.0, 0.0);
-        for (int j = lane; j < n1; j += 32) c_fma(acc, brow[j], vv[j]);
-        acc = warp_all_sum2(acc);
-        if (lane == 0) pv[i] = make_double2(tau * acc.x, tau * acc.y);
+      {   // p_i = tau sum_j B_ij v_j = tau sum_j conj(B_ji) v_j: rows of B read along i, j split in chunks
+        const int parts = kT / n1 < 1 ? 1 : kT / n1;
+        for (int t = tid; t < parts * n1; t += kT) {
+          const int i = t % n1, q = t / n1;
+          const int j0 = (int)((int64_t)q * n1 / parts), j1 = (int)((int64_t)(q + 1) * n1 / parts);
+          double2 acc = make_double2(0.0, 0.0);
+          for (int j = j0; j < j1; ++j) c_fma_conj(acc, A[(k + 1 + j) * lda + (k + 1 + i)], vv[j]);
+          tmp[t] = acc;
+        }
+        __syncthreads();
+        for (int i = tid; i < n1; i += kT) {
+          double2 acc = tmp[i];
+          for (int q = 1; q < parts; ++q) {
+            acc.x += tmp[q * n1 + i].x;
+            acc.y += tmp[q * n1 + i].y;
+          }
+          pv[i] = make_double2(tau * acc.x, tau * acc.y);
+        }
       }
       __syncthreads();
       double2 vp = make_double2(0.0, 0.0);
@@ -172,13 +188,13 @@ __global__ void __launch_bounds__(kT) k_eig_tridiag(EigCtx p) {
 // Implicit QL with Wilkinson-type shifts on the real symmetric tridiagonal T_r = P^+ T P
 // (P diagonal phases, P_{i+1} = P_i conj(t_i)/|t_i|), one thread per step: GB300 retires a warp's
 // FP64 instruction only every few tens of clocks per SM sub-partition, so the sequential scalar
-// recurrence runs with 32 steps side by side in the lanes of a warp.  The plane rotations are
+// recurrence runs with kQlLanes steps side by side in the lanes of a warp, spread over many SMs.  The plane rotations are
 // recorded (index, c, s) for k_eig_rotate; the eigenvalues go to lam.  At most 60 iterations per
 // eigenvalue and p.rot_cap rotations per step; past either limit kErrEig is set.
 __global__ void __launch_bounds__(32) k_eig_ql(EigCtx p) {
   extern __shared__ __align__(16) unsigned char sm[];
-  const int d = p.d, lane = threadIdx.x, step = blockIdx.x * 32 + lane;
-  if (step >= p.N) return;   // no block-wide synchronisation in this kernel
+  const int d = p.d, lane = threadIdx.x, step = blockIdx.x * kQlLanes + lane;
+  if (lane >= kQlLanes || step >= p.N) return;   // no block-wide synchronisation in this kernel
   double* a = reinterpret_cast<double*>(sm) + lane;   // a[i * 32]
   double* e = a + 32 * d;                              // e[i * 32]
   const double* ta = p.tri_a + (size_t)step * d;
@@ -283,31 +299,46 @@ __global__ void __launch_bounds__(128) k_eig_rotate(EigCtx p) {
 // U_n = V_n diag(exp(-i lambda dt)) V_n^+ written over the step's Householder vectors.
 __global__ void __launch_bounds__(kT) k_eig_vectors(EigCtx p) {
   extern __shared__ __align__(16) unsigned char sm[];
-  const int d = p.d, step = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, lda = d + 1;
+  const int d = p.d, step = blockIdx.x, tid = threadIdx.x, lda = d + 1;
   double2* A = reinterpret_cast<double2*>(sm);
   double2* vv = A + (size_t)d * lda;
   double2* pv = vv + d;
+  double2* tmp = pv + 2 * d;   // kT partial sums (same layout as the reduction kernel)
   const size_t dd = (size_t)d * d;
   const double2* hv = p.U + (size_t)step * dd;
   const double* htau = p.htau + (size_t)step * d;
   double2* V = p.V + (size_t)step * dd;
   for (int idx = tid; idx < d * d; idx += kT) A[(idx / d) * lda + idx % d] = V[idx];
   __syncthreads();
+  // H_k Y = Y - tau v (v^+ Y) on rows k+1..d-1: thread (c, q) sums rows of chunk q of column c,
+  // then subtracts from the same rows; the chunk sums of a column meet in tmp.
+  const int parts = kT / d < 1 ? 1 : kT / d;
   for (int k = d - 3; k >= 0; --k) {
     const double tau = htau[k];
     if (tau == 0.0) continue;
     const int n1 = d - k - 1;
     for (int i = tid; i < n1; i += kT) vv[i] = hv[(size_t)k * d + i];
     __syncthreads();
-    for (int c = warp; c < d; c += kWarps) {
+    const int c = tid % d, q = tid / d;
+    const bool active = q < parts;
+    const int i0 = (int)((int64_t)q * n1 / parts), i1 = (int)((int64_t)(q + 1) * n1 / parts);
+    if (active) {
       double2 acc = make_double2(0.0, 0.0);
-      for (int i = lane; i < n1; i += 32) c_fma_conj(acc, vv[i], A[(k + 1 + i) * lda + c]);
-      acc = warp_all_sum2(acc);
-      acc.x *= tau;
-      acc.y *= tau;
-      for (int i = lane; i < n1; i += 32) {
+      for (int i = i0; i < i1; ++i) c_fma_conj(acc, vv[i], A[(k + 1 + i) * lda + c]);
+      tmp[tid] = acc;
+    }
+    __syncthreads();
+    if (active) {
+      double2 sc = tmp[c];
+      for (int r = 1; r < parts; ++r) {
+        sc.x += tmp[r * d + c].x;
+        sc.y += tmp[r * d + c].y;
+      }
+      sc.x *= tau;
+      sc.y *= tau;
+      for (int i = i0; i < i1; ++i) {
         double2& y = A[(k + 1 + i) * lda + c];
-        const double2 t = c_mul(vv[i], acc);
+        const double2 t = c_mul(vv[i], sc);
         y.x -= t.x;
         y.y -= t.y;
       }
@@ -590,14 +621,21 @@ __global__ void __launch_bounds__(kT, 1) k_eig_grad(EigCtx p) {
       c[i] = acc;
     }
     __syncwarp();
-    constexpr int kPer = (kEigMaxDim + 31) / 32;   // entries a = lane + 32 q of T_:b held per lane
+    // T_ab only where some H_k[a][b] != 0 (column b of the controls' union pattern, at most d rows)
+    constexpr int kPer = (kEigMaxDim + 31) / 32;   // pattern entries e0 + lane + 32 q held per lane
+    const int e0 = p.cp_ptr[b], ne = p.cp_ptr[b + 1] - e0;
     double2 t[kPer];
+    int arow[kPer];
 #pragma unroll
     for (int q = 0; q < kPer; ++q) {
-      const int a = lane + 32 * q;
+      const int e = lane + 32 * q;
       double2 acc = make_double2(0.0, 0.0);
-      if (a < d)
+      arow[q] = 0;
+      if (e < ne) {
+        const int a = p.cp_row[e0 + e];
+        arow[q] = a;
         for (int i = 0; i < d; ++i) c_fma_conj(acc, Vt[(size_t)i * d + a], c[i]);
+      }
       t[q] = acc;
     }
     for (int k = 0; k < K; ++k) {
@@ -605,9 +643,8 @@ __global__ void __launch_bounds__(kT, 1) k_eig_grad(EigCtx p) {
       double im = 0.0;
 #pragma unroll
       for (int q = 0; q < kPer; ++q) {
-        const int a = lane + 32 * q;
-        if (a < d) {
-          const double2 hba = hb[a];
+        if (lane + 32 * q < ne) {
+          const double2 hba = hb[arow[q]];
           im = fma(hba.x, t[q].y, fma(-hba.y, t[q].x, im));
         }
       }
@@ -673,7 +710,7 @@ cudaError_t launch_sweep_kernel(KernelT kern, const EigCtx& c, size_t smem, cuda
 
 cudaError_t eig_forward(const EigCtx& c, cudaStream_t st) {
   k_eig_tridiag<<<c.N, kT, eig_step_smem(c.d), st>>>(c);
-  k_eig_ql<<<(c.N + 31) / 32, 32, eig_ql_smem(c.d), st>>>(c);
+  k_eig_ql<<<(c.N + kQlLanes - 1) / kQlLanes, 32, eig_ql_smem(c.d), st>>>(c);
   k_eig_rotate<<<c.N, (c.d + 31) / 32 * 32, eig_rotate_smem(c.d), st>>>(c);
   k_eig_vectors<<<c.N, kT, eig_step_smem(c.d), st>>>(c);
   cudaError_t e = cudaGetLastError();

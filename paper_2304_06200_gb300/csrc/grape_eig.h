@@ -16,6 +16,8 @@ struct EigCtx {
   const double2* H0;      // d x d dense drift, row-major
   const double2* Hk;      // K x d x d dense controls, row-major (Hermitian)
   const double* u;        // K x N controls
+  const int* cp_ptr;      // d + 1: column b of the union pattern of the controls holds rows
+  const int* cp_row;      //   cp_row[cp_ptr[b] .. cp_ptr[b + 1]) (ascending)
   double* lam;            // N x d eigenvalues of H_n
   double2* V;             // N x d x d eigenvectors (column c of V_n is the c-th eigenvector)
   double2* Vt;            // N x d x d transposed copy (Vt_n[c][i] = V_n[i][c])

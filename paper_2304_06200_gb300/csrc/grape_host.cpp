@@ -450,6 +450,24 @@ grape_status build_eig(grape_problem* P, const grape_desc* d, const std::vector<
   c.w_fid = P->w_fid;
   c.w_forbid = P->w_forbid;
   c.w_tint = P->w_tint;
+  // column-wise union pattern of the controls: the entries (a, b) where the gradient needs T_ab
+  std::vector<int> cp_ptr(dim + 1, 0), cp_row;
+  for (int64_t b = 0; b < dim; ++b) {
+    for (int64_t a = 0; a < dim; ++a) {
+      bool nz = false;
+      for (int k = 1; k <= K && !nz; ++k) {
+        const double2 v = dense[(size_t)k * dd + (size_t)a * dim + b];
+        nz = v.x != 0.0 || v.y != 0.0;
+      }
+      if (nz) cp_row.push_back((int)a);
+    }
+    cp_ptr[b + 1] = (int)cp_row.size();
+  }
+  int *cp_ptr_d, *cp_row_d;
+  if ((st = upload(P, &cp_ptr_d, cp_ptr.data(), cp_ptr.size()))) return st;
+  if ((st = upload(P, &cp_row_d, cp_row.data(), std::max<size_t>(cp_row.size(), 1)))) return st;
+  c.cp_ptr = cp_ptr_d;
+  c.cp_row = cp_row_d;
   double2* ops_d;
   if ((st = upload(P, &ops_d, dense.data(), dense.size()))) return st;
   c.H0 = ops_d;
