@@ -520,3 +520,15 @@ def test_eig_propagator_optimizer_and_errors():
         hg.schedule()
     c1, _ = hg.cost_and_grad(p.u0)     # the problem stays usable after a reported error
     assert c1 == c0
+
+
+@pytest.mark.parametrize("propagator", ["taylor", "eig"])
+def test_closed_form_golden_values(propagator):
+    """Both propagators against the 40-digit closed forms of tests/golden/rabi_closed_forms.txt."""
+    from test_golden import TERMS, golden_rows, rabi_case
+    for delta, u, dt, N, vals in golden_rows():
+        for term, col in TERMS.items():
+            p, uu = rabi_case(delta, u, dt, N, term)
+            cost, grad = _hg(p, propagator=propagator).cost_and_grad(uu)
+            assert abs(cost - vals[col]) <= 1e-11, (term, delta, u, cost, vals[col])
+            assert abs(np.sum(grad) - vals[col + 1]) <= 1e-10 * max(1.0, abs(vals[col + 1])), (term, delta, u)
