@@ -82,6 +82,14 @@ __device__ __forceinline__ void team_sync() {
   }
 }
 
+// The two halves of the cluster barrier: work placed between them overlaps the barrier latency.
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
 // ------------------------------------------------------------------ block reductions (deterministic)
 
 __device__ double block_sum(double v, double* red) {
@@ -401,6 +409,19 @@ __global__ void __launch_bounds__(512, 1) k_forward(SweepParams p) {
   const int64_t col0 = (int64_t)team * p.dim + r0;
   for (int i = threadIdx.x; i < nrows; i += blockDim.x) c.psi[i] = p.psi0[col0 + i];
   double c2acc = 0.0;
+  const bool split_rows = nrows <= (int)blockDim.x;   // one row per thread: split-barrier term loop
+  // The thread's row: entries [ea, eb), of which [la, lb) have their column in this CTA's rows
+  // (columns ascend within a row and owners ascend with the column, so they are contiguous).
+  int ea = 0, eb = 0, la = 0, lb = 0;
+  __syncthreads();   // the local pattern written by sweep_setup
+  if (split_rows && (int)threadIdx.x < nrows) {
+    ea = c.lrow[threadIdx.x];
+    eb = c.lrow[threadIdx.x + 1];
+    la = ea;
+    while (la < eb && ((c.lcol[la] >> kOwnerShift) & 0xFFu) < (uint32_t)rank) ++la;
+    lb = la;
+    while (lb < eb && ((c.lcol[lb] >> kOwnerShift) & 0xFFu) == (uint32_t)rank) ++lb;
+  }
   team_sync<CLUSTER>();
   for (int n = 0; n < p.N; ++n) {
     const int m = p.ms_m[n], s = p.ms_s[n];
@@ -413,6 +434,59 @@ __global__ void __launch_bounds__(512, 1) k_forward(SweepParams p) {
       for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
         X0[i] = from_d2<T>(c.psi[i]);
         c.inc[i] = make_double2(0.0, 0.0);
+      }
+      if constexpr (CLUSTER && sizeof(C2) == 16) {
+        if (split_rows) {
+          // Each term: the entries whose column lies in this CTA's rows are summed between the
+          // arrive and the wait of the previous term's cluster barrier; the remote ones after it.
+          // X_q goes to buffer q & 1, which the other CTAs last read (as X_{q-2}) before they
+          // arrived at barrier q-1, so writing it after wait(q-1) is safe; the last term of the
+          // substep closes with a full barrier before X_0 of the next substep is written.
+          __syncthreads();
+          cluster_arrive();
+          const int i = threadIdx.x;
+          for (int q = 1; q <= m; ++q) {
+            const int src = (q - 1) & 1, dst = q & 1;
+            const C2* xs = X0 + src * R;
+            C2 y = czero<C2>();
+            if (i < nrows)
+              for (int e = la; e < lb; ++e) cmacT(y, c.vals[e], xs[c.lcol[e] & kLocalMask]);
+            cluster_wait();
+            if (i < nrows) {
+              // one loop over the remote entries on both sides of the local run, so that a warp
+              // pays for its longest remote list once
+              const int nl = la - ea, nr = nl + (eb - lb);
+              for (int k = 0; k < nr; ++k) {
+                const int e = k < nl ? ea + k : lb + (k - nl);
+                const uint32_t enc = c.lcol[e];
+                cmacT(y, c.vals[e], tab[src].ptr[(enc >> kOwnerShift) & 0xFFu][enc & kLocalMask]);
+              }
+              const T iq = (T)c_inv_int[q];
+              y.x *= iq;
+              y.y *= iq;
+              X0[dst * R + i] = y;
+              double2 a = c.inc[i];
+              const double2 yd = to_d2(y);
+              a.x += yd.x;
+              a.y += yd.y;
+              c.inc[i] = a;
+            }
+            if (q < m) {
+              __syncthreads();
+              cluster_arrive();
+            } else {
+              team_sync<CLUSTER>();
+            }
+          }
+          for (int j = threadIdx.x; j < nrows; j += blockDim.x) {
+            double2 v = c.psi[j];
+            const double2 a = c.inc[j];
+            v.x += a.x;
+            v.y += a.y;
+            c.psi[j] = v;
+          }
+          continue;
+        }
       }
       team_sync<CLUSTER>();
       for (int q = 1; q <= m; ++q) {
