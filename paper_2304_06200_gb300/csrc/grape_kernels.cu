@@ -605,6 +605,54 @@ __device__ __forceinline__ void phase_a(Team<T, CLUSTER>& tm, int m, WOut wout) 
     wout(m - 1, i, w0);
   }
   team_sync<CLUSTER>();
+  if constexpr (CLUSTER && sizeof(C2) == 16) {
+    if (tm.nrows <= (int)blockDim.x) {
+      // One row per thread: the exchange buffers are written first, then the cluster barrier is
+      // opened and the row's bookkeeping (increment, Horner slot store, costate) runs before the
+      // wait, so that it and the slot store overlap the barrier.  Same arithmetic as the loop below.
+      const int i = threadIdx.x;
+      for (int q = 1; q <= m; ++q) {
+        const int src = (q - 1) & 1, dst = q & 1;
+        const T iq = (T)c_inv_int[q];
+        const double fq = c_inv_fact[m - q];
+        C2 ya = czero<C2>(), yw = czero<C2>(), w = czero<C2>();
+        double2 ch = make_double2(0.0, 0.0);
+        if (i < tm.nrows) {
+          row_mv2<T, CLUSTER>(c.vals, c.lcol, c.lrow[i], c.lrow[i + 1], tm.X(src), tm.tab[src], tm.X(2 + src),
+                              tm.tab[2 + src], ya, yw);
+          ya.x *= -iq;
+          ya.y *= -iq;
+          tm.X(dst)[i] = ya;
+          ch = c.chi[i];
+          if (q < m) {
+            w = horner(ch, fq, yw);
+            tm.X(2 + dst)[i] = w;
+          }
+        }
+        __syncthreads();
+        cluster_arrive();
+        if (i < tm.nrows) {
+          double2 a = c.inc[i];
+          a.x += ya.x;
+          a.y += ya.y;
+          c.inc[i] = a;
+          if (q < m)
+            wout(m - 1 - q, i, w);
+          else
+            c.chi[i] = make_double2(fma(ch.x, fq, -yw.x), fma(ch.y, fq, -yw.y));
+        }
+        cluster_wait();
+      }
+      for (int j = threadIdx.x; j < tm.nrows; j += blockDim.x) {
+        double2 v = c.psi[j];
+        const double2 a = c.inc[j];
+        v.x += a.x;
+        v.y += a.y;
+        c.psi[j] = v;
+      }
+      return;
+    }
+  }
   for (int q = 1; q <= m; ++q) {
     const int src = (q - 1) & 1, dst = q & 1;
     const T iq = (T)c_inv_int[q];
