@@ -636,7 +636,7 @@ def dense_compare(local, n_steps):
     return res
 
 
-def _timed_eval(hg, p, u0, dev, reps=3):
+def _timed_fwd_bwd(hg, p, u0, dev, reps=3):
     """Median forward / backward milliseconds of one evaluation (CUDA events), plus its cost and gradient."""
     import torch
     u = torch.tensor(u0, dtype=torch.float64, device=dev)
@@ -683,7 +683,7 @@ def eig_compare(local):
         ref = None
         for prop in ("taylor", "eig"):
             hg = GrapeProblem(p, device=local, propagator=prop)
-            r, c, g = _timed_eval(hg, p, u0, dev)
+            r, c, g = _timed_fwd_bwd(hg, p, u0, dev)
             if prop == "taylor":
                 r["taylor_terms_per_sweep"] = hg.info()["total_terms"]
                 ref = (c, g)
