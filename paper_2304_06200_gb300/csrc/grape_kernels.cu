@@ -376,6 +376,12 @@ struct Team {
   int r0, nrows, R, rank, CL;
   int64_t e0;
   int nnz_loc;
+  // One row per thread (FP64 cluster teams): the thread's row is entries [ea, eb), its entries with a
+  // column in this CTA's rows are the run [la, la + nloc) (columns ascend, so do their owners), and
+  // l1 = the smallest nloc of the warp's rows: the first l1 of the run are summed before the wait
+  // of the cluster barrier, the other entries in one loop after it.
+  bool one_row;
+  int ea, eb, la, l1;
 };
 
 // ------------------------------------------------------------------ forward sweep
@@ -604,45 +610,67 @@ __device__ __forceinline__ void phase_a(Team<T, CLUSTER>& tm, int m, WOut wout) 
     tm.X(2)[i] = w0;
     wout(m - 1, i, w0);
   }
-  team_sync<CLUSTER>();
   if constexpr (CLUSTER && sizeof(C2) == 16) {
-    if (tm.nrows <= (int)blockDim.x) {
-      // One row per thread: the exchange buffers are written first, then the cluster barrier is
-      // opened and the row's bookkeeping (increment, Horner slot store, costate) runs before the
-      // wait, so that it and the slot store overlap the barrier.  Same arithmetic as the loop below.
+    if (tm.one_row) {
+      // Split cluster barrier.  Term q: the first l1 local entries of the row (reading this CTA's
+      // rows of X_{q-1}) before wait(q-1), the other entries after it; X_q is written, the barrier
+      // is opened (arrive(q)), and the row's bookkeeping (increment, Horner slot, costate) runs
+      // while the other CTAs finish.  X_q goes to buffer q & 1, which the others last read as
+      // X_{q-2} before they arrived at barrier q-1.  The loop trip counts are those of a single
+      // row loop (l1 is uniform in the warp), so no FP64 instruction is added.
+      __syncthreads();
+      cluster_arrive();
       const int i = threadIdx.x;
+      const bool act = i < tm.nrows;
+      const int nleft = tm.la - tm.ea, nrest = (tm.eb - tm.ea) - tm.l1;
       for (int q = 1; q <= m; ++q) {
         const int src = (q - 1) & 1, dst = q & 1;
-        const T iq = (T)c_inv_int[q];
-        const double fq = c_inv_fact[m - q];
+        const C2* xa = tm.X(src);
+        const C2* xw = tm.X(2 + src);
         C2 ya = czero<C2>(), yw = czero<C2>(), w = czero<C2>();
         double2 ch = make_double2(0.0, 0.0);
-        if (i < tm.nrows) {
-          row_mv2<T, CLUSTER>(c.vals, c.lcol, c.lrow[i], c.lrow[i + 1], tm.X(src), tm.tab[src], tm.X(2 + src),
-                              tm.tab[2 + src], ya, yw);
+        if (act)
+          for (int k = 0; k < tm.l1; ++k) {
+            const int e = tm.la + k;
+            const uint32_t loc = c.lcol[e] & kLocalMask;
+            const C2 v = c.vals[e];
+            cmacT(ya, v, xa[loc]);
+            cmacT(yw, v, xw[loc]);
+          }
+        cluster_wait();
+        if (act) {
+          for (int k = 0; k < nrest; ++k) {
+            const int e = k < nleft ? tm.ea + k : tm.la + tm.l1 + (k - nleft);
+            const uint32_t enc = c.lcol[e];
+            const C2 v = c.vals[e];
+            cmacT(ya, v, xload<T, CLUSTER>(xa, tm.tab[src], enc));
+            cmacT(yw, v, xload<T, CLUSTER>(xw, tm.tab[2 + src], enc));
+          }
+          const T iq = (T)c_inv_int[q];
           ya.x *= -iq;
           ya.y *= -iq;
           tm.X(dst)[i] = ya;
           ch = c.chi[i];
           if (q < m) {
-            w = horner(ch, fq, yw);
+            w = horner(ch, c_inv_fact[m - q], yw);
             tm.X(2 + dst)[i] = w;
           }
         }
         __syncthreads();
         cluster_arrive();
-        if (i < tm.nrows) {
+        if (act) {
           double2 a = c.inc[i];
           a.x += ya.x;
           a.y += ya.y;
           c.inc[i] = a;
+          const double fq = c_inv_fact[m - q];
           if (q < m)
             wout(m - 1 - q, i, w);
           else
             c.chi[i] = make_double2(fma(ch.x, fq, -yw.x), fma(ch.y, fq, -yw.y));
         }
-        cluster_wait();
       }
+      cluster_wait();
       for (int j = threadIdx.x; j < tm.nrows; j += blockDim.x) {
         double2 v = c.psi[j];
         const double2 a = c.inc[j];
@@ -653,6 +681,7 @@ __device__ __forceinline__ void phase_a(Team<T, CLUSTER>& tm, int m, WOut wout) 
       return;
     }
   }
+  team_sync<CLUSTER>();
   for (int q = 1; q <= m; ++q) {
     const int src = (q - 1) & 1, dst = q & 1;
     const T iq = (T)c_inv_int[q];
@@ -698,6 +727,54 @@ __device__ __forceinline__ void phase_b(Team<T, CLUSTER>& tm, int m, WIn win) {
   const Carve<T>& c = tm.c;
   // With one row per thread, w_{p+1} is fetched while term p runs (it may come from L2).
   const bool one_row = tm.nrows <= (int)blockDim.x;
+  if constexpr (CLUSTER && sizeof(C2) == 16) {
+    if (tm.one_row) {
+      // Split cluster barrier as in phase A: the first l1 local entries before the wait, the rest
+      // after it.  The last term writes nothing that others read, so it ends after its wait.
+      __syncthreads();
+      cluster_arrive();
+      const int i = threadIdx.x;
+      const bool act = i < tm.nrows;
+      const int nleft = tm.la - tm.ea, nrest = (tm.eb - tm.ea) - tm.l1;
+      C2 wnext = act ? win(0, i) : czero<C2>();
+      for (int pp = 0; pp < m; ++pp) {
+        const int src = pp & 1, dst = src ^ 1;
+        const bool more = pp < m - 1;
+        const C2* xs = tm.X(4 + src);
+        C2 wp = wnext, y0 = czero<C2>();
+        auto entry = [&](int e, const C2 x, uint32_t enc) {
+          if (more) cmacT(y0, c.vals[e], x);
+          if (enc & kCtrlBit) {
+            double2 acc = c.W[e];
+            cmac_conjT(acc, wp, x);
+            c.W[e] = acc;
+          }
+        };
+        if (act) {
+          if (more) wnext = win(pp + 1, i);
+          for (int k = 0; k < tm.l1; ++k) {
+            const int e = tm.la + k;
+            const uint32_t enc = c.lcol[e];
+            entry(e, xs[enc & kLocalMask], enc);
+          }
+        }
+        cluster_wait();
+        if (act) {
+          for (int k = 0; k < nrest; ++k) {
+            const int e = k < nleft ? tm.ea + k : tm.la + tm.l1 + (k - nleft);
+            const uint32_t enc = c.lcol[e];
+            entry(e, xload<T, CLUSTER>(xs, tm.tab[4 + src], enc), enc);
+          }
+          if (more) tm.X(4 + dst)[i] = y0;
+        }
+        if (more) {
+          __syncthreads();
+          cluster_arrive();
+        }
+      }
+      return;
+    }
+  }
   C2 wnext = (one_row && (int)threadIdx.x < tm.nrows) ? win(0, threadIdx.x) : czero<C2>();
   team_sync<CLUSTER>();
   for (int pp = 0; pp < m; ++pp) {
@@ -854,6 +931,26 @@ __device__ __forceinline__ void team_init(Team<T, CLUSTER>& tm, unsigned char* s
       for (int b = 0; b < 6; ++b) tab[b].ptr[threadIdx.x] = cl.map_shared_rank(tm.X(b), threadIdx.x);
   }
   sweep_setup(p, tm.c.lrow, tm.c.lcol, tm.r0, tm.nrows, tm.e0, tm.nnz_loc);
+  tm.one_row = CLUSTER && sizeof(cx<T>) == 16 && tm.nrows <= (int)blockDim.x;
+  tm.ea = tm.eb = tm.la = tm.l1 = 0;
+  __syncthreads();   // the local pattern
+  if (tm.one_row) {
+    int nloc = 1 << 30;
+    if ((int)threadIdx.x < tm.nrows) {
+      const int* lrow = tm.c.lrow;
+      const uint32_t* lcol = tm.c.lcol;
+      tm.ea = lrow[threadIdx.x];
+      tm.eb = lrow[threadIdx.x + 1];
+      int a = tm.ea;
+      while (a < tm.eb && ((lcol[a] >> kOwnerShift) & 0xFFu) < (uint32_t)rank) ++a;
+      int b = a;
+      while (b < tm.eb && ((lcol[b] >> kOwnerShift) & 0xFFu) == (uint32_t)rank) ++b;
+      tm.la = a;
+      nloc = b - a;
+    }
+    const int wmin = __reduce_min_sync(0xffffffffu, nloc);
+    tm.l1 = wmin == (1 << 30) ? 0 : wmin;
+  }
 }
 
 // ------------------------------------------------------------------ backward sweep, one team per column
