@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import tempfile
 import warnings
 
 import numpy as np
@@ -93,7 +94,7 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"grape_bench_clocks_rank{index}_{os.getpid()}.csv")
 
     def start(self):
         try:

@@ -183,12 +183,20 @@ grape_status grape_cost(grape_problem* prob, const double* u, double* cost, int3
  * GRAPE_ESTATE if no forward sweep has run. */
 grape_status grape_grad(grape_problem* prob, double* grad, int32_t on_device, void* stream);
 
-/* GRAPE by steepest descent (Sec. II: a <- a - eta grad C): n_iter iterations, each a full
- * evaluation (forward sweep, cost, backward sweep, gradient) followed by the update, recorded once
- * into a CUDA graph (on the first call and whenever eta changes) and launched n_iter times.
- *   u      K x N controls: initial values in, final values out (host or device per on_device).
- *   costs  n_iter doubles: the cost at the start of each iteration.
- * Not available for GRAPE_TC_FP16 problems (their sweeps are driven from the host). */
+/* GRAPE by steepest descent (Sec. II, Eq. (4): a^(j+1) = a^(j) - eta grad C(a^(j)), constant
+ * learning rate eta): n_iter iterations, each a full evaluation (forward sweep, cost, backward
+ * sweep, gradient) followed by the update u - (eta * g) (two roundings), recorded once into a CUDA
+ * graph on a problem-owned stream (on the first call, when eta changes and when n_iter exceeds all
+ * earlier calls) and launched n_iter times on `stream`.
+ *   u         K x N controls, row-major: initial values in, final values out.  Caller-owned; host
+ *             memory if on_device == 0, device memory on the problem's device otherwise.
+ *   n_iter    >= 1.
+ *   eta       finite, > 0.
+ *   costs     n_iter doubles (same memory kind as u): costs[j] = C(a^(j)), the cost before update j.
+ * Errors: GRAPE_EINVAL for bad arguments or a GRAPE_TC_FP16 problem (its sweeps are driven from
+ * the host); device errors of any iteration (non-finite controls, ETOL, ETIMEOUT) are returned when
+ * on_device == 0 (the call then synchronises `stream`), else by grape_sync_status.  A following
+ * grape_grad needs a new grape_cost (the stored sweep state belongs to the last iterate). */
 grape_status grape_optimize(grape_problem* prob, double* u, int32_t n_iter, double eta, double* costs,
                             int32_t on_device, void* stream);
 

@@ -532,3 +532,29 @@ def test_closed_form_golden_values(propagator):
             cost, grad = _hg(p, propagator=propagator).cost_and_grad(uu)
             assert abs(cost - vals[col]) <= 1e-11, (term, delta, u, cost, vals[col])
             assert abs(np.sum(grad) - vals[col + 1]) <= 1e-10 * max(1.0, abs(vals[col + 1])), (term, delta, u)
+
+
+def test_c3_full_size_in_the_bench_configuration():
+    """d = 4000, N = 2000 with the partitions bench.py times (forward 16 CTAs per column, two-team
+    backward): bitwise equal to the one-team backward, and sampled gradient entries equal to central
+    differences of the GPU's own cost (schedule unchanged by the perturbation)."""
+    p = build_config("c3_gate_d4000")
+    hg = _hg(p)
+    inf = hg.info()
+    assert inf["backward_mode"] == 2 and inf["cluster_forward"] == 16
+    u = np.array(p.u0)
+    cost, grad = hg.cost_and_grad(u)
+    m0, s0, _ = hg.schedule()
+    one_team = _hg(p, cluster=inf["cluster"], backward_mode=1)
+    c1, g1 = one_team.cost_and_grad(u)
+    assert c1 == cost and np.array_equal(g1, grad)
+    one_team.close()
+    h = 1e-5
+    for k, n in ((0, 3), (3, 1000), (5, 1996)):
+        up = u.copy(); up[k, n] += h
+        um = u.copy(); um[k, n] -= h
+        cp = hg.cost(up)
+        assert np.array_equal(hg.schedule()[0], m0) and np.array_equal(hg.schedule()[1], s0)
+        cm = hg.cost(um)
+        fd = (cp - cm) / (2 * h)
+        assert abs(fd - grad[k, n]) <= 1e-6 * np.abs(grad).max(), (k, n, fd, grad[k, n])
