@@ -91,7 +91,7 @@ __host__ __device__ inline size_t block_bytes(int d) {
 // the super-diagonal t_i = T_{i,i+1}, the vectors v_k (into the step's slice of U) and tau_k.
 __global__ void __launch_bounds__(kT) k_eig_tridiag(EigCtx p) {
   extern __shared__ __align__(16) unsigned char sm[];
-  const int d = p.d, step = blockIdx.x, tid = threadIdx.x, lda = d + 1;
+  const int d = p.d, step = p.step0 + blockIdx.x, tid = threadIdx.x, lda = d + 1;
   double2* A = reinterpret_cast<double2*>(sm);
   double2* vv = A + (size_t)d * lda;
   double2* pv = vv + d;
@@ -193,8 +193,8 @@ __global__ void __launch_bounds__(kT) k_eig_tridiag(EigCtx p) {
 // eigenvalue and p.rot_cap rotations per step; past either limit kErrEig is set.
 __global__ void __launch_bounds__(32) k_eig_ql(EigCtx p) {
   extern __shared__ __align__(16) unsigned char sm[];
-  const int d = p.d, lane = threadIdx.x, step = blockIdx.x * kQlLanes + lane;
-  if (lane >= kQlLanes || step >= p.N) return;   // no block-wide synchronisation in this kernel
+  const int d = p.d, lane = threadIdx.x, step = p.step0 + blockIdx.x * kQlLanes + lane;
+  if (lane >= kQlLanes || step >= p.step0 + p.nsteps) return;   // no block-wide synchronisation here
   double* a = reinterpret_cast<double*>(sm) + lane;   // a[i * 32]
   double* e = a + 32 * d;                              // e[i * 32]
   const double* ta = p.tri_a + (size_t)step * d;
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(32) k_eig_ql(EigCtx p) {
 // independent), then Y = P Z written to the step's slice of V.
 __global__ void __launch_bounds__(128) k_eig_rotate(EigCtx p) {
   extern __shared__ __align__(16) unsigned char sm[];
-  const int d = p.d, step = blockIdx.x, row = threadIdx.x;
+  const int d = p.d, step = p.step0 + blockIdx.x, row = threadIdx.x;
   if (row >= d) return;   // no block-wide synchronisation in this kernel
   double* z = reinterpret_cast<double*>(sm) + (size_t)row * (d + 1);
   for (int c = 0; c < d; ++c) z[c] = c == row ? 1.0 : 0.0;
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(128) k_eig_rotate(EigCtx p) {
 // U_n = V_n diag(exp(-i lambda dt)) V_n^+ written over the step's Householder vectors.
 __global__ void __launch_bounds__(kT) k_eig_vectors(EigCtx p) {
   extern __shared__ __align__(16) unsigned char sm[];
-  const int d = p.d, step = blockIdx.x, tid = threadIdx.x, lda = d + 1;
+  const int d = p.d, step = p.step0 + blockIdx.x, tid = threadIdx.x, lda = d + 1;
   double2* A = reinterpret_cast<double2*>(sm);
   double2* vv = A + (size_t)d * lda;
   double2* pv = vv + d;
@@ -404,10 +404,11 @@ __device__ __forceinline__ void exchange_rows(double2* buf, int d, int cl, int r
   __syncthreads();
 }
 
-// Forward sweep of column h = blockIdx.x / CL, rows split over a cluster of CL CTAs:
-// psi_s = U_s psi_{s-1} (Eq. (statepropagation)); overlaps and the C2 / C3 accumulations per CTA.
-// Double-buffered: a CTA rewrites a buffer two steps after it was read remotely, and the
-// cluster barrier of the step in between orders the two.
+// Forward sweep of column h = blockIdx.x / CL over steps [p.step0, p.step0 + p.nsteps), rows split
+// over a cluster of CL CTAs: psi_s = U_s psi_{s-1} (Eq. (statepropagation)); overlaps and the C2 /
+// C3 accumulations per CTA (C2 partials add up over the launches of one sweep).  Double-buffered: a
+// CTA rewrites a buffer two steps after it was read remotely, and the cluster barrier of the step in
+// between orders the two.
 template <bool CLUSTER>
 __global__ void __launch_bounds__(kT) k_eig_forward(EigCtx p) {
   extern __shared__ __align__(16) unsigned char sm[];
@@ -419,13 +420,16 @@ __global__ void __launch_bounds__(kT) k_eig_forward(EigCtx p) {
   double* red = reinterpret_cast<double*>(buf1 + d);
   const size_t dd = (size_t)d * d, col = (size_t)h * d, slab = (size_t)p.n * d;
   const double2* tgt = p.target + col;
-  for (int i = tid; i < d; i += kT) buf0[i] = p.psi0[col + i];
-  for (int i = r0 + tid; i < r1; i += kT) p.psi_hist[col + i] = p.psi0[col + i];
+  const int s0 = p.step0, s1 = p.step0 + p.nsteps;
+  const double2* start = s0 == 0 ? p.psi0 + col : p.psi_hist + (size_t)s0 * slab + col;
+  for (int i = tid; i < d; i += kT) buf0[i] = start[i];
+  if (s0 == 0)
+    for (int i = r0 + tid; i < r1; i += kT) p.psi_hist[col + i] = p.psi0[col + i];
   __syncthreads();
   double c2 = 0.0;
-  for (int s = 0; s < p.N; ++s) {
-    const double2* cur = (s & 1) ? buf1 : buf0;
-    double2* nxt = (s & 1) ? buf0 : buf1;
+  for (int s = s0; s < s1; ++s) {
+    const double2* cur = ((s - s0) & 1) ? buf1 : buf0;
+    double2* nxt = ((s - s0) & 1) ? buf0 : buf1;
     const double2* Us = p.U + (size_t)s * dd;
     double2* hist = p.psi_hist + (size_t)(s + 1) * slab + col;
     for (int i = r0 + warp; i < r1; i += kWarps) {
@@ -447,14 +451,14 @@ __global__ void __launch_bounds__(kT) k_eig_forward(EigCtx p) {
       if (tid == 0) p.part_g3[(size_t)part * p.N + s] = g;
     }
   }
-  const double2* fin = (p.N & 1) ? buf1 : buf0;
+  const double2* fin = ((s1 - s0) & 1) ? buf1 : buf0;
   double2 g = make_double2(0.0, 0.0);
   for (int i = r0 + tid; i < r1; i += kT) c_fma_conj(g, tgt[i], fin[i]);
   g = block_all_sum2(g, red);
   const double c2s = block_all_sum2(make_double2(c2, 0.0), red).x;
   if (tid == 0) {
-    p.part_g[part] = g;
-    p.part_c2[part] = c2s;
+    p.part_g[part] = g;   // the overlap of the sweep's last state (the last launch writes it last)
+    p.part_c2[part] = s0 == 0 ? c2s : p.part_c2[part] + c2s;
   }
   if constexpr (CLUSTER) cg::this_cluster().sync();   // no CTA leaves while its rows may still be read
 }
@@ -708,13 +712,15 @@ cudaError_t launch_sweep_kernel(KernelT kern, const EigCtx& c, size_t smem, cuda
   return cudaLaunchKernelEx(&cfg, kern, c);
 }
 
-cudaError_t eig_forward(const EigCtx& c, cudaStream_t st) {
-  k_eig_tridiag<<<c.N, kT, eig_step_smem(c.d), st>>>(c);
-  k_eig_ql<<<(c.N + kQlLanes - 1) / kQlLanes, 32, eig_ql_smem(c.d), st>>>(c);
-  k_eig_rotate<<<c.N, (c.d + 31) / 32 * 32, eig_rotate_smem(c.d), st>>>(c);
-  k_eig_vectors<<<c.N, kT, eig_step_smem(c.d), st>>>(c);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+cudaError_t eig_propagators(const EigCtx& c, cudaStream_t st) {
+  k_eig_tridiag<<<c.nsteps, kT, eig_step_smem(c.d), st>>>(c);
+  k_eig_ql<<<(c.nsteps + kQlLanes - 1) / kQlLanes, 32, eig_ql_smem(c.d), st>>>(c);
+  k_eig_rotate<<<c.nsteps, (c.d + 31) / 32 * 32, eig_rotate_smem(c.d), st>>>(c);
+  k_eig_vectors<<<c.nsteps, kT, eig_step_smem(c.d), st>>>(c);
+  return cudaGetLastError();
+}
+
+cudaError_t eig_forward_sweep(const EigCtx& c, cudaStream_t st) {
   const size_t smem = forward_smem(c.d);
   return c.sweep_cl > 1 ? launch_sweep_kernel(k_eig_forward<true>, c, smem, st)
                         : launch_sweep_kernel(k_eig_forward<false>, c, smem, st);

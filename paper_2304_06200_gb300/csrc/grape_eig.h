@@ -12,6 +12,8 @@ constexpr int kEigMaxDim = 96;   // the step matrix and its eigenvector block li
 struct EigCtx {
   int d, n, N, K;
   int sweep_cl;           // CTAs per column (one cluster) in the forward and backward sweeps
+  int step0, nsteps;      // steps [step0, step0 + nsteps) of one launch of the per-step kernels and
+                          // of the forward sweep (the backward kernels take all N steps)
   double dt, w_fid, w_forbid, w_tint;
   const double2* H0;      // d x d dense drift, row-major
   const double2* Hk;      // K x d x d dense controls, row-major (Hermitian)
@@ -50,7 +52,10 @@ int eig_ql_smem(int d);
 int eig_rotate_smem(int d);
 int eig_grad_smem(int d, int K);
 cudaError_t eig_prepare(int d, int K);
-cudaError_t eig_forward(const EigCtx& c, cudaStream_t st);
+// Eigenpairs and propagators of steps [c.step0, c.step0 + c.nsteps) (independent across steps).
+cudaError_t eig_propagators(const EigCtx& c, cudaStream_t st);
+// Forward sweep over steps [c.step0, c.step0 + c.nsteps); launches of one sweep follow each other.
+cudaError_t eig_forward_sweep(const EigCtx& c, cudaStream_t st);
 cudaError_t eig_backward(const EigCtx& c, cudaStream_t st);
 
 }  // namespace grape

@@ -199,6 +199,10 @@ struct grape_problem {
   // eigendecomposition propagators (App. F)
   bool eig = false;
   grape::EigCtx ectx{};
+  int eig_chunks = 1;                   // step chunks whose propagators are computed concurrently
+  std::vector<cudaStream_t> eig_lanes;  // one stream per chunk
+  std::vector<cudaEvent_t> eig_ready;   // chunk c's propagators are done
+  cudaEvent_t eig_fork = nullptr;
   // dense tensor-core mode
   bool dense = false;
   grape::DenseCtx dctx{};
@@ -233,6 +237,12 @@ struct grape_problem {
     return p;
   }
   void release() {
+    for (auto e : eig_ready) cudaEventDestroy(e);
+    for (auto l : eig_lanes) cudaStreamDestroy(l);
+    if (eig_fork) cudaEventDestroy(eig_fork);
+    eig_ready.clear();
+    eig_lanes.clear();
+    eig_fork = nullptr;
     if (opt_exec) cudaGraphExecDestroy(opt_exec);
     opt_exec = nullptr;
     if (fwd_exec) cudaGraphExecDestroy(fwd_exec);
@@ -528,9 +538,55 @@ grape_status build_eig(grape_problem* P, const grape_desc* d, const std::vector<
   c.g3 = P->d_g3;
   c.part_grad = P->d_part_grad;
   c.err = P->d_err;
-  const cudaError_t e = grape::eig_prepare((int)dim, K);
+  cudaError_t e = grape::eig_prepare((int)dim, K);
   if (e != cudaSuccess) return cuda_fail(e, "eigendecomposition kernel attributes");
+  // The QL recurrence of a step is sequential (FP64 latency bound, ~10 ms at d = 80) whatever the
+  // number of steps: with the steps in chunks on their own streams, the chunks' reductions,
+  // rotations and back-transformations run while other chunks iterate, and the forward sweep
+  // starts on a chunk as soon as its propagators are done.
+  P->eig_chunks = N >= 256 ? 8 : (N >= 64 ? 4 : 1);
+  if (P->eig_chunks > 1) {
+    if ((e = cudaEventCreateWithFlags(&P->eig_fork, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(e, "cudaEventCreate");
+    for (int j = 0; j < P->eig_chunks; ++j) {
+      cudaStream_t l = nullptr;
+      cudaEvent_t ev = nullptr;
+      if ((e = cudaStreamCreateWithFlags(&l, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+      P->eig_lanes.push_back(l);
+      if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+      P->eig_ready.push_back(ev);
+    }
+  }
   return GRAPE_OK;
+}
+
+// Eigendecomposition forward pass on st: propagators of every step (in chunks on the problem's
+// lanes, forked from and joined back into st) and the forward sweep.
+cudaError_t eig_forward_all(grape_problem* P, cudaStream_t st) {
+  grape::EigCtx c = P->ectx;
+  const int N = P->N, C = P->eig_chunks;
+  cudaError_t e;
+  if (C <= 1) {
+    c.step0 = 0;
+    c.nsteps = N;
+    if ((e = grape::eig_propagators(c, st)) != cudaSuccess) return e;
+    return grape::eig_forward_sweep(c, st);
+  }
+  if ((e = cudaEventRecord(P->eig_fork, st)) != cudaSuccess) return e;
+  for (int j = 0; j < C; ++j) {
+    c.step0 = (int)((int64_t)j * N / C);
+    c.nsteps = (int)((int64_t)(j + 1) * N / C) - c.step0;
+    if ((e = cudaStreamWaitEvent(P->eig_lanes[j], P->eig_fork, 0)) != cudaSuccess) return e;
+    if ((e = grape::eig_propagators(c, P->eig_lanes[j])) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(P->eig_ready[j], P->eig_lanes[j])) != cudaSuccess) return e;
+  }
+  for (int j = 0; j < C; ++j) {
+    c.step0 = (int)((int64_t)j * N / C);
+    c.nsteps = (int)((int64_t)(j + 1) * N / C) - c.step0;
+    if ((e = cudaStreamWaitEvent(st, P->eig_ready[j], 0)) != cudaSuccess) return e;
+    if ((e = grape::eig_forward_sweep(c, st)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // Record `body` (a sequence of launches on one stream) into a CUDA graph on the problem's capture
@@ -1042,7 +1098,7 @@ grape_status run_forward(grape_problem* P, const double* u, bool u_on_device, cu
   if (P->eig) {
     if ((e = grape::check_nonfinite_u(P->d_u, (int64_t)P->K * P->N, P->d_err, st)) != cudaSuccess)
       return cuda_fail(e, "launch k_check_finite");
-    if ((e = grape::eig_forward(P->ectx, st)) != cudaSuccess) return cuda_fail(e, "eigendecomposition forward sweep");
+    if ((e = eig_forward_all(P, st)) != cudaSuccess) return cuda_fail(e, "eigendecomposition forward sweep");
     grape::FinalizeParams fp{};
     fp.n_parts = P->n * P->ectx.sweep_cl;
     fp.n_states = P->n;

@@ -462,7 +462,7 @@ def test_eig_propagator_random_problems(dim, K, n, N, density):
 
 
 @pytest.mark.parametrize("name,N,tint", [("c1_state_transfer_d30", 200, 0.0), ("c2_gate_d80", 150, 0.0),
-                                         ("c2_gate_d80", 60, 0.7)])
+                                         ("c2_gate_d80", 60, 0.7), ("c1_state_transfer_d30", 300, 0.4)])
 def test_eig_propagator_workloads(name, N, tint):
     p = build_config(name, n_steps=N)
     p.w_tint = tint
@@ -502,9 +502,11 @@ def test_eig_and_taylor_propagators_agree_on_a_three_transmon_gate():
     assert np.linalg.norm(g_t - g_e) <= 1e-8 * np.linalg.norm(g_e)
 
 
-def test_eig_propagator_optimizer_and_errors():
+@pytest.mark.parametrize("N", [40, 300])
+def test_eig_propagator_optimizer_and_errors(N):
+    """Steepest descent recorded in a graph (N = 300: the step chunks run on forked streams)."""
     from paper_2304_06200_gb300 import GrapeError
-    p = build_config("c1_state_transfer_d30", n_steps=40)
+    p = build_config("c1_state_transfer_d30", n_steps=N)
     hg = _hg(p, propagator="eig")
     c0, g0 = hg.cost_and_grad(p.u0)
     u1, costs = hg.optimize(p.u0, 3, 0.02)
@@ -536,8 +538,8 @@ def test_closed_form_golden_values(propagator):
 
 def test_c3_full_size_in_the_bench_configuration():
     """d = 4000, N = 2000 with the partitions bench.py times (forward 16 CTAs per column, two-team
-    backward): bitwise equal to the one-team backward, and sampled gradient entries equal to central
-    differences of the GPU's own cost (schedule unchanged by the perturbation)."""
+    backward): equal to the one-team backward within rounding, and sampled gradient entries equal to
+    central differences of the GPU's own cost (schedule unchanged by the perturbation)."""
     p = build_config("c3_gate_d4000")
     hg = _hg(p)
     inf = hg.info()
@@ -545,9 +547,12 @@ def test_c3_full_size_in_the_bench_configuration():
     u = np.array(p.u0)
     cost, grad = hg.cost_and_grad(u)
     m0, s0, _ = hg.schedule()
+    # the one-team problem gets the backward's team size for its forward sweep as well, so the two
+    # differ by rounding only (bitwise equality at equal partitions is tested above)
     one_team = _hg(p, cluster=inf["cluster"], backward_mode=1)
     c1, g1 = one_team.cost_and_grad(u)
-    assert c1 == cost and np.array_equal(g1, grad)
+    assert abs(c1 - cost) <= 1e-13 * abs(cost)
+    assert np.linalg.norm(g1 - grad) <= 1e-11 * np.linalg.norm(grad)
     one_team.close()
     h = 1e-5
     for k, n in ((0, 3), (3, 1000), (5, 1996)):
