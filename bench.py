@@ -599,7 +599,7 @@ def dense_compare(local, n_steps):
     dev = torch.device("cuda", local)
     res = {"workload": workload_description(p) + ", H stored dense"}
     ref = None
-    for prec in ("fp64", "tc_fp16"):
+    for prec in ("fp64", "tc_fp16", "tc_bf16"):
         hg = GrapeProblem(p, device=local, precision=prec)
         u = torch.tensor(p.u0, dtype=torch.float64, device=dev)
         cost = torch.zeros((), dtype=torch.float64, device=dev)

@@ -67,9 +67,11 @@ typedef enum { GRAPE_CSR = 0, GRAPE_DENSE = 1 } grape_format;
 typedef enum {
   GRAPE_FP64 = 0,        /* complex128 throughout                                        */
   GRAPE_FP32_BULK = 1,   /* Taylor increments in complex64, states/costates kept FP64     */
-  GRAPE_TC_FP16 = 2      /* dense operator: every Taylor product is a real-split GEMM on the
+  GRAPE_TC_FP16 = 2,     /* dense operator: every Taylor product is a real-split GEMM on the
                             tensor cores (FP16 hi/lo operands, FP32 accumulation); states,
                             costates and reductions FP64.  Needs dim % 128 == 0, n_states <= 16. */
+  GRAPE_TC_BF16 = 3      /* as GRAPE_TC_FP16 with BF16 hi/lo operands (8 + 8 significant bits
+                            instead of 11 + 11: wider exponent range, ~2^-16 relative operands) */
 } grape_precision;
 
 /* How each step's propagator exp(-i H_n dt) acts.
@@ -193,7 +195,7 @@ grape_status grape_grad(grape_problem* prob, double* grad, int32_t on_device, vo
  *   n_iter    >= 1.
  *   eta       finite, > 0.
  *   costs     n_iter doubles (same memory kind as u): costs[j] = C(a^(j)), the cost before update j.
- * Errors: GRAPE_EINVAL for bad arguments or a GRAPE_TC_FP16 problem (its sweeps are driven from
+ * Errors: GRAPE_EINVAL for bad arguments or a tensor-core problem (its sweeps are driven from
  * the host); device errors of any iteration (non-finite controls, ETOL, ETIMEOUT) are returned when
  * on_device == 0 (the call then synchronises `stream`), else by grape_sync_status.  A following
  * grape_grad needs a new grape_cost (the stored sweep state belongs to the last iterate). */

@@ -8,7 +8,7 @@ import os
 from .build import LIB, build_library
 
 GRAPE_CSR, GRAPE_DENSE = 0, 1
-GRAPE_FP64, GRAPE_FP32_BULK, GRAPE_TC_FP16 = 0, 1, 2
+GRAPE_FP64, GRAPE_FP32_BULK, GRAPE_TC_FP16, GRAPE_TC_BF16 = 0, 1, 2, 3
 GRAPE_PROP_TAYLOR, GRAPE_PROP_EIG = 0, 1
 
 STATUS = {

@@ -16,6 +16,7 @@
 // 16 bytes per core matrix, K-adjacent core matrices 128 bytes apart, 8-row groups 1024 bytes
 // apart), one thread issues the MMAs, and the K-split partials are summed deterministically through
 // distributed shared memory by rank 0 of the cluster.
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include <cstdint>
@@ -86,6 +87,7 @@ struct ApplyArgs {
   float2* y;               // output: d x ncols complex, column-major (column h contiguous)
   int d, ncols, nreal;     // nreal = 2 * ncols padded to a multiple of 16 (MMA N)
   float alpha;             // y = alpha * B x
+  int bf16;                // operands are bf16 bit patterns (else fp16)
   int* err;
 };
 
@@ -138,8 +140,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_apply(ApplyArgs a) {
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
 
-  // idesc: D f32, A/B f16, both K-major, N = nreal, M = 128
-  const uint32_t idesc = (1u << 4) | ((uint32_t)(nreal >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
+  // idesc: D f32, A/B f16 or bf16, both K-major, N = nreal, M = 128
+  // A and B always share one type (bits 7-9 and 10-12: 0 = f16, 1 = bf16)
+  const uint32_t ab_type = a.bf16 ? 1u : 0u;
+  const uint32_t idesc = (1u << 4) | (ab_type << 7) | (ab_type << 10) | ((uint32_t)(nreal >> 3) << 17) |
+                         ((uint32_t)(kTM >> 4) << 24);
   uint32_t phase[2] = {0u, 0u};
   int ok = 1;
   load_chunk(0, stage[0]);
@@ -262,12 +267,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_apply(ApplyArgs a) {
 
 // ------------------------------------------------------------------ elementwise chain kernels
 
-__device__ __forceinline__ void split_f16(float v, __half& hi, __half& lo) {
-  hi = __float2half_rn(v);
-  lo = __float2half_rn(v - __half2float(hi));
+// v = hi + lo in two 16-bit floats: fp16 (11 significant bits each) or, for BF, bf16 (8 each,
+// stored as raw bits in the same 16-bit arrays).
+template <bool BF>
+__device__ __forceinline__ void split16(float v, __half& hi, __half& lo) {
+  if constexpr (BF) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+    __half_raw rh, rl;
+    rh.x = __bfloat16_as_ushort(h);
+    rl.x = __bfloat16_as_ushort(l);
+    hi = __half(rh);
+    lo = __half(rl);
+  } else {
+    hi = __float2half_rn(v);
+    lo = __float2half_rn(v - __half2float(hi));
+  }
 }
 
 // X (real columns 2h, 2h+1 of block `blk`) <- split of a complex FP64 (scaled) or FP32 block
+template <bool BF>
 __global__ void k_split_d(const double2* __restrict__ v, double scale, int d, int ncols, int col_off, __half* xh,
                           __half* xl) {
   const int64_t total = (int64_t)d * ncols;
@@ -275,16 +294,17 @@ __global__ void k_split_d(const double2* __restrict__ v, double scale, int d, in
     const int h = (int)(i / d), r = (int)(i % d);
     const double2 z = v[i];
     __half a, b;
-    split_f16((float)(z.x * scale), a, b);
+    split16<BF>((float)(z.x * scale), a, b);
     xh[(int64_t)(2 * (h + col_off)) * d + r] = a;
     xl[(int64_t)(2 * (h + col_off)) * d + r] = b;
-    split_f16((float)(z.y * scale), a, b);
+    split16<BF>((float)(z.y * scale), a, b);
     xh[(int64_t)(2 * (h + col_off) + 1) * d + r] = a;
     xl[(int64_t)(2 * (h + col_off) + 1) * d + r] = b;
   }
 }
 
 // forward term: x_q = y (already scaled by 1/q), inc += y, X <- split(y)
+template <bool BF>
 __global__ void k_fwd_term(const float2* __restrict__ y, double2* inc, int d, int ncols, __half* xh, __half* xl) {
   const int64_t total = (int64_t)d * ncols;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -295,10 +315,10 @@ __global__ void k_fwd_term(const float2* __restrict__ y, double2* inc, int d, in
     a.y += z.y;
     inc[i] = a;
     __half p, q;
-    split_f16(z.x, p, q);
+    split16<BF>(z.x, p, q);
     xh[(int64_t)(2 * h) * d + r] = p;
     xl[(int64_t)(2 * h) * d + r] = q;
-    split_f16(z.y, p, q);
+    split16<BF>(z.y, p, q);
     xh[(int64_t)(2 * h + 1) * d + r] = p;
     xl[(int64_t)(2 * h + 1) * d + r] = q;
   }
@@ -316,6 +336,7 @@ __global__ void k_axpy_d(double2* a, const double2* __restrict__ b, int64_t tota
 
 // phase A term q: y holds (B [a | w]) for the psi chain (columns 0..n-1) and the Horner chain (n..2n-1).
 //   a_q = -y_a / q (inc += a_q), w_{m-1-q} = chi/(m-q)! - y_w  (q < m), chi^(l) = chi - y_w (q == m)
+template <bool BF>
 __global__ void k_phase_a_term(const float2* __restrict__ y, double2* inc, double2* chi, float2* wslot, int d, int n,
                                int q, int m, double iq, double fq, __half* xh, __half* xl) {
   const int64_t total = (int64_t)d * n;
@@ -329,20 +350,20 @@ __global__ void k_phase_a_term(const float2* __restrict__ y, double2* inc, doubl
     a.y += ai;
     inc[i] = a;
     __half p, s2;
-    split_f16(ar, p, s2);
+    split16<BF>(ar, p, s2);
     xh[(int64_t)(2 * h) * d + r] = p;
     xl[(int64_t)(2 * h) * d + r] = s2;
-    split_f16(ai, p, s2);
+    split16<BF>(ai, p, s2);
     xh[(int64_t)(2 * h + 1) * d + r] = p;
     xl[(int64_t)(2 * h + 1) * d + r] = s2;
     const double2 ch = chi[i];
     if (q < m) {
       const float wr = (float)(ch.x * fq) - yw.x, wi = (float)(ch.y * fq) - yw.y;
       wslot[(int64_t)(m - 1 - q) * total + i] = make_float2(wr, wi);
-      split_f16(wr, p, s2);
+      split16<BF>(wr, p, s2);
       xh[(int64_t)(2 * (h + n)) * d + r] = p;
       xl[(int64_t)(2 * (h + n)) * d + r] = s2;
-      split_f16(wi, p, s2);
+      split16<BF>(wi, p, s2);
       xh[(int64_t)(2 * (h + n) + 1) * d + r] = p;
       xl[(int64_t)(2 * (h + n) + 1) * d + r] = s2;
     } else {
@@ -352,6 +373,7 @@ __global__ void k_phase_a_term(const float2* __restrict__ y, double2* inc, doubl
 }
 
 // phase A start: X <- [split(psi) | split(chi / m!)], w_{m-1} = chi / m!, inc = 0
+template <bool BF>
 __global__ void k_phase_a_start(const double2* __restrict__ psi, const double2* __restrict__ chi, double2* inc,
                                 float2* wslot, int d, int n, int m, double fm, __half* xh, __half* xl) {
   const int64_t total = (int64_t)d * n;
@@ -359,26 +381,27 @@ __global__ void k_phase_a_start(const double2* __restrict__ psi, const double2* 
     const int h = (int)(i / d), r = (int)(i % d);
     const double2 v = psi[i];
     __half p, s2;
-    split_f16((float)v.x, p, s2);
+    split16<BF>((float)v.x, p, s2);
     xh[(int64_t)(2 * h) * d + r] = p;
     xl[(int64_t)(2 * h) * d + r] = s2;
-    split_f16((float)v.y, p, s2);
+    split16<BF>((float)v.y, p, s2);
     xh[(int64_t)(2 * h + 1) * d + r] = p;
     xl[(int64_t)(2 * h + 1) * d + r] = s2;
     inc[i] = make_double2(0.0, 0.0);
     const double2 ch = chi[i];
     const float wr = (float)(ch.x * fm), wi = (float)(ch.y * fm);
     wslot[(int64_t)(m - 1) * total + i] = make_float2(wr, wi);
-    split_f16(wr, p, s2);
+    split16<BF>(wr, p, s2);
     xh[(int64_t)(2 * (h + n)) * d + r] = p;
     xl[(int64_t)(2 * (h + n)) * d + r] = s2;
-    split_f16(wi, p, s2);
+    split16<BF>(wi, p, s2);
     xh[(int64_t)(2 * (h + n) + 1) * d + r] = p;
     xl[(int64_t)(2 * (h + n) + 1) * d + r] = s2;
   }
 }
 
 // phase B: xcur <- y (the next x_p, FP32) and X <- split(y)
+template <bool BF>
 __global__ void k_phase_b_term(const float2* __restrict__ y, float2* xcur, int d, int n, __half* xh, __half* xl) {
   const int64_t total = (int64_t)d * n;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -386,10 +409,10 @@ __global__ void k_phase_b_term(const float2* __restrict__ y, float2* xcur, int d
     const float2 z = y[i];
     xcur[i] = z;
     __half p, s2;
-    split_f16(z.x, p, s2);
+    split16<BF>(z.x, p, s2);
     xh[(int64_t)(2 * h) * d + r] = p;
     xl[(int64_t)(2 * h) * d + r] = s2;
-    split_f16(z.y, p, s2);
+    split16<BF>(z.y, p, s2);
     xh[(int64_t)(2 * h + 1) * d + r] = p;
     xl[(int64_t)(2 * h + 1) * d + r] = s2;
   }
@@ -423,6 +446,7 @@ __global__ void k_w_accum(const float2* __restrict__ wp, const float2* __restric
 
 // dense operator of step n: B = -i (dt/s) (H0 + sum_k u_kn H_k) on the union pattern, split into the
 // FP16 hi/lo parts of Br = (dt/s) Im H and Bi = -(dt/s) Re H (entries off the pattern stay zero)
+template <bool BF>
 __global__ void k_dense_assemble(const int64_t* __restrict__ rowptr, const int* __restrict__ ucol,
                                  const double2* __restrict__ h0v, const int* __restrict__ ectr_ptr,
                                  const int* __restrict__ ectr_k, const double2* __restrict__ ectr_val,
@@ -438,10 +462,10 @@ __global__ void k_dense_assemble(const int64_t* __restrict__ rowptr, const int* 
       }
       const int64_t o = (int64_t)i * d + ucol[e];
       __half p, q;
-      split_f16((float)(scale * v.y), p, q);
+      split16<BF>((float)(scale * v.y), p, q);
       brh[o] = p;
       brl[o] = q;
-      split_f16((float)(-scale * v.x), p, q);
+      split16<BF>((float)(-scale * v.x), p, q);
       bih[o] = p;
       bil[o] = q;
     }
@@ -571,6 +595,15 @@ int ew_grid(int64_t total) {
 
 int dense_apply_smem(int nreal) { return 2 * stage_bytes(nreal); }
 
+// Launch of a split kernel with the operand type of the problem (fp16 or bf16 pairs).
+#define SPLIT_LAUNCH(kern, grid, block, st, ...)                               \
+  do {                                                                          \
+    if (c.bf16)                                                                 \
+      kern<true><<<(grid), (block), 0, (st)>>>(__VA_ARGS__);                    \
+    else                                                                        \
+      kern<false><<<(grid), (block), 0, (st)>>>(__VA_ARGS__);                   \
+  } while (0)
+
 // y = alpha * B x for the first `ncols` complex columns held in X (real columns 2h, 2h+1).
 static cudaError_t apply(const DenseCtx& c, int ncols, float alpha, float2* y, cudaStream_t st) {
   ApplyArgs a{};
@@ -585,6 +618,7 @@ static cudaError_t apply(const DenseCtx& c, int ncols, float alpha, float2* y, c
   a.ncols = ncols;
   a.nreal = ((2 * ncols + 15) / 16) * 16;
   a.alpha = alpha;
+  a.bf16 = c.bf16;
   a.err = c.err;
   const int smem = dense_apply_smem(a.nreal);
   cudaError_t e;
@@ -654,15 +688,15 @@ cudaError_t dense_forward(const DenseCtx& c, const int* m_host, const int* s_hos
   for (int step = 0; step < c.N; ++step) {
     const int m = m_host[step], s = s_host[step];
     if (m <= 0 || s <= 0) continue;
-    k_dense_assemble<<<std::min(d, 2048), 256, 0, st>>>(c.rowptr, c.ucol, c.h0v, c.ectr_ptr, c.ectr_k, c.ectr_val,
+    SPLIT_LAUNCH(k_dense_assemble, std::min(d, 2048), 256, st, c.rowptr, c.ucol, c.h0v, c.ectr_ptr, c.ectr_k, c.ectr_val,
                                                        c.u, c.N, step, c.dt / s, d, c.brh, c.brl, c.bih, c.bil);
     DCHK(cudaGetLastError());
     for (int l = 0; l < s; ++l) {
-      k_split_d<<<g, 256, 0, st>>>(c.psi, 1.0, d, n, 0, c.xh, c.xl);
+      SPLIT_LAUNCH(k_split_d, g, 256, st, c.psi, 1.0, d, n, 0, c.xh, c.xl);
       DCHK(cudaMemsetAsync(c.inc, 0, tot * sizeof(double2), st));
       for (int q = 1; q <= m; ++q) {
         DCHK(apply(c, n, 1.0f / q, c.y, st));
-        k_fwd_term<<<g, 256, 0, st>>>(c.y, c.inc, d, n, c.xh, c.xl);
+        SPLIT_LAUNCH(k_fwd_term, g, 256, st, c.y, c.inc, d, n, c.xh, c.xl);
         DCHK(cudaGetLastError());
       }
       k_axpy_d<<<g, 256, 0, st>>>(c.psi, c.inc, tot);
@@ -700,17 +734,17 @@ cudaError_t dense_backward(const DenseCtx& c, const int* m_host, const int* s_ho
   for (int step = c.N - 1; step >= 0; --step) {
     const int m = m_host[step], s = s_host[step];
     if (m <= 0 || s <= 0) continue;
-    k_dense_assemble<<<std::min(d, 2048), 256, 0, st>>>(c.rowptr, c.ucol, c.h0v, c.ectr_ptr, c.ectr_k, c.ectr_val,
+    SPLIT_LAUNCH(k_dense_assemble, std::min(d, 2048), 256, st, c.rowptr, c.ucol, c.h0v, c.ectr_ptr, c.ectr_k, c.ectr_val,
                                                        c.u, c.N, step, c.dt / s, d, c.brh, c.brl, c.bih, c.bil);
     DCHK(cudaGetLastError());
     DCHK(cudaMemsetAsync(c.W, 0, (size_t)std::max(c.nce, 1) * sizeof(double2), st));
     for (int l = s - 1; l >= 0; --l) {
       // phase A: [psi | Horner] chains with -B
-      k_phase_a_start<<<g, 256, 0, st>>>(c.psi, c.chi, c.inc, c.wslot, d, n, m, c.inv_fact[m], c.xh, c.xl);
+      SPLIT_LAUNCH(k_phase_a_start, g, 256, st, c.psi, c.chi, c.inc, c.wslot, d, n, m, c.inv_fact[m], c.xh, c.xl);
       DCHK(cudaGetLastError());
       for (int q = 1; q <= m; ++q) {
         DCHK(apply(c, 2 * n, 1.0f, c.y, st));
-        k_phase_a_term<<<g, 256, 0, st>>>(c.y, c.inc, c.chi, c.wslot, d, n, q, m, 1.0 / q, c.inv_fact[m - q], c.xh,
+        SPLIT_LAUNCH(k_phase_a_term, g, 256, st, c.y, c.inc, c.chi, c.wslot, d, n, q, m, 1.0 / q, c.inv_fact[m - q], c.xh,
                                          c.xl);
         DCHK(cudaGetLastError());
       }
@@ -718,7 +752,7 @@ cudaError_t dense_backward(const DenseCtx& c, const int* m_host, const int* s_ho
       DCHK(cudaGetLastError());
       // phase B: x chain with B, W accumulation on control entries
       k_psi_to_f32<<<g, 256, 0, st>>>(c.psi, c.xcur, tot);
-      k_split_d<<<g, 256, 0, st>>>(c.psi, 1.0, d, n, 0, c.xh, c.xl);
+      SPLIT_LAUNCH(k_split_d, g, 256, st, c.psi, 1.0, d, n, 0, c.xh, c.xl);
       DCHK(cudaGetLastError());
       for (int p = 0; p < m; ++p) {
         if (c.nce > 0) {
@@ -728,7 +762,7 @@ cudaError_t dense_backward(const DenseCtx& c, const int* m_host, const int* s_ho
         }
         if (p < m - 1) {
           DCHK(apply(c, n, 1.0f, c.y, st));
-          k_phase_b_term<<<g, 256, 0, st>>>(c.y, c.xcur, d, n, c.xh, c.xl);
+          SPLIT_LAUNCH(k_phase_b_term, g, 256, st, c.y, c.xcur, d, n, c.xh, c.xl);
           DCHK(cudaGetLastError());
         }
       }

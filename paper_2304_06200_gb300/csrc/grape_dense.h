@@ -10,6 +10,7 @@ namespace grape {
 
 struct DenseCtx {
   int d, n, N, K, ksplit;
+  int bf16;                 // operand pairs are bf16 (GRAPE_TC_BF16), else fp16 (GRAPE_TC_FP16)
   double dt, w_fid, w_forbid, w_tint;
   int ckpt_every, n_ckpt;
   double inv_fact[62];

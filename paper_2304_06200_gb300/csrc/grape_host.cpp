@@ -287,7 +287,7 @@ int sm_count(int dev) {
   return std::max(v, 1);
 }
 
-// Device buffers of the dense tensor-core mode (GRAPE_TC_FP16).
+// Device buffers of the dense tensor-core modes (GRAPE_TC_FP16, GRAPE_TC_BF16).
 grape_status build_dense(grape_problem* P, const grape_desc* d, const std::vector<int64_t>& rowptr,
                          const std::vector<int32_t>& ucol, const std::vector<double2>& h0v, const std::vector<int>& cptr,
                          const std::vector<int>& cidx, const std::vector<double2>& cval, const std::vector<int>& ectr_ptr,
@@ -319,6 +319,7 @@ grape_status build_dense(grape_problem* P, const grape_desc* d, const std::vecto
   c.N = N;
   c.K = K;
   c.ksplit = 1;   // chosen below, after the kernel attributes are set
+  c.bf16 = P->precision == GRAPE_TC_BF16 ? 1 : 0;
   c.dt = P->dt;
   c.w_fid = P->w_fid;
   c.w_forbid = P->w_forbid;
@@ -696,7 +697,8 @@ grape_status build(grape_problem* P, const grape_desc* d) {
   if (P->table.x_max < 0.0) return fail(GRAPE_ETOL, "no (m, s) pair satisfies E_A <= tau even for ||A||_1 = 0");
   P->m_cap = P->table.m_cap;
   P->s_cap = P->table.s_cap;
-  if (P->precision == GRAPE_TC_FP16) return build_dense(P, d, rowptr, ucol, h0v, cptr, cidx, cval, ectr_ptr, ectr_k, ectr_val);
+  if (P->precision == GRAPE_TC_FP16 || P->precision == GRAPE_TC_BF16)
+    return build_dense(P, d, rowptr, ucol, h0v, cptr, cidx, cval, ectr_ptr, ectr_k, ectr_val);
   // ---- partitions: CTAs per column team (CL) for the forward and the backward sweep.
   // Cost model per Taylor term and CTA, in SM clocks: a * (entries x chains) + b * (rows x chains)
   // + team barrier, with a = 4 FMA per complex multiply-add at 1.7 FP64 lanes/clk (FP32: ~100
@@ -1016,10 +1018,11 @@ grape_status grape_problem_create(const grape_desc* d, grape_problem** out) {
   if (!(d->dt > 0.0) || !std::isfinite(d->dt)) return fail(GRAPE_EINVAL, "dt must be finite and > 0");
   if (!(d->tau > 0.0 && d->tau < 1.0)) return fail(GRAPE_EINVAL, "tau must be in (0, 1)");
   if (d->m_max < 0 || d->m_max > grape::kMaxTaylor) return fail(GRAPE_EINVAL, "m_max must be in 0..60");
-  if (d->precision != GRAPE_FP64 && d->precision != GRAPE_FP32_BULK && d->precision != GRAPE_TC_FP16)
-    return fail(GRAPE_EINVAL, "precision must be GRAPE_FP64, GRAPE_FP32_BULK or GRAPE_TC_FP16");
-  if (d->precision == GRAPE_TC_FP16 && (d->dim % 128 != 0 || d->n_states > 16))
-    return fail(GRAPE_EINVAL, "GRAPE_TC_FP16 needs dim % 128 == 0 and n_states <= 16");
+  if (d->precision != GRAPE_FP64 && d->precision != GRAPE_FP32_BULK && d->precision != GRAPE_TC_FP16 &&
+      d->precision != GRAPE_TC_BF16)
+    return fail(GRAPE_EINVAL, "precision must be GRAPE_FP64, GRAPE_FP32_BULK, GRAPE_TC_FP16 or GRAPE_TC_BF16");
+  if ((d->precision == GRAPE_TC_FP16 || d->precision == GRAPE_TC_BF16) && (d->dim % 128 != 0 || d->n_states > 16))
+    return fail(GRAPE_EINVAL, "the tensor-core modes need dim % 128 == 0 and n_states <= 16");
   if (d->propagator != GRAPE_PROP_TAYLOR && d->propagator != GRAPE_PROP_EIG)
     return fail(GRAPE_EINVAL, "propagator must be GRAPE_PROP_TAYLOR or GRAPE_PROP_EIG");
   if (d->propagator == GRAPE_PROP_EIG && (d->precision != GRAPE_FP64 || d->dim > grape::kEigMaxDim))
@@ -1437,7 +1440,7 @@ grape_status grape_batch_create(grape_problem* const* probs, int32_t count, int3
   for (int i = 0; i < count; ++i) {
     if (!probs[i]) return fail(GRAPE_EINVAL, "NULL problem in batch");
     if (probs[i]->device != probs[0]->device) return fail(GRAPE_EINVAL, "batch problems must share one device");
-    if (probs[i]->dense) return fail(GRAPE_EINVAL, "GRAPE_TC_FP16 problems are driven from the host and cannot join a batch");
+    if (probs[i]->dense) return fail(GRAPE_EINVAL, "tensor-core problems are driven from the host and cannot join a batch");
     if (probs[i]->bwd_mode != 1)
       return fail(GRAPE_EINVAL, "batch members must use backward_mode 1 (two-team sweeps wait on each other and must "
                                 "not share the GPU with concurrent kernels)");
@@ -1516,7 +1519,7 @@ grape_status grape_optimize(grape_problem* P, double* u, int32_t n_iter, double 
                             void* stream) {
   if (!P || (!u && P->K > 0) || !costs || n_iter < 1) return fail(GRAPE_EINVAL, "bad argument");
   if (!(eta > 0.0) || !std::isfinite(eta)) return fail(GRAPE_EINVAL, "eta must be finite and > 0");
-  if (P->dense) return fail(GRAPE_EINVAL, "GRAPE_TC_FP16 problems are driven from the host and cannot be recorded");
+  if (P->dense) return fail(GRAPE_EINVAL, "tensor-core problems are driven from the host and cannot be recorded");
   DeviceGuard guard(P->device);
   if (!guard.ok) return fail(GRAPE_ECUDA, "cudaSetDevice failed");
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -15,7 +15,8 @@ import numpy as np
 from . import _abi
 from ._abi import GrapeDesc, GrapeInfo, GrapeOp, check, lib
 
-PRECISIONS = {"fp64": _abi.GRAPE_FP64, "fp32_bulk": _abi.GRAPE_FP32_BULK, "tc_fp16": _abi.GRAPE_TC_FP16}
+PRECISIONS = {"fp64": _abi.GRAPE_FP64, "fp32_bulk": _abi.GRAPE_FP32_BULK, "tc_fp16": _abi.GRAPE_TC_FP16,
+              "tc_bf16": _abi.GRAPE_TC_BF16}
 PROPAGATORS = {"taylor": _abi.GRAPE_PROP_TAYLOR, "eig": _abi.GRAPE_PROP_EIG}
 
 

@@ -322,13 +322,19 @@ def _dense_problem(n_t, n_c, n, N, seed, drive=10.0):
     return p
 
 
+# BF16 pairs carry 16 significant bits against FP16's 22: a looser bound for the BF16 mode
+TC_BF16_RTOL = 1e-3
+
+
+@pytest.mark.parametrize("precision", ["tc_fp16", "tc_bf16"])
 @pytest.mark.parametrize("n_t,n_c,n,N", [(4, 32, 4, 5), (8, 32, 8, 4), (8, 16, 3, 6)])
-def test_tensor_core_dense_path_parity(n_t, n_c, n, N):
-    """Dense H: every Taylor product on tcgen05 (FP16 hi/lo, FP32 accumulation), FP64 states."""
+def test_tensor_core_dense_path_parity(n_t, n_c, n, N, precision):
+    """Dense H: every Taylor product on tcgen05 (FP16 or BF16 hi/lo pairs, FP32 accumulation), FP64 states."""
     p = _dense_problem(n_t, n_c, n, N, seed=800 + n_t * n_c)
-    hg = _hg(p, precision="tc_fp16")
+    hg = _hg(p, precision=precision)
     cost, grad = hg.cost_and_grad(p.u0)
-    _check(p, p.u0, cost, grad, cost_rtol=TC_RTOL, grad_rtol=TC_RTOL)
+    tol = TC_RTOL if precision == "tc_fp16" else TC_BF16_RTOL
+    _check(p, p.u0, cost, grad, cost_rtol=tol, grad_rtol=tol)
     c2, g2 = hg.cost_and_grad(p.u0)        # repeatable (deterministic cluster reduction)
     assert c2 == cost and np.array_equal(g2, grad)
 
