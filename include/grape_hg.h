@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-#define GRAPE_ABI_VERSION 2
+#define GRAPE_ABI_VERSION 3
 
 typedef struct grape_problem grape_problem;
 
@@ -137,6 +137,9 @@ typedef struct {
                                   C3 = 1 - 1/(N n^2) sum_{n'=1..N} |sum_h <phi_T^h|psi_n'^h>|^2
                                   (App. A, C3st / C3g; 0 = off)                                 */
   int32_t propagator;          /* grape_propagator (0 = Taylor)                               */
+  int64_t wait_limit;          /* polls (about 0.1 us apart) before a device wait of the two-team
+                                  backward sweep gives up and the call returns GRAPE_ETIMEOUT;
+                                  0 = default (2^24, about two seconds)                        */
 } grape_desc;
 
 /* Information about a problem (valid after create; schedule fields after an evaluation). */

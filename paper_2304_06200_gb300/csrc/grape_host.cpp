@@ -147,6 +147,7 @@ struct grape_problem {
   double dt = 0, w_fid = 0, w_forbid = 0, w_amp = 0, tau = 0;
   double b_cap = 0;   // cap on ||B||_1 = ||A||_1 / s in the schedule (0 = the paper's rule unchanged)
   double w_tint = 0;  // weight of the time-integrated infidelity C3
+  long long wait_limit = 1LL << 24;   // polls before a device wait gives up
   int precision = 0, ckpt_every = 0, n_ckpt = 0, m_cap = 0, s_cap = 0, sigma = 0;
   int64_t nnz = 0, n_ctr = 0;
   bool has_omega = false;
@@ -1030,6 +1031,7 @@ grape_status grape_problem_create(const grape_desc* d, grape_problem** out) {
   if (d->cluster < 0 || d->cluster > grape::kMaxCluster) return fail(GRAPE_EINVAL, "cluster must be 0 (automatic) or 1..16");
   if (d->n_controls > 0 && !d->Hk) return fail(GRAPE_EINVAL, "Hk is NULL");
   if (d->bulk_norm_cap < 0.0 || !std::isfinite(d->bulk_norm_cap)) return fail(GRAPE_EINVAL, "bulk_norm_cap must be >= 0");
+  if (d->wait_limit < 0) return fail(GRAPE_EINVAL, "wait_limit must be >= 0");
   if (!d->psi0 || !d->target) return fail(GRAPE_EINVAL, "psi0 / target is NULL");
   if ((d->alloc == nullptr) != (d->free == nullptr)) return fail(GRAPE_EINVAL, "alloc and free must both be set or both NULL");
   const double ws[4] = {d->w_fid, d->w_forbid, d->w_amp, d->w_tint};
@@ -1055,6 +1057,7 @@ grape_status grape_problem_create(const grape_desc* d, grape_problem** out) {
   P->w_forbid = d->w_forbid;
   P->w_amp = d->w_amp;
   P->w_tint = d->w_tint;
+  P->wait_limit = d->wait_limit > 0 ? d->wait_limit : (1LL << 24);
   P->tau = d->tau;
   P->precision = d->precision;
   P->m_cap = d->m_max == 0 ? grape::kMaxTaylor : d->m_max;
@@ -1220,7 +1223,7 @@ grape_status run_backward(grape_problem* P, cudaStream_t st) {
     p.ring_depth = P->ring_depth;
     p.ready = P->d_flags;
     p.done = P->d_flags + (size_t)P->n * P->bwd.CL;
-    p.spin_limit = 1LL << 24;
+    p.spin_limit = P->wait_limit;
     if ((e = cudaMemsetAsync(P->d_flags, 0, sizeof(unsigned) * 2 * (size_t)P->n * P->bwd.CL, st)) != cudaSuccess)
       return cuda_fail(e, "cudaMemsetAsync (flags)");
     if ((e = grape::launch_backward_split(p, P->precision, P->bwd.smem, P->bwd.threads, st)) != cudaSuccess)

@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol(L):
     assert sorted(EXPORTED) == declared
     for name in declared:
         assert hasattr(L, name), name
-    assert L.grape_abi_version() == 2
+    assert L.grape_abi_version() == 3
 
 
 def test_status_strings(L):
@@ -106,3 +106,13 @@ def test_create_rejects_bad_propagator_choices(L):
     d.dim = 97
     assert L.grape_problem_create(C.byref(d), C.byref(h)) == 1
     assert not h.value
+
+
+def test_create_rejects_a_negative_wait_limit(L):
+    from paper_2304_06200_gb300._abi import GrapeDesc
+    h = C.c_void_p()
+    d = GrapeDesc()
+    d.dim, d.n_steps, d.n_states, d.dt, d.tau = 4, 3, 1, 0.1, 1e-8
+    d.wait_limit = -1
+    assert L.grape_problem_create(C.byref(d), C.byref(h)) == 1
+    assert b"wait_limit" in L.grape_last_error()

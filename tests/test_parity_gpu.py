@@ -569,3 +569,41 @@ def test_c3_full_size_in_the_bench_configuration():
         cm = hg.cost(um)
         fd = (cp - cm) / (2 * h)
         assert abs(fd - grad[k, n]) <= 1e-6 * np.abs(grad).max(), (k, n, fd, grad[k, n])
+
+
+def test_bounded_wait_gives_up_with_a_status():
+    """Failure detection without a GPU fault: with a one-poll wait limit the two-team backward's
+    first wait for its partner runs out; both teams leave uniformly, the call returns
+    GRAPE_ETIMEOUT, and the device stays usable."""
+    from paper_2304_06200_gb300 import GrapeError
+    p = build_config("c2_gate_d80", n_steps=30)
+    impatient = _hg(p, backward_mode=2, wait_limit=1)
+    assert impatient.info()["backward_mode"] == 2
+    with pytest.raises(GrapeError) as ei:
+        impatient.cost_and_grad(p.u0)
+    assert ei.value.name == "GRAPE_ETIMEOUT"
+    impatient.close()
+    c, g = _hg(p, backward_mode=2).cost_and_grad(p.u0)
+    _check(p, p.u0, c, g)
+
+
+def test_allocation_failure_is_reported():
+    """An allocator that refuses (the torch caching allocator under a memory-fraction cap) gives
+    GRAPE_ENOMEM from create, and nothing is left allocated."""
+    import torch
+    from paper_2304_06200_gb300 import GrapeError
+    p = build_config("c3_gate_d4000", n_steps=200)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    before = torch.cuda.memory_allocated()
+    torch.cuda.set_per_process_memory_fraction(1e-5)
+    try:
+        with pytest.raises(GrapeError) as ei:
+            _hg(p)
+        assert ei.value.name == "GRAPE_ENOMEM"
+    finally:
+        torch.cuda.set_per_process_memory_fraction(1.0)
+    assert torch.cuda.memory_allocated() == before
+    c, _ = _hg(build_config("c1_state_transfer_d30", n_steps=5)).cost_and_grad(build_config(
+        "c1_state_transfer_d30", n_steps=5).u0)
+    assert np.isfinite(c)
