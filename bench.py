@@ -276,6 +276,8 @@ def run_ours(args):
             extra["eig_vs_taylor"] = eig_compare(local)
         if args.dense:
             extra["dense_d2048_tc"] = dense_compare(local, args.dense_steps)
+        if args.batch:
+            extra["c5_batch"] = batch_compare(local, args.autotune)
         print(json.dumps({"extras": extra}), flush=True)
         return
     p = build_config(args.workload, seed=None if rank == 0 else 1000 + rank, n_steps=args.n_steps)
@@ -713,8 +715,9 @@ def batch_compare(local, tune=False):
     for p in insts:
         if tune:
             hg, rep = autotune(p, precision="fp32_bulk", device=local, probe_steps=32, m_caps=(0, 30),
-                               clusters=[0, 1, 4, 8, 16])
-            tune_report.append({"name": p.name, "cluster": rep["cluster"], "m_max": rep["m_max"]})
+                               clusters=[0, 1, 4, 8, 16], ckpt_choices=(0, 200))
+            tune_report.append({"name": p.name, "cluster": rep["cluster"], "m_max": rep["m_max"],
+                                "ckpt_every": rep["ckpt_every"]})
         else:
             hg = GrapeProblem(p, device=local, precision="fp32_bulk", backward_mode=1)
         members.append(hg)

@@ -264,14 +264,16 @@ class GrapeBatch:
 
 
 def autotune(problem, precision: str = "fp64", device: int = 0, probe_steps: int = 48, backward_mode: int = 1,
-             clusters=None, m_caps=(0, 30, 20), repeats: int = 2):
-    """Pick the team size (CTAs per column) and Taylor-order cap with the fastest measured evaluation.
+             clusters=None, m_caps=(0, 30, 20), ckpt_choices=(0,), repeats: int = 2, tie: float = 0.02):
+    """Pick the team size (CTAs per column), Taylor-order cap and checkpoint spacing M.
 
     Each candidate is timed (CUDA events, after one warm-up) on the first ``probe_steps`` steps of the
-    problem; the winner is returned as ``(GrapeProblem for the full problem, report)``.  Candidates
-    whose descriptor is rejected (shared memory, co-residency) are skipped.  The Taylor-order cap
-    changes the (m, s) the paper's rule returns (a smaller cap forces more substeps), never the
-    tolerance.
+    problem.  The fastest wins; among candidates within ``tie`` (relative) of it, the one holding the
+    least device memory (larger M stores fewer checkpoints).  Returns ``(GrapeProblem for the full
+    problem, report)``.  Candidates whose descriptor is rejected (shared memory, co-residency) are
+    skipped.  The Taylor-order cap changes the (m, s) the paper's rule returns (a smaller cap forces
+    more substeps), never the tolerance; M changes the memory and the re-propagation drift bound,
+    not the arithmetic between checkpoints.
     """
     import torch
 
@@ -283,36 +285,45 @@ def autotune(problem, precision: str = "fp64", device: int = 0, probe_steps: int
     cost = torch.zeros((), dtype=torch.float64, device=u.device)
     grad = torch.zeros_like(u)
     report = []
-    best = None
+    timed = []
     for cl in clusters:
         for mc in m_caps:
-            try:
-                hg = GrapeProblem(problem, precision=precision, cluster=cl, device=device, m_max=mc, n_steps=ns,
-                                  backward_mode=backward_mode)
-            except Exception as exc:  # rejected configuration
-                report.append({"cluster": cl, "m_max": mc, "skipped": str(exc)[:80]})
-                continue
-            hg.cost_and_grad_device(u, cost, grad)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for _ in range(repeats):
+            for M in ckpt_choices:
+                # the probe covers ns steps: checkpoints are spaced as they would be in the full problem
+                # up to ns, and their memory is scaled to the full N below
+                try:
+                    hg = GrapeProblem(problem, precision=precision, cluster=cl, device=device, m_max=mc,
+                                      n_steps=ns, backward_mode=backward_mode, ckpt_every=M)
+                except Exception as exc:  # rejected configuration
+                    report.append({"cluster": cl, "m_max": mc, "ckpt_every": M, "skipped": str(exc)[:80]})
+                    continue
                 hg.cost_and_grad_device(u, cost, grad)
-            e1.record()
-            torch.cuda.synchronize()
-            hg.sync_status()
-            ms = e0.elapsed_time(e1) / repeats
-            inf = hg.info()
-            report.append({"cluster": cl, "m_max": mc, "ms": ms, "cluster_used": inf["cluster"],
-                           "terms": inf["total_terms"]})
-            if best is None or ms < best[0]:
-                best = (ms, cl, mc)
-            hg.close()
-    if best is None:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(repeats):
+                    hg.cost_and_grad_device(u, cost, grad)
+                e1.record()
+                torch.cuda.synchronize()
+                hg.sync_status()
+                ms = e0.elapsed_time(e1) / repeats
+                inf = hg.info()
+                Meff = M if M != 0 else min(50, N)
+                ckpt_bytes = 0 if Meff < 0 else ((N - 1) // max(Meff, 1)) * problem.dim * problem.n_states * 16
+                rec = {"cluster": cl, "m_max": mc, "ckpt_every": M, "ms": ms, "cluster_used": inf["cluster"],
+                       "terms": inf["total_terms"], "checkpoint_bytes_full_N": int(ckpt_bytes)}
+                report.append(rec)
+                timed.append(rec)
+                hg.close()
+    if not timed:
         raise RuntimeError("autotune: no candidate configuration was accepted")
-    _, cl, mc = best
-    full = GrapeProblem(problem, precision=precision, cluster=cl, device=device, m_max=mc, backward_mode=backward_mode)
-    return full, {"cluster": cl, "m_max": mc, "candidates": report}
+    fastest = min(r["ms"] for r in timed)
+    near = [r for r in timed if r["ms"] <= fastest * (1.0 + tie)]
+    best = min(near, key=lambda r: (r["checkpoint_bytes_full_N"], r["ms"]))
+    cl, mc, M = best["cluster"], best["m_max"], best["ckpt_every"]
+    full = GrapeProblem(problem, precision=precision, cluster=cl, device=device, m_max=mc, backward_mode=backward_mode,
+                        ckpt_every=M)
+    return full, {"cluster": cl, "m_max": mc, "ckpt_every": M, "candidates": report}
 
 
 def select_ms(x: float, tau: float, sigma: int, precision: str = "fp64", m_max: int = 60, s_max: int = 4096):

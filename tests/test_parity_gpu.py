@@ -300,8 +300,9 @@ def test_batch_rejects_two_team_members():
 def test_autotune_returns_a_correct_problem():
     from paper_2304_06200_gb300 import autotune
     p = build_config("c2_gate_d80", n_steps=40)
-    hg, rep = autotune(p, clusters=[0, 1, 2], m_caps=(0, 20), probe_steps=8)
+    hg, rep = autotune(p, clusters=[0, 1, 2], m_caps=(0, 20), ckpt_choices=(0, 10, -1), probe_steps=8)
     assert any("ms" in r for r in rep["candidates"])
+    assert rep["ckpt_every"] in (0, 10, -1)
     cost, grad = hg.cost_and_grad(p.u0)
     _check(p, p.u0, cost, grad)
 
