@@ -608,3 +608,21 @@ def test_allocation_failure_is_reported():
     c, _ = _hg(build_config("c1_state_transfer_d30", n_steps=5)).cost_and_grad(build_config(
         "c1_state_transfer_d30", n_steps=5).u0)
     assert np.isfinite(c)
+
+
+def test_batch_with_eigendecomposition_members():
+    """A batch mixing Taylor and eigendecomposition members (the latter forking their step chunks
+    onto their own streams inside the recorded graph): equal to the individual evaluations."""
+    from paper_2304_06200_gb300 import GrapeBatch
+    raw = [build_config("c1_state_transfer_d30", n_steps=300), build_config("c2_gate_d80", n_steps=70),
+           random_problem(48, 2, 3, 20, seed=5151, density=0.5)]
+    probs = [_hg(raw[0], propagator="eig"), _hg(raw[1], backward_mode=1), _hg(raw[2], propagator="eig")]
+    singles = [hg.cost_and_grad(p.u0) for p, hg in zip(raw, probs)]
+    batch = GrapeBatch(probs, n_streams=2)
+    for _ in range(2):
+        costs, grads = batch.cost_and_grad([p.u0 for p in raw])
+        for (c, g), cb, gb in zip(singles, costs, grads):
+            assert c == cb
+            assert np.array_equal(g, gb)
+    _check(raw[0], raw[0].u0, costs[0], grads[0], cost_rtol=EIG_COST_RTOL, grad_rtol=EIG_GRAD_RTOL)
+    batch.close()
