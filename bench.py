@@ -278,6 +278,8 @@ def run_ours(args):
             extra["dense_d2048_tc"] = dense_compare(local, args.dense_steps)
         if args.batch:
             extra["c5_batch"] = batch_compare(local, args.autotune)
+        if args.c4:
+            extra["c4"] = c4_compare(local)
         print(json.dumps({"extras": extra}), flush=True)
         return
     p = build_config(args.workload, seed=None if rank == 0 else 1000 + rank, n_steps=args.n_steps)

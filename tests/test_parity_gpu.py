@@ -626,3 +626,19 @@ def test_batch_with_eigendecomposition_members():
             assert np.array_equal(g, gb)
     _check(raw[0], raw[0].u0, costs[0], grads[0], cost_rtol=EIG_COST_RTOL, grad_rtol=EIG_GRAD_RTOL)
     batch.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
+def test_maximum_controls_and_full_rank_gate(precision):
+    """K = 32 controls (the maximum) on a full-rank gate (n = d = 40), and zero controls (H = H0)."""
+    p = random_problem(40, 32, 40, 3, seed=3232, density=0.2)
+    hg = _hg(p, precision=precision)
+    tol = COST_RTOL if precision == "fp64" else FP32_RTOL
+    gtol = GRAD_RTOL if precision == "fp64" else FP32_RTOL
+    for u in (p.u0, np.zeros_like(p.u0)):
+        cost, grad = hg.cost_and_grad(u)
+        _check(p, u, cost, grad, cost_rtol=tol, grad_rtol=gtol)
+    from paper_2304_06200_gb300 import GrapeError
+    q = random_problem(8, 33, 1, 2, seed=1)
+    with pytest.raises(GrapeError):
+        _hg(q)
