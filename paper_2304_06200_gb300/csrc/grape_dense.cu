@@ -71,8 +71,18 @@ __device__ __forceinline__ int mbar_wait(uint64_t* mbar, uint32_t parity, long l
   return (int)done;
 }
 
-__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
+// One tiled TMA load of a 4-D box into this CTA's shared memory, completing on `mbar`.
+__device__ __forceinline__ void tma_load_4d(void* sdst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_u32(sdst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(mbar))
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
 }
 
 // byte offset of (row r, k) inside a K-major no-swizzle tile with kcores core matrices along K
@@ -81,9 +91,10 @@ __device__ __forceinline__ int core_off(int r, int k, int kcores) {
 }
 
 struct ApplyArgs {
-  const __half* op[4];     // Br_hi, Br_lo, Bi_hi, Bi_lo: d x d row-major (K contiguous)
-  const __half* xh;        // X high parts: ncols_real x d (row c = real column c, K contiguous)
-  const __half* xl;        // X low parts
+  // Tensor maps (4-D views whose boxes land in the K-major no-swizzle core-matrix layout):
+  // [0..3] Br_hi, Br_lo, Bi_hi, Bi_lo (d x d row-major, K contiguous), [4] X high, [5] X low
+  // (rows = real columns of the block, K contiguous).
+  CUtensorMap tm[6];
   float2* y;               // output: d x ncols complex, column-major (column h contiguous)
   int d, ncols, nreal;     // nreal = 2 * ncols padded to a multiple of 16 (MMA N)
   float alpha;             // y = alpha * B x
@@ -91,12 +102,16 @@ struct ApplyArgs {
   int* err;
 };
 
-// Tile bytes: four operator tiles (128 x 64 fp16 = 16 KB each) + X hi/lo tiles (nreal x 64 fp16).
+// Tile bytes: four operator tiles (128 x 64 16-bit = 16 KB each) + X hi/lo tiles (nreal x 64 16-bit).
 __host__ __device__ inline int stage_bytes(int nreal) { return 4 * 16384 + 2 * nreal * 128; }
+// Pipeline depth: three stages while they fit (nreal <= 32), else two.
+__host__ __device__ inline int stage_count(int nreal) { return 3 * stage_bytes(nreal) <= 221184 ? 3 : 2; }
+constexpr int kMaxStages = 3;
 
-__global__ void __launch_bounds__(kThreads, 1) k_dense_apply(ApplyArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) k_dense_apply(const __grid_constant__ ApplyArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t full[kMaxStages];    // stage loaded (TMA transaction bytes)
+  __shared__ __align__(8) uint64_t empty[kMaxStages];   // stage's MMAs done (tcgen05.commit)
   __shared__ uint32_t tmem_base;
   __shared__ int s_ok;
   const int tid = threadIdx.x;
@@ -105,11 +120,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_apply(ApplyArgs a) {
   const int Kc = a.d / KS;                      // this CTA's K range [ks * Kc, (ks + 1) * Kc)
   const int nchunks = Kc / kKC;
   const int nreal = a.nreal;
-  const int SB = stage_bytes(nreal);
-  unsigned char* stage[2] = {smem, smem + SB};
+  const int SB = stage_bytes(nreal);            // a multiple of 1024 (nreal is a multiple of 16)
+  const int NS = stage_count(nreal);
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+    for (int st = 0; st < NS; ++st) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[st])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[st])));
+    }
     s_ok = 1;
   }
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -122,50 +139,38 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_apply(ApplyArgs a) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
 
-  auto load_chunk = [&](int c, unsigned char* st) {
-    const int k0 = ks * Kc + c * kKC;
-    // operator tiles: 128 rows x 8 sixteen-byte pieces each
-    for (int idx = tid; idx < 4 * kTM * 8; idx += kThreads) {
-      const int mat = idx / (kTM * 8), rem = idx % (kTM * 8), r = rem / 8, piece = rem % 8;
-      const __half* g = a.op[mat] + (int64_t)(row0 + r) * a.d + k0 + piece * 8;
-      cp_async16(st + mat * 16384 + core_off(r, piece * 8, 8), g);
-    }
-    // X tiles: nreal rows (real columns) x 8 pieces, hi then lo; padded rows read column 0 (ignored)
-    for (int idx = tid; idx < 2 * nreal * 8; idx += kThreads) {
-      const int part = idx / (nreal * 8), rem = idx % (nreal * 8), r = rem / 8, piece = rem % 8;
-      const int rr = r < 2 * a.ncols ? r : 0;
-      const __half* g = (part == 0 ? a.xh : a.xl) + (int64_t)rr * a.d + k0 + piece * 8;
-      cp_async16(st + 4 * 16384 + part * nreal * 128 + core_off(r, piece * 8, 8), g);
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  };
-
   // idesc: D f32, A/B f16 or bf16, both K-major, N = nreal, M = 128
   // A and B always share one type (bits 7-9 and 10-12: 0 = f16, 1 = bf16)
   const uint32_t ab_type = a.bf16 ? 1u : 0u;
   const uint32_t idesc = (1u << 4) | (ab_type << 7) | (ab_type << 10) | ((uint32_t)(nreal >> 3) << 17) |
                          ((uint32_t)(kTM >> 4) << 24);
-  uint32_t phase[2] = {0u, 0u};
   int ok = 1;
-  load_chunk(0, stage[0]);
-  for (int c = 0; c < nchunks; ++c) {
-    const int sc = c & 1;
-    if (c + 1 < nchunks) {
-      const int sn = (c + 1) & 1;
-      if (c >= 1) {   // the MMAs of chunk c-1 read stage sn: wait before overwriting it
-        if (!mbar_wait(&mbar[sn], phase[sn], 1LL << 26)) ok = 0;
-        phase[sn] ^= 1u;
+  // One thread drives the pipeline: TMA loads into NS stages (4-D boxes: 8 K x 8 rows per core
+  // matrix, 8 core matrices along K, 16 (operator) or 2 (X, per load) 8-row groups), the MMAs of
+  // each stage as soon as it has landed, and the refill of the stage the previous chunk used once
+  // its MMAs have completed.  The other threads wait for the epilogue.
+  if (tid == 0) {
+    const uint32_t tx = (uint32_t)SB;
+    auto issue = [&](int ch) {
+      const int st = ch % NS;
+      unsigned char* base = smem + st * SB;
+      const int kc0 = (ks * Kc + ch * kKC) / 8;
+      mbar_expect_tx(&full[st], tx);
+      for (int mat = 0; mat < 4; ++mat) tma_load_4d(base + mat * 16384, &a.tm[mat], 0, 0, kc0, row0 / 8, &full[st]);
+      for (int g = 0; g < nreal / 16; ++g) {
+        tma_load_4d(base + 4 * 16384 + g * 2048, &a.tm[4], 0, 0, kc0, 2 * g, &full[st]);
+        tma_load_4d(base + 4 * 16384 + nreal * 128 + g * 2048, &a.tm[5], 0, 0, kc0, 2 * g, &full[st]);
       }
-      load_chunk(c + 1, stage[sn]);
-      asm volatile("cp.async.wait_group 1;" ::: "memory");
-    } else {
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
+    };
+    uint32_t fbits = 0, ebits = 0;   // phase parity per stage
+    const int pre = nchunks < NS ? nchunks : NS;
+    for (int ch = 0; ch < pre; ++ch) issue(ch);
+    for (int ch = 0; ch < nchunks; ++ch) {
+      const int st = ch % NS;
+      if (!mbar_wait(&full[st], (fbits >> st) & 1u, 1LL << 26)) ok = 0;
+      fbits ^= 1u << st;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sbase = smem_u32(stage[sc]);
+      const uint32_t sbase = smem_u32(smem + st * SB);
       const uint32_t xh = sbase + 4 * 16384, xl = xh + nreal * 128;
       for (int kk = 0; kk < kKC / 16; ++kk) {
         const uint32_t ko = kk * 256;   // 16 K = two core matrices along K
@@ -174,7 +179,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_apply(ApplyArgs a) {
         const uint64_t arl = smem_desc(sbase + 1 * 16384 + ko, 128, 1024);
         const uint64_t aih = smem_desc(sbase + 2 * 16384 + ko, 128, 1024);
         const uint64_t ail = smem_desc(sbase + 3 * 16384 + ko, 128, 1024);
-        const uint32_t first = (c == 0 && kk == 0) ? 0u : 1u;
+        const uint32_t first = (ch == 0 && kk == 0) ? 0u : 1u;
         mma_f16(tmem, arh, bh, idesc, first);
         mma_f16(tmem, arh, bl, idesc, 1u);
         mma_f16(tmem, arl, bh, idesc, 1u);
@@ -182,13 +187,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_apply(ApplyArgs a) {
         mma_f16(tmem + 64, aih, bl, idesc, 1u);
         mma_f16(tmem + 64, ail, bh, idesc, 1u);
       }
-      mma_commit(&mbar[sc]);
+      mma_commit(&empty[st]);
+      const int cr = ch - 1 + NS;   // refill the previous chunk's stage
+      if (ch >= 1 && cr < nchunks) {
+        const int sr = (ch - 1) % NS;
+        if (!mbar_wait(&empty[sr], (ebits >> sr) & 1u, 1LL << 26)) ok = 0;
+        ebits ^= 1u << sr;
+        issue(cr);
+      }
     }
-  }
-  // wait for the last chunk's MMAs (the earlier ones completed before it: MMAs complete in order)
-  {
-    const int sl = (nchunks - 1) & 1;
-    if (!mbar_wait(&mbar[sl], phase[sl], 1LL << 26)) ok = 0;
+    // the last chunk's MMAs (earlier ones complete before it: MMAs complete in order)
+    const int sl = (nchunks - 1) % NS;
+    if (!mbar_wait(&empty[sl], (ebits >> sl) & 1u, 1LL << 26)) ok = 0;
   }
   if (!ok) {
     s_ok = 0;
@@ -593,7 +603,39 @@ int ew_grid(int64_t total) {
 
 }  // namespace
 
-int dense_apply_smem(int nreal) { return 2 * stage_bytes(nreal); }
+int dense_apply_smem(int nreal) { return stage_count(nreal) * stage_bytes(nreal); }
+
+// 4-D view of a rows x d matrix of 16-bit values (row-major) whose box (8, 8, 8, g) lands in shared
+// memory in the K-major no-swizzle core-matrix order: dimension 0 = 8 consecutive K values (16 B),
+// 1 = 8 consecutive rows (stride d), 2 = the 8-wide K group (stride 16 B), 3 = the 8-row group
+// (stride 8 d).  A box of g row groups is 8 x 8 x 8 x g values = g KB.
+cudaError_t dense_make_maps(DenseCtx& c) {
+  using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess) return e;
+  if (!fn || q != cudaDriverEntryPointSuccess) return cudaErrorNotSupported;
+  auto encode = reinterpret_cast<EncodeFn>(fn);
+  const uint64_t d = (uint64_t)c.d;
+  auto make = [&](CUtensorMap* m, const __half* base, uint64_t rows, uint32_t groups) -> cudaError_t {
+    const cuuint64_t gdim[4] = {8, 8, d / 8, rows / 8};
+    const cuuint64_t gstride[3] = {d * 2, 16, d * 16};
+    const cuuint32_t box[4] = {8, 8, (uint32_t)(kKC / 8), groups};
+    const cuuint32_t estride[4] = {1, 1, 1, 1};
+    const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<__half*>(base), gdim, gstride, box,
+                              estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+  };
+  const __half* ops[4] = {c.brh, c.brl, c.bih, c.bil};
+  for (int i = 0; i < 4; ++i)
+    if ((e = make(&c.tm[i], ops[i], d, kTM / 8)) != cudaSuccess) return e;
+  if ((e = make(&c.tm[4], c.xh, (uint64_t)c.x_rows, 2)) != cudaSuccess) return e;
+  return make(&c.tm[5], c.xl, (uint64_t)c.x_rows, 2);
+}
 
 // Launch of a split kernel with the operand type of the problem (fp16 or bf16 pairs).
 #define SPLIT_LAUNCH(kern, grid, block, st, ...)                               \
@@ -607,12 +649,7 @@ int dense_apply_smem(int nreal) { return 2 * stage_bytes(nreal); }
 // y = alpha * B x for the first `ncols` complex columns held in X (real columns 2h, 2h+1).
 static cudaError_t apply(const DenseCtx& c, int ncols, float alpha, float2* y, cudaStream_t st) {
   ApplyArgs a{};
-  a.op[0] = c.brh;
-  a.op[1] = c.brl;
-  a.op[2] = c.bih;
-  a.op[3] = c.bil;
-  a.xh = c.xh;
-  a.xl = c.xl;
+  for (int i = 0; i < 6; ++i) a.tm[i] = c.tm[i];
   a.y = y;
   a.d = c.d;
   a.ncols = ncols;
@@ -649,7 +686,8 @@ static cudaError_t apply(const DenseCtx& c, int ncols, float alpha, float2* y, c
 
 // Kernel attributes are process-wide settings: set them once (outside any stream capture).
 cudaError_t dense_prepare() {
-  return cudaFuncSetAttribute(k_dense_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, dense_apply_smem(64));
+  const int smax = dense_apply_smem(32) > dense_apply_smem(64) ? dense_apply_smem(32) : dense_apply_smem(64);
+  return cudaFuncSetAttribute(k_dense_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
 }
 
 // K-split (cluster size) for dimension d: the largest of 8, 4, 2, 1 whose d/128 clusters can all be
@@ -661,7 +699,7 @@ int dense_choose_ksplit(int d) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ks, d / kTM);
     cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = dense_apply_smem(64);
+    cfg.dynamicSmemBytes = dense_apply_smem(32) > dense_apply_smem(64) ? dense_apply_smem(32) : dense_apply_smem(64);
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = ks;

@@ -1,6 +1,7 @@
 // Dense-operator (tensor-core) variant of the HG evaluation: host-side driver interface.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -9,7 +10,9 @@
 namespace grape {
 
 struct DenseCtx {
+  CUtensorMap tm[6];        // TMA views of brh, brl, bih, bil, xh, xl (made by dense_make_maps)
   int d, n, N, K, ksplit;
+  int x_rows;               // rows allocated in xh / xl (>= 4 n, >= 64, a multiple of 16)
   int bf16;                 // operand pairs are bf16 (GRAPE_TC_BF16), else fp16 (GRAPE_TC_FP16)
   double dt, w_fid, w_forbid, w_tint;
   int ckpt_every, n_ckpt;
@@ -47,6 +50,9 @@ struct DenseCtx {
 };
 
 int dense_apply_smem(int nreal);
+// Tensor maps of the operator and X buffers (after they are allocated); cudaErrorNotSupported if the
+// driver offers no tensor-map encoder.
+cudaError_t dense_make_maps(DenseCtx& c);
 cudaError_t dense_prepare();
 int dense_choose_ksplit(int d);
 cudaError_t dense_forward(const DenseCtx& c, const int* m_host, const int* s_host, cudaStream_t st);

@@ -338,8 +338,11 @@ grape_status build_dense(grape_problem* P, const grape_desc* d, const std::vecto
   c.bih = hp[2];
   c.bil = hp[3];
   __half *xh, *xl;
-  if ((st = dzeros(P, &xh, (size_t)4 * n * dim))) return st;
-  if ((st = dzeros(P, &xl, (size_t)4 * n * dim))) return st;
+  // X holds up to 4 n real columns; every TMA box of it (16 rows) and the padded MMA width (a
+  // multiple of 16, at most 64) stay inside the allocation
+  c.x_rows = std::max(64, (4 * n + 15) / 16 * 16);
+  if ((st = dzeros(P, &xh, (size_t)c.x_rows * dim))) return st;
+  if ((st = dzeros(P, &xl, (size_t)c.x_rows * dim))) return st;
   c.xh = xh;
   c.xl = xl;
   float2* y;
@@ -421,6 +424,7 @@ grape_status build_dense(grape_problem* P, const grape_desc* d, const std::vecto
   P->s_host.assign(N, 0);
   cudaError_t e = grape::dense_prepare();
   if (e != cudaSuccess) return cuda_fail(e, "dense kernel attributes");
+  if ((e = grape::dense_make_maps(c)) != cudaSuccess) return cuda_fail(e, "tensor maps of the dense operator");
   c.ksplit = grape::dense_choose_ksplit((int)dim);
   if ((e = cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
     return cuda_fail(e, "cudaStreamCreate");
