@@ -71,13 +71,13 @@ __device__ __forceinline__ int mbar_wait(uint64_t* mbar, uint32_t parity, long l
   return (int)done;
 }
 
-// One tiled TMA load of a 4-D box into this CTA's shared memory, completing on `mbar`.
-__device__ __forceinline__ void tma_load_4d(void* sdst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+// One tiled TMA load of a 3-D box into this CTA's shared memory, completing on `mbar`.
+__device__ __forceinline__ void tma_load_3d(void* sdst, const CUtensorMap* map, int c0, int c1, int c2,
                                             uint64_t* mbar) {
   asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-      "[%6];" ::"r"(smem_u32(sdst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(mbar))
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(sdst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(mbar))
       : "memory");
 }
 
@@ -145,8 +145,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_apply(const __grid_consta
   const uint32_t idesc = (1u << 4) | (ab_type << 7) | (ab_type << 10) | ((uint32_t)(nreal >> 3) << 17) |
                          ((uint32_t)(kTM >> 4) << 24);
   int ok = 1;
-  // One thread drives the pipeline: TMA loads into NS stages (4-D boxes: 8 K x 8 rows per core
-  // matrix, 8 core matrices along K, 16 (operator) or 2 (X, per load) 8-row groups), the MMAs of
+  // One thread drives the pipeline: TMA loads into NS stages (3-D boxes: 8 x 8 blocks, 8 along K,
+  // 16 (operator) or 2 (X, per load) 8-row groups of the tiled storage), the MMAs of
   // each stage as soon as it has landed, and the refill of the stage the previous chunk used once
   // its MMAs have completed.  The other threads wait for the epilogue.
   if (tid == 0) {
@@ -156,10 +156,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_apply(const __grid_consta
       unsigned char* base = smem + st * SB;
       const int kc0 = (ks * Kc + ch * kKC) / 8;
       mbar_expect_tx(&full[st], tx);
-      for (int mat = 0; mat < 4; ++mat) tma_load_4d(base + mat * 16384, &a.tm[mat], 0, 0, kc0, row0 / 8, &full[st]);
+      for (int mat = 0; mat < 4; ++mat) tma_load_3d(base + mat * 16384, &a.tm[mat], 0, kc0, row0 / 8, &full[st]);
       for (int g = 0; g < nreal / 16; ++g) {
-        tma_load_4d(base + 4 * 16384 + g * 2048, &a.tm[4], 0, 0, kc0, 2 * g, &full[st]);
-        tma_load_4d(base + 4 * 16384 + nreal * 128 + g * 2048, &a.tm[5], 0, 0, kc0, 2 * g, &full[st]);
+        tma_load_3d(base + 4 * 16384 + g * 2048, &a.tm[4], 0, kc0, 2 * g, &full[st]);
+        tma_load_3d(base + 4 * 16384 + nreal * 128 + g * 2048, &a.tm[5], 0, kc0, 2 * g, &full[st]);
       }
     };
     uint32_t fbits = 0, ebits = 0;   // phase parity per stage
@@ -241,17 +241,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_apply(const __grid_consta
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  // deterministic K-split reduction over the cluster: rank 0 sums ranks 0..KS-1 in order
+  // deterministic K-split reduction over the cluster: CTA ks sums rows [ks * 128 / KS, (ks + 1) * 128 / KS)
+  // of every column over ranks 0..KS-1 in order
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-  if (ks == 0) {
+  {
     const float* parts[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       parts[r] = part;
       if (r < KS) asm volatile("mapa.u64 %0, %1, %2;" : "=l"(parts[r]) : "l"(part), "r"(r));
     }
-    for (int idx = tid; idx < kTM * ncols; idx += kThreads) {
-      const int row = idx % kTM, h = idx / kTM;   // consecutive threads: consecutive rows
+    const int rows_per = kTM / KS, rbase = ks * rows_per;
+    for (int idx = tid; idx < rows_per * ncols; idx += kThreads) {
+      const int row = rbase + idx % rows_per, h = idx / rows_per;   // consecutive threads: consecutive rows
       float vr[8], vi[8];
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
@@ -276,6 +278,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_apply(const __grid_consta
 }
 
 // ------------------------------------------------------------------ elementwise chain kernels
+
+// Storage of the 16-bit operator and X buffers: 8 x 8 blocks (8 rows x 16 bytes) contiguous, blocks
+// ordered by 8-row group and then by 8-wide K group, so that a tile's core matrices of one row group
+// are one contiguous run in global memory (and TMA moves 1 KB runs).
+__device__ __forceinline__ int64_t tiled(int64_t row, int64_t k, int d) {
+  return ((((row >> 3) * (int64_t)(d >> 3) + (k >> 3)) << 6) + ((row & 7) << 3) + (k & 7));
+}
 
 // v = hi + lo in two 16-bit floats: fp16 (11 significant bits each) or, for BF, bf16 (8 each,
 // stored as raw bits in the same 16-bit arrays).
@@ -305,11 +314,11 @@ __global__ void k_split_d(const double2* __restrict__ v, double scale, int d, in
     const double2 z = v[i];
     __half a, b;
     split16<BF>((float)(z.x * scale), a, b);
-    xh[(int64_t)(2 * (h + col_off)) * d + r] = a;
-    xl[(int64_t)(2 * (h + col_off)) * d + r] = b;
+    xh[tiled(2 * (h + col_off), r, d)] = a;
+    xl[tiled(2 * (h + col_off), r, d)] = b;
     split16<BF>((float)(z.y * scale), a, b);
-    xh[(int64_t)(2 * (h + col_off) + 1) * d + r] = a;
-    xl[(int64_t)(2 * (h + col_off) + 1) * d + r] = b;
+    xh[tiled(2 * (h + col_off) + 1, r, d)] = a;
+    xl[tiled(2 * (h + col_off) + 1, r, d)] = b;
   }
 }
 
@@ -326,11 +335,11 @@ __global__ void k_fwd_term(const float2* __restrict__ y, double2* inc, int d, in
     inc[i] = a;
     __half p, q;
     split16<BF>(z.x, p, q);
-    xh[(int64_t)(2 * h) * d + r] = p;
-    xl[(int64_t)(2 * h) * d + r] = q;
+    xh[tiled(2 * h, r, d)] = p;
+    xl[tiled(2 * h, r, d)] = q;
     split16<BF>(z.y, p, q);
-    xh[(int64_t)(2 * h + 1) * d + r] = p;
-    xl[(int64_t)(2 * h + 1) * d + r] = q;
+    xh[tiled(2 * h + 1, r, d)] = p;
+    xl[tiled(2 * h + 1, r, d)] = q;
   }
 }
 
@@ -361,21 +370,21 @@ __global__ void k_phase_a_term(const float2* __restrict__ y, double2* inc, doubl
     inc[i] = a;
     __half p, s2;
     split16<BF>(ar, p, s2);
-    xh[(int64_t)(2 * h) * d + r] = p;
-    xl[(int64_t)(2 * h) * d + r] = s2;
+    xh[tiled(2 * h, r, d)] = p;
+    xl[tiled(2 * h, r, d)] = s2;
     split16<BF>(ai, p, s2);
-    xh[(int64_t)(2 * h + 1) * d + r] = p;
-    xl[(int64_t)(2 * h + 1) * d + r] = s2;
+    xh[tiled(2 * h + 1, r, d)] = p;
+    xl[tiled(2 * h + 1, r, d)] = s2;
     const double2 ch = chi[i];
     if (q < m) {
       const float wr = (float)(ch.x * fq) - yw.x, wi = (float)(ch.y * fq) - yw.y;
       wslot[(int64_t)(m - 1 - q) * total + i] = make_float2(wr, wi);
       split16<BF>(wr, p, s2);
-      xh[(int64_t)(2 * (h + n)) * d + r] = p;
-      xl[(int64_t)(2 * (h + n)) * d + r] = s2;
+      xh[tiled(2 * (h + n), r, d)] = p;
+      xl[tiled(2 * (h + n), r, d)] = s2;
       split16<BF>(wi, p, s2);
-      xh[(int64_t)(2 * (h + n) + 1) * d + r] = p;
-      xl[(int64_t)(2 * (h + n) + 1) * d + r] = s2;
+      xh[tiled(2 * (h + n) + 1, r, d)] = p;
+      xl[tiled(2 * (h + n) + 1, r, d)] = s2;
     } else {
       chi[i] = make_double2(ch.x - yw.x, ch.y - yw.y);
     }
@@ -392,21 +401,21 @@ __global__ void k_phase_a_start(const double2* __restrict__ psi, const double2* 
     const double2 v = psi[i];
     __half p, s2;
     split16<BF>((float)v.x, p, s2);
-    xh[(int64_t)(2 * h) * d + r] = p;
-    xl[(int64_t)(2 * h) * d + r] = s2;
+    xh[tiled(2 * h, r, d)] = p;
+    xl[tiled(2 * h, r, d)] = s2;
     split16<BF>((float)v.y, p, s2);
-    xh[(int64_t)(2 * h + 1) * d + r] = p;
-    xl[(int64_t)(2 * h + 1) * d + r] = s2;
+    xh[tiled(2 * h + 1, r, d)] = p;
+    xl[tiled(2 * h + 1, r, d)] = s2;
     inc[i] = make_double2(0.0, 0.0);
     const double2 ch = chi[i];
     const float wr = (float)(ch.x * fm), wi = (float)(ch.y * fm);
     wslot[(int64_t)(m - 1) * total + i] = make_float2(wr, wi);
     split16<BF>(wr, p, s2);
-    xh[(int64_t)(2 * (h + n)) * d + r] = p;
-    xl[(int64_t)(2 * (h + n)) * d + r] = s2;
+    xh[tiled(2 * (h + n), r, d)] = p;
+    xl[tiled(2 * (h + n), r, d)] = s2;
     split16<BF>(wi, p, s2);
-    xh[(int64_t)(2 * (h + n) + 1) * d + r] = p;
-    xl[(int64_t)(2 * (h + n) + 1) * d + r] = s2;
+    xh[tiled(2 * (h + n) + 1, r, d)] = p;
+    xl[tiled(2 * (h + n) + 1, r, d)] = s2;
   }
 }
 
@@ -420,11 +429,11 @@ __global__ void k_phase_b_term(const float2* __restrict__ y, float2* xcur, int d
     xcur[i] = z;
     __half p, s2;
     split16<BF>(z.x, p, s2);
-    xh[(int64_t)(2 * h) * d + r] = p;
-    xl[(int64_t)(2 * h) * d + r] = s2;
+    xh[tiled(2 * h, r, d)] = p;
+    xl[tiled(2 * h, r, d)] = s2;
     split16<BF>(z.y, p, s2);
-    xh[(int64_t)(2 * h + 1) * d + r] = p;
-    xl[(int64_t)(2 * h + 1) * d + r] = s2;
+    xh[tiled(2 * h + 1, r, d)] = p;
+    xl[tiled(2 * h + 1, r, d)] = s2;
   }
 }
 
@@ -470,7 +479,7 @@ __global__ void k_dense_assemble(const int64_t* __restrict__ rowptr, const int* 
         v.x = fma(uk, ectr_val[c].x, v.x);
         v.y = fma(uk, ectr_val[c].y, v.y);
       }
-      const int64_t o = (int64_t)i * d + ucol[e];
+      const int64_t o = tiled(i, ucol[e], d);
       __half p, q;
       split16<BF>((float)(scale * v.y), p, q);
       brh[o] = p;
@@ -605,10 +614,10 @@ int ew_grid(int64_t total) {
 
 int dense_apply_smem(int nreal) { return stage_count(nreal) * stage_bytes(nreal); }
 
-// 4-D view of a rows x d matrix of 16-bit values (row-major) whose box (8, 8, 8, g) lands in shared
-// memory in the K-major no-swizzle core-matrix order: dimension 0 = 8 consecutive K values (16 B),
-// 1 = 8 consecutive rows (stride d), 2 = the 8-wide K group (stride 16 B), 3 = the 8-row group
-// (stride 8 d).  A box of g row groups is 8 x 8 x 8 x g values = g KB.
+// 3-D view of a rows x d matrix of 16-bit values in the tiled storage above: dimension 0 = the 64
+// values of one 8 x 8 block (128 B, rows of 16 B), 1 = the K group (stride 128 B), 2 = the 8-row
+// group (stride d / 8 * 128 B).  A box (64, 8, g) is g row groups of 8 contiguous blocks (1 KB runs)
+// and lands in shared memory in the K-major no-swizzle core-matrix order.
 cudaError_t dense_make_maps(DenseCtx& c) {
   using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -621,13 +630,13 @@ cudaError_t dense_make_maps(DenseCtx& c) {
   auto encode = reinterpret_cast<EncodeFn>(fn);
   const uint64_t d = (uint64_t)c.d;
   auto make = [&](CUtensorMap* m, const __half* base, uint64_t rows, uint32_t groups) -> cudaError_t {
-    const cuuint64_t gdim[4] = {8, 8, d / 8, rows / 8};
-    const cuuint64_t gstride[3] = {d * 2, 16, d * 16};
-    const cuuint32_t box[4] = {8, 8, (uint32_t)(kKC / 8), groups};
-    const cuuint32_t estride[4] = {1, 1, 1, 1};
-    const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<__half*>(base), gdim, gstride, box,
+    const cuuint64_t gdim[3] = {64, d / 8, rows / 8};
+    const cuuint64_t gstride[2] = {128, d / 8 * 128};
+    const cuuint32_t box[3] = {64, (uint32_t)(kKC / 8), groups};
+    const cuuint32_t estride[3] = {1, 1, 1};
+    const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<__half*>(base), gdim, gstride, box,
                               estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
   };
   const __half* ops[4] = {c.brh, c.brl, c.bih, c.bil};
