@@ -117,8 +117,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_apply(const __grid_consta
   const int tid = threadIdx.x;
   const int ks = blockIdx.x, KS = gridDim.x;
   const int row0 = blockIdx.y * kTM;
-  const int Kc = a.d / KS;                      // this CTA's K range [ks * Kc, (ks + 1) * Kc)
-  const int nchunks = Kc / kKC;
+  // this CTA's K range: 64-wide chunks [c_lo, c_hi) of the d / 64, split as evenly as KS allows
+  const int tchunks = a.d / kKC;
+  const int c_lo = (int)((int64_t)ks * tchunks / KS), c_hi = (int)((int64_t)(ks + 1) * tchunks / KS);
+  const int nchunks = c_hi - c_lo;
   const int nreal = a.nreal;
   const int SB = stage_bytes(nreal);            // a multiple of 1024 (nreal is a multiple of 16)
   const int NS = stage_count(nreal);
@@ -154,7 +156,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_apply(const __grid_consta
     auto issue = [&](int ch) {
       const int st = ch % NS;
       unsigned char* base = smem + st * SB;
-      const int kc0 = (ks * Kc + ch * kKC) / 8;
+      const int kc0 = (c_lo + ch) * (kKC / 8);
       mbar_expect_tx(&full[st], tx);
       for (int mat = 0; mat < 4; ++mat) tma_load_3d(base + mat * 16384, &a.tm[mat], 0, kc0, row0 / 8, &full[st]);
       for (int g = 0; g < nreal / 16; ++g) {
@@ -242,7 +244,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_apply(const __grid_consta
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   // deterministic K-split reduction over the cluster: CTA ks sums rows [ks * 128 / KS, (ks + 1) * 128 / KS)
-  // of every column over ranks 0..KS-1 in order
+  // (integer division) of every column over ranks 0..KS-1 in order
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
   {
     const float* parts[8];
@@ -251,7 +253,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_apply(const __grid_consta
       parts[r] = part;
       if (r < KS) asm volatile("mapa.u64 %0, %1, %2;" : "=l"(parts[r]) : "l"(part), "r"(r));
     }
-    const int rows_per = kTM / KS, rbase = ks * rows_per;
+    const int rbase = ks * kTM / KS, rows_per = (ks + 1) * kTM / KS - rbase;
     for (int idx = tid; idx < rows_per * ncols; idx += kThreads) {
       const int row = rbase + idx % rows_per, h = idx / rows_per;   // consecutive threads: consecutive rows
       float vr[8], vi[8];
@@ -699,12 +701,12 @@ cudaError_t dense_prepare() {
   return cudaFuncSetAttribute(k_dense_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
 }
 
-// K-split (cluster size) for dimension d: the largest of 8, 4, 2, 1 whose d/128 clusters can all be
-// resident at once (a cluster left for a second wave doubles the time of every product) and whose
-// K range per CTA is a whole number of 64-wide chunks.
+// K-split (cluster size) for dimension d: the largest of 8..1 whose d/128 clusters can all be resident
+// at once (a cluster left for a second wave doubles the time of every product; on GB300 15 clusters
+// of 8 fit but 16 of 7) and that leaves every CTA at least one 64-wide K chunk.
 int dense_choose_ksplit(int d) {
-  for (int ks = 8; ks >= 1; ks /= 2) {
-    if (d % ks != 0 || (d / ks) % kKC != 0) continue;
+  for (int ks = 8; ks >= 1; --ks) {
+    if (d / kKC < ks) continue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ks, d / kTM);
     cfg.blockDim = dim3(kThreads);
