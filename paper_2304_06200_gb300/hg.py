@@ -135,6 +135,7 @@ class GrapeProblem:
         self._h = handle
         self.precision = precision
         self.propagator = propagator
+        self.forward_count = 0   # forward sweeps run on this problem (the stored sweep state is the last one's)
 
     # ------------------------------------------------------------------ host-pointer API
     def cost_and_grad(self, u: np.ndarray, want_grad: bool = True):
@@ -144,6 +145,7 @@ class GrapeProblem:
             raise ValueError(f"u shape {u.shape} != {(self.K, self.N)}")
         cost = np.zeros(1)
         grad = np.zeros((self.K, self.N)) if want_grad else None
+        self.forward_count += 1
         check(self._lib.grape_cost_and_grad(self._h, u.ctypes.data, cost.ctypes.data,
                                             grad.ctypes.data if want_grad else None, 0, None),
               "grape_cost_and_grad")
@@ -152,6 +154,7 @@ class GrapeProblem:
     def cost(self, u: np.ndarray) -> float:
         u = np.ascontiguousarray(u, dtype=np.float64)
         cost = np.zeros(1)
+        self.forward_count += 1
         check(self._lib.grape_cost(self._h, u.ctypes.data, cost.ctypes.data, 0, None), "grape_cost")
         return float(cost[0])
 
@@ -161,6 +164,7 @@ class GrapeProblem:
         import torch
 
         st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        self.forward_count += 1
         check(self._lib.grape_cost_and_grad(self._h, u.data_ptr(), cost.data_ptr(),
                                             grad.data_ptr() if grad is not None else None, 1, st),
               "grape_cost_and_grad")
@@ -169,6 +173,7 @@ class GrapeProblem:
         import torch
 
         st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        self.forward_count += 1
         check(self._lib.grape_cost(self._h, u.data_ptr(), cost.data_ptr(), 1, st), "grape_cost")
 
     def grad_device(self, grad, stream=None):
@@ -187,6 +192,7 @@ class GrapeProblem:
         """Steepest descent (one recorded CUDA graph per iteration): returns (final u, costs per iteration)."""
         u = np.array(u, dtype=np.float64, order="C", copy=True)
         costs = np.zeros(int(n_iter))
+        self.forward_count += 1
         check(self._lib.grape_optimize(self._h, u.ctypes.data, int(n_iter), float(eta), costs.ctypes.data, 0, None),
               "grape_optimize")
         return u, costs
@@ -239,6 +245,8 @@ class GrapeBatch:
         costs = np.zeros(len(us))
         up = (C.c_void_p * len(us))(*[u.ctypes.data for u in us])
         gp = (C.c_void_p * len(us))(*[g.ctypes.data for g in grads])
+        for p in self.problems:
+            p.forward_count += 1
         check(self._lib.grape_batch_cost_and_grad(self._h, up, costs.ctypes.data, gp, 0, None), "grape_batch_cost_and_grad")
         return costs, grads
 
@@ -249,6 +257,8 @@ class GrapeBatch:
         st = (stream or torch.cuda.current_stream(self.problems[0].device)).cuda_stream
         up = (C.c_void_p * len(us))(*[u.data_ptr() for u in us])
         gp = (C.c_void_p * len(us))(*[g.data_ptr() for g in grads])
+        for p in self.problems:
+            p.forward_count += 1
         check(self._lib.grape_batch_cost_and_grad(self._h, up, costs.data_ptr(), gp, 1, st), "grape_batch_cost_and_grad")
 
     def close(self):
@@ -348,8 +358,9 @@ def _make_function():
     class GrapeHG(torch.autograd.Function):
         """cost = GrapeHG.apply(u, problem): forward sweep in forward(), backward sweep in backward().
 
-        One backward per forward: a second forward on the same problem before the
-        backward overwrites the saved checkpoints.
+        The backward sweep uses the checkpoints of the problem's last forward sweep; if another
+        evaluation ran on the problem in between (a second forward, finite differences), the
+        forward sweep is run again at the saved controls first.
         """
 
         @staticmethod
@@ -358,11 +369,17 @@ def _make_function():
             cost = torch.empty((), dtype=torch.float64, device=u.device)
             prob.cost_device(u, cost)
             ctx.prob = prob
+            ctx.u = u
+            ctx.forward_index = prob.forward_count
             return cost
 
         @staticmethod
         def backward(ctx, grad_out):
             prob = ctx.prob
+            if prob.forward_count != ctx.forward_index:
+                redo = torch.empty((), dtype=torch.float64, device=ctx.u.device)
+                prob.cost_device(ctx.u, redo)
+                ctx.forward_index = prob.forward_count
             g = torch.empty((prob.K, prob.N), dtype=torch.float64, device=grad_out.device)
             prob.grad_device(g)
             return grad_out * g, None

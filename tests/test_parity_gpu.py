@@ -642,3 +642,67 @@ def test_maximum_controls_and_full_rank_gate(precision):
     q = random_problem(8, 33, 1, 2, seed=1)
     with pytest.raises(GrapeError):
         _hg(q)
+
+
+def test_memory_does_not_grow_with_the_number_of_steps():
+    """HG keeps no per-step states (Table I: memory independent of N): without checkpoints the device
+    memory grows only by the per-step controls, gradient, schedule and overlap arrays."""
+    p = build_config("c3_gate_d4000")
+    b = {}
+    for N in (100, 400):
+        hg = _hg(p, n_steps=N, ckpt_every=-1)
+        b[N] = hg.info()["device_bytes"]
+        hg.close()
+    per_step = (b[400] - b[100]) / 300
+    state_bytes = p.dim * p.n_states * 16
+    assert per_step < 0.01 * state_bytes, (per_step, state_bytes)
+
+
+def test_c4_dimension_reduced_n_properties():
+    """d = 16000, 16 states (the C4 system) at N = 3: central differences of the GPU's own cost match
+    sampled gradient entries, and the FP32-bulk result agrees with FP64 at the stated accuracy."""
+    p = build_config("c4_gate_d16000", n_steps=3)
+    hg = _hg(p)
+    u = np.array(p.u0) * 20
+    cost, grad = hg.cost_and_grad(u)
+    m0, s0, _ = hg.schedule()
+    h = 1e-5
+    for k, n in ((0, 0), (4, 2)):
+        up = u.copy(); up[k, n] += h
+        um = u.copy(); um[k, n] -= h
+        cp = hg.cost(up)
+        assert np.array_equal(hg.schedule()[0], m0) and np.array_equal(hg.schedule()[1], s0)
+        cm = hg.cost(um)
+        assert abs((cp - cm) / (2 * h) - grad[k, n]) <= 1e-6 * np.abs(grad).max()
+    c32, g32 = _hg(p, precision="fp32_bulk").cost_and_grad(u)
+    assert abs(c32 - cost) <= FP32_RTOL * abs(cost)
+    assert np.linalg.norm(g32 - grad) <= FP32_RTOL * np.linalg.norm(grad)
+
+
+def test_autograd_gradcheck():
+    """torch.autograd.gradcheck of the Function (analytic Jacobian against finite differences)."""
+    import torch
+    from paper_2304_06200_gb300 import grape_hg
+    p = build_config("c1_state_transfer_d30", n_steps=5)
+    hg = _hg(p)
+    u = torch.tensor(p.u0 * 5, device="cuda", dtype=torch.float64, requires_grad=True)
+    assert torch.autograd.gradcheck(lambda x: grape_hg().apply(x, hg), (u,), eps=1e-6, atol=1e-7, rtol=1e-5)
+
+
+def test_autograd_backward_after_an_interleaved_forward():
+    """A second forward on the same problem before the first backward: the backward still returns
+    the gradient at its own forward's controls."""
+    import torch
+    from paper_2304_06200_gb300 import grape_hg
+    p = build_config("c2_gate_d80", n_steps=20)
+    hg = _hg(p)
+    _, g_ref = hg.cost_and_grad(p.u0)
+    u1 = torch.tensor(p.u0, device="cuda", requires_grad=True)
+    u2 = torch.tensor(p.u0 * 3, device="cuda", requires_grad=True)
+    c1 = grape_hg().apply(u1, hg)
+    c2 = grape_hg().apply(u2, hg)       # overwrites the problem's sweep state
+    c1.backward()
+    np.testing.assert_array_equal(u1.grad.cpu().numpy(), g_ref)
+    c2.backward()
+    _, g2 = hg.cost_and_grad(p.u0 * 3)
+    np.testing.assert_array_equal(u2.grad.cpu().numpy(), g2)
