@@ -777,8 +777,10 @@ def run_reference(args):
     from workloads import build_config
 
     p = build_config(args.workload)
+    # warm-up: the oracle has no compiled state to warm beyond the BLAS/LAPACK thread pools, which a
+    # small instance wakes as well as a full step (keeps the untimed part of the run short)
     for _ in range(max(args.warmup, 0)):
-        oracle_sample(args.workload)
+        oracle_sample("c1_state_transfer_d30")
     secs = 0.0
     steps = 0
     for _ in range(args.steps):
