@@ -12,10 +12,12 @@
  * that re-propagates psi and the costate with the adjoint step and accumulates
  * <costate| dU_n/du_kn |psi_{n-1}> (Eqs. (stgradient), (gategradient),
  * (C2stgrad)), the derivative being that of the Taylor approximant at frozen
- * (m, s) (Eq. (auxiliary equation)).
+ * (m, s) (Eq. (auxiliary equation)).  Alternatively (descriptor field `propagator`) each step
+ * propagator comes from a Hermitian eigendecomposition and its derivative from the divided
+ * differences of exp on the spectrum (App. F), exact up to rounding.
  *
  * Cost (all terms optional through their weights):
- *   C     = w_fid * C1 + w_forbid * C2 + w_amp * C_amp
+ *   C     = w_fid * C1 + w_forbid * C2 + w_amp * C_amp + w_tint * C3
  *   C1    = 1 - |g / n|^2,  g = sum_h <phi_T^h | psi_N^h>     Eq. (C1st) / gate form, Sec. III.A
  *   C2    = 1/(N n) sum_{n'=1..N} sum_h <psi_n'^h|Omega|psi_n'^h>   App. A, Eq. (c2st)
  *   C_amp = 1/N sum_{k,n} u_kn^2                    amplitude penalty named in Sec. II
@@ -206,7 +208,8 @@ grape_status grape_optimize(grape_problem* prob, double* u, int32_t n_iter, doub
                             int32_t on_device, void* stream);
 
 /* Wait for the problem's pending work on `stream` and return the device error word
- * (GRAPE_OK, GRAPE_ETOL, GRAPE_ENONFINITE or GRAPE_ETIMEOUT); the word is then cleared. */
+ * (GRAPE_OK, GRAPE_ETOL: no feasible (m, s) or an eigenvalue iteration that did not converge,
+ * GRAPE_ENONFINITE or GRAPE_ETIMEOUT); the word is then cleared. */
 grape_status grape_sync_status(grape_problem* prob, void* stream);
 
 /* Problem information (see grape_info). */
