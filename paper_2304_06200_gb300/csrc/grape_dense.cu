@@ -11,11 +11,14 @@
 // grape_kernels.cu; here it is driven from the host, one tensor-core product per Taylor term.
 //
 // Kernel k_dense_apply: grid (KS, d / 128), clusters of KS CTAs split the K (= d) dimension; each
-// CTA streams its 128-row slab of the four operator matrices and the matching X columns through a
-// two-stage cp.async pipeline into shared memory (K-major, no-swizzle core-matrix layout: 8 rows x
-// 16 bytes per core matrix, K-adjacent core matrices 128 bytes apart, 8-row groups 1024 bytes
-// apart), one thread issues the MMAs, and the K-split partials are summed deterministically through
-// distributed shared memory by rank 0 of the cluster.
+// CTA streams its 128-row slab of the four operator matrices and the matching X columns by TMA into
+// shared memory (K-major, no-swizzle core-matrix layout: 8 rows x 16 bytes per core matrix,
+// K-adjacent core matrices 128 bytes apart, 8-row groups 1024 bytes apart; the operand buffers are
+// stored as contiguous 8 x 8 blocks so that a tile is a few 1 KB runs), one thread drives the TMA
+// ring and issues the MMAs, the K-split partials are summed deterministically through distributed
+// shared memory (each CTA of the cluster sums a slice of the rows), and the epilogue applies the
+// chain's element-wise step for those rows (increments, Horner slots, costate, next X operand in the
+// other of two X buffers), so one launch carries one Taylor term.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -90,16 +93,57 @@ __device__ __forceinline__ int core_off(int r, int k, int kcores) {
   return (r >> 3) * (kcores * 128) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
+// Storage of the 16-bit operator and X buffers: 8 x 8 blocks (8 rows x 16 bytes) contiguous, blocks
+// ordered by 8-row group and then by 8-wide K group, so that a tile's core matrices of one row group
+// are one contiguous run in global memory (and TMA moves 1 KB runs).
+__device__ __forceinline__ int64_t tiled(int64_t row, int64_t k, int d) {
+  return ((((row >> 3) * (int64_t)(d >> 3) + (k >> 3)) << 6) + ((row & 7) << 3) + (k & 7));
+}
+
+// v = hi + lo in two 16-bit floats: fp16 (11 significant bits each) or, for BF, bf16 (8 each,
+// stored as raw bits in the same 16-bit arrays).
+template <bool BF>
+__device__ __forceinline__ void split16(float v, __half& hi, __half& lo) {
+  if constexpr (BF) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+    __half_raw rh, rl;
+    rh.x = __bfloat16_as_ushort(h);
+    rl.x = __bfloat16_as_ushort(l);
+    hi = __half(rh);
+    lo = __half(rl);
+  } else {
+    hi = __float2half_rn(v);
+    lo = __float2half_rn(v - __half2float(hi));
+  }
+}
+
+// X (real columns 2h, 2h+1 of block `blk`) <- split of a complex FP64 (scaled) or FP32 block
 struct ApplyArgs {
   // Tensor maps (4-D views whose boxes land in the K-major no-swizzle core-matrix layout):
   // [0..3] Br_hi, Br_lo, Bi_hi, Bi_lo (d x d row-major, K contiguous), [4] X high, [5] X low
   // (rows = real columns of the block, K contiguous).
   CUtensorMap tm[6];
-  float2* y;               // output: d x ncols complex, column-major (column h contiguous)
+  float2* y;               // mode 0 output: d x ncols complex, column-major (column h contiguous)
   int d, ncols, nreal;     // nreal = 2 * ncols padded to a multiple of 16 (MMA N)
   float alpha;             // y = alpha * B x
   int bf16;                // operands are bf16 bit patterns (else fp16)
   int* err;
+  // Epilogue: what is done with y (each CTA for its rows after the cluster reduction).
+  //   0: store y.
+  //   1: forward term: inc += y, X' <- split(y).
+  //   2: phase A term q (ncols = 2n: psi chain h < n, Horner chain h >= n):
+  //      a = -y_a / q, inc += a, X'_a <- split(a); q < m: w = chi (m-q)!^-1 - y_w, wslot[m-1-q] = w,
+  //      X'_w <- split(w); q == m: chi <- chi - y_w.
+  //   3: phase B term: xcur = y, X' <- split(y).
+  // X' (xnh, xnl) is the other X buffer: the one this launch reads (through the tensor maps) is
+  // still being read by other CTAs.
+  int mode, n, q, m;
+  float iq;
+  double fq;
+  __half *xnh, *xnl;
+  double2 *inc, *chi;
+  float2 *wslot, *xcur;
 };
 
 // Tile bytes: four operator tiles (128 x 64 16-bit = 16 KB each) + X hi/lo tiles (nreal x 64 16-bit).
@@ -254,8 +298,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_apply(const __grid_consta
       if (r < KS) asm volatile("mapa.u64 %0, %1, %2;" : "=l"(parts[r]) : "l"(part), "r"(r));
     }
     const int rbase = ks * kTM / KS, rows_per = (ks + 1) * kTM / KS - rbase;
-    for (int idx = tid; idx < rows_per * ncols; idx += kThreads) {
-      const int row = rbase + idx % rows_per, h = idx / rows_per;   // consecutive threads: consecutive rows
+    auto ysum = [&](int h, int row) -> float2 {   // fixed rank order: deterministic
       float vr[8], vi[8];
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
@@ -272,7 +315,55 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_apply(const __grid_consta
           si += vi[r];
         }
       }
-      a.y[(int64_t)h * a.d + row0 + row] = make_float2(a.alpha * sr, a.alpha * si);
+      return make_float2(a.alpha * sr, a.alpha * si);
+    };
+    auto put = [&](int col, int grow, float v) {   // X' entry (real column col, row grow)
+      __half p, q;
+      if (a.bf16)
+        split16<true>(v, p, q);
+      else
+        split16<false>(v, p, q);
+      a.xnh[tiled(col, grow, a.d)] = p;
+      a.xnl[tiled(col, grow, a.d)] = q;
+    };
+    const int hcols = a.mode == 2 ? a.n : ncols;
+    for (int idx = tid; idx < rows_per * hcols; idx += kThreads) {
+      const int row = rbase + idx % rows_per, h = idx / rows_per;   // consecutive threads: consecutive rows
+      const int grow = row0 + row;
+      const int64_t i = (int64_t)h * a.d + grow;
+      const float2 y = ysum(h, row);
+      if (a.mode == 0) {
+        a.y[i] = y;
+      } else if (a.mode == 1) {
+        double2 acc = a.inc[i];
+        acc.x += y.x;
+        acc.y += y.y;
+        a.inc[i] = acc;
+        put(2 * h, grow, y.x);
+        put(2 * h + 1, grow, y.y);
+      } else if (a.mode == 3) {
+        a.xcur[i] = y;
+        put(2 * h, grow, y.x);
+        put(2 * h + 1, grow, y.y);
+      } else {
+        const float2 yw = ysum(h + a.n, row);
+        const float ar = -a.iq * y.x, ai = -a.iq * y.y;
+        double2 acc = a.inc[i];
+        acc.x += ar;
+        acc.y += ai;
+        a.inc[i] = acc;
+        put(2 * h, grow, ar);
+        put(2 * h + 1, grow, ai);
+        const double2 ch = a.chi[i];
+        if (a.q < a.m) {
+          const float wr = (float)(ch.x * a.fq) - yw.x, wi = (float)(ch.y * a.fq) - yw.y;
+          a.wslot[(int64_t)(a.m - 1 - a.q) * ((int64_t)a.d * a.n) + i] = make_float2(wr, wi);
+          put(2 * (h + a.n), grow, wr);
+          put(2 * (h + a.n) + 1, grow, wi);
+        } else {
+          a.chi[i] = make_double2(ch.x - yw.x, ch.y - yw.y);
+        }
+      }
     }
   }
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
@@ -281,32 +372,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_apply(const __grid_consta
 
 // ------------------------------------------------------------------ elementwise chain kernels
 
-// Storage of the 16-bit operator and X buffers: 8 x 8 blocks (8 rows x 16 bytes) contiguous, blocks
-// ordered by 8-row group and then by 8-wide K group, so that a tile's core matrices of one row group
-// are one contiguous run in global memory (and TMA moves 1 KB runs).
-__device__ __forceinline__ int64_t tiled(int64_t row, int64_t k, int d) {
-  return ((((row >> 3) * (int64_t)(d >> 3) + (k >> 3)) << 6) + ((row & 7) << 3) + (k & 7));
-}
-
-// v = hi + lo in two 16-bit floats: fp16 (11 significant bits each) or, for BF, bf16 (8 each,
-// stored as raw bits in the same 16-bit arrays).
-template <bool BF>
-__device__ __forceinline__ void split16(float v, __half& hi, __half& lo) {
-  if constexpr (BF) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
-    __half_raw rh, rl;
-    rh.x = __bfloat16_as_ushort(h);
-    rl.x = __bfloat16_as_ushort(l);
-    hi = __half(rh);
-    lo = __half(rl);
-  } else {
-    hi = __float2half_rn(v);
-    lo = __float2half_rn(v - __half2float(hi));
-  }
-}
-
-// X (real columns 2h, 2h+1 of block `blk`) <- split of a complex FP64 (scaled) or FP32 block
 template <bool BF>
 __global__ void k_split_d(const double2* __restrict__ v, double scale, int d, int ncols, int col_off, __half* xh,
                           __half* xl) {
@@ -324,27 +389,6 @@ __global__ void k_split_d(const double2* __restrict__ v, double scale, int d, in
   }
 }
 
-// forward term: x_q = y (already scaled by 1/q), inc += y, X <- split(y)
-template <bool BF>
-__global__ void k_fwd_term(const float2* __restrict__ y, double2* inc, int d, int ncols, __half* xh, __half* xl) {
-  const int64_t total = (int64_t)d * ncols;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int h = (int)(i / d), r = (int)(i % d);
-    const float2 z = y[i];
-    double2 a = inc[i];
-    a.x += z.x;
-    a.y += z.y;
-    inc[i] = a;
-    __half p, q;
-    split16<BF>(z.x, p, q);
-    xh[tiled(2 * h, r, d)] = p;
-    xl[tiled(2 * h, r, d)] = q;
-    split16<BF>(z.y, p, q);
-    xh[tiled(2 * h + 1, r, d)] = p;
-    xl[tiled(2 * h + 1, r, d)] = q;
-  }
-}
-
 __global__ void k_axpy_d(double2* a, const double2* __restrict__ b, int64_t total) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     double2 v = a[i];
@@ -352,44 +396,6 @@ __global__ void k_axpy_d(double2* a, const double2* __restrict__ b, int64_t tota
     v.x += w.x;
     v.y += w.y;
     a[i] = v;
-  }
-}
-
-// phase A term q: y holds (B [a | w]) for the psi chain (columns 0..n-1) and the Horner chain (n..2n-1).
-//   a_q = -y_a / q (inc += a_q), w_{m-1-q} = chi/(m-q)! - y_w  (q < m), chi^(l) = chi - y_w (q == m)
-template <bool BF>
-__global__ void k_phase_a_term(const float2* __restrict__ y, double2* inc, double2* chi, float2* wslot, int d, int n,
-                               int q, int m, double iq, double fq, __half* xh, __half* xl) {
-  const int64_t total = (int64_t)d * n;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int h = (int)(i / d), r = (int)(i % d);
-    const float2 ya = y[i];
-    const float2 yw = y[total + i];
-    const float ar = (float)(-iq) * ya.x, ai = (float)(-iq) * ya.y;
-    double2 a = inc[i];
-    a.x += ar;
-    a.y += ai;
-    inc[i] = a;
-    __half p, s2;
-    split16<BF>(ar, p, s2);
-    xh[tiled(2 * h, r, d)] = p;
-    xl[tiled(2 * h, r, d)] = s2;
-    split16<BF>(ai, p, s2);
-    xh[tiled(2 * h + 1, r, d)] = p;
-    xl[tiled(2 * h + 1, r, d)] = s2;
-    const double2 ch = chi[i];
-    if (q < m) {
-      const float wr = (float)(ch.x * fq) - yw.x, wi = (float)(ch.y * fq) - yw.y;
-      wslot[(int64_t)(m - 1 - q) * total + i] = make_float2(wr, wi);
-      split16<BF>(wr, p, s2);
-      xh[tiled(2 * (h + n), r, d)] = p;
-      xl[tiled(2 * (h + n), r, d)] = s2;
-      split16<BF>(wi, p, s2);
-      xh[tiled(2 * (h + n) + 1, r, d)] = p;
-      xl[tiled(2 * (h + n) + 1, r, d)] = s2;
-    } else {
-      chi[i] = make_double2(ch.x - yw.x, ch.y - yw.y);
-    }
   }
 }
 
@@ -418,24 +424,6 @@ __global__ void k_phase_a_start(const double2* __restrict__ psi, const double2* 
     split16<BF>(wi, p, s2);
     xh[tiled(2 * (h + n) + 1, r, d)] = p;
     xl[tiled(2 * (h + n) + 1, r, d)] = s2;
-  }
-}
-
-// phase B: xcur <- y (the next x_p, FP32) and X <- split(y)
-template <bool BF>
-__global__ void k_phase_b_term(const float2* __restrict__ y, float2* xcur, int d, int n, __half* xh, __half* xl) {
-  const int64_t total = (int64_t)d * n;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int h = (int)(i / d), r = (int)(i % d);
-    const float2 z = y[i];
-    xcur[i] = z;
-    __half p, s2;
-    split16<BF>(z.x, p, s2);
-    xh[tiled(2 * h, r, d)] = p;
-    xl[tiled(2 * h, r, d)] = s2;
-    split16<BF>(z.y, p, s2);
-    xh[tiled(2 * h + 1, r, d)] = p;
-    xl[tiled(2 * h + 1, r, d)] = s2;
   }
 }
 
@@ -645,7 +633,9 @@ cudaError_t dense_make_maps(DenseCtx& c) {
   for (int i = 0; i < 4; ++i)
     if ((e = make(&c.tm[i], ops[i], d, kTM / 8)) != cudaSuccess) return e;
   if ((e = make(&c.tm[4], c.xh, (uint64_t)c.x_rows, 2)) != cudaSuccess) return e;
-  return make(&c.tm[5], c.xl, (uint64_t)c.x_rows, 2);
+  if ((e = make(&c.tm[5], c.xl, (uint64_t)c.x_rows, 2)) != cudaSuccess) return e;
+  if ((e = make(&c.tm[6], c.xh2, (uint64_t)c.x_rows, 2)) != cudaSuccess) return e;
+  return make(&c.tm[7], c.xl2, (uint64_t)c.x_rows, 2);
 }
 
 // Launch of a split kernel with the operand type of the problem (fp16 or bf16 pairs).
@@ -658,9 +648,38 @@ cudaError_t dense_make_maps(DenseCtx& c) {
   } while (0)
 
 // y = alpha * B x for the first `ncols` complex columns held in X (real columns 2h, 2h+1).
-static cudaError_t apply(const DenseCtx& c, int ncols, float alpha, float2* y, cudaStream_t st) {
+// The epilogue of one product (ApplyArgs::mode and its operands).
+struct Epilogue {
+  int mode = 0, q = 0, m = 0;
+  float iq = 0.f;
+  double fq = 0.0;
+  double2 *inc = nullptr, *chi = nullptr;
+  float2 *wslot = nullptr, *xcur = nullptr;
+};
+
+static __half* xbuf_h(const DenseCtx& c, int sel) { return sel ? c.xh2 : c.xh; }
+static __half* xbuf_l(const DenseCtx& c, int sel) { return sel ? c.xl2 : c.xl; }
+
+// y = alpha * B x for the first `ncols` complex columns held in X buffer `xsel` (real columns 2h,
+// 2h+1), followed by the epilogue, which writes the next operand into X buffer 1 - xsel.
+static cudaError_t apply(const DenseCtx& c, int ncols, float alpha, float2* y, cudaStream_t st, int xsel,
+                         const Epilogue& ep) {
   ApplyArgs a{};
-  for (int i = 0; i < 6; ++i) a.tm[i] = c.tm[i];
+  for (int i = 0; i < 4; ++i) a.tm[i] = c.tm[i];
+  a.tm[4] = c.tm[4 + 2 * xsel];
+  a.tm[5] = c.tm[5 + 2 * xsel];
+  a.xnh = xbuf_h(c, 1 - xsel);
+  a.xnl = xbuf_l(c, 1 - xsel);
+  a.mode = ep.mode;
+  a.n = c.n;
+  a.q = ep.q;
+  a.m = ep.m;
+  a.iq = ep.iq;
+  a.fq = ep.fq;
+  a.inc = ep.inc;
+  a.chi = ep.chi;
+  a.wslot = ep.wslot;
+  a.xcur = ep.xcur;
   a.y = y;
   a.d = c.d;
   a.ncols = ncols;
@@ -741,12 +760,15 @@ cudaError_t dense_forward(const DenseCtx& c, const int* m_host, const int* s_hos
                                                        c.u, c.N, step, c.dt / s, d, c.brh, c.brl, c.bih, c.bil);
     DCHK(cudaGetLastError());
     for (int l = 0; l < s; ++l) {
+      int xsel = 0;
       SPLIT_LAUNCH(k_split_d, g, 256, st, c.psi, 1.0, d, n, 0, c.xh, c.xl);
       DCHK(cudaMemsetAsync(c.inc, 0, tot * sizeof(double2), st));
-      for (int q = 1; q <= m; ++q) {
-        DCHK(apply(c, n, 1.0f / q, c.y, st));
-        SPLIT_LAUNCH(k_fwd_term, g, 256, st, c.y, c.inc, d, n, c.xh, c.xl);
-        DCHK(cudaGetLastError());
+      for (int q = 1; q <= m; ++q) {   // x_q = (B / q) x_{q-1}; inc += x_q (fused epilogue)
+        Epilogue ep;
+        ep.mode = 1;
+        ep.inc = c.inc;
+        DCHK(apply(c, n, 1.0f / q, c.y, st, xsel, ep));
+        xsel ^= 1;
       }
       k_axpy_d<<<g, 256, 0, st>>>(c.psi, c.inc, tot);
       DCHK(cudaGetLastError());
@@ -789,18 +811,27 @@ cudaError_t dense_backward(const DenseCtx& c, const int* m_host, const int* s_ho
     DCHK(cudaMemsetAsync(c.W, 0, (size_t)std::max(c.nce, 1) * sizeof(double2), st));
     for (int l = s - 1; l >= 0; --l) {
       // phase A: [psi | Horner] chains with -B
+      int xsel = 0;
       SPLIT_LAUNCH(k_phase_a_start, g, 256, st, c.psi, c.chi, c.inc, c.wslot, d, n, m, c.inv_fact[m], c.xh, c.xl);
       DCHK(cudaGetLastError());
-      for (int q = 1; q <= m; ++q) {
-        DCHK(apply(c, 2 * n, 1.0f, c.y, st));
-        SPLIT_LAUNCH(k_phase_a_term, g, 256, st, c.y, c.inc, c.chi, c.wslot, d, n, q, m, 1.0 / q, c.inv_fact[m - q], c.xh,
-                                         c.xl);
-        DCHK(cudaGetLastError());
+      for (int q = 1; q <= m; ++q) {   // fused epilogue: increments, Horner slots, costate
+        Epilogue ep;
+        ep.mode = 2;
+        ep.q = q;
+        ep.m = m;
+        ep.iq = (float)(1.0 / q);
+        ep.fq = c.inv_fact[m - q];
+        ep.inc = c.inc;
+        ep.chi = c.chi;
+        ep.wslot = c.wslot;
+        DCHK(apply(c, 2 * n, 1.0f, c.y, st, xsel, ep));
+        xsel ^= 1;
       }
       k_axpy_d<<<g, 256, 0, st>>>(c.psi, c.inc, tot);   // psi^(l)
       DCHK(cudaGetLastError());
       // phase B: x chain with B, W accumulation on control entries
       k_psi_to_f32<<<g, 256, 0, st>>>(c.psi, c.xcur, tot);
+      xsel = 0;
       SPLIT_LAUNCH(k_split_d, g, 256, st, c.psi, 1.0, d, n, 0, c.xh, c.xl);
       DCHK(cudaGetLastError());
       for (int p = 0; p < m; ++p) {
@@ -809,10 +840,12 @@ cudaError_t dense_backward(const DenseCtx& c, const int* m_host, const int* s_ho
                                                     d, n);
           DCHK(cudaGetLastError());
         }
-        if (p < m - 1) {
-          DCHK(apply(c, n, 1.0f, c.y, st));
-          SPLIT_LAUNCH(k_phase_b_term, g, 256, st, c.y, c.xcur, d, n, c.xh, c.xl);
-          DCHK(cudaGetLastError());
+        if (p < m - 1) {   // x_{p+1} = B x_p (fused epilogue: xcur, next X)
+          Epilogue ep;
+          ep.mode = 3;
+          ep.xcur = c.xcur;
+          DCHK(apply(c, n, 1.0f, c.y, st, xsel, ep));
+          xsel ^= 1;
         }
       }
     }

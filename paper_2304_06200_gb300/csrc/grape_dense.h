@@ -10,7 +10,7 @@
 namespace grape {
 
 struct DenseCtx {
-  CUtensorMap tm[6];        // TMA views of brh, brl, bih, bil, xh, xl (made by dense_make_maps)
+  CUtensorMap tm[8];        // TMA views of brh, brl, bih, bil, xh, xl, xh2, xl2 (dense_make_maps)
   int d, n, N, K, ksplit;
   int x_rows;               // rows allocated in xh / xl (>= 4 n, >= 64, a multiple of 16)
   int bf16;                 // operand pairs are bf16 (GRAPE_TC_BF16), else fp16 (GRAPE_TC_FP16)
@@ -19,7 +19,8 @@ struct DenseCtx {
   double inv_fact[62];
   // operator of the current step (FP16 hi/lo of Br and Bi, d x d row-major) and work blocks
   __half *brh, *brl, *bih, *bil;
-  __half *xh, *xl;          // (4 n) x d: real columns of up to 2 n complex columns
+  __half *xh, *xl;          // x_rows x d: real columns of up to 2 n complex columns (tiled storage)
+  __half *xh2, *xl2;        // the second X buffer pair: a product reads one and writes the other
   float2* y;                // d x 2n complex, column-major
   double2 *psi, *chi, *inc; // d x n
   float2* wslot;            // m_cap x d x n Horner vectors (FP32)

@@ -345,6 +345,10 @@ grape_status build_dense(grape_problem* P, const grape_desc* d, const std::vecto
   if ((st = dzeros(P, &xl, (size_t)c.x_rows * dim))) return st;
   c.xh = xh;
   c.xl = xl;
+  if ((st = dzeros(P, &xh, (size_t)c.x_rows * dim))) return st;
+  if ((st = dzeros(P, &xl, (size_t)c.x_rows * dim))) return st;
+  c.xh2 = xh;
+  c.xl2 = xl;
   float2* y;
   if ((st = dzeros(P, &y, 2 * blk))) return st;
   c.y = y;
