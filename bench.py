@@ -280,6 +280,8 @@ def run_ours(args):
             extra["c5_batch"] = batch_compare(local, args.autotune)
         if args.c4:
             extra["c4"] = c4_compare(local)
+        if args.m_sweep:
+            extra["checkpoint_sweep"] = checkpoint_sweep(args.workload, local, args.n_steps)
         print(json.dumps({"extras": extra}), flush=True)
         return
     p = build_config(args.workload, seed=None if rank == 0 else 1000 + rank, n_steps=args.n_steps)
