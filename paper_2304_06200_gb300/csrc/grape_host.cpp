@@ -206,6 +206,7 @@ struct grape_problem {
   cudaEvent_t eig_fork = nullptr;
   // dense tensor-core mode
   bool dense = false;
+  bool diag_first = false;          // diagonal entries first in their rows (all H_ii real)
   grape::DenseCtx dctx{};
   std::vector<int> m_host, s_host;
   // steepest-descent iteration recorded as a CUDA graph (grape_optimize)
@@ -708,6 +709,58 @@ grape_status build(grape_problem* P, const grape_desc* d) {
   P->s_cap = P->table.s_cap;
   if (P->precision == GRAPE_TC_FP16 || P->precision == GRAPE_TC_BF16)
     return build_dense(P, d, rowptr, ucol, h0v, cptr, cidx, cval, ectr_ptr, ectr_k, ectr_val);
+  // ---- diagonal entries first.  A Hermitian H_n has a real diagonal; when every operator's stored
+  // diagonal is exactly real, B_ii = -i (dt/s) H_ii is imaginary and the sweeps apply it with two
+  // multiplies instead of a complex multiply-add.  The sweeps find it as the first entry of its row
+  // (the other entries keep their ascending order, so each CTA's own columns stay contiguous).
+  bool diag_real = true;
+  for (int k = 0; k <= K && diag_real; ++k)
+    for (int64_t i = 0; i < dim && diag_real; ++i)
+      for (int64_t e = ops[k].rowptr[i]; e < ops[k].rowptr[i + 1]; ++e)
+        if (ops[k].col[e] == i && ops[k].val[e].imag() != 0.0) {
+          diag_real = false;
+          break;
+        }
+  if (diag_real) {
+    std::vector<int64_t> to(nnz), from(nnz);   // new index of an entry, entry at a new index
+    for (int64_t i = 0; i < dim; ++i) {
+      const int64_t b = rowptr[i], e = rowptr[i + 1];
+      for (int64_t t = b; t < e; ++t) to[t] = t;
+      const int64_t pd = uindex(i, (int32_t)i);
+      if (pd < e && ucol[pd] == (int32_t)i) {
+        for (int64_t t = b; t < pd; ++t) to[t] = t + 1;
+        to[pd] = b;
+      }
+    }
+    for (int64_t t = 0; t < nnz; ++t) from[to[t]] = t;
+    std::vector<int32_t> ucol2(nnz);
+    std::vector<double2> h0v2(nnz);
+    for (int64_t t = 0; t < nnz; ++t) {
+      ucol2[t] = ucol[from[t]];
+      h0v2[t] = h0v[from[t]];
+    }
+    ucol.swap(ucol2);
+    h0v.swap(h0v2);
+    for (int k = 0; k < K; ++k) {   // per-control lists: remap, keep them sorted by entry
+      std::vector<std::pair<int, double2>> lst;
+      for (int c = cptr[k]; c < cptr[k + 1]; ++c) lst.emplace_back((int)to[cidx[c]], cval[c]);
+      std::sort(lst.begin(), lst.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+      for (int c = cptr[k]; c < cptr[k + 1]; ++c) {
+        cidx[c] = lst[c - cptr[k]].first;
+        cval[c] = lst[c - cptr[k]].second;
+      }
+    }
+    ectr_k.clear();
+    ectr_val.clear();
+    for (int64_t t = 0; t < nnz; ++t) {
+      for (auto& pr : per_entry[from[t]]) {
+        ectr_k.push_back(pr.first);
+        ectr_val.push_back(pr.second);
+      }
+      ectr_ptr[t + 1] = (int)ectr_k.size();
+    }
+    P->diag_first = true;
+  }
   // ---- partitions: CTAs per column team (CL) for the forward and the backward sweep.
   // Cost model per Taylor term and CTA, in SM clocks: a * (entries x chains) + b * (rows x chains)
   // + team barrier, with a = 4 FMA per complex multiply-add at 1.7 FP64 lanes/clk (FP32: ~100
@@ -923,6 +976,7 @@ grape::SweepParams sweep_params(grape_problem* P, const KPlan& kp) {
   p.ckpt_every = P->ckpt_every;
   p.n_ckpt = P->n_ckpt;
   p.m_cap = P->m_cap;
+  p.diag_first = P->diag_first ? 1 : 0;
   p.rowptr = P->d_rowptr;
   p.colenc = kp.d_colenc;
   p.h0v = P->d_h0v;

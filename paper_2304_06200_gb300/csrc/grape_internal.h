@@ -29,6 +29,8 @@ struct SweepParams {
   int n_ckpt;                          // number of stored checkpoints
   int m_cap;
   // union pattern (global)
+  int diag_first;                      // 1: every diagonal H_ii is real and, where present, is the
+                                       // first entry of its row (B_ii = -i dt H_ii / s is imaginary)
   const int64_t* rowptr;               // dim + 1
   const uint32_t* colenc;              // nnz, per CL-partition encoding (owner, local, ctrl bit)
   const double2* h0v;                  // nnz drift values on the union pattern

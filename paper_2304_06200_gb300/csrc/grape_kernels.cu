@@ -25,9 +25,10 @@ namespace cg = cooperative_groups;
 
 namespace grape {
 
-// 1/q and 1/q! for q = 0..kMaxTaylor
+// 1/q, 1/q! and (-1)^q / q! for q = 0..kMaxTaylor
 __constant__ double c_inv_int[kMaxTaylor + 2];
 __constant__ double c_inv_fact[kMaxTaylor + 2];
+__constant__ double c_sgn_fact[kMaxTaylor + 2];
 
 static bool g_constants_ready[64] = {false};
 
@@ -36,15 +37,17 @@ static cudaError_t ensure_constants() {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 0 && dev < 64 && g_constants_ready[dev]) return cudaSuccess;
-  double inv_int[kMaxTaylor + 2], inv_fact[kMaxTaylor + 2];
+  double inv_int[kMaxTaylor + 2], inv_fact[kMaxTaylor + 2], sgn_fact[kMaxTaylor + 2];
   inv_int[0] = 0.0;
   inv_fact[0] = 1.0;
   for (int q = 1; q < kMaxTaylor + 2; ++q) {
     inv_int[q] = 1.0 / q;
     inv_fact[q] = inv_fact[q - 1] / q;
   }
+  for (int q = 0; q < kMaxTaylor + 2; ++q) sgn_fact[q] = (q & 1) ? -inv_fact[q] : inv_fact[q];
   e = cudaMemcpyToSymbol(c_inv_int, inv_int, sizeof(inv_int));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_inv_fact, inv_fact, sizeof(inv_fact));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_sgn_fact, sgn_fact, sizeof(sgn_fact));
   if (e == cudaSuccess && dev >= 0 && dev < 64) g_constants_ready[dev] = true;
   return e;
 }
@@ -220,6 +223,10 @@ __device__ __forceinline__ float2 horner(const double2 ch, double f, const float
   return make_float2((float)(ch.x * f) - yw.x, (float)(ch.y * f) - yw.y);
 }
 
+// B_ii x with B_ii = (0, b) imaginary (H_ii real): two multiplies.  As the first term of a row sum it
+// equals the complex multiply-add on a zero accumulator.
+__device__ __forceinline__ double2 diag_mul(double b, const double2 x) { return make_double2(-b * x.y, b * x.x); }
+
 template <typename T>
 struct Carve {
   cx<T>* xb;          // exchange buffers (local)
@@ -276,6 +283,11 @@ __device__ __forceinline__ void assemble(const SweepParams& p, cx<T>* vals, int6
     }
     vals[e] = from_d2<T>(make_double2(scale * v.y, -scale * v.x));   // -i v
   }
+}
+
+// Entry ea of local row i is the row's diagonal (stored first when every H_ii is real).
+__device__ __forceinline__ bool diag_at(const SweepParams& p, const uint32_t* lcol, int ea, int eb, int rank, int i) {
+  return p.diag_first && ea < eb && (lcol[ea] & ~kCtrlBit) == (((uint32_t)rank << kOwnerShift) | (uint32_t)i);
 }
 
 __device__ __forceinline__ void load_controls(const SweepParams& p, int n, double* s_u) {
@@ -380,8 +392,9 @@ struct Team {
   // column in this CTA's rows are the run [la, la + nloc) (columns ascend, so do their owners), and
   // l1 = the smallest nloc of the warp's rows: the first l1 of the run are summed before the wait
   // of the cluster barrier, the other entries in one loop after it.
+  // A diagonal stored first (entry ed, else -1) is not part of [ea, eb): it is applied separately.
   bool one_row;
-  int ea, eb, la, l1;
+  int ea, eb, la, l1, ed;
 };
 
 // ------------------------------------------------------------------ forward sweep
@@ -389,6 +402,9 @@ struct Team {
 // psi_n = (e^{B}_m)^s psi_{n-1} by the recursions b_j = (B/j) b_{j-1} (App. C Eq. (recursive relation 1))
 // and c_l = e^B_m c_{l-1} (Eq. (recursive relation2)); C2 accumulates <psi_n|Omega|psi_n> (App. A).
 // The state psi and the per-substep sum of the terms are FP64; the terms themselves use the bulk type.
+// FP64 terms are kept unscaled, x_j = B^j c_{l-1} = j! b_j, and the sum takes x_j / j! in one fused
+// multiply-add (one FP64 operation per component fewer than scaling every term by 1/j); FP32 terms
+// keep the 1/j scaling, which bounds their range.
 template <typename T, bool CLUSTER>
 __global__ void __launch_bounds__(512, 1) k_forward(SweepParams p) {
   using C2 = cx<T>;
@@ -418,11 +434,13 @@ __global__ void __launch_bounds__(512, 1) k_forward(SweepParams p) {
   const bool split_rows = nrows <= (int)blockDim.x;   // one row per thread: split-barrier term loop
   // The thread's row: entries [ea, eb), of which [la, lb) have their column in this CTA's rows
   // (columns ascend within a row and owners ascend with the column, so they are contiguous).
-  int ea = 0, eb = 0, la = 0, lb = 0;
+  // A diagonal stored first (ed) is applied separately, with two multiplies.
+  int ea = 0, eb = 0, la = 0, lb = 0, ed = -1;
   __syncthreads();   // the local pattern written by sweep_setup
   if (split_rows && (int)threadIdx.x < nrows) {
     ea = c.lrow[threadIdx.x];
     eb = c.lrow[threadIdx.x + 1];
+    if (diag_at(p, c.lcol, ea, eb, rank, threadIdx.x)) ed = ea++;
     la = ea;
     while (la < eb && ((c.lcol[la] >> kOwnerShift) & 0xFFu) < (uint32_t)rank) ++la;
     lb = la;
@@ -455,8 +473,10 @@ __global__ void __launch_bounds__(512, 1) k_forward(SweepParams p) {
             const int src = (q - 1) & 1, dst = q & 1;
             const C2* xs = X0 + src * R;
             C2 y = czero<C2>();
-            if (i < nrows)
+            if (i < nrows) {
+              if (ed >= 0) y = diag_mul(c.vals[ed].y, xs[i]);
               for (int e = la; e < lb; ++e) cmacT(y, c.vals[e], xs[c.lcol[e] & kLocalMask]);
+            }
             cluster_wait();
             if (i < nrows) {
               // one loop over the remote entries on both sides of the local run, so that a warp
@@ -467,14 +487,11 @@ __global__ void __launch_bounds__(512, 1) k_forward(SweepParams p) {
                 const uint32_t enc = c.lcol[e];
                 cmacT(y, c.vals[e], tab[src].ptr[(enc >> kOwnerShift) & 0xFFu][enc & kLocalMask]);
               }
-              const T iq = (T)c_inv_int[q];
-              y.x *= iq;
-              y.y *= iq;
-              X0[dst * R + i] = y;
+              X0[dst * R + i] = y;   // B^q c (unscaled)
               double2 a = c.inc[i];
-              const double2 yd = to_d2(y);
-              a.x += yd.x;
-              a.y += yd.y;
+              const double fq = c_inv_fact[q];
+              a.x = fma(y.x, fq, a.x);
+              a.y = fma(y.y, fq, a.y);
               c.inc[i] = a;
             }
             if (q < m) {
@@ -498,17 +515,25 @@ __global__ void __launch_bounds__(512, 1) k_forward(SweepParams p) {
       for (int q = 1; q <= m; ++q) {
         const int src = (q - 1) & 1, dst = q & 1;
         const T iq = (T)c_inv_int[q];
+        const double fq = c_inv_fact[q];
         const C2* xs = X0 + src * R;
         C2* xd = X0 + dst * R;
         for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
           C2 y = row_mv<T, CLUSTER>(c.vals, c.lcol, c.lrow[i], c.lrow[i + 1], xs, tab[src]);
-          y.x *= iq;
-          y.y *= iq;
-          xd[i] = y;
           double2 a = c.inc[i];
-          const double2 yd = to_d2(y);
-          a.x += yd.x;
-          a.y += yd.y;
+          if constexpr (sizeof(C2) == 16) {   // B^q c unscaled; the sum takes 1/q!
+            xd[i] = y;
+            const double2 yd = to_d2(y);
+            a.x = fma(yd.x, fq, a.x);
+            a.y = fma(yd.y, fq, a.y);
+          } else {
+            y.x *= iq;
+            y.y *= iq;
+            xd[i] = y;
+            const double2 yd = to_d2(y);
+            a.x += yd.x;
+            a.y += yd.y;
+          }
           c.inc[i] = a;
         }
         team_sync<CLUSTER>();
@@ -597,7 +622,9 @@ __device__ __forceinline__ void costate_init(const SweepParams& p, double2* psi,
   }
 }
 
-// Phase A of one substep.  wout(p, i, w) stores Horner vector w_p of local row i.
+// Phase A of one substep.  wout(p, i, w) stores Horner vector w_p of local row i.  The psi chain
+// psi^(l) = P(-B) psi^(l+1) keeps its FP64 terms unscaled (B^q psi^(l+1)) and sums them with the
+// weights (-1)^q / q!; FP32 terms are scaled by -1/q at every step.
 template <typename T, bool CLUSTER, typename WOut>
 __device__ __forceinline__ void phase_a(Team<T, CLUSTER>& tm, int m, WOut wout) {
   using C2 = cx<T>;
@@ -629,7 +656,12 @@ __device__ __forceinline__ void phase_a(Team<T, CLUSTER>& tm, int m, WOut wout) 
         const C2* xw = tm.X(2 + src);
         C2 ya = czero<C2>(), yw = czero<C2>(), w = czero<C2>();
         double2 ch = make_double2(0.0, 0.0);
-        if (act)
+        if (act) {
+          if (tm.ed >= 0) {
+            const double b = c.vals[tm.ed].y;
+            ya = diag_mul(b, xa[i]);
+            yw = diag_mul(b, xw[i]);
+          }
           for (int k = 0; k < tm.l1; ++k) {
             const int e = tm.la + k;
             const uint32_t loc = c.lcol[e] & kLocalMask;
@@ -637,6 +669,7 @@ __device__ __forceinline__ void phase_a(Team<T, CLUSTER>& tm, int m, WOut wout) 
             cmacT(ya, v, xa[loc]);
             cmacT(yw, v, xw[loc]);
           }
+        }
         cluster_wait();
         if (act) {
           for (int k = 0; k < nrest; ++k) {
@@ -646,10 +679,7 @@ __device__ __forceinline__ void phase_a(Team<T, CLUSTER>& tm, int m, WOut wout) 
             cmacT(ya, v, xload<T, CLUSTER>(xa, tm.tab[src], enc));
             cmacT(yw, v, xload<T, CLUSTER>(xw, tm.tab[2 + src], enc));
           }
-          const T iq = (T)c_inv_int[q];
-          ya.x *= -iq;
-          ya.y *= -iq;
-          tm.X(dst)[i] = ya;
+          tm.X(dst)[i] = ya;   // B^q psi^(l+1), unscaled
           ch = c.chi[i];
           if (q < m) {
             w = horner(ch, c_inv_fact[m - q], yw);
@@ -660,8 +690,9 @@ __device__ __forceinline__ void phase_a(Team<T, CLUSTER>& tm, int m, WOut wout) 
         cluster_arrive();
         if (act) {
           double2 a = c.inc[i];
-          a.x += ya.x;
-          a.y += ya.y;
+          const double sq = c_sgn_fact[q];   // (-B)^q / q! = (-1)^q / q! B^q
+          a.x = fma(ya.x, sq, a.x);
+          a.y = fma(ya.y, sq, a.y);
           c.inc[i] = a;
           const double fq = c_inv_fact[m - q];
           if (q < m)
@@ -690,13 +721,20 @@ __device__ __forceinline__ void phase_a(Team<T, CLUSTER>& tm, int m, WOut wout) 
       C2 ya, yw;
       row_mv2<T, CLUSTER>(c.vals, c.lcol, c.lrow[i], c.lrow[i + 1], tm.X(src), tm.tab[src], tm.X(2 + src),
                           tm.tab[2 + src], ya, yw);
-      ya.x *= -iq;                                   // (-B) a_{q-1} / q
-      ya.y *= -iq;
-      tm.X(dst)[i] = ya;
       double2 a = c.inc[i];
-      const double2 yad = to_d2(ya);
-      a.x += yad.x;
-      a.y += yad.y;
+      if constexpr (sizeof(C2) == 16) {              // FP64: B^q psi unscaled, the sum takes (-1)^q / q!
+        tm.X(dst)[i] = ya;
+        const double sq = c_sgn_fact[q];
+        a.x = fma(ya.x, sq, a.x);
+        a.y = fma(ya.y, sq, a.y);
+      } else {
+        ya.x *= -iq;                                 // (-B) a_{q-1} / q
+        ya.y *= -iq;
+        tm.X(dst)[i] = ya;
+        const double2 yad = to_d2(ya);
+        a.x += yad.x;
+        a.y += yad.y;
+      }
       c.inc[i] = a;
       const double2 ch = c.chi[i];
       if (q < m) {
@@ -752,6 +790,15 @@ __device__ __forceinline__ void phase_b(Team<T, CLUSTER>& tm, int m, WIn win) {
         };
         if (act) {
           if (more) wnext = win(pp + 1, i);
+          if (tm.ed >= 0) {
+            const C2 x = xs[i];
+            if (more) y0 = diag_mul(c.vals[tm.ed].y, x);
+            if (c.lcol[tm.ed] & kCtrlBit) {
+              double2 acc = c.W[tm.ed];
+              cmac_conjT(acc, wp, x);
+              c.W[tm.ed] = acc;
+            }
+          }
           for (int k = 0; k < tm.l1; ++k) {
             const int e = tm.la + k;
             const uint32_t enc = c.lcol[e];
@@ -933,6 +980,7 @@ __device__ __forceinline__ void team_init(Team<T, CLUSTER>& tm, unsigned char* s
   sweep_setup(p, tm.c.lrow, tm.c.lcol, tm.r0, tm.nrows, tm.e0, tm.nnz_loc);
   tm.one_row = CLUSTER && sizeof(cx<T>) == 16 && tm.nrows <= (int)blockDim.x;
   tm.ea = tm.eb = tm.la = tm.l1 = 0;
+  tm.ed = -1;
   __syncthreads();   // the local pattern
   if (tm.one_row) {
     int nloc = 1 << 30;
@@ -941,6 +989,7 @@ __device__ __forceinline__ void team_init(Team<T, CLUSTER>& tm, unsigned char* s
       const uint32_t* lcol = tm.c.lcol;
       tm.ea = lrow[threadIdx.x];
       tm.eb = lrow[threadIdx.x + 1];
+      if (diag_at(p, lcol, tm.ea, tm.eb, rank, threadIdx.x)) tm.ed = tm.ea++;
       int a = tm.ea;
       while (a < tm.eb && ((lcol[a] >> kOwnerShift) & 0xFFu) < (uint32_t)rank) ++a;
       int b = a;
