@@ -709,10 +709,12 @@ grape_status build(grape_problem* P, const grape_desc* d) {
   P->s_cap = P->table.s_cap;
   if (P->precision == GRAPE_TC_FP16 || P->precision == GRAPE_TC_BF16)
     return build_dense(P, d, rowptr, ucol, h0v, cptr, cidx, cval, ectr_ptr, ectr_k, ectr_val);
-  // ---- diagonal entries first.  A Hermitian H_n has a real diagonal; when every operator's stored
-  // diagonal is exactly real, B_ii = -i (dt/s) H_ii is imaginary and the sweeps apply it with two
-  // multiplies instead of a complex multiply-add.  The sweeps find it as the first entry of its row
-  // (the other entries keep their ascending order, so each CTA's own columns stay contiguous).
+  // ---- row layout.  A Hermitian H_n has a real diagonal: when every operator's stored diagonal is
+  // exactly real, B_ii = -i (dt/s) H_ii is imaginary and is stored first in its row.  Off-diagonal
+  // entries whose every H_ij term (drift and controls) is real have an imaginary B_ij, those whose
+  // every term is imaginary a real B_ij; they follow in two segments, then the general entries.  The
+  // one-row-per-thread sweeps apply the first three kinds with two multiplies instead of four; each
+  // segment keeps ascending columns, so a CTA's own columns stay contiguous among the general ones.
   bool diag_real = true;
   for (int k = 0; k <= K && diag_real; ++k)
     for (int64_t i = 0; i < dim && diag_real; ++i)
@@ -721,18 +723,32 @@ grape_status build(grape_problem* P, const grape_desc* d) {
           diag_real = false;
           break;
         }
-  if (diag_real) {
+  P->diag_first = diag_real;
+  std::vector<uint32_t> eclass(nnz, 0);   // kImagBBit / kRealBBit per entry (new order)
+  {
+    std::vector<int> seg(nnz, 3);
+    for (int64_t e = 0; e < nnz; ++e) {
+      bool nonreal = h0v[e].y != 0.0, nonimag = h0v[e].x != 0.0;
+      for (auto& pr : per_entry[e]) {
+        nonreal = nonreal || pr.second.y != 0.0;
+        nonimag = nonimag || pr.second.x != 0.0;
+      }
+      seg[e] = !nonreal ? 1 : (!nonimag ? 2 : 3);
+    }
     std::vector<int64_t> to(nnz), from(nnz);   // new index of an entry, entry at a new index
+    std::vector<std::pair<int, int64_t>> key;
     for (int64_t i = 0; i < dim; ++i) {
       const int64_t b = rowptr[i], e = rowptr[i + 1];
-      for (int64_t t = b; t < e; ++t) to[t] = t;
-      const int64_t pd = uindex(i, (int32_t)i);
-      if (pd < e && ucol[pd] == (int32_t)i) {
-        for (int64_t t = b; t < pd; ++t) to[t] = t + 1;
-        to[pd] = b;
+      key.clear();
+      for (int64_t t = b; t < e; ++t) key.emplace_back(ucol[t] == (int32_t)i && diag_real ? 0 : seg[t], t);
+      std::stable_sort(key.begin(), key.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+      for (int64_t t = b; t < e; ++t) {
+        from[t] = key[t - b].second;
+        to[from[t]] = t;
+        const int sg = key[t - b].first;
+        eclass[t] = sg == 1 ? grape::kImagBBit : (sg == 2 ? grape::kRealBBit : 0u);
       }
     }
-    for (int64_t t = 0; t < nnz; ++t) from[to[t]] = t;
     std::vector<int32_t> ucol2(nnz);
     std::vector<double2> h0v2(nnz);
     for (int64_t t = 0; t < nnz; ++t) {
@@ -759,7 +775,6 @@ grape_status build(grape_problem* P, const grape_desc* d) {
       }
       ectr_ptr[t + 1] = (int)ectr_k.size();
     }
-    P->diag_first = true;
   }
   // ---- partitions: CTAs per column team (CL) for the forward and the backward sweep.
   // Cost model per Taylor term and CTA, in SM clocks: a * (entries x chains) + b * (rows x chains)
@@ -877,7 +892,7 @@ grape_status build(grape_problem* P, const grape_desc* d) {
       for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
         const int32_t j = ucol[e];
         const uint32_t owner = (uint32_t)(j / R), local = (uint32_t)(j - (int64_t)owner * R);
-        uint32_t x = (owner << grape::kOwnerShift) | local;
+        uint32_t x = (owner << grape::kOwnerShift) | local | eclass[e];
         if (ectr_ptr[e + 1] > ectr_ptr[e]) x |= grape::kCtrlBit;
         enc[e] = x;
       }

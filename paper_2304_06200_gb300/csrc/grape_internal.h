@@ -12,6 +12,8 @@ constexpr int kMaxCluster = 16;
 constexpr int kOwnerShift = 20;      // column encoding: bit 31 = entry carries control terms,
 constexpr uint32_t kLocalMask = (1u << kOwnerShift) - 1u;   // bits 20..27 owner CTA, bits 0..19 local row
 constexpr uint32_t kCtrlBit = 1u << 31;
+constexpr uint32_t kImagBBit = 1u << 30;   // off-diagonal entry whose B_ij is imaginary (every H_ij term real)
+constexpr uint32_t kRealBBit = 1u << 29;   // off-diagonal entry whose B_ij is real (every H_ij term imaginary)
 
 // Device error word values (same numbering as grape_status).
 constexpr int kErrTol = 4;
@@ -30,7 +32,9 @@ struct SweepParams {
   int m_cap;
   // union pattern (global)
   int diag_first;                      // 1: every diagonal H_ii is real and, where present, is the
-                                       // first entry of its row (B_ii = -i dt H_ii / s is imaginary)
+                                       // first entry of its row (B_ii = -i dt H_ii / s is imaginary).
+                                       // Rows continue with the kImagBBit entries, then the kRealBBit
+                                       // entries, then the rest; each segment in ascending columns.
   const int64_t* rowptr;               // dim + 1
   const uint32_t* colenc;              // nnz, per CL-partition encoding (owner, local, ctrl bit)
   const double2* h0v;                  // nnz drift values on the union pattern

@@ -226,6 +226,15 @@ __device__ __forceinline__ float2 horner(const double2 ch, double f, const float
 // B_ii x with B_ii = (0, b) imaginary (H_ii real): two multiplies.  As the first term of a row sum it
 // equals the complex multiply-add on a zero accumulator.
 __device__ __forceinline__ double2 diag_mul(double b, const double2 x) { return make_double2(-b * x.y, b * x.x); }
+// y += (0, b) x and y += (b, 0) x: an imaginary or a real B_ij in two fused multiply-adds
+__device__ __forceinline__ void mac_imag(double2& y, double b, const double2 x) {
+  y.x = fma(-b, x.y, y.x);
+  y.y = fma(b, x.x, y.y);
+}
+__device__ __forceinline__ void mac_real(double2& y, double b, const double2 x) {
+  y.x = fma(b, x.x, y.x);
+  y.y = fma(b, x.y, y.y);
+}
 
 template <typename T>
 struct Carve {
@@ -288,6 +297,15 @@ __device__ __forceinline__ void assemble(const SweepParams& p, cx<T>* vals, int6
 // Entry ea of local row i is the row's diagonal (stored first when every H_ii is real).
 __device__ __forceinline__ bool diag_at(const SweepParams& p, const uint32_t* lcol, int ea, int eb, int rank, int i) {
   return p.diag_first && ea < eb && (lcol[ea] & ~kCtrlBit) == (((uint32_t)rank << kOwnerShift) | (uint32_t)i);
+}
+
+// Segments of a row after its diagonal: [ea, *ci) imaginary B_ij, [*ci, *cr) real B_ij, the rest general.
+__device__ __forceinline__ void row_segments(const uint32_t* lcol, int ea, int eb, int* ci, int* cr) {
+  int e = ea;
+  while (e < eb && (lcol[e] & kImagBBit)) ++e;
+  *ci = e;
+  while (e < eb && (lcol[e] & kRealBBit)) ++e;
+  *cr = e;
 }
 
 __device__ __forceinline__ void load_controls(const SweepParams& p, int n, double* s_u) {
@@ -388,13 +406,14 @@ struct Team {
   int r0, nrows, R, rank, CL;
   int64_t e0;
   int nnz_loc;
-  // One row per thread (FP64 cluster teams): the thread's row is entries [ea, eb), its entries with a
-  // column in this CTA's rows are the run [la, la + nloc) (columns ascend, so do their owners), and
-  // l1 = the smallest nloc of the warp's rows: the first l1 of the run are summed before the wait
+  // One row per thread (FP64 cluster teams): the thread's general entries are [ea, eb), those with a
+  // column in this CTA's rows are the run [la, la + nloc) (their columns ascend, so do their owners),
+  // and l1 = the smallest nloc of the warp's rows: the first l1 of the run are summed before the wait
   // of the cluster barrier, the other entries in one loop after it.
-  // A diagonal stored first (entry ed, else -1) is not part of [ea, eb): it is applied separately.
+  // A diagonal stored first (entry ed, else -1) and the single-phase entries [c0, ci) (imaginary
+  // B_ij) and [ci, ea) (real B_ij) precede [ea, eb): they are applied with two multiplies.
   bool one_row;
-  int ea, eb, la, l1, ed;
+  int ea, eb, la, l1, ed, c0, ci;
 };
 
 // ------------------------------------------------------------------ forward sweep
@@ -432,15 +451,18 @@ __global__ void __launch_bounds__(512, 1) k_forward(SweepParams p) {
   for (int i = threadIdx.x; i < nrows; i += blockDim.x) c.psi[i] = p.psi0[col0 + i];
   double c2acc = 0.0;
   const bool split_rows = nrows <= (int)blockDim.x;   // one row per thread: split-barrier term loop
-  // The thread's row: entries [ea, eb), of which [la, lb) have their column in this CTA's rows
-  // (columns ascend within a row and owners ascend with the column, so they are contiguous).
-  // A diagonal stored first (ed) is applied separately, with two multiplies.
-  int ea = 0, eb = 0, la = 0, lb = 0, ed = -1;
+  // The thread's row: a diagonal stored first (ed), the single-phase entries [c0, ci) (imaginary B_ij)
+  // and [ci, ea) (real B_ij), applied with two multiplies each, then the general entries [ea, eb), of
+  // which [la, lb) have their column in this CTA's rows (the general entries' columns ascend, and so
+  // do their owners, so these are contiguous).
+  int ea = 0, eb = 0, la = 0, lb = 0, ed = -1, c0 = 0, ci = 0;
   __syncthreads();   // the local pattern written by sweep_setup
   if (split_rows && (int)threadIdx.x < nrows) {
     ea = c.lrow[threadIdx.x];
     eb = c.lrow[threadIdx.x + 1];
     if (diag_at(p, c.lcol, ea, eb, rank, threadIdx.x)) ed = ea++;
+    c0 = ea;
+    row_segments(c.lcol, c0, eb, &ci, &ea);
     la = ea;
     while (la < eb && ((c.lcol[la] >> kOwnerShift) & 0xFFu) < (uint32_t)rank) ++la;
     lb = la;
@@ -479,6 +501,14 @@ __global__ void __launch_bounds__(512, 1) k_forward(SweepParams p) {
             }
             cluster_wait();
             if (i < nrows) {
+              for (int e = c0; e < ci; ++e) {
+                const uint32_t enc = c.lcol[e];
+                mac_imag(y, c.vals[e].y, tab[src].ptr[(enc >> kOwnerShift) & 0xFFu][enc & kLocalMask]);
+              }
+              for (int e = ci; e < ea; ++e) {
+                const uint32_t enc = c.lcol[e];
+                mac_real(y, c.vals[e].x, tab[src].ptr[(enc >> kOwnerShift) & 0xFFu][enc & kLocalMask]);
+              }
               // one loop over the remote entries on both sides of the local run, so that a warp
               // pays for its longest remote list once
               const int nl = la - ea, nr = nl + (eb - lb);
@@ -672,6 +702,18 @@ __device__ __forceinline__ void phase_a(Team<T, CLUSTER>& tm, int m, WOut wout) 
         }
         cluster_wait();
         if (act) {
+          for (int e = tm.c0; e < tm.ci; ++e) {
+            const uint32_t enc = c.lcol[e];
+            const double b = c.vals[e].y;
+            mac_imag(ya, b, xload<T, CLUSTER>(xa, tm.tab[src], enc));
+            mac_imag(yw, b, xload<T, CLUSTER>(xw, tm.tab[2 + src], enc));
+          }
+          for (int e = tm.ci; e < tm.ea; ++e) {
+            const uint32_t enc = c.lcol[e];
+            const double b = c.vals[e].x;
+            mac_real(ya, b, xload<T, CLUSTER>(xa, tm.tab[src], enc));
+            mac_real(yw, b, xload<T, CLUSTER>(xw, tm.tab[2 + src], enc));
+          }
           for (int k = 0; k < nrest; ++k) {
             const int e = k < nleft ? tm.ea + k : tm.la + tm.l1 + (k - nleft);
             const uint32_t enc = c.lcol[e];
@@ -807,6 +849,24 @@ __device__ __forceinline__ void phase_b(Team<T, CLUSTER>& tm, int m, WIn win) {
         }
         cluster_wait();
         if (act) {
+          // single-phase entries: two multiplies for the chain (imaginary B_ij, then real B_ij)
+          auto single = [&](int e, bool imag) {
+            const uint32_t enc = c.lcol[e];
+            const C2 x = xload<T, CLUSTER>(xs, tm.tab[4 + src], enc);
+            if (more) {
+              if (imag)
+                mac_imag(y0, c.vals[e].y, x);
+              else
+                mac_real(y0, c.vals[e].x, x);
+            }
+            if (enc & kCtrlBit) {
+              double2 acc = c.W[e];
+              cmac_conjT(acc, wp, x);
+              c.W[e] = acc;
+            }
+          };
+          for (int e = tm.c0; e < tm.ci; ++e) single(e, true);
+          for (int e = tm.ci; e < tm.ea; ++e) single(e, false);
           for (int k = 0; k < nrest; ++k) {
             const int e = k < nleft ? tm.ea + k : tm.la + tm.l1 + (k - nleft);
             const uint32_t enc = c.lcol[e];
@@ -979,7 +1039,7 @@ __device__ __forceinline__ void team_init(Team<T, CLUSTER>& tm, unsigned char* s
   }
   sweep_setup(p, tm.c.lrow, tm.c.lcol, tm.r0, tm.nrows, tm.e0, tm.nnz_loc);
   tm.one_row = CLUSTER && sizeof(cx<T>) == 16 && tm.nrows <= (int)blockDim.x;
-  tm.ea = tm.eb = tm.la = tm.l1 = 0;
+  tm.ea = tm.eb = tm.la = tm.l1 = tm.c0 = tm.ci = 0;
   tm.ed = -1;
   __syncthreads();   // the local pattern
   if (tm.one_row) {
@@ -990,6 +1050,8 @@ __device__ __forceinline__ void team_init(Team<T, CLUSTER>& tm, unsigned char* s
       tm.ea = lrow[threadIdx.x];
       tm.eb = lrow[threadIdx.x + 1];
       if (diag_at(p, lcol, tm.ea, tm.eb, rank, threadIdx.x)) tm.ed = tm.ea++;
+      tm.c0 = tm.ea;
+      row_segments(lcol, tm.c0, tm.eb, &tm.ci, &tm.ea);
       int a = tm.ea;
       while (a < tm.eb && ((lcol[a] >> kOwnerShift) & 0xFFu) < (uint32_t)rank) ++a;
       int b = a;

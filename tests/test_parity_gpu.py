@@ -129,6 +129,59 @@ def test_checkpoint_spacing_does_not_change_the_result(ckpt):
     _check(p, u, cost, grad, ref=ref)
 
 
+def _single_phase_entries(p, seed, diag_imag=0.0):
+    """p with every off-diagonal pair of every operator made real (imaginary B_ij), imaginary (real
+    B_ij) or left complex, by a seeded choice per pair; each pair stays Hermitian.  With diag_imag > 0
+    the drift's diagonal gets an imaginary part that tiny (within the Hermitian check's tolerance),
+    which turns the diagonal into a general entry."""
+    import dataclasses
+
+    import scipy.sparse as sp
+    rng = np.random.default_rng(seed)
+    kind = {}
+
+    def fix(m, drift):
+        m = sp.csr_matrix(m).tocoo()
+        data = m.data.astype(np.complex128)
+        for t, (i, j) in enumerate(zip(m.row, m.col)):
+            if i == j:
+                if drift and diag_imag:
+                    data[t] = data[t].real + 1j * diag_imag
+                continue
+            key = (min(i, j), max(i, j))
+            if key not in kind:
+                kind[key] = int(rng.integers(0, 3))
+            if kind[key] == 0:
+                data[t] = data[t].real
+            elif kind[key] == 1:
+                data[t] = 1j * data[t].imag
+        return sp.csr_matrix((data, (m.row, m.col)), shape=m.shape)
+
+    q = dataclasses.replace(p, H0=fix(p.H0, True), Hk=[fix(h, False) for h in p.Hk])
+    return q, [sum(1 for v in kind.values() if v == c) for c in range(3)]
+
+
+@pytest.mark.parametrize("cluster,mode,diag_imag", [(4, 1, 0.0), (4, 2, 0.0), (8, 2, 0.0), (16, 1, 0.0),
+                                                    (4, 2, 1e-14)])
+def test_single_phase_entries_in_cluster_sweeps(cluster, mode, diag_imag):
+    """Real, imaginary and general H_ij in the same rows (and a diagonal that is not exactly real):
+    the one-row-per-thread cluster sweeps that apply the single-phase entries with two multiplies
+    agree with the oracle and, where the diagonal is real, with a generic-loop run (one CTA)."""
+    p, counts = _single_phase_entries(random_problem(600, 3, 2, 6, seed=4242, band=4, density=0.004),
+                                      seed=7, diag_imag=diag_imag)
+    assert min(counts) > 100
+    u = p.u0 * 3
+    hg = _hg(p, cluster=cluster, backward_mode=mode)
+    inf = hg.info()
+    assert inf["cluster"] == cluster and inf["backward_mode"] == mode
+    cost, grad = hg.cost_and_grad(u)
+    _check(p, u, cost, grad)
+    if not diag_imag:
+        c1, g1 = _hg(p, cluster=1, backward_mode=1).cost_and_grad(u)
+        assert abs(cost - c1) <= 1e-13 * abs(c1)
+        assert np.linalg.norm(grad - g1) <= 1e-11 * np.linalg.norm(g1)
+
+
 @pytest.mark.parametrize("cluster", [1, 2, 4, 8, 16])
 def test_team_sizes_agree(cluster):
     """Same problem split over 1..16 CTAs per column: identical cost and gradient within rounding."""
