@@ -60,6 +60,10 @@ def parse_args(argv=None):
                     help="skip the main measurement and print only the requested comparisons (for profiling them)")
     ap.add_argument("--eig", action="store_true",
                     help="also compare the eigendecomposition propagator (App. F) with the Taylor kernels")
+    ap.add_argument("--families", action="store_true",
+                    help="also time the three-transmon, qubit-chain and fluxonium-pair Hamiltonians (FP64, FP32 bulk)")
+    ap.add_argument("--optimize", action="store_true",
+                    help="also time steepest descent in a CUDA graph against a host-driven loop (c2_gate_d80)")
     ap.add_argument("--backward-mode", type=int, default=0, help="0 auto, 1 one team per column, 2 two teams")
     return ap.parse_args(argv)
 
@@ -282,6 +286,10 @@ def run_ours(args):
             extra["c4"] = c4_compare(local)
         if args.m_sweep:
             extra["checkpoint_sweep"] = checkpoint_sweep(args.workload, local, args.n_steps)
+        if args.families:
+            extra["families"] = families_compare(local)
+        if args.optimize:
+            extra["steepest_descent"] = optimize_compare(local)
         print(json.dumps({"extras": extra}), flush=True)
         return
     p = build_config(args.workload, seed=None if rank == 0 else 1000 + rank, n_steps=args.n_steps)
@@ -434,6 +442,10 @@ def run_ours(args):
         extra["dense_d2048_tc"] = dense_compare(local, args.dense_steps)
     if args.eig:
         extra["eig_vs_taylor"] = eig_compare(local)
+    if args.families:
+        extra["families"] = families_compare(local)
+    if args.optimize:
+        extra["steepest_descent"] = optimize_compare(local)
 
     out = {
         "metric": METRIC, "value": round(value, 6), "unit": "evals/s", "n_gpus": world, "steps": args.steps,
@@ -547,6 +559,92 @@ def checkpoint_sweep(name, local, n_steps=None):
                     "grad_norm": float(torch.linalg.norm(grad).item())})
         hg.close()
         del u, cost, grad
+    return out
+
+
+def families_compare(local, n_steps=500):
+    """The other Hamiltonian families at a few hundred to a thousand levels: three transmons (Hadamard
+    gate, 8 levels each, d = 512), a 10-qubit chain (d = 1024) and a fluxonium pair (24 oscillator
+    levels each, d = 576); N = 500 steps, controls at 3x their seeded amplitude, FP64 and FP32 bulk."""
+    import numpy as np
+    import torch
+    from paper_2304_06200_gb300 import GrapeProblem
+    from workloads import fluxonium_problem, hadamard3_problem, qubit_chain_problem
+
+    dev = torch.device("cuda", local)
+    out = {}
+    for name, build, size, dt in (("h2_three_transmons", hadamard3_problem, 8, 0.5),
+                                  ("h3_qubit_chain", qubit_chain_problem, 10, 0.2),
+                                  ("h4_fluxonium_pair", fluxonium_problem, 24, 0.05)):
+        p = build(size, n_steps, dt, seed=70 + size)
+        res = {"dim": int(p.dim), "controls": len(p.Hk), "states": int(p.psi0.shape[1]), "N": n_steps, "dt_ns": dt}
+        ref = None
+        for prec in ("fp64", "fp32_bulk"):
+            hg = GrapeProblem(p, device=local, precision=prec)
+            u = torch.tensor(p.u0 * 3.0, dtype=torch.float64, device=dev)
+            cost = torch.zeros((), dtype=torch.float64, device=dev)
+            grad = torch.zeros_like(u)
+            ms = _timed_eval(hg, u, cost, grad, reps=3)
+            inf = hg.info()
+            r = {"evals_per_s": round(1e3 / ms, 3), "ms_per_eval": round(ms, 2), "cluster_fwd": inf["cluster_forward"],
+                 "cluster_bwd": inf["cluster"], "backward_teams_per_column": inf["backward_mode"],
+                 "taylor_terms_per_sweep": inf["total_terms"], "union_nnz": inf["union_nnz"]}
+            g = grad.cpu().numpy()
+            if ref is None:
+                ref = (float(cost.item()), g)
+                r["cost"] = ref[0]
+            else:
+                r["cost_rel_diff_vs_fp64"] = abs(float(cost.item()) - ref[0]) / abs(ref[0])
+                r["grad_rel_diff_vs_fp64"] = float(np.linalg.norm(g - ref[1]) / np.linalg.norm(ref[1]))
+            res[prec] = r
+            hg.close()
+        out[name] = res
+    return out
+
+
+def optimize_compare(local, n_iter=20):
+    """Steepest descent u <- u - eta grad (Eq. (4)) on c1_state_transfer_d30 and c2_gate_d80:
+    grape_optimize, one recorded CUDA graph per iteration with u resident on the device, against a
+    host loop of grape_cost_and_grad plus a NumPy update, at the same step size: the largest
+    eta = 2^-k * 0.1 |u| / |grad| (k = 0..12) whose first two iterations lower the cost.  Wall time of
+    the whole call on the host for both (both return host results)."""
+    import numpy as np
+    import torch
+    from paper_2304_06200_gb300 import GrapeProblem
+    from workloads import build_config
+
+    out = {}
+    for name in ("c1_state_transfer_d30", "c2_gate_d80"):
+        p = build_config(name)
+        hg = GrapeProblem(p, device=local)
+        _, g0 = hg.cost_and_grad(p.u0)
+        eta = 0.1 * float(np.linalg.norm(p.u0) / np.linalg.norm(g0))
+        for _ in range(13):
+            _, c2 = hg.optimize(p.u0, 3, eta)      # also records the iteration graph for this eta
+            if c2[2] < c2[1] < c2[0]:
+                break
+            eta *= 0.5
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        u_g, costs_g = hg.optimize(p.u0, n_iter, eta)
+        t1 = time.perf_counter()
+        u = np.array(p.u0, dtype=np.float64)
+        costs_h = []
+        t2 = time.perf_counter()
+        for _ in range(n_iter):
+            c, g = hg.cost_and_grad(u)
+            costs_h.append(c)
+            u = u - eta * g
+        t3 = time.perf_counter()
+        hg.close()
+        costs_h = np.array(costs_h)
+        out[name] = {"workload": workload_description(p), "iterations": n_iter, "eta": eta,
+                     "graph_ms_per_iter": round((t1 - t0) * 1e3 / n_iter, 3),
+                     "host_loop_ms_per_iter": round((t3 - t2) * 1e3 / n_iter, 3),
+                     "cost_first": float(costs_g[0]), "cost_last": float(costs_g[-1]),
+                     "monotone": bool(np.all(np.diff(costs_g) < 0)),
+                     "max_cost_rel_diff_graph_vs_host": float(np.max(np.abs(costs_g - costs_h) / np.abs(costs_h))),
+                     "u_rel_diff_graph_vs_host": float(np.linalg.norm(u_g - u) / np.linalg.norm(u))}
     return out
 
 
