@@ -93,6 +93,18 @@ __device__ __forceinline__ void cluster_wait() {
   asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
+// The split barrier of the one-row-per-thread term loops.  A team of one CTA needs neither half: the
+// __syncthreads that ends every term already orders each buffer's writes before the next term's
+// reads (and its reads before the writes two terms later).
+template <bool CLUSTER>
+__device__ __forceinline__ void split_arrive() {
+  if constexpr (CLUSTER) cluster_arrive();
+}
+template <bool CLUSTER>
+__device__ __forceinline__ void split_wait() {
+  if constexpr (CLUSTER) cluster_wait();
+}
+
 // ------------------------------------------------------------------ block reductions (deterministic)
 
 __device__ double block_sum(double v, double* red) {
@@ -481,7 +493,7 @@ __global__ void __launch_bounds__(512, 1) k_forward(SweepParams p) {
         X0[i] = from_d2<T>(c.psi[i]);
         c.inc[i] = make_double2(0.0, 0.0);
       }
-      if constexpr (CLUSTER && sizeof(C2) == 16) {
+      if constexpr (sizeof(C2) == 16) {
         if (split_rows) {
           // Each term: the entries whose column lies in this CTA's rows are summed between the
           // arrive and the wait of the previous term's cluster barrier; the remote ones after it.
@@ -489,7 +501,7 @@ __global__ void __launch_bounds__(512, 1) k_forward(SweepParams p) {
           // arrived at barrier q-1, so writing it after wait(q-1) is safe; the last term of the
           // substep closes with a full barrier before X_0 of the next substep is written.
           __syncthreads();
-          cluster_arrive();
+          split_arrive<CLUSTER>();
           const int i = threadIdx.x;
           for (int q = 1; q <= m; ++q) {
             const int src = (q - 1) & 1, dst = q & 1;
@@ -499,15 +511,15 @@ __global__ void __launch_bounds__(512, 1) k_forward(SweepParams p) {
               if (ed >= 0) y = diag_mul(c.vals[ed].y, xs[i]);
               for (int e = la; e < lb; ++e) cmacT(y, c.vals[e], xs[c.lcol[e] & kLocalMask]);
             }
-            cluster_wait();
+            split_wait<CLUSTER>();
             if (i < nrows) {
               for (int e = c0; e < ci; ++e) {
                 const uint32_t enc = c.lcol[e];
-                mac_imag(y, c.vals[e].y, tab[src].ptr[(enc >> kOwnerShift) & 0xFFu][enc & kLocalMask]);
+                mac_imag(y, c.vals[e].y, xload<T, CLUSTER>(xs, tab[src], enc));
               }
               for (int e = ci; e < ea; ++e) {
                 const uint32_t enc = c.lcol[e];
-                mac_real(y, c.vals[e].x, tab[src].ptr[(enc >> kOwnerShift) & 0xFFu][enc & kLocalMask]);
+                mac_real(y, c.vals[e].x, xload<T, CLUSTER>(xs, tab[src], enc));
               }
               // one loop over the remote entries on both sides of the local run, so that a warp
               // pays for its longest remote list once
@@ -515,7 +527,7 @@ __global__ void __launch_bounds__(512, 1) k_forward(SweepParams p) {
               for (int k = 0; k < nr; ++k) {
                 const int e = k < nl ? ea + k : lb + (k - nl);
                 const uint32_t enc = c.lcol[e];
-                cmacT(y, c.vals[e], tab[src].ptr[(enc >> kOwnerShift) & 0xFFu][enc & kLocalMask]);
+                cmacT(y, c.vals[e], xload<T, CLUSTER>(xs, tab[src], enc));
               }
               X0[dst * R + i] = y;   // B^q c (unscaled)
               double2 a = c.inc[i];
@@ -526,7 +538,7 @@ __global__ void __launch_bounds__(512, 1) k_forward(SweepParams p) {
             }
             if (q < m) {
               __syncthreads();
-              cluster_arrive();
+              split_arrive<CLUSTER>();
             } else {
               team_sync<CLUSTER>();
             }
@@ -667,7 +679,7 @@ __device__ __forceinline__ void phase_a(Team<T, CLUSTER>& tm, int m, WOut wout) 
     tm.X(2)[i] = w0;
     wout(m - 1, i, w0);
   }
-  if constexpr (CLUSTER && sizeof(C2) == 16) {
+  if constexpr (sizeof(C2) == 16) {
     if (tm.one_row) {
       // Split cluster barrier.  Term q: the first l1 local entries of the row (reading this CTA's
       // rows of X_{q-1}) before wait(q-1), the other entries after it; X_q is written, the barrier
@@ -676,7 +688,7 @@ __device__ __forceinline__ void phase_a(Team<T, CLUSTER>& tm, int m, WOut wout) 
       // X_{q-2} before they arrived at barrier q-1.  The loop trip counts are those of a single
       // row loop (l1 is uniform in the warp), so no FP64 instruction is added.
       __syncthreads();
-      cluster_arrive();
+      split_arrive<CLUSTER>();
       const int i = threadIdx.x;
       const bool act = i < tm.nrows;
       const int nleft = tm.la - tm.ea, nrest = (tm.eb - tm.ea) - tm.l1;
@@ -700,7 +712,7 @@ __device__ __forceinline__ void phase_a(Team<T, CLUSTER>& tm, int m, WOut wout) 
             cmacT(yw, v, xw[loc]);
           }
         }
-        cluster_wait();
+        split_wait<CLUSTER>();
         if (act) {
           for (int e = tm.c0; e < tm.ci; ++e) {
             const uint32_t enc = c.lcol[e];
@@ -729,7 +741,7 @@ __device__ __forceinline__ void phase_a(Team<T, CLUSTER>& tm, int m, WOut wout) 
           }
         }
         __syncthreads();
-        cluster_arrive();
+        split_arrive<CLUSTER>();
         if (act) {
           double2 a = c.inc[i];
           const double sq = c_sgn_fact[q];   // (-B)^q / q! = (-1)^q / q! B^q
@@ -743,7 +755,7 @@ __device__ __forceinline__ void phase_a(Team<T, CLUSTER>& tm, int m, WOut wout) 
             c.chi[i] = make_double2(fma(ch.x, fq, -yw.x), fma(ch.y, fq, -yw.y));
         }
       }
-      cluster_wait();
+      split_wait<CLUSTER>();
       for (int j = threadIdx.x; j < tm.nrows; j += blockDim.x) {
         double2 v = c.psi[j];
         const double2 a = c.inc[j];
@@ -807,12 +819,12 @@ __device__ __forceinline__ void phase_b(Team<T, CLUSTER>& tm, int m, WIn win) {
   const Carve<T>& c = tm.c;
   // With one row per thread, w_{p+1} is fetched while term p runs (it may come from L2).
   const bool one_row = tm.nrows <= (int)blockDim.x;
-  if constexpr (CLUSTER && sizeof(C2) == 16) {
+  if constexpr (sizeof(C2) == 16) {
     if (tm.one_row) {
       // Split cluster barrier as in phase A: the first l1 local entries before the wait, the rest
       // after it.  The last term writes nothing that others read, so it ends after its wait.
       __syncthreads();
-      cluster_arrive();
+      split_arrive<CLUSTER>();
       const int i = threadIdx.x;
       const bool act = i < tm.nrows;
       const int nleft = tm.la - tm.ea, nrest = (tm.eb - tm.ea) - tm.l1;
@@ -847,7 +859,7 @@ __device__ __forceinline__ void phase_b(Team<T, CLUSTER>& tm, int m, WIn win) {
             entry(e, xs[enc & kLocalMask], enc);
           }
         }
-        cluster_wait();
+        split_wait<CLUSTER>();
         if (act) {
           // single-phase entries: two multiplies for the chain (imaginary B_ij, then real B_ij)
           auto single = [&](int e, bool imag) {
@@ -876,7 +888,7 @@ __device__ __forceinline__ void phase_b(Team<T, CLUSTER>& tm, int m, WIn win) {
         }
         if (more) {
           __syncthreads();
-          cluster_arrive();
+          split_arrive<CLUSTER>();
         }
       }
       return;
@@ -1038,7 +1050,7 @@ __device__ __forceinline__ void team_init(Team<T, CLUSTER>& tm, unsigned char* s
       for (int b = 0; b < 6; ++b) tab[b].ptr[threadIdx.x] = cl.map_shared_rank(tm.X(b), threadIdx.x);
   }
   sweep_setup(p, tm.c.lrow, tm.c.lcol, tm.r0, tm.nrows, tm.e0, tm.nnz_loc);
-  tm.one_row = CLUSTER && sizeof(cx<T>) == 16 && tm.nrows <= (int)blockDim.x;
+  tm.one_row = sizeof(cx<T>) == 16 && tm.nrows <= (int)blockDim.x;
   tm.ea = tm.eb = tm.la = tm.l1 = tm.c0 = tm.ci = 0;
   tm.ed = -1;
   __syncthreads();   // the local pattern
