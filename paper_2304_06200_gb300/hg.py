@@ -273,6 +273,26 @@ class GrapeBatch:
             pass
 
 
+def checkpoint_bytes(ckpt_every: int, n_steps: int, dim: int, n_states: int) -> int:
+    """Device bytes of the stored checkpoints for spacing M = ckpt_every (0: the default
+    min(50, N); negative: none): floor((N - 1) / M) states of dim x n_states complex128."""
+    m_eff = ckpt_every if ckpt_every != 0 else min(50, n_steps)
+    if m_eff < 0:
+        return 0
+    return ((n_steps - 1) // max(m_eff, 1)) * dim * n_states * 16
+
+
+def select_candidate(timed, tie: float = 0.02) -> dict:
+    """The autotuner's choice among timed candidates (dicts with "ms" and
+    "checkpoint_bytes_full_N"): the fastest, unless others lie within ``tie`` (relative) of it, in
+    which case the one storing the fewest checkpoint bytes (then the faster of equals)."""
+    if not timed:
+        raise RuntimeError("autotune: no candidate configuration was accepted")
+    fastest = min(r["ms"] for r in timed)
+    near = [r for r in timed if r["ms"] <= fastest * (1.0 + tie)]
+    return min(near, key=lambda r: (r["checkpoint_bytes_full_N"], r["ms"]))
+
+
 def autotune(problem, precision: str = "fp64", device: int = 0, probe_steps: int = 48, backward_mode: int = 1,
              clusters=None, m_caps=(0, 30, 20), ckpt_choices=(0,), repeats: int = 2, tie: float = 0.02):
     """Pick the team size (CTAs per column), Taylor-order cap and checkpoint spacing M.
@@ -318,18 +338,13 @@ def autotune(problem, precision: str = "fp64", device: int = 0, probe_steps: int
                 hg.sync_status()
                 ms = e0.elapsed_time(e1) / repeats
                 inf = hg.info()
-                Meff = M if M != 0 else min(50, N)
-                ckpt_bytes = 0 if Meff < 0 else ((N - 1) // max(Meff, 1)) * problem.dim * problem.n_states * 16
+                ckpt_bytes = checkpoint_bytes(M, N, problem.dim, problem.n_states)
                 rec = {"cluster": cl, "m_max": mc, "ckpt_every": M, "ms": ms, "cluster_used": inf["cluster"],
                        "terms": inf["total_terms"], "checkpoint_bytes_full_N": int(ckpt_bytes)}
                 report.append(rec)
                 timed.append(rec)
                 hg.close()
-    if not timed:
-        raise RuntimeError("autotune: no candidate configuration was accepted")
-    fastest = min(r["ms"] for r in timed)
-    near = [r for r in timed if r["ms"] <= fastest * (1.0 + tie)]
-    best = min(near, key=lambda r: (r["checkpoint_bytes_full_N"], r["ms"]))
+    best = select_candidate(timed, tie)
     cl, mc, M = best["cluster"], best["m_max"], best["ckpt_every"]
     full = GrapeProblem(problem, precision=precision, cluster=cl, device=device, m_max=mc, backward_mode=backward_mode,
                         ckpt_every=M)
