@@ -8,15 +8,25 @@
 // thread owns one row at a time.  Every Taylor term y = B x needs entries of x
 // owned by other CTAs of the team: those are read from the owners' shared
 // memory (distributed shared memory), and terms are separated by one team
-// barrier (__syncthreads for CL = 1, barrier.cluster otherwise).  Nothing is
-// exchanged through global memory inside a sweep.
+// barrier (__syncthreads for CL = 1, barrier.cluster otherwise; with one row per
+// thread its arrive and wait are split around the CTA-local entries).  Within a
+// team nothing goes through global memory; the two teams of k_backward_split
+// hand over through a ring of slots in global memory.
+//
+// Row layout.  Each row of the union pattern holds its diagonal first (when every
+// H_ii is real), then the entries whose B_ij is imaginary, then those whose B_ij
+// is real, then the general ones; the one-row-per-thread loops apply the first
+// three kinds with two multiplies instead of a complex multiply-add.
 //
 // Kernels
-//   k_schedule      ||A_n||_1 = dt max_i sum_j |H_n,ij| and the (m_n, s_n) lookup (Sec. III.B, App. C)
-//   k_forward       psi_n = (e^{B_n}_m)^s psi_{n-1}, C2 sum, checkpoints, psi_N, <phi_T|psi_N> partials
-//   k_finalize      g, C1, C2, C_amp, cost
-//   k_backward      adjoint re-propagation of psi and the costate, gradient terms per step
-//   k_grad_reduce   sum of per-CTA gradient partials + amplitude-penalty gradient
+//   k_schedule        ||A_n||_1 = dt max_i sum_j |H_n,ij| and the (m_n, s_n) lookup (Sec. III.B, App. C)
+//   k_forward         psi_n = (e^{B_n}_m)^s psi_{n-1}, C2 sum, C3 overlaps, checkpoints, psi_N, <phi_T|psi_N> partials
+//   k_finalize        g, C1, C2, C3, C_amp, cost
+//   k_backward        adjoint re-propagation of psi and the costate, gradient terms per step (one team per column)
+//   k_backward_split  the same with two concurrent teams per column (phase A / phase B of every substep)
+//   k_grad_reduce     sum of per-CTA gradient partials + amplitude-penalty gradient
+//   k_sd_update       steepest-descent step u - (eta g) and the iterate's cost (Sec. II, Eq. (4))
+//   k_check_finite    non-finite controls set the device error word
 #include "grape_internal.h"
 
 #include <cooperative_groups.h>
