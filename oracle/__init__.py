@@ -12,6 +12,10 @@ Contents
                    (App. C), plus a plain truncated-Taylor action for pins.
 ``fullad_torch``   a second reference: CPU complex128 torch full automatic
                    differentiation through ``torch.linalg.matrix_exp`` per step.
+``sparse_reference`` the same exact-exponential cost and gradient for large sparse
+                   problems: exponential actions by ``scipy.sparse.linalg.expm_multiply``
+                   and the auxiliary block-matrix derivative (Sec. III.B), pinned to
+                   ``grape_oracle`` on small problems.
 
 Every function cites the passage of arXiv:2304.06200 it follows.
 """

@@ -118,3 +118,76 @@ def test_bound_infeasible_at_tiny_tau():
 
 def test_unit_roundoff_is_fp64():
     assert U64 == 2.0 ** -53
+
+
+@pytest.mark.parametrize("tau,expected", [(1e-8, (41, 3)), (1e-10, (32, 5)), (1e-12, (19, 22))])
+def test_rule_reproduces_independent_probe_at_norm_30(tau, expected):
+    """(m, s) at ||A||_1 = 30, sigma' = 9, m <= 60 (Sec. III.B rule on Eq. (overallupperbound)).
+
+    The expected pairs were computed once, independently of this module, by a separate evaluation of
+    the bound when the workloads were sized (the C3 transmon-cavity norm is about 30)."""
+    assert select_ms(30.0, tau, 9) == expected
+
+
+def _beta_decimal(b: float, indices):
+    """sum_k gamma_{indices[k]} b^k / k! in 60-digit decimal arithmetic, gamma_n = n u'/(1 - n u'),
+    u' = 2 sqrt(2) u / (1 - 2u), u = 2^-53 (App. C.2)."""
+    getcontext().prec = 60
+    u = Decimal(1) / Decimal(2 ** 53)
+    up = 2 * Decimal(2).sqrt() * u / (1 - 2 * u)
+    B = Decimal(repr(b))
+    total = Decimal(0)
+    for k, n in enumerate(indices):
+        g = n * up / (1 - n * up)
+        total += g * B ** k / math.factorial(k)
+    return total
+
+
+# The gamma indices of Eq. (B23), k (sigma' + 2) + m + 2 for k = 0..m, listed by hand for small cases.
+@pytest.mark.parametrize("b,m,sigma,indices", [
+    (0.7, 1, 1, [3, 6]),
+    (1.3, 2, 3, [4, 9, 14]),
+    (2.5, 3, 9, [5, 16, 27, 38]),
+    (0.2, 4, 5, [6, 13, 20, 27, 34]),
+])
+def test_beta_matches_hand_listed_gamma_indices(b, m, sigma, indices):
+    """With s = 1 the rounding bound of Eq. (rouding) is beta itself; beta must equal the hand-listed sum.
+
+    A plausible slip in the index (sigma' + 1 instead of sigma' + 2, or m + 1 instead of m + 2)
+    moves beta by far more than the tolerance, which the second assertion checks."""
+    beta = float(_beta_decimal(b, indices))
+    assert rounding_bound(b, m, 1, sigma) == pytest.approx(beta, rel=1e-13)
+    slipped = float(_beta_decimal(b, [n - k for k, n in enumerate(indices)]))
+    assert abs(slipped - beta) > 1e-4 * beta
+    shifted = float(_beta_decimal(b, [n - 1 for n in indices]))
+    assert abs(shifted - beta) > 1e-4 * beta
+
+
+@pytest.mark.parametrize("x,seed", [(0.5, 11), (2.0, 12), (6.0, 13)])
+def test_error_bound_holds_for_single_precision_arithmetic(x, seed):
+    """E_A with u = 2^-24 bounds the error of the action actually evaluated in complex64 (App. C)."""
+    from oracle.taylor_bound import U32
+
+    d = 10
+    H = _rand_herm(d, seed)
+    A = -1j * (x / one_norm(H)) * H
+    sigma = d
+    rng = np.random.default_rng(seed)
+    psi = rng.standard_normal(d) + 1j * rng.standard_normal(d)
+    psi /= np.linalg.norm(psi)
+    exact = sla.expm(A) @ psi
+    for m, s in [(12, 1), (8, 2), (10, 4)]:
+        EA = error_bound(one_norm(A), m, s, sigma, U32)
+        if math.isinf(EA):
+            continue
+        Bf = (A / s).astype(np.complex64)
+        c = psi.astype(np.complex64)
+        for _ in range(s):
+            term = c
+            acc = c.copy()
+            for j in range(1, m + 1):
+                term = (Bf @ term) / np.float32(j)
+                acc = acc + term
+            c = acc
+        err = np.linalg.norm(exact - c.astype(np.complex128))
+        assert err <= EA, (m, s, err, EA)
