@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define GRAPE_ABI_VERSION 3
+#define GRAPE_ABI_VERSION 4
 
 typedef struct grape_problem grape_problem;
 
@@ -130,7 +130,12 @@ typedef struct {
   void* alloc_ctx;
   int32_t backward_mode;       /* 0 = automatic, 1 = one team per column runs both backward
                                   phases, 2 = two concurrent teams per column (phase A / phase B),
-                                  needs all 2 * n_states teams co-resident                    */
+                                  needs all 2 * n_states teams co-resident, 3 = three-stage: the
+                                  forward stores every state, one team per column runs only the
+                                  costate chain and stores its Horner vectors, the gradient terms
+                                  of every step are computed independently on the remaining SMs
+                                  (needs ckpt_every 0 or 1; memory N * dim * n_states * 16 bytes
+                                  for the states plus two blocks of Horner vectors)            */
   double bulk_norm_cap;        /* > 0: the (m, s) rule only considers s >= ||A||_1 / cap, i.e.
                                   ||B||_1 <= cap, which bounds the largest Taylor term (reduces
                                   FP32-bulk rounding); 0 = default (2.0 for GRAPE_FP32_BULK, no
@@ -142,6 +147,11 @@ typedef struct {
   int64_t wait_limit;          /* polls (about 0.1 us apart) before a device wait of the two-team
                                   backward sweep gives up and the call returns GRAPE_ETIMEOUT;
                                   0 = default (2^24, about two seconds)                        */
+  int32_t grad_cluster;        /* three-stage backward: CTAs per (step, column) team of the gradient
+                                  kernel, 0 = automatic (the smallest team whose working set fits
+                                  shared memory), else 1..16                                   */
+  int32_t block_steps;         /* three-stage backward: steps per block (the unit handed from the
+                                  costate chain to the gradient kernel), 0 = automatic          */
 } grape_desc;
 
 /* Information about a problem (valid after create; schedule fields after an evaluation). */
@@ -157,9 +167,15 @@ typedef struct {
   int32_t smem_bytes;          /* dynamic shared memory per CTA of the sweep kernels       */
   int64_t total_terms;         /* sum over steps of m_n * s_n for the last evaluation (-1 before) */
   double max_norm;             /* max_n ||A_n||_1 of the last evaluation (-1 before)       */
-  int32_t backward_mode;       /* 1 = one team per column, 2 = two concurrent teams per column */
+  int32_t backward_mode;       /* 1 = one team per column, 2 = two concurrent teams per column,
+                                  3 = three-stage (costate chain + per-step gradient kernels)  */
   int32_t cluster_forward;     /* CTAs per column team of the forward sweep                */
   int32_t propagator;          /* grape_propagator of the problem                          */
+  int32_t grad_cluster;        /* three-stage backward: CTAs per gradient team (0 = not used)  */
+  int32_t block_steps;         /* three-stage backward: steps per block (0 = not used)         */
+  int32_t fused_fallback;      /* three-stage backward: 1 if the last evaluation's Horner vectors
+                                  did not fit the block buffers and the one-team fused backward
+                                  ran instead, 0 if the three stages ran, -1 otherwise          */
 } grape_info;
 
 /* Create a problem (Sec. II: H(t) = H_s + sum_k a_k(t) h_k, piecewise constant over N steps
@@ -250,17 +266,20 @@ void grape_batch_destroy(grape_batch* batch);
 grape_status grape_batch_cost_and_grad(grape_batch* batch, const double* const* u, double* costs,
                                        double* const* grads, int32_t on_device, void* stream);
 
-/* Allocation-free propagation of one step (the paper has no counterpart: this entry point
- * exists for callers that cannot allocate device memory).  Such callers include code that runs
+/* Allocation-free propagation of one step.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory.  Such callers include code that runs
  * while a stream is being captured into a CUDA graph (cudaMalloc is not allowed there), real-time
  * loops that cannot afford cudaMalloc/cudaFree (both can synchronise the whole device), and host
  * programs that hand out all device memory from their own fixed pool.  The call computes
- *     psi_out = (e^{B}_m)^s psi_in,   B = -i dt H / s
- * (the scaled truncated-Taylor action of Sec. III.B) for a dim x n_states block, column-major,
- * and uses no memory besides the caller's buffers and a 16 MiB array built into the library:
+ *     psi_out = (e^{B}_m)^s psi_in,   B = -i dt H / s,   e^{B}_m = sum_{q=0..m} B^q / q!
+ * for a dim x n_states block, column-major, and uses no memory besides the caller's buffers and a
+ * 16 MiB array built into the library:
  *   - rowptr[dim+1] (int64), colind[nnz] (int32), values[2*nnz] (complex): H in CSR, DEVICE
- *     pointers; column indices outside [0, dim) are ignored.  m in 1..60 and s >= 1 are taken as
- *     given (grape_select_ms gives the paper's choice).
+ *     pointers.  Expected: rowptr[0] = 0, non-decreasing, rowptr[dim] = nnz.  The kernel clamps
+ *     every row's entry range to [0, nnz) and skips column indices outside [0, dim), so malformed
+ *     arrays give wrong numbers, never reads outside the arrays.
+ *   - m in 1..60 and 1 <= s <= 4096 are taken as given (grape_select_ms gives the error-bound
+ *     choice); s bounds the call's work, s * m sparse products per column.
  *   - psi_in, psi_out: dim x n_states complex DEVICE arrays (may be the same array).
  *   - Limit: 3 * dim * n_states <= 349525 (16 MiB / 48 bytes); larger requests return GRAPE_EINVAL
  *     before anything is launched.
@@ -272,9 +291,9 @@ grape_status grape_batch_cost_and_grad(grape_batch* batch, const double* const* 
  *     streams, or different host threads) race and corrupt each other's results.  Serialise them.
  *     Nothing in the array needs to start at zero; it keeps the last call's contents.
  *   - Asynchronous on `stream` (NULL = legacy default stream); launch errors are returned. */
-grape_status grape_taylor_step_noalloc(int64_t dim, int32_t n_states, const int64_t* rowptr, const int32_t* colind,
-                                       const double* values, double dt, int32_t m, int32_t s, const double* psi_in,
-                                       double* psi_out, void* stream);
+grape_status grape_taylor_step_noalloc(int64_t dim, int64_t nnz, int32_t n_states, const int64_t* rowptr,
+                                       const int32_t* colind, const double* values, double dt, int32_t m, int32_t s,
+                                       const double* psi_in, double* psi_out, void* stream);
 
 const char* grape_status_string(grape_status st);
 const char* grape_last_error(void);

@@ -42,7 +42,8 @@ class GrapeDesc(C.Structure):
                 ("tau", C.c_double), ("m_max", C.c_int32), ("ckpt_every", C.c_int32), ("precision", C.c_int32),
                 ("cluster", C.c_int32), ("device", C.c_int32),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p), ("backward_mode", C.c_int32),
-                ("bulk_norm_cap", C.c_double), ("w_tint", C.c_double), ("propagator", C.c_int32), ("wait_limit", C.c_int64)]
+                ("bulk_norm_cap", C.c_double), ("w_tint", C.c_double), ("propagator", C.c_int32), ("wait_limit", C.c_int64),
+                ("grad_cluster", C.c_int32), ("block_steps", C.c_int32)]
 
 
 class GrapeInfo(C.Structure):
@@ -50,7 +51,8 @@ class GrapeInfo(C.Structure):
                 ("sigma", C.c_int32), ("m_cap", C.c_int32), ("s_cap", C.c_int32), ("cluster", C.c_int32),
                 ("ckpt_every", C.c_int32), ("smem_bytes", C.c_int32), ("total_terms", C.c_int64),
                 ("max_norm", C.c_double), ("backward_mode", C.c_int32), ("cluster_forward", C.c_int32),
-                ("propagator", C.c_int32)]
+                ("propagator", C.c_int32), ("grad_cluster", C.c_int32), ("block_steps", C.c_int32),
+                ("fused_fallback", C.c_int32)]
 
 
 _LIB = None
@@ -88,7 +90,7 @@ def lib(path: str | None = None):
     L.grape_select_ms.restype = C.c_int
     L.grape_error_bound.argtypes = [C.c_double, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
     L.grape_error_bound.restype = C.c_double
-    L.grape_taylor_step_noalloc.argtypes = [C.c_int64, C.c_int32, P, P, P, C.c_double, C.c_int32, C.c_int32, P, P, P]
+    L.grape_taylor_step_noalloc.argtypes = [C.c_int64, C.c_int64, C.c_int32, P, P, P, C.c_double, C.c_int32, C.c_int32, P, P, P]
     L.grape_taylor_step_noalloc.restype = C.c_int
     L.grape_batch_create.argtypes = [C.POINTER(P), C.c_int32, C.c_int32, C.POINTER(P)]
     L.grape_batch_create.restype = C.c_int

@@ -10,7 +10,7 @@
 //
 // Kernels:
 //   k_eig_tridiag   one CTA per step: H_n and its Householder reduction to tridiagonal form
-//   k_eig_ql        one thread per step: implicit QL on the real tridiagonal, rotations recorded
+//   k_eig_qr        one thread per step: symmetric QR steps (Wilkinson shift) on the real tridiagonal, rotations recorded
 //   k_eig_rotate    one thread per row of a step: the recorded rotations applied to the identity
 //   k_eig_vectors   one CTA per step: back-transformation to the eigenvectors, U_n = V diag(e) V^+
 //   k_eig_forward   one CTA per column: psi_n = U_n psi_{n-1} (Eq. (statepropagation)), overlaps
@@ -30,7 +30,7 @@ namespace {
 
 constexpr int kT = 256;
 constexpr int kWarps = kT / 32;
-constexpr int kQlLanes = 8;   // steps per warp in k_eig_ql (the rest of the warp idles)
+constexpr int kQrLanes = 8;   // steps per warp in k_eig_qr (the rest of the warp idles)
 
 __device__ __forceinline__ double2 c_mul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -185,95 +185,106 @@ __global__ void __launch_bounds__(kT) k_eig_tridiag(EigCtx p) {
   }
 }
 
-// Implicit QL with Wilkinson-type shifts on the real symmetric tridiagonal T_r = P^+ T P
-// (P diagonal phases, P_{i+1} = P_i conj(t_i)/|t_i|), one thread per step: GB300 retires a warp's
-// FP64 instruction only every few tens of clocks per SM sub-partition, so the sequential scalar
-// recurrence runs with kQlLanes steps side by side in the lanes of a warp, spread over many SMs.  The plane rotations are
-// recorded (index, c, s) for k_eig_rotate; the eigenvalues go to lam.  At most 60 iterations per
-// eigenvalue and p.rot_cap rotations per step; past either limit kErrEig is set.
-__global__ void __launch_bounds__(32) k_eig_ql(EigCtx p) {
+// Eigenvalues of the real symmetric tridiagonal T_r = P^+ T P (P diagonal phases,
+// P_{i+1} = P_i conj(t_i)/|t_i|) by the symmetric QR algorithm with implicit Wilkinson-shifted steps
+// (Golub & Van Loan, Matrix Computations, 4th ed., Sec. 8.3: Algorithm 8.3.2 for one step,
+// Algorithm 8.3.3 for deflation).  The unreduced block [lo, hi] at the bottom of the part not yet
+// converged gets one step at a time:
+//   * shift mu = the eigenvalue of its trailing 2x2 block closer to a_hi;
+//   * the first rotation maps the first column of T - mu I, (a_lo - mu, b_lo), onto its norm;
+//   * each rotation R_k = [[c, s], [-s, c]] on rows/columns k, k+1 (T <- R_k T R_k^T) turns the
+//     entry b_{k+1} below it into a bulge at (k, k+2), which the next rotation removes; the last
+//     rotation leaves T tridiagonal again;
+//   * an off-diagonal |b_i| <= u (|a_i| + |a_{i+1}|) is set to zero, which splits the matrix; a zero
+//     at the bottom of the block (hi) frees the eigenvalue a_hi.
+// One thread per step: GB300 retires a warp's FP64 instruction only every few tens of clocks per
+// SM sub-partition, so the sequential scalar recurrence runs with kQrLanes steps side by side in
+// the lanes of a warp, spread over many SMs.  Every rotation is recorded (index k, c, s) for
+// k_eig_rotate, the eigenvalues go to lam.  At most kMaxQrSteps steps per eigenvalue and p.rot_cap
+// rotations per step; past either limit kErrEig is set.
+constexpr int kMaxQrSteps = 60;
+
+__device__ __forceinline__ bool offdiag_negligible(double b, double a0, double a1) {
+  return fabs(b) <= 0x1p-53 * (fabs(a0) + fabs(a1));
+}
+
+__global__ void __launch_bounds__(32) k_eig_qr(EigCtx p) {
   extern __shared__ __align__(16) unsigned char sm[];
-  const int d = p.d, lane = threadIdx.x, step = p.step0 + blockIdx.x * kQlLanes + lane;
-  if (lane >= kQlLanes || step >= p.step0 + p.nsteps) return;   // no block-wide synchronisation here
-  double* a = reinterpret_cast<double*>(sm) + lane;   // a[i * 32]
-  double* e = a + 32 * d;                              // e[i * 32]
+  const int d = p.d, lane = threadIdx.x, step = p.step0 + blockIdx.x * kQrLanes + lane;
+  if (lane >= kQrLanes || step >= p.step0 + p.nsteps) return;   // no block-wide synchronisation here
+  // the lane's diagonal dg[i * 32] and off-diagonal od[i * 32] = T_r[i][i+1], interleaved by lane
+  double* dg = reinterpret_cast<double*>(sm) + lane;
+  double* od = dg + 32 * d;
   const double* ta = p.tri_a + (size_t)step * d;
   const double2* tt = p.tri_t + (size_t)step * d;
   double2* ph = p.phase + (size_t)step * d;
   double2 phi = make_double2(1.0, 0.0);
   for (int i = 0; i < d; ++i) {
-    a[i * 32] = ta[i];
+    dg[i * 32] = ta[i];
     ph[i] = phi;
-    double at = 0.0;
+    double mag = 0.0;
     if (i + 1 < d) {
       const double2 t = tt[i];
-      at = hypot(t.x, t.y);
-      if (at > 0.0) phi = c_mul(phi, make_double2(t.x / at, -t.y / at));
+      mag = hypot(t.x, t.y);
+      if (mag > 0.0) phi = c_mul(phi, make_double2(t.x / mag, -t.y / mag));
     }
-    e[i * 32] = at;
+    od[i * 32] = mag;
   }
   const int cap = p.rot_cap;
   int* ri = p.rot_i + (size_t)step * cap;
   double2* rcs = p.rot_cs + (size_t)step * cap;
-  int nrot = 0;
+  int nrot = 0, steps_here = 0;
   bool failed = false;
-  for (int l = 0; l < d; ++l) {
-    int iter = 0;
-    for (;;) {
-      int m = l;
-      for (; m < d - 1; ++m) {
-        const double dd = fabs(a[m * 32]) + fabs(a[(m + 1) * 32]);
-        if (fabs(e[m * 32]) + dd == dd) break;
+  int hi = d - 1;
+  while (hi > 0) {
+    if (offdiag_negligible(od[(hi - 1) * 32], dg[(hi - 1) * 32], dg[hi * 32])) {
+      od[(hi - 1) * 32] = 0.0;   // a_hi is an eigenvalue
+      --hi;
+      steps_here = 0;
+      continue;
+    }
+    int lo = hi - 1;   // top of the unreduced block that ends at hi
+    while (lo > 0 && !offdiag_negligible(od[(lo - 1) * 32], dg[(lo - 1) * 32], dg[lo * 32])) --lo;
+    if (lo > 0) od[(lo - 1) * 32] = 0.0;
+    if (++steps_here > kMaxQrSteps) {
+      failed = true;
+      break;
+    }
+    // Wilkinson shift: eigenvalue of [[a_{hi-1}, b], [b, a_hi]] closer to a_hi
+    const double half_gap = 0.5 * (dg[(hi - 1) * 32] - dg[hi * 32]);
+    const double bt = od[(hi - 1) * 32];
+    const double mu = dg[hi * 32] - bt * (bt / (half_gap + copysign(hypot(half_gap, bt), half_gap)));
+    double x = dg[lo * 32] - mu, z = od[lo * 32];
+    for (int k = lo; k < hi; ++k) {
+      const double r = hypot(x, z);
+      const double c = r > 0.0 ? x / r : 1.0, s = r > 0.0 ? z / r : 0.0;
+      if (k > lo) od[(k - 1) * 32] = r;   // the bulge at (k - 1, k + 1) is gone
+      const double a0 = dg[k * 32], a1 = dg[(k + 1) * 32], b0 = od[k * 32];
+      const double cc = c * c, ss = s * s, cs2 = 2.0 * c * s;
+      dg[k * 32] = cc * a0 + cs2 * b0 + ss * a1;
+      dg[(k + 1) * 32] = ss * a0 - cs2 * b0 + cc * a1;
+      od[k * 32] = c * s * (a1 - a0) + (cc - ss) * b0;
+      if (k + 1 < hi) {
+        const double b1 = od[(k + 1) * 32];
+        z = s * b1;                   // new bulge at (k, k + 2)
+        od[(k + 1) * 32] = c * b1;
       }
-      if (m == l) break;
-      if (++iter > 60) {
-        failed = true;
-        break;
+      x = od[k * 32];
+      if (nrot < cap) {
+        ri[nrot] = k;
+        rcs[nrot] = make_double2(c, s);
       }
-      double g = (a[(l + 1) * 32] - a[l * 32]) / (2.0 * e[l * 32]);
-      double r = hypot(g, 1.0);
-      g = a[m * 32] - a[l * 32] + e[l * 32] / (g + copysign(r, g));
-      double s = 1.0, c = 1.0, shift = 0.0;
-      bool split = false;
-      for (int i = m - 1; i >= l; --i) {
-        const double f = s * e[i * 32], b = c * e[i * 32];
-        const double r2 = fma(f, f, g * g);   // entries of H dt are far from the overflow range
-        if (r2 == 0.0) {   // underflow: the off-diagonal element splits the matrix here
-          e[(i + 1) * 32] = 0.0;
-          a[(i + 1) * 32] -= shift;
-          e[m * 32] = 0.0;
-          split = true;
-          break;
-        }
-        const double ir = rsqrt(r2);
-        r = r2 * ir;
-        e[(i + 1) * 32] = r;
-        s = f * ir;
-        c = g * ir;
-        g = a[(i + 1) * 32] - shift;
-        r = (a[i * 32] - g) * s + 2.0 * c * b;
-        shift = s * r;
-        a[(i + 1) * 32] = g + shift;
-        g = c * r - b;
-        if (nrot < cap) {
-          ri[nrot] = i;
-          rcs[nrot] = make_double2(c, s);
-        }
-        ++nrot;
-      }
-      if (split) continue;
-      a[l * 32] -= shift;
-      e[l * 32] = g;
-      e[m * 32] = 0.0;
+      ++nrot;
     }
   }
   if (failed || nrot > cap) atomicCAS(p.err, 0, kErrEig);
   p.rot_n[step] = nrot < cap ? nrot : cap;
-  for (int i = 0; i < d; ++i) p.lam[(size_t)step * d + i] = a[i * 32];
+  for (int i = 0; i < d; ++i) p.lam[(size_t)step * d + i] = dg[i * 32];
 }
 
-// Eigenvectors of T_r: Z = I G_1 G_2 ..., every thread rotating its own row of Z (the rows are
-// independent), then Y = P Z written to the step's slice of V.
+// Eigenvectors of T_r: T_r = Q diag(lam) Q^T with Q = R_1^T R_2^T ..., the recorded rotations in
+// order; every thread forms its own row of Q (the rows are independent), z <- z R_k^T on entries
+// k, k+1, then Y = P Q is written to the step's slice of V.
 __global__ void __launch_bounds__(128) k_eig_rotate(EigCtx p) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int d = p.d, step = p.step0 + blockIdx.x, row = threadIdx.x;
@@ -287,8 +298,8 @@ __global__ void __launch_bounds__(128) k_eig_rotate(EigCtx p) {
     const int i = ri[r];
     const double2 cs = rcs[r];
     const double z0 = z[i], z1 = z[i + 1];
-    z[i + 1] = fma(cs.y, z0, cs.x * z1);
-    z[i] = fma(cs.x, z0, -cs.y * z1);
+    z[i] = fma(cs.x, z0, cs.y * z1);
+    z[i + 1] = fma(cs.x, z1, -cs.y * z0);
   }
   const double2 ph = p.phase[(size_t)step * d + row];
   double2* y = p.V + (size_t)step * d * d + (size_t)row * d;
@@ -672,7 +683,7 @@ size_t backward_smem(int d) { return (size_t)16 * (2 * d + kT); }
 
 int eig_step_smem(int d) { return (int)block_bytes(d); }
 
-int eig_ql_smem(int d) { return 8 * 2 * 32 * d; }
+int eig_qr_smem(int d) { return 8 * 2 * 32 * d; }
 
 int eig_rotate_smem(int d) { return 8 * d * (d + 1); }
 
@@ -685,7 +696,7 @@ cudaError_t eig_prepare(int d, int K) {
   cudaError_t e = cudaFuncSetAttribute(k_eig_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, eig_step_smem(d));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_eig_vectors, cudaFuncAttributeMaxDynamicSharedMemorySize, eig_step_smem(d));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eig_ql, cudaFuncAttributeMaxDynamicSharedMemorySize, eig_ql_smem(d));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eig_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, eig_qr_smem(d));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_eig_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize, eig_rotate_smem(d));
   if (e == cudaSuccess)
@@ -714,7 +725,7 @@ cudaError_t launch_sweep_kernel(KernelT kern, const EigCtx& c, size_t smem, cuda
 
 cudaError_t eig_propagators(const EigCtx& c, cudaStream_t st) {
   k_eig_tridiag<<<c.nsteps, kT, eig_step_smem(c.d), st>>>(c);
-  k_eig_ql<<<(c.nsteps + kQlLanes - 1) / kQlLanes, 32, eig_ql_smem(c.d), st>>>(c);
+  k_eig_qr<<<(c.nsteps + kQrLanes - 1) / kQrLanes, 32, eig_qr_smem(c.d), st>>>(c);
   k_eig_rotate<<<c.nsteps, (c.d + 31) / 32 * 32, eig_rotate_smem(c.d), st>>>(c);
   k_eig_vectors<<<c.nsteps, kT, eig_step_smem(c.d), st>>>(c);
   return cudaGetLastError();

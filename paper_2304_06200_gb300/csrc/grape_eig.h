@@ -48,7 +48,7 @@ struct EigCtx {
 };
 
 int eig_step_smem(int d);
-int eig_ql_smem(int d);
+int eig_qr_smem(int d);
 int eig_rotate_smem(int d);
 int eig_grad_smem(int d, int K);
 cudaError_t eig_prepare(int d, int K);

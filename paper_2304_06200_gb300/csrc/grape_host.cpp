@@ -197,6 +197,21 @@ struct grape_problem {
   unsigned* d_flags = nullptr;      // ready[n*CL], done[n*CL]
   // launch plans of the forward and the backward sweep
   KPlan fwd, bwd;
+  // three-stage backward (bwd_mode 3): k_costate on the forward's partition, k_gradient on grd;
+  // the fused plan bwd stays as the fallback for schedules whose Horner vectors overflow the buffers
+  KPlan grd;
+  int steps_per_block = 0;
+  int64_t hbuf_terms = 0;                // capacity of one block buffer, in terms
+  static constexpr int kHbufDepth = 3;   // block buffers of Horner vectors in flight
+  static constexpr int kGradStreams = 2; // k_gradient launches alternate between these streams
+  void* d_hbuf[kHbufDepth] = {nullptr, nullptr, nullptr};
+  double2* d_chi_io = nullptr;           // costate between k_costate launches
+  int* d_plan_flag = nullptr;            // set by k_plan: 1 = the fused fallback runs
+  int* d_cslice_g = nullptr;             // control slices of the gradient partition
+  cudaStream_t g_stream[kGradStreams] = {nullptr, nullptr};   // k_gradient launches
+  cudaEvent_t ev_b = nullptr, ev_g[kHbufDepth] = {nullptr, nullptr, nullptr};
+  int prio_hi = 0;                       // launch priority of the costate chain
+  int64_t scr_g_off = 0;                 // k_gradient's region of d_scratch (double2 units)
   // eigendecomposition propagators (App. F)
   bool eig = false;
   grape::EigCtx ectx{};
@@ -238,7 +253,28 @@ struct grape_problem {
     }
     return p;
   }
+  // Release one allocation made by dalloc (the device must no longer use it).
+  void dfree(void* p) {
+    for (size_t i = 0; i < allocations.size(); ++i)
+      if (allocations[i].first == p) {
+        if (free_fn) free_fn(p, allocations[i].second, alloc_ctx);
+        else cudaFree(p);
+        device_bytes -= (int64_t)allocations[i].second;
+        allocations.erase(allocations.begin() + (long)i);
+        return;
+      }
+  }
   void release() {
+    if (ev_b) cudaEventDestroy(ev_b);
+    ev_b = nullptr;
+    for (auto& e : ev_g) {
+      if (e) cudaEventDestroy(e);
+      e = nullptr;
+    }
+    for (auto& g : g_stream) {
+      if (g) cudaStreamDestroy(g);
+      g = nullptr;
+    }
     for (auto e : eig_ready) cudaEventDestroy(e);
     for (auto l : eig_lanes) cudaStreamDestroy(l);
     if (eig_fork) cudaEventDestroy(eig_fork);
@@ -501,8 +537,8 @@ grape_status build_eig(grape_problem* P, const grape_desc* d, const std::vector<
   if ((st = dzeros(P, &ph, (size_t)(N + 1) * blk)) || (st = dzeros(P, &ch, (size_t)(N + 1) * blk)) ||
       (st = dzeros(P, &xs, (size_t)N * 2 * blk)))
     return st;
-  // QL rotations: about d^2 for a whole tridiagonal eigenproblem (1-2 shifted sweeps per eigenvalue
-  // over the unreduced part); four times that before the step reports kErrEig
+  // QR rotations: about d^2 for a whole tridiagonal eigenproblem (1-2 shifted steps per eigenvalue,
+  // each one rotation per row of the unreduced block); four times that before the step reports kErrEig
   c.rot_cap = (int)(4 * dd + 64);
   double *tri_a;
   double2 *tri_t, *phase, *rot_cs;
@@ -551,7 +587,7 @@ grape_status build_eig(grape_problem* P, const grape_desc* d, const std::vector<
   c.err = P->d_err;
   cudaError_t e = grape::eig_prepare((int)dim, K);
   if (e != cudaSuccess) return cuda_fail(e, "eigendecomposition kernel attributes");
-  // The QL recurrence of a step is sequential (FP64 latency bound, ~10 ms at d = 80) whatever the
+  // The QR recurrence of a step is sequential (FP64 latency bound, ~10 ms at d = 80) whatever the
   // number of steps: with the steps in chunks on their own streams, the chunks' reductions,
   // rotations and back-transformations run while other chunks iterate, and the forward sweep
   // starts on a chunk as soon as its propagators are done.
@@ -823,7 +859,12 @@ grape_status build(grape_problem* P, const grape_desc* d) {
     return true;
   };
   int mode_req = d->backward_mode;
-  if (mode_req < 0 || mode_req > 2) return fail(GRAPE_EINVAL, "backward_mode must be 0, 1 or 2");
+  if (mode_req < 0 || mode_req > 3) return fail(GRAPE_EINVAL, "backward_mode must be 0, 1, 2 or 3");
+  if (mode_req == 3 && d->ckpt_every != 0 && d->ckpt_every != 1)
+    return fail(GRAPE_EINVAL, "backward_mode 3 stores every state: ckpt_every must be 0 or 1");
+  if (d->grad_cluster < 0 || d->grad_cluster > grape::kMaxCluster)
+    return fail(GRAPE_EINVAL, "grad_cluster must be 0 (automatic) or 1..16");
+  if (d->block_steps < 0) return fail(GRAPE_EINVAL, "block_steps must be >= 0");
   // forward
   {
     double best = 1e300;
@@ -848,7 +889,55 @@ grape_status build(grape_problem* P, const grape_desc* d) {
     P->fwd.smem = grape::make_layout(false, R, mnl, P->fwd.in_smem, 0, cb).total;
     P->fwd.threads = threads_for(R);
   }
-  // backward: one team per column (fused) or two concurrent teams (split) when co-resident
+  // Three-stage backward: the costate chain runs on the forward's partition (n * CL_f SMs); it pays
+  // when at least half of the GPU is left for the gradient kernel, and the states of every step
+  // (N * dim * n * 16 bytes) are stored.  Automatic choice: at most 8 GiB of states.
+  bool three = false;
+  {
+    const double state_bytes = (double)P->N * (double)dim * P->n * 16.0;
+    const bool ckpt_ok = d->ckpt_every == 0 || d->ckpt_every == 1;
+    if (mode_req == 3) three = true;
+    else if (mode_req == 0)
+      three = ckpt_ok && P->N >= 2 && 2 * P->n * P->fwd.CL <= nsm && state_bytes <= 8.0 * (1 << 30);
+  }
+  // k_gradient partition: the smallest team (at most 512 rows per CTA) whose exchange buffers, states,
+  // values, W accumulators and pattern all fit shared memory; else the smallest with W in shared
+  // memory, else the smallest that fits at all (the rest in the CTA's global scratch).
+  if (three) {
+    const int full = 1 | 2 | (cb == 8 ? 4 : 0);
+    int pick = 0, pick_in = 0;
+    for (int pass = 0; pass < 3 && !pick; ++pass) {
+      for (int CL = 1; CL <= grape::kMaxCluster && !pick; ++CL) {
+        if (d->grad_cluster > 0 && CL != d->grad_cluster) continue;
+        if (CL > 1 && CL > dim) continue;
+        int R = 0, mnl = 0;
+        if (!rows_entries(CL, &R, &mnl)) continue;
+        const int want = pass == 0 ? full : (pass == 1 ? 2 | (cb == 8 ? 4 : 0) : 0);
+        if (pass == 0 && R > 512 && d->grad_cluster == 0) continue;
+        if (grape::make_glayout(R, mnl, want, cb).total > smem_max) continue;
+        pick = CL;
+        pick_in = want;
+        P->grd.R = R;
+        P->grd.mnl = mnl;
+      }
+    }
+    if (!pick) {
+      if (mode_req == 3) return fail(GRAPE_EINVAL, "backward_mode 3: the gradient kernel does not fit shared memory");
+      three = false;
+    } else {
+      P->grd.CL = pick;
+      P->grd.in_smem = pick_in;
+      P->grd.m_smem = 0;
+      P->grd.smem = grape::make_glayout(P->grd.R, P->grd.mnl, pick_in, cb).total;
+      P->grd.threads = threads_for(P->grd.R);
+      const int free_sms = std::max(nsm - P->n * P->fwd.CL, P->n * pick);
+      int S = d->block_steps > 0 ? d->block_steps : std::max(1, free_sms / (P->n * pick));
+      P->steps_per_block = std::min(S, P->N);
+    }
+  }
+  // backward: one team per column (fused) or two concurrent teams (split) when co-resident; with the
+  // three-stage backward, the fused plan is its fallback
+  if (three) mode_req = 1;
   {
     double best = 1e300;
     for (int CL = 1; CL <= grape::kMaxCluster; ++CL) {
@@ -885,6 +974,7 @@ grape_status build(grape_problem* P, const grape_desc* d) {
       return fail(GRAPE_EINVAL, "problem does not fit the backward sweep's shared memory");
     }
   }
+  if (three) P->bwd_mode = 3;
   // column encodings (owner CTA, local row, control bit) of both partitions, control slices of the backward one
   auto encode = [&](int R, std::vector<uint32_t>& enc) {
     enc.resize(nnz);
@@ -897,35 +987,41 @@ grape_status build(grape_problem* P, const grape_desc* d) {
         enc[e] = x;
       }
   };
-  std::vector<uint32_t> colenc_f, colenc_b;
+  std::vector<uint32_t> colenc_f, colenc_b, colenc_g;
   encode(P->fwd.R, colenc_f);
   encode(P->bwd.R, colenc_b);
-  const int CLb = P->bwd.CL, Rb = P->bwd.R;
-  std::vector<int> cslice((size_t)std::max(K, 1) * CLb * 2, 0);
-  for (int k = 0; k < K; ++k)
-    for (int r = 0; r < CLb; ++r) {
-      const int64_t r0 = std::min<int64_t>((int64_t)r * Rb, dim), r1 = std::min<int64_t>(r0 + Rb, dim);
-      const auto b = cidx.begin() + cptr[k], e = cidx.begin() + cptr[k + 1];
-      cslice[(k * CLb + r) * 2] = (int)(std::lower_bound(b, e, (int)rowptr[r0]) - cidx.begin());
-      cslice[(k * CLb + r) * 2 + 1] = (int)(std::lower_bound(b, e, (int)rowptr[r1]) - cidx.begin());
-    }
+  if (three) encode(P->grd.R, colenc_g);
+  auto slices = [&](int CLx, int Rx, std::vector<int>& cs) {
+    cs.assign((size_t)std::max(K, 1) * CLx * 2, 0);
+    for (int k = 0; k < K; ++k)
+      for (int r = 0; r < CLx; ++r) {
+        const int64_t r0 = std::min<int64_t>((int64_t)r * Rx, dim), r1 = std::min<int64_t>(r0 + Rx, dim);
+        const auto b = cidx.begin() + cptr[k], e = cidx.begin() + cptr[k + 1];
+        cs[(k * CLx + r) * 2] = (int)(std::lower_bound(b, e, (int)rowptr[r0]) - cidx.begin());
+        cs[(k * CLx + r) * 2 + 1] = (int)(std::lower_bound(b, e, (int)rowptr[r1]) - cidx.begin());
+      }
+  };
+  std::vector<int> cslice, cslice_g;
+  slices(P->bwd.CL, P->bwd.R, cslice);
+  if (three) slices(P->grd.CL, P->grd.R, cslice_g);
   // per-CTA global scratch (buffers that do not fit in shared memory), in double2 units
-  for (KPlan* kp : {&P->fwd, &P->bwd}) {
+  for (KPlan* kp : {&P->fwd, &P->bwd, &P->grd}) {
+    if (kp->CL == 0) continue;
     kp->scr_vals = 0;
     kp->scr_W = kp->mnl;
     kp->scr_Wb = 2 * (int64_t)kp->mnl;
     kp->scr_wslot = 3 * (int64_t)kp->mnl;
-    const int wslots = kp == &P->bwd && P->bwd_mode == 1 ? std::max(0, P->m_cap - kp->m_smem) : 0;
+    const int wslots = kp == &P->bwd && P->bwd_mode != 2 ? std::max(0, P->m_cap - kp->m_smem) : 0;
     kp->stride = (3 * (int64_t)kp->mnl + (int64_t)wslots * kp->R + 15) / 16 * 16;
   }
   // ---- checkpoints
   int M = d->ckpt_every;
-  if (M == 0) M = std::min(50, P->N);
+  if (M == 0) M = three ? 1 : std::min(50, P->N);
   if (M < 0) M = 0;
   P->ckpt_every = M;
   P->n_ckpt = M > 0 ? (P->N - 1) / M : 0;
   // ---- device memory
-  const int parts_f = P->n * P->fwd.CL, parts_b = P->n * P->bwd.CL;
+  const int parts_f = P->n * P->fwd.CL, parts_b = std::max(P->n * P->bwd.CL, P->n * P->grd.CL);
   std::vector<double> tabX(P->table.X), tabS(P->table.smax);
   if ((st = upload(P, &P->d_rowptr, rowptr.data(), rowptr.size()))) return st;
   if ((st = upload(P, &P->fwd.d_colenc, colenc_f.data(), colenc_f.size()))) return st;
@@ -968,8 +1064,58 @@ grape_status build(grape_problem* P, const grape_desc* d) {
     if ((st = dzeros(P, &P->d_flags, (size_t)2 * parts_b))) return st;
   }
   const int64_t scr_f = (int64_t)parts_f * P->fwd.stride;
-  const int64_t scr_b = (int64_t)(P->bwd_mode == 2 ? 2 * parts_b : parts_b) * P->bwd.stride;
-  if ((st = dzeros(P, &P->d_scratch, (size_t)std::max(scr_f, scr_b)))) return st;
+  const int64_t scr_b = (int64_t)(P->bwd_mode == 2 ? 2 * P->n * P->bwd.CL : P->n * P->bwd.CL) * P->bwd.stride;
+  // k_costate (forward partition) and k_gradient run at the same time: disjoint scratch regions
+  int64_t scr_g = 0;
+  if (three) scr_g = (int64_t)P->steps_per_block * P->n * P->grd.CL * P->grd.stride;
+  P->scr_g_off = scr_f;
+  if ((st = dzeros(P, &P->d_scratch, (size_t)std::max(scr_f + scr_g, scr_b)))) return st;
+  if (three) {
+    // Block buffers of Horner vectors, first sized for the schedule of 1.25 times the drift's norm (at
+    // least 2 m_cap terms per step).  Outside stream capture every evaluation reads its schedule back
+    // and grows them when a block needs more; under capture k_plan selects the fused fallback for a
+    // schedule that does not fit.
+    double xd = 0.0;
+    for (int64_t i = 0; i < dim; ++i) {
+      double a = 0.0;
+      for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) a += std::hypot(h0v[e].x, h0v[e].y);
+      xd = std::max(xd, a);
+    }
+    auto mu_of = [&](double x) -> int64_t {
+      int s0 = 1;
+      if (P->b_cap > 0.0) s0 = std::max(1, (int)std::ceil(x / P->b_cap));
+      for (int s1 = s0; s1 <= P->s_cap; ++s1)
+        if (P->table.smax[s1 - 1] >= x)
+          for (int m1 = 1; m1 <= P->m_cap; ++m1)
+            if (P->table.X[(size_t)(s1 - 1) * P->m_cap + (m1 - 1)] >= x) return (int64_t)m1 * s1;
+      return 0;
+    };
+    const int64_t mu = std::max<int64_t>(mu_of(1.25 * P->dt * xd), 2 * P->m_cap);
+    P->hbuf_terms = mu * P->steps_per_block;
+    P->m_host.assign(P->N, 0);
+    P->s_host.assign(P->N, 0);
+    const size_t hb = (size_t)P->hbuf_terms * (size_t)dim * P->n * (size_t)cb;
+    for (auto& h : P->d_hbuf) {
+      h = P->dalloc(hb);
+      if (!h) return fail(GRAPE_ENOMEM, "device allocation failed");
+    }
+    if ((st = upload(P, &P->grd.d_colenc, colenc_g.data(), colenc_g.size()))) return st;
+    if ((st = upload(P, &P->d_cslice_g, cslice_g.data(), cslice_g.size()))) return st;
+    if ((st = dzeros(P, &P->d_chi_io, blk))) return st;
+    if ((st = dzeros(P, &P->d_plan_flag, 1))) return st;
+    int lo = 0, hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetStreamPriorityRange");
+    P->prio_hi = hi;
+    for (auto& g : P->g_stream)
+      if ((e = cudaStreamCreateWithPriority(&g, cudaStreamNonBlocking, lo)) != cudaSuccess)
+        return cuda_fail(e, "cudaStreamCreateWithPriority");
+    if ((e = cudaEventCreateWithFlags(&P->ev_b, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(e, "cudaEventCreateWithFlags");
+    for (auto& ev : P->ev_g)
+      if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "cudaEventCreateWithFlags");
+  }
   return GRAPE_OK;
 }
 
@@ -1039,7 +1185,7 @@ grape_status read_error_word(grape_problem* P, cudaStream_t st) {
       case grape::kErrTol: return fail(GRAPE_ETOL, "a step has no (m, s) with E_A(m, s) <= tau");
       case grape::kErrNonFinite: return fail(GRAPE_ENONFINITE, "a control amplitude or step norm is not finite");
       case grape::kErrTimeout: return fail(GRAPE_ETIMEOUT, "a bounded device wait gave up");
-      case grape::kErrEig: return fail(GRAPE_ETOL, "the tridiagonal QL iteration of a step did not converge");
+      case grape::kErrEig: return fail(GRAPE_ETOL, "the tridiagonal QR iteration of a step did not converge");
       default: return fail(GRAPE_ECUDA, "unknown device error word");
     }
   }
@@ -1294,6 +1440,93 @@ grape_status run_backward(grape_problem* P, cudaStream_t st) {
       return grape::dense_backward(P->dctx, P->m_host.data(), P->s_host.data(), cs);
     });
     if (e != cudaSuccess) return cuda_fail(e, "dense backward sweep");
+  } else if (P->bwd_mode == 3) {
+    // k_plan decides whether the block buffers hold this schedule's Horner vectors.  Then, per block
+    // of steps (descending), the costate chain on the caller's stream (high launch priority) and the
+    // gradient kernel of the block on one of the gradient streams (alternating, so that consecutive
+    // blocks' gradient kernels overlap and fill the SMs the chain leaves) once the chain has stored
+    // the block; kHbufDepth buffers rotate, so the chain waits for the gradient kernel of the block
+    // kHbufDepth ahead.  The fused backward is queued after the join and returns at once unless
+    // k_plan selected it.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(st, &cap)) != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
+    if (cap == cudaStreamCaptureStatusNone) {
+      // the schedule of this evaluation (k_schedule ran before the forward sweep)
+      if ((e = cudaMemcpyAsync(P->m_host.data(), P->d_ms_m, P->N * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+          (e = cudaMemcpyAsync(P->s_host.data(), P->d_ms_s, P->N * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+          (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(e, "schedule download");
+      int64_t need = 0;
+      for (int b0 = 0; b0 < P->N; b0 += P->steps_per_block) {
+        int64_t t = 0;
+        for (int n = b0; n < std::min(P->N, b0 + P->steps_per_block); ++n)
+          if (P->m_host[n] > 0 && P->s_host[n] > 0) t += (int64_t)P->m_host[n] * P->s_host[n];
+        need = std::max(need, t);
+      }
+      if (need > P->hbuf_terms) {   // nothing runs on the device: the stream was just synchronised
+        if (P->opt_exec) {            // a recorded optimizer iteration refers to the old buffers
+          cudaGraphExecDestroy(P->opt_exec);
+          P->opt_exec = nullptr;
+        }
+        const int64_t terms = need + need / 4;
+        const size_t cbytes = P->precision == GRAPE_FP32_BULK ? 8 : 16;
+        const size_t hb = (size_t)terms * (size_t)P->dim * P->n * cbytes;
+        for (auto& h : P->d_hbuf) {
+          P->dfree(h);
+          h = P->dalloc(hb);
+          if (!h) {
+            for (auto& h2 : P->d_hbuf) { P->dfree(h2); h2 = nullptr; }
+            P->bwd_mode = 1;   // no room for the block buffers: the fused backward from now on
+            break;
+          }
+        }
+        if (P->bwd_mode == 3) P->hbuf_terms = terms;
+      }
+    }
+    if (P->bwd_mode != 3) return run_backward(P, st);
+    grape::PlanParams pp{};
+    pp.N = P->N;
+    pp.steps_per_block = P->steps_per_block;
+    pp.cap_terms = P->hbuf_terms;
+    pp.ms_m = P->d_ms_m;
+    pp.ms_s = P->d_ms_s;
+    pp.flag = P->d_plan_flag;
+    if ((e = grape::launch_plan(pp, st)) != cudaSuccess) return cuda_fail(e, "launch k_plan");
+    grape::SweepParams pc = sweep_params(P, P->fwd);
+    pc.chi_io = P->d_chi_io;
+    pc.plan_flag = P->d_plan_flag;
+    pc.hbuf_terms = P->hbuf_terms;
+    grape::SweepParams pg = sweep_params(P, P->grd);
+    pg.cslice = P->d_cslice_g;
+    pg.scratch = P->d_scratch + P->scr_g_off;
+    pg.plan_flag = P->d_plan_flag;
+    pg.hbuf_terms = P->hbuf_terms;
+    const int S = P->steps_per_block, nb = (P->N + S - 1) / S;
+    constexpr int D = grape_problem::kHbufDepth, G = grape_problem::kGradStreams;
+    for (int b = nb - 1; b >= 0; --b) {
+      const int slot = b % D;
+      cudaStream_t gs = P->g_stream[b % G];
+      pc.n_begin = pg.n_begin = b * S;
+      pc.n_end = pg.n_end = std::min(P->N, (b + 1) * S);
+      pc.hbuf = pg.hbuf = P->d_hbuf[slot];
+      if (b + D <= nb - 1 && (e = cudaStreamWaitEvent(st, P->ev_g[slot], 0)) != cudaSuccess)
+        return cuda_fail(e, "cudaStreamWaitEvent");
+      if ((e = grape::launch_costate(pc, P->precision, P->fwd.smem, P->fwd.threads, P->prio_hi, st)) != cudaSuccess)
+        return cuda_fail(e, "launch k_costate");
+      if ((e = cudaEventRecord(P->ev_b, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+      if ((e = cudaStreamWaitEvent(gs, P->ev_b, 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+      if ((e = grape::launch_gradient(pg, P->precision, P->grd.smem, P->grd.threads, gs)) != cudaSuccess)
+        return cuda_fail(e, "launch k_gradient");
+      if ((e = cudaEventRecord(P->ev_g[slot], gs)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    }
+    // join: the last gradient kernel of each stream (blocks 0 .. G-1, slots b % D)
+    for (int b = 0; b < std::min(G, nb); ++b)
+      if ((e = cudaStreamWaitEvent(st, P->ev_g[b % D], 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+    grape::SweepParams pf = sweep_params(P, P->bwd);
+    pf.plan_flag = P->d_plan_flag;
+    pf.gate_on_flag = 1;
+    if ((e = grape::launch_backward(pf, P->precision, P->bwd.smem, P->bwd.threads, st)) != cudaSuccess)
+      return cuda_fail(e, "launch k_backward (fallback)");
   } else if (P->bwd_mode == 2) {
     p.ring = P->d_ring;
     p.ring_slot = P->ring_slot;
@@ -1312,6 +1545,11 @@ grape_status run_backward(grape_problem* P, cudaStream_t st) {
   if (P->K > 0) {
     grape::GradReduceParams gp{};
     gp.n_parts = (P->dense || P->eig) ? 1 : P->n * P->bwd.CL;
+    if (!P->dense && !P->eig && P->bwd_mode == 3) {
+      gp.n_parts = P->n * P->grd.CL;
+      gp.n_parts_alt = P->n * P->bwd.CL;
+      gp.plan_flag = P->d_plan_flag;
+    }
     gp.N = P->N;
     gp.K = P->K;
     gp.w_amp = P->w_amp;
@@ -1694,6 +1932,19 @@ grape_status grape_problem_info(grape_problem* P, grape_info* info) {
   info->max_norm = -1.0;
   info->backward_mode = P->bwd_mode;
   info->propagator = P->eig ? GRAPE_PROP_EIG : GRAPE_PROP_TAYLOR;
+  info->fused_fallback = -1;
+  if (P->bwd_mode == 3) {
+    info->grad_cluster = P->grd.CL;
+    info->block_steps = P->steps_per_block;
+    if (P->evaluated) {
+      DeviceGuard guard(P->device);
+      int flag = 0;
+      cudaStreamSynchronize(P->last_stream);
+      if (cudaMemcpy(&flag, P->d_plan_flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(GRAPE_ECUDA, "cudaMemcpy (plan flag)");
+      info->fused_fallback = flag;
+    }
+  }
   if (P->evaluated && !P->eig) {
     DeviceGuard guard(P->device);
     std::vector<int> m(P->N), s(P->N);

@@ -80,6 +80,26 @@ struct SweepParams {
   unsigned* ready;                     // n_states x CL: substeps published by team A's CTA
   unsigned* done;                      // n_states x CL: substeps consumed by team B's CTA
   long long spin_limit;                // polls before a wait gives up (sets the timeout error)
+  // three-stage backward: k_costate (costate chain) and k_gradient (per-step gradient) work on the
+  // block of steps [n_begin, n_end); k_plan decides once per evaluation whether they run
+  int n_begin, n_end;
+  double2* chi_io;                     // d x n: the costate carried from one k_costate launch to the next
+  void* hbuf;                          // Horner vectors of the block, bulk type: [term][column][row]
+  int64_t hbuf_terms;                  // capacity of hbuf in terms
+  const int* plan_flag;                // 0: the three-stage kernels run; 1: the fused k_backward runs instead
+  int gate_on_flag;                    // k_backward: 1 = run only when *plan_flag != 0 (the fallback)
+};
+
+// Block plan of the three-stage backward: per block of S steps the Horner vectors of every term must
+// fit in the block's buffer; if any block's sum of m_n s_n exceeds the capacity the flag is set and
+// the fused one-team backward runs instead (both paths are queued, each returns at once when the
+// flag says the other one runs).
+struct PlanParams {
+  int N, steps_per_block;
+  int64_t cap_terms;
+  const int* ms_m;
+  const int* ms_s;
+  int* flag;
 };
 
 struct ScheduleParams {
@@ -116,6 +136,8 @@ struct FinalizeParams {
 
 struct GradReduceParams {
   int n_parts, N, K;
+  int n_parts_alt;                     // parts summed when *plan_flag != 0 (the fused fallback ran)
+  const int* plan_flag;                // nullptr: always n_parts
   double w_amp;
   const double* part_grad;
   const double* u;
@@ -159,6 +181,26 @@ __host__ __device__ inline SmemLayout make_layout(bool backward, int R, int max_
   return L;
 }
 
+// Layout of k_gradient (byte offsets): the x chain's two exchange buffers, psi^(l), the increment,
+// then vals (in_smem bit 0) and W (bit 1, FP64 accumulators per local entry) and, for the FP32
+// bulk, the FP32 staging of W (bit 2), then the local pattern.
+__host__ __device__ inline SmemLayout make_glayout(int R, int max_nnz_loc, int in_smem, int cplx_bytes) {
+  SmemLayout L;
+  int off = 0;
+  L.xbuf = off; off += align16(2 * R * cplx_bytes);
+  L.psi = off;  off += align16(R * 16);
+  L.chi = -1;
+  L.inc = off;  off += align16(R * 16);
+  L.vals = -1; L.W = -1; L.Wb = -1; L.wslot = -1;
+  if (in_smem & 1) { L.vals = off; off += align16(max_nnz_loc * cplx_bytes); }
+  if (in_smem & 2) { L.W = off; off += align16(max_nnz_loc * 16); }
+  if (cplx_bytes == 8 && (in_smem & 4)) { L.Wb = off; off += align16(max_nnz_loc * 8); }
+  L.lrow = off; off += align16((R + 1) * 4);
+  L.lcol = off; off += align16(max_nnz_loc * 4);
+  L.total = off;
+  return L;
+}
+
 // Launchers (grape_kernels.cu).  Return cudaGetLastError() of the launch.
 cudaError_t launch_schedule(const ScheduleParams& p, cudaStream_t st);
 cudaError_t launch_forward(const SweepParams& p, int precision, int smem_bytes, int threads, cudaStream_t st);
@@ -166,6 +208,11 @@ cudaError_t launch_backward(const SweepParams& p, int precision, int smem_bytes,
 cudaError_t launch_backward_split(const SweepParams& p, int precision, int smem_bytes, int threads, cudaStream_t st);
 // Largest number of co-resident clusters (or blocks when CL == 1) of the split backward kernel.
 int split_capacity(int precision, int CL, int smem_bytes, int threads);
+cudaError_t launch_plan(const PlanParams& p, cudaStream_t st);
+// priority: launch priority of the costate chain (the critical path), e.g. the device's greatest
+cudaError_t launch_costate(const SweepParams& p, int precision, int smem_bytes, int threads, int priority,
+                           cudaStream_t st);
+cudaError_t launch_gradient(const SweepParams& p, int precision, int smem_bytes, int threads, cudaStream_t st);
 cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t st);
 cudaError_t launch_grad_reduce(const GradReduceParams& p, cudaStream_t st);
 cudaError_t check_nonfinite_u(const double* u, int64_t count, int* err, cudaStream_t st);

@@ -1091,6 +1091,7 @@ __device__ __forceinline__ void team_init(Team<T, CLUSTER>& tm, unsigned char* s
 template <typename T, bool CLUSTER>
 __global__ void __launch_bounds__(512, 1) k_backward(SweepParams p) {
   using C2 = cx<T>;
+  if (p.gate_on_flag && *p.plan_flag == 0) return;   // the three-stage backward ran (uniform over the grid)
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32];
   __shared__ double s_u[kMaxControls];
@@ -1268,6 +1269,487 @@ __global__ void __launch_bounds__(512, 1) k_backward_split(SweepParams p) {
   team_sync<CLUSTER>();
 }
 
+// ------------------------------------------------------------------ three-stage backward
+//
+// The backward sweep split by role.  Its only sequential part is the costate chain: for every step
+// n = N..1 and substep l = s-1..0 the Horner recursion
+//     w_{m-1} = chi/m!,   w_p = chi/(p+1)! + (-B) w_{p+1},   chi^(l) = w_{-1} = P(-B) chi^(l+1)
+// (m products per substep on one team of CL CTAs per column: k_costate), which stores every w_p of a
+// block of steps.  The states are not re-propagated backwards: the forward sweep stored psi_n of
+// every step, and the Taylor vectors x_p = B^p psi^(l), psi^(l) = P^l psi_n, do not depend on the
+// costate, so k_gradient regenerates them for all steps of a block side by side, on the SMs the
+// chain leaves idle, and accumulates W_ij += conj(w_p[i]) x_p[j] once the block's w_p are stored.
+// This is the fused sweep's derivative (Eq. (auxiliary equation), dP regrouped as
+// sum_p <w_p| C |x_p>), evaluated on the forward's own psi^(l).
+//
+// Launch order per block b (descending): k_costate(b) on the critical stream, then k_gradient(b) on
+// a second stream after an event; the block buffers alternate, and k_costate(b - 2) waits for
+// k_gradient(b).  No kernel waits for another one on the device.
+
+// psi_n, the input state of step n: psi_0, else the state the forward stored after step n - 1 (every
+// step is stored when the three-stage backward runs).
+__device__ __forceinline__ const double2* step_state(const SweepParams& p, int n, int col) {
+  return n == 0 ? p.psi0 + (int64_t)col * p.dim : p.ckpt + ((int64_t)(n - 1) * p.n_states + col) * p.dim;
+}
+
+// Terms of the block's steps [n_begin, n): the offset of step n's first Horner vector in the block buffer.
+__device__ __forceinline__ int64_t block_term_offset(const SweepParams& p, int n) {
+  int64_t t = 0;
+  for (int k = p.n_begin; k < n; ++k) {
+    const int mk = p.ms_m[k], sk = p.ms_s[k];
+    if (mk > 0 && sk > 0) t += (int64_t)mk * sk;
+  }
+  return t;
+}
+
+// One block: does every block of steps fit the Horner buffers?  Sets *flag = 0 (three-stage path)
+// or 1 (the fused backward runs).
+__global__ void __launch_bounds__(256) k_plan(PlanParams p) {
+  __shared__ int over;
+  if (threadIdx.x == 0) over = 0;
+  __syncthreads();
+  const int nb = (p.N + p.steps_per_block - 1) / p.steps_per_block;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    int64_t t = 0;
+    const int n1 = min(p.N, (b + 1) * p.steps_per_block);
+    for (int n = b * p.steps_per_block; n < n1; ++n) {
+      const int m = p.ms_m[n], s = p.ms_s[n];
+      if (m > 0 && s > 0) t += (int64_t)m * s;
+    }
+    if (t > p.cap_terms) over = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *p.flag = over;
+}
+
+// chi_N = -(w_fid g / n^2) phi_T + (w_forbid/(N n)) Omega psi_N (+ the C3 source of psi_N) on the CTA's rows.
+__device__ __forceinline__ void costate_final(const SweepParams& p, double2* chi, int64_t col0, int r0, int nrows,
+                                              double c2w) {
+  const double nS = (double)p.n_states;
+  const double2 g = *p.g_final;
+  double2 coefA = make_double2(-p.w_fid * g.x / (nS * nS), -p.w_fid * g.y / (nS * nS));
+  if (p.w_tint != 0.0) {
+    const double c3w = -p.w_tint / ((double)p.N * nS * nS);
+    const double2 gN = p.g3[p.N - 1];
+    coefA.x = fma(c3w, gN.x, coefA.x);
+    coefA.y = fma(c3w, gN.y, coefA.y);
+  }
+  for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+    double2 ch = cmul(coefA, p.target[col0 + i]);
+    if (c2w != 0.0) {
+      const double w = c2w * p.omega[r0 + i];
+      const double2 v = p.psiN[col0 + i];
+      ch.x = fma(w, v.x, ch.x);
+      ch.y = fma(w, v.y, ch.y);
+    }
+    chi[i] = ch;
+  }
+}
+
+// Costate chain over the block [n_begin, n_end), one team per column (the forward sweep's partition
+// and shared-memory layout; its psi rows hold chi here).  chi enters from p.chi_io (or chi_N in the
+// last block) and leaves through it.
+template <typename T, bool CLUSTER>
+__global__ void __launch_bounds__(512, 1) k_costate(SweepParams p) {
+  using C2 = cx<T>;
+  if (*p.plan_flag != 0) return;   // the fused backward runs instead (the same word for the whole grid)
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double s_u[kMaxControls];
+  __shared__ XTab<T> tab[2];
+  const int part = blockIdx.x;
+  const int col = part / p.CL, rank = part % p.CL;
+  const int r0 = min(rank * p.R, p.dim), r1 = min(r0 + p.R, p.dim), nrows = r1 - r0;
+  const int64_t e0 = p.rowptr[r0];
+  const int nnz_loc = (int)(p.rowptr[r1] - e0);
+  const Carve<T> c = carve<T>(smem, p, false, part);
+  C2* const X0 = c.xb;
+  double2* const chi = c.psi;
+  const int R = p.R;
+  if constexpr (CLUSTER) {
+    cg::cluster_group cl = cg::this_cluster();
+    if (threadIdx.x < p.CL) {
+      tab[0].ptr[threadIdx.x] = cl.map_shared_rank(X0, threadIdx.x);
+      tab[1].ptr[threadIdx.x] = cl.map_shared_rank(X0 + R, threadIdx.x);
+    }
+  }
+  sweep_setup(p, c.lrow, c.lcol, r0, nrows, e0, nnz_loc);
+  const int64_t col0 = (int64_t)col * p.dim + r0;
+  const double c2w = (p.omega && p.w_forbid != 0.0) ? p.w_forbid / ((double)p.N * p.n_states) : 0.0;
+  if (p.n_end == p.N)
+    costate_final(p, chi, col0, r0, nrows, c2w);
+  else
+    for (int i = threadIdx.x; i < nrows; i += blockDim.x) chi[i] = p.chi_io[col0 + i];
+  const bool split_rows = nrows <= (int)blockDim.x;
+  int ea = 0, eb = 0, la = 0, lb = 0, ed = -1, c0 = 0, ci = 0;
+  __syncthreads();   // the local pattern written by sweep_setup
+  if (split_rows && (int)threadIdx.x < nrows) {
+    ea = c.lrow[threadIdx.x];
+    eb = c.lrow[threadIdx.x + 1];
+    if (diag_at(p, c.lcol, ea, eb, rank, threadIdx.x)) ed = ea++;
+    c0 = ea;
+    row_segments(c.lcol, c0, eb, &ci, &ea);
+    la = ea;
+    while (la < eb && ((c.lcol[la] >> kOwnerShift) & 0xFFu) < (uint32_t)rank) ++la;
+    lb = la;
+    while (lb < eb && ((c.lcol[lb] >> kOwnerShift) & 0xFFu) == (uint32_t)rank) ++lb;
+  }
+  team_sync<CLUSTER>();
+  C2* const hb = reinterpret_cast<C2*>(p.hbuf);
+  const int64_t hstride = (int64_t)p.n_states * p.dim;   // bulk elements per stored term
+  int64_t toff = block_term_offset(p, p.n_end);
+  for (int n = p.n_end - 1; n >= p.n_begin; --n) {
+    const int m = p.ms_m[n], s = p.ms_s[n];
+    if (s <= 0 || m <= 0) continue;   // flagged by k_schedule; uniform over the team
+    toff -= (int64_t)m * s;
+    load_controls(p, n, s_u);
+    __syncthreads();
+    assemble<T>(p, c.vals, e0, nnz_loc, p.dt / s, s_u);
+    __syncthreads();
+    for (int l = s - 1; l >= 0; --l) {
+      C2* const hl = hb + (toff + (int64_t)l * m) * hstride + col0;   // w_p of substep l: hl[p * hstride + i]
+      const double fm = c_inv_fact[m];
+      for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+        const C2 w = from_d2<T>(cscale(chi[i], fm));
+        X0[i] = w;
+        hl[(int64_t)(m - 1) * hstride + i] = w;
+      }
+      if constexpr (sizeof(C2) == 16) {
+        if (split_rows) {
+          // Same split cluster barrier as the forward sweep: term q reads w_{m-q} from buffer
+          // (q - 1) & 1 and writes w_{m-1-q} to buffer q & 1.
+          __syncthreads();
+          split_arrive<CLUSTER>();
+          const int i = threadIdx.x;
+          for (int q = 1; q <= m; ++q) {
+            const int src = (q - 1) & 1, dst = q & 1;
+            const C2* xs = X0 + src * R;
+            C2 y = czero<C2>();
+            if (i < nrows) {
+              if (ed >= 0) y = diag_mul(c.vals[ed].y, xs[i]);
+              for (int e = la; e < lb; ++e) cmacT(y, c.vals[e], xs[c.lcol[e] & kLocalMask]);
+            }
+            split_wait<CLUSTER>();
+            if (i < nrows) {
+              for (int e = c0; e < ci; ++e) mac_imag(y, c.vals[e].y, xload<T, CLUSTER>(xs, tab[src], c.lcol[e]));
+              for (int e = ci; e < ea; ++e) mac_real(y, c.vals[e].x, xload<T, CLUSTER>(xs, tab[src], c.lcol[e]));
+              const int nl = la - ea, nr = nl + (eb - lb);
+              for (int k = 0; k < nr; ++k) {
+                const int e = k < nl ? ea + k : lb + (k - nl);
+                cmacT(y, c.vals[e], xload<T, CLUSTER>(xs, tab[src], c.lcol[e]));
+              }
+              const double2 ch = chi[i];
+              if (q < m) {
+                y = horner(ch, c_inv_fact[m - q], y);   // w_{m-1-q} = chi/(m-q)! + (-B) w_{m-q}
+                X0[dst * R + i] = y;
+              } else {
+                chi[i] = make_double2(fma(ch.x, c_inv_fact[0], -y.x), fma(ch.y, c_inv_fact[0], -y.y));   // w_{-1}
+              }
+            }
+            if (q < m) {
+              __syncthreads();
+              split_arrive<CLUSTER>();
+              // the global copy of w_{m-1-q} is issued after the arrive: the arrive's release then does
+              // not wait for it (only the next term's does, by when it has long completed)
+              if (i < nrows) hl[(int64_t)(m - 1 - q) * hstride + i] = y;
+            } else {
+              team_sync<CLUSTER>();
+            }
+          }
+          continue;
+        }
+      }
+      team_sync<CLUSTER>();
+      for (int q = 1; q <= m; ++q) {
+        const int src = (q - 1) & 1, dst = q & 1;
+        for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+          const C2 y = row_mv<T, CLUSTER>(c.vals, c.lcol, c.lrow[i], c.lrow[i + 1], X0 + src * R, tab[src]);
+          const double2 ch = chi[i];
+          if (q < m) {
+            const C2 w = horner(ch, c_inv_fact[m - q], y);
+            X0[dst * R + i] = w;
+            hl[(int64_t)(m - 1 - q) * hstride + i] = w;
+          } else {
+            const double2 yd = to_d2(y);
+            chi[i] = make_double2(fma(ch.x, c_inv_fact[0], -yd.x), fma(ch.y, c_inv_fact[0], -yd.y));
+          }
+        }
+        team_sync<CLUSTER>();
+      }
+    }
+    // end of step n: the sources of the state psi_n (n >= 1), C3 then C2 (App. A recursions)
+    if (n >= 1) {
+      if (p.w_tint != 0.0) {
+        const double nS = (double)p.n_states;
+        const double c3w = -p.w_tint / ((double)p.N * nS * nS);
+        const double2 gn = p.g3[n - 1];
+        const double2 cf = make_double2(c3w * gn.x, c3w * gn.y);
+        for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+          const double2 t = p.target[col0 + i];
+          double2 ch = chi[i];
+          ch.x += cf.x * t.x - cf.y * t.y;
+          ch.y += cf.x * t.y + cf.y * t.x;
+          chi[i] = ch;
+        }
+      }
+      if (c2w != 0.0) {
+        const double2* st = step_state(p, n, col) + r0;
+        for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+          const double w = c2w * p.omega[r0 + i];
+          const double2 v = st[i];
+          double2 ch = chi[i];
+          ch.x = fma(w, v.x, ch.x);
+          ch.y = fma(w, v.y, ch.y);
+          chi[i] = ch;
+        }
+      }
+    }
+  }
+  for (int i = threadIdx.x; i < nrows; i += blockDim.x) p.chi_io[col0 + i] = chi[i];
+  team_sync<CLUSTER>();   // no CTA leaves while a team member may still read its shared memory
+}
+
+// Gradient terms of the block's steps, one team of CL CTAs per (step, column): psi^(0) = psi_n from
+// the forward's stored states; per substep l the x chain x_0 = psi^(l), x_{p+1} = B x_p with
+// W_ij += conj(w_p[i]) x_p[j] on the control entries (w_p of substep l from k_costate), and
+// psi^(l+1) = sum_{q<=m} x_q / q! for the next substep; then the step's partials
+// 2 Re sum_ij (C_k)_ij W_ij, C_k = -i dt h_k / s.  Independent across steps and columns.
+template <typename T, bool CLUSTER>
+__global__ void __launch_bounds__(512, 1) k_gradient(SweepParams p) {
+  using C2 = cx<T>;
+  constexpr bool kStage = sizeof(C2) == 8;   // FP32 bulk: W staged per substep in float
+  if (*p.plan_flag != 0) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[32];
+  __shared__ double s_u[kMaxControls];
+  __shared__ XTab<T> tab[2];
+  const int part = blockIdx.x;
+  const int unit = part / p.CL, rank = part % p.CL;
+  const int n = p.n_begin + unit / p.n_states, col = unit % p.n_states;
+  const int out_part = col * p.CL + rank;
+  const int r0 = min(rank * p.R, p.dim), r1 = min(r0 + p.R, p.dim), nrows = r1 - r0;
+  const int64_t e0 = p.rowptr[r0];
+  const int nnz_loc = (int)(p.rowptr[r1] - e0);
+  const SmemLayout L = make_glayout(p.R, p.max_nnz_loc, p.in_smem, (int)sizeof(C2));
+  double2* const scr = p.scratch + (int64_t)part * p.scratch_stride;
+  C2* const X0 = reinterpret_cast<C2*>(smem + L.xbuf);
+  double2* const psi = reinterpret_cast<double2*>(smem + L.psi);
+  double2* const inc = reinterpret_cast<double2*>(smem + L.inc);
+  C2* const vals = L.vals >= 0 ? reinterpret_cast<C2*>(smem + L.vals) : reinterpret_cast<C2*>(scr + p.scr_vals);
+  double2* const W = L.W >= 0 ? reinterpret_cast<double2*>(smem + L.W) : scr + p.scr_W;
+  float2* const Wb = L.Wb >= 0 ? reinterpret_cast<float2*>(smem + L.Wb) : reinterpret_cast<float2*>(scr + p.scr_Wb);
+  int* const lrow = reinterpret_cast<int*>(smem + L.lrow);
+  uint32_t* const lcol = reinterpret_cast<uint32_t*>(smem + L.lcol);
+  const int R = p.R;
+  const int m = p.ms_m[n], s = p.ms_s[n];
+  if (m <= 0 || s <= 0) {   // flagged by k_schedule (the call returns an error); keep the partials defined
+    if (threadIdx.x < p.K) p.part_grad[((int64_t)out_part * p.N + n) * p.K + threadIdx.x] = 0.0;
+    return;   // uniform over the team: no team member waits at a barrier or reads this CTA's memory
+  }
+  if constexpr (CLUSTER) {
+    cg::cluster_group cl = cg::this_cluster();
+    if (threadIdx.x < p.CL) {
+      tab[0].ptr[threadIdx.x] = cl.map_shared_rank(X0, threadIdx.x);
+      tab[1].ptr[threadIdx.x] = cl.map_shared_rank(X0 + R, threadIdx.x);
+    }
+  }
+  sweep_setup(p, lrow, lcol, r0, nrows, e0, nnz_loc);
+  load_controls(p, n, s_u);
+  const double2* st = step_state(p, n, col) + r0;
+  for (int i = threadIdx.x; i < nrows; i += blockDim.x) psi[i] = st[i];
+  for (int e = threadIdx.x; e < nnz_loc; e += blockDim.x) {
+    W[e] = make_double2(0.0, 0.0);
+    if (kStage) Wb[e] = make_float2(0.0f, 0.0f);
+  }
+  __syncthreads();
+  assemble<T>(p, vals, e0, nnz_loc, p.dt / s, s_u);
+  const bool one_row = sizeof(C2) == 16 && nrows <= (int)blockDim.x;
+  int ea = 0, eb = 0, la = 0, l1 = 0, ed = -1, c0 = 0, ci = 0;
+  {
+    int nloc = 1 << 30;
+    if (one_row && (int)threadIdx.x < nrows) {
+      ea = lrow[threadIdx.x];
+      eb = lrow[threadIdx.x + 1];
+      if (diag_at(p, lcol, ea, eb, rank, threadIdx.x)) ed = ea++;
+      c0 = ea;
+      row_segments(lcol, c0, eb, &ci, &ea);
+      int a = ea;
+      while (a < eb && ((lcol[a] >> kOwnerShift) & 0xFFu) < (uint32_t)rank) ++a;
+      int b = a;
+      while (b < eb && ((lcol[b] >> kOwnerShift) & 0xFFu) == (uint32_t)rank) ++b;
+      la = a;
+      nloc = b - a;
+    }
+    const int wmin = __reduce_min_sync(0xffffffffu, nloc);
+    l1 = wmin == (1 << 30) ? 0 : wmin;
+  }
+  const C2* const hb = reinterpret_cast<const C2*>(p.hbuf);
+  const int64_t hstride = (int64_t)p.n_states * p.dim;
+  const int64_t toff = block_term_offset(p, n);
+  __syncthreads();   // vals and the row segments
+  for (int l = 0; l < s; ++l) {
+    const C2* const hl = hb + (toff + (int64_t)l * m) * hstride + (int64_t)col * p.dim + r0;
+    const bool last = l == s - 1;
+    for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+      X0[i] = from_d2<T>(psi[i]);
+      inc[i] = make_double2(0.0, 0.0);
+    }
+    bool split_done = false;
+    if constexpr (sizeof(C2) == 16) {
+     if (one_row) {
+      split_done = true;
+      // Split cluster barrier (as in the fused sweep's phase B): term p sums the first l1 local
+      // entries before the wait, the rest after it; x_{p+1} goes to buffer (p + 1) & 1.  The last
+      // term of the substep ends with a full barrier: the next substep overwrites buffer 0.
+      __syncthreads();
+      split_arrive<CLUSTER>();
+      const int i = threadIdx.x;
+      const bool act = i < nrows;
+      const int nleft = la - ea, nrest = (eb - ea) - l1;
+      C2 wnext = act ? __ldcg(hl + i) : czero<C2>();
+      for (int pp = 0; pp < m; ++pp) {
+        const int src = pp & 1, dst = src ^ 1;
+        const bool more = pp < m - 1 || !last;
+        const C2* xs = X0 + src * R;
+        const C2 wp = wnext;
+        C2 y0 = czero<C2>();
+        auto wacc = [&](int e, const C2 x) {
+          double2 acc = W[e];
+          cmac_conjT(acc, wp, x);
+          W[e] = acc;
+        };
+        if (act) {
+          if (pp + 1 < m) wnext = __ldcg(hl + (int64_t)(pp + 1) * hstride + i);
+          if (ed >= 0) {
+            const C2 x = xs[i];
+            if (more) y0 = diag_mul(vals[ed].y, x);
+            if (lcol[ed] & kCtrlBit) wacc(ed, x);
+          }
+          for (int k = 0; k < l1; ++k) {
+            const int e = la + k;
+            const uint32_t enc = lcol[e];
+            const C2 x = xs[enc & kLocalMask];
+            if (more) cmacT(y0, vals[e], x);
+            if (enc & kCtrlBit) wacc(e, x);
+          }
+        }
+        split_wait<CLUSTER>();
+        if (act) {
+          for (int e = c0; e < ci; ++e) {
+            const uint32_t enc = lcol[e];
+            const C2 x = xload<T, CLUSTER>(xs, tab[src], enc);
+            if (more) mac_imag(y0, vals[e].y, x);
+            if (enc & kCtrlBit) wacc(e, x);
+          }
+          for (int e = ci; e < ea; ++e) {
+            const uint32_t enc = lcol[e];
+            const C2 x = xload<T, CLUSTER>(xs, tab[src], enc);
+            if (more) mac_real(y0, vals[e].x, x);
+            if (enc & kCtrlBit) wacc(e, x);
+          }
+          for (int k = 0; k < nrest; ++k) {
+            const int e = k < nleft ? ea + k : la + l1 + (k - nleft);
+            const uint32_t enc = lcol[e];
+            const C2 x = xload<T, CLUSTER>(xs, tab[src], enc);
+            if (more) cmacT(y0, vals[e], x);
+            if (enc & kCtrlBit) wacc(e, x);
+          }
+          if (more) {
+            if (pp < m - 1) X0[dst * R + i] = y0;   // x_{p+1} = B^{p+1} psi^(l), unscaled
+            double2 a = inc[i];
+            const double f = c_inv_fact[pp + 1];
+            a.x = fma(y0.x, f, a.x);
+            a.y = fma(y0.y, f, a.y);
+            inc[i] = a;
+          }
+        }
+        if (pp < m - 1) {
+          __syncthreads();
+          split_arrive<CLUSTER>();
+        } else {
+          team_sync<CLUSTER>();
+        }
+      }
+     }
+    }
+    if (!split_done) {
+      team_sync<CLUSTER>();
+      for (int pp = 0; pp < m; ++pp) {
+        const int src = pp & 1, dst = src ^ 1;
+        const bool more = pp < m - 1 || !last;
+        const C2* xs = X0 + src * R;
+        for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+          const C2 wp = __ldcg(hl + (int64_t)pp * hstride + i);
+          C2 y0 = czero<C2>(), y1 = czero<C2>();
+          const int ra = lrow[i], rb = lrow[i + 1];
+          auto wacc = [&](int e, const C2 x) {
+            if constexpr (kStage) {
+              float2 acc = Wb[e];
+              cmac_conjT(acc, wp, x);
+              Wb[e] = acc;
+            } else {
+              double2 acc = W[e];
+              cmac_conjT(acc, wp, x);
+              W[e] = acc;
+            }
+          };
+          int e = ra;
+          for (; e + 2 <= rb; e += 2) {
+            const uint32_t q0 = lcol[e], q1 = lcol[e + 1];
+            const C2 x0 = xload<T, CLUSTER>(xs, tab[src], q0);
+            const C2 x1 = xload<T, CLUSTER>(xs, tab[src], q1);
+            if (more) {
+              cmacT(y0, vals[e], x0);
+              cmacT(y1, vals[e + 1], x1);
+            }
+            if (q0 & kCtrlBit) wacc(e, x0);
+            if (q1 & kCtrlBit) wacc(e + 1, x1);
+          }
+          if (e < rb) {
+            const uint32_t q0 = lcol[e];
+            const C2 x0 = xload<T, CLUSTER>(xs, tab[src], q0);
+            if (more) cmacT(y0, vals[e], x0);
+            if (q0 & kCtrlBit) wacc(e, x0);
+          }
+          if (more) {
+            const C2 y = make_cx<T>(y0.x + y1.x, y0.y + y1.y);
+            if (pp < m - 1) X0[dst * R + i] = y;
+            const double2 yd = to_d2(y);
+            double2 a = inc[i];
+            const double f = c_inv_fact[pp + 1];
+            a.x = fma(yd.x, f, a.x);
+            a.y = fma(yd.y, f, a.y);
+            inc[i] = a;
+          }
+        }
+        team_sync<CLUSTER>();
+      }
+      if constexpr (kStage) {   // fold the substep's FP32 sums into the FP64 accumulators (row owner)
+        for (int i = threadIdx.x; i < nrows; i += blockDim.x)
+          for (int e = lrow[i]; e < lrow[i + 1]; ++e)
+            if (lcol[e] & kCtrlBit) {
+              const float2 b = Wb[e];
+              double2 a = W[e];
+              a.x += b.x;
+              a.y += b.y;
+              W[e] = a;
+              Wb[e] = make_float2(0.0f, 0.0f);
+            }
+      }
+    }
+    if (!last)
+      for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+        double2 v = psi[i];
+        const double2 a = inc[i];
+        v.x += a.x;
+        v.y += a.y;
+        psi[i] = v;   // psi^(l+1)
+      }
+  }
+  __syncthreads();
+  grad_partials(p, W, rank, out_part, n, s, e0, red);
+  team_sync<CLUSTER>();   // no CTA leaves while a team member may still read its shared memory
+}
+
 // ------------------------------------------------------------------ finalize (one block)
 
 __global__ void __launch_bounds__(256) k_finalize(FinalizeParams p) {
@@ -1321,8 +1803,9 @@ __global__ void k_grad_reduce(GradReduceParams p) {
   const int64_t total = (int64_t)p.K * p.N;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
     const int k = (int)(idx / p.N), n = (int)(idx % p.N);
+    const int n_parts = (p.plan_flag && *p.plan_flag != 0) ? p.n_parts_alt : p.n_parts;
     double acc = 0.0;
-    for (int part = 0; part < p.n_parts; ++part) acc += p.part_grad[((int64_t)part * p.N + n) * p.K + k];
+    for (int part = 0; part < n_parts; ++part) acc += p.part_grad[((int64_t)part * p.N + n) * p.K + k];
     p.grad[idx] = acc + p.w_amp * 2.0 * p.u[idx] / (double)p.N;
   }
 }
@@ -1497,6 +1980,70 @@ int split_capacity(int precision, int CL, int smem_bytes, int threads) {
                : capacity_of(k_backward_split<double, false>, CL, smem_bytes, threads);
   cudaGetLastError();
   return r;
+}
+
+cudaError_t launch_plan(const PlanParams& p, cudaStream_t st) {
+  k_plan<<<1, 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename KernelT>
+static cudaError_t launch_role(KernelT kern, const SweepParams& p, int blocks, int smem_bytes, int threads, int priority,
+                               bool use_priority, cudaStream_t st) {
+  cudaError_t e = ensure_constants();
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem_bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  int na = 0;
+  if (p.CL > 1) {
+    if (p.CL > 8) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
+    attr[na].id = cudaLaunchAttributeClusterDimension;
+    attr[na].val.clusterDim.x = p.CL;
+    attr[na].val.clusterDim.y = 1;
+    attr[na].val.clusterDim.z = 1;
+    ++na;
+  }
+  if (use_priority) {
+    attr[na].id = cudaLaunchAttributePriority;
+    attr[na].val.priority = priority;
+    ++na;
+  }
+  cfg.attrs = na ? attr : nullptr;
+  cfg.numAttrs = na;
+  e = cudaLaunchKernelEx(&cfg, kern, p);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_costate(const SweepParams& p, int precision, int smem_bytes, int threads, int priority,
+                           cudaStream_t st) {
+  const int blocks = p.n_states * p.CL;
+  if (precision == 1) {
+    if (p.CL > 1) return launch_role(k_costate<float, true>, p, blocks, smem_bytes, threads, priority, true, st);
+    return launch_role(k_costate<float, false>, p, blocks, smem_bytes, threads, priority, true, st);
+  }
+  if (p.CL > 1) return launch_role(k_costate<double, true>, p, blocks, smem_bytes, threads, priority, true, st);
+  return launch_role(k_costate<double, false>, p, blocks, smem_bytes, threads, priority, true, st);
+}
+
+cudaError_t launch_gradient(const SweepParams& p, int precision, int smem_bytes, int threads, cudaStream_t st) {
+  const int blocks = (p.n_end - p.n_begin) * p.n_states * p.CL;
+  if (blocks <= 0) return cudaSuccess;
+  if (precision == 1) {
+    if (p.CL > 1) return launch_role(k_gradient<float, true>, p, blocks, smem_bytes, threads, 0, false, st);
+    return launch_role(k_gradient<float, false>, p, blocks, smem_bytes, threads, 0, false, st);
+  }
+  if (p.CL > 1) return launch_role(k_gradient<double, true>, p, blocks, smem_bytes, threads, 0, false, st);
+  return launch_role(k_gradient<double, false>, p, blocks, smem_bytes, threads, 0, false, st);
 }
 
 cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t st) {

@@ -19,6 +19,9 @@ namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;   // 16 MiB
 constexpr size_t kNoAllocScratchElems = kNoAllocScratchBytes / sizeof(double2);
+// Largest substep count accepted: the same cap as the (m, s) table of the descriptor path.  It bounds
+// one call's sequential work (s * m sparse products per column in one CTA).
+constexpr int32_t kNoAllocMaxS = 4096;
 
 // Shared by every call on a device; keeps whatever the last call left in it.
 static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocScratchElems];
@@ -30,8 +33,10 @@ double2* g_scratch_addr[kMaxDevices] = {nullptr};
 // psi_out = (e^{B}_m)^s psi_in with B = -i dt H / s: the forward sweep's inner loop for one step
 // (b_q = (B/q) b_{q-1}, summed per substep), one CTA per column, the three working vectors of a
 // column in the static scratch array.  Every buffer is written before it is read, so nothing in
-// the scratch needs to start at zero.
-__global__ void __launch_bounds__(256) k_taylor_step_noalloc(int dim, const int64_t* __restrict__ rowptr,
+// the scratch needs to start at zero.  Each row's entry range is clamped to [0, nnz) and column
+// indices outside [0, dim) are skipped, so a malformed rowptr or colind cannot make the kernel read
+// outside the caller's arrays.
+__global__ void __launch_bounds__(256) k_taylor_step_noalloc(int dim, int64_t nnz, const int64_t* __restrict__ rowptr,
                                                              const int32_t* __restrict__ colind,
                                                              const double2* __restrict__ vals, double scale, int m,
                                                              int s, const double2* psi_in, double2* psi_out,
@@ -51,7 +56,8 @@ __global__ void __launch_bounds__(256) k_taylor_step_noalloc(int dim, const int6
       const double iq = 1.0 / q;
       for (int i = threadIdx.x; i < dim; i += blockDim.x) {
         double2 y = make_double2(0.0, 0.0);
-        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        const int64_t ea = max(rowptr[i], (int64_t)0), eb = min(rowptr[i + 1], nnz);
+        for (int64_t e = ea; e < eb; ++e) {
           const double2 v = vals[e];
           const double2 b = make_double2(scale * v.y, -scale * v.x);   // -i (dt/s) H_ij
           const int32_t j = colind[e];
@@ -83,13 +89,14 @@ grape_status noalloc_fail(grape_status st, const std::string& msg) {
 
 }  // namespace
 
-extern "C" grape_status grape_taylor_step_noalloc(int64_t dim, int32_t n_states, const int64_t* rowptr,
+extern "C" grape_status grape_taylor_step_noalloc(int64_t dim, int64_t nnz, int32_t n_states, const int64_t* rowptr,
                                                   const int32_t* colind, const double* values, double dt, int32_t m,
                                                   int32_t s, const double* psi_in, double* psi_out, void* stream) {
   if (dim < 1 || dim >= (int64_t(1) << 31) || n_states < 1)
     return noalloc_fail(GRAPE_EINVAL, "grape_taylor_step_noalloc: dim and n_states must be >= 1");
-  if (m < 1 || m > grape::kMaxTaylor || s < 1)
-    return noalloc_fail(GRAPE_EINVAL, "grape_taylor_step_noalloc: need 1 <= m <= 60 and s >= 1");
+  if (nnz < 0) return noalloc_fail(GRAPE_EINVAL, "grape_taylor_step_noalloc: nnz must be >= 0");
+  if (m < 1 || m > grape::kMaxTaylor || s < 1 || s > kNoAllocMaxS)
+    return noalloc_fail(GRAPE_EINVAL, "grape_taylor_step_noalloc: need 1 <= m <= 60 and 1 <= s <= 4096");
   if (!(dt > 0.0) || !std::isfinite(dt)) return noalloc_fail(GRAPE_EINVAL, "grape_taylor_step_noalloc: dt must be finite and > 0");
   if (!rowptr || !colind || !values || !psi_in || !psi_out)
     return noalloc_fail(GRAPE_EINVAL, "grape_taylor_step_noalloc: NULL pointer");
@@ -116,7 +123,7 @@ extern "C" grape_status grape_taylor_step_noalloc(int64_t dim, int32_t n_states,
     scratch = g_scratch_addr[dev];
   }
   k_taylor_step_noalloc<<<n_states, 256, 0, static_cast<cudaStream_t>(stream)>>>(
-      (int)dim, rowptr, colind, reinterpret_cast<const double2*>(values), dt / s, m, s,
+      (int)dim, nnz, rowptr, colind, reinterpret_cast<const double2*>(values), dt / s, m, s,
       reinterpret_cast<const double2*>(psi_in), reinterpret_cast<double2*>(psi_out), scratch);
   e = cudaGetLastError();
   if (e != cudaSuccess) return noalloc_fail(GRAPE_ECUDA, std::string("launch k_taylor_step_noalloc: ") + cudaGetErrorString(e));

@@ -211,6 +211,98 @@ def test_split_and_fused_backward_agree_bitwise(name, N, cluster, drive):
     assert c3 == c2 and np.array_equal(g3, g2)
 
 
+@pytest.mark.parametrize("name,N,cluster,gcl,steps,drive,prec", [
+    ("c2_gate_d80", 60, 0, 0, 0, 10.0, "fp64"),
+    ("c2_gate_d80", 37, 4, 2, 5, 20.0, "fp64"),
+    ("c1_state_transfer_d30", 40, 16, 4, 1, 5.0, "fp64"),
+    ("c2_gate_d80", 25, 12, 16, 25, 10.0, "fp64"),
+    ("c1_state_transfer_d30", 21, 7, 3, 4, 3.0, "fp64"),
+    ("c2_gate_d80", 30, 0, 0, 0, 10.0, "fp32_bulk"),
+    ("c2_gate_d80", 30, 8, 2, 3, 10.0, "fp32_bulk"),
+])
+def test_three_stage_backward_matches_the_oracle(name, N, cluster, gcl, steps, drive, prec):
+    """Costate chain + per-step gradient kernels on the states the forward stored: against the oracle
+    and against the fused one-team backward, for team sizes 1..16 of both kernels and block lengths
+    from one step to all steps (with a ragged last block)."""
+    p = build_config(name, n_steps=N)
+    u = p.u0 * drive
+    hg = _hg(p, cluster=cluster, backward_mode=3, grad_cluster=gcl, block_steps=steps, precision=prec)
+    inf = hg.info()
+    assert inf["backward_mode"] == 3 and inf["ckpt_every"] == 1
+    assert (gcl == 0 or inf["grad_cluster"] == gcl) and (steps == 0 or inf["block_steps"] == min(steps, N))
+    cost, grad = hg.cost_and_grad(u)
+    assert hg.info()["fused_fallback"] == 0
+    tol = (COST_RTOL, GRAD_RTOL) if prec == "fp64" else (FP32_RTOL, FP32_RTOL)
+    _check(p, u, cost, grad, *tol)
+    fused = _hg(p, cluster=cluster, backward_mode=1, precision=prec)
+    c1, g1 = fused.cost_and_grad(u)
+    assert c1 == cost                          # same forward sweep
+    gtol = 1e-12 if prec == "fp64" else 1e-6
+    assert np.linalg.norm(g1 - grad) <= gtol * np.linalg.norm(g1)
+    c2, g2 = hg.cost_and_grad(u)               # repeatable: block buffers and flags reset every call
+    assert c2 == cost and np.array_equal(g2, grad)
+
+
+@pytest.mark.parametrize("dim,K,n,N,cluster,gcl,steps", [
+    (2, 1, 1, 3, 1, 1, 1), (33, 3, 2, 9, 2, 3, 4), (130, 4, 3, 7, 8, 5, 2), (257, 3, 2, 5, 16, 16, 5),
+    (97, 1, 5, 4, 0, 0, 0), (65, 5, 2, 6, 4, 1, 3),
+])
+def test_three_stage_random_ragged_problems(dim, K, n, N, cluster, gcl, steps):
+    p = random_problem(dim, K, n, N, seed=2000 + dim + K + n + N)
+    hg = _hg(p, cluster=cluster, backward_mode=3, grad_cluster=gcl, block_steps=steps)
+    cost, grad = hg.cost_and_grad(p.u0)
+    assert hg.info()["fused_fallback"] == 0
+    _check(p, p.u0, cost, grad)
+
+
+def _weak_drift_problem():
+    p = random_problem(40, 2, 2, 6, seed=77)
+    p.H0 = p.H0 * 1e-3
+    p.Hk = [h * 1e-3 for h in p.Hk]
+    return p
+
+
+def test_three_stage_block_buffers_grow_with_the_schedule():
+    """The block buffers start from the drift's schedule; a call whose controls need more Taylor terms
+    grows them (outside stream capture) and still runs the three stages."""
+    p = _weak_drift_problem()
+    hg = _hg(p, backward_mode=3, block_steps=1)
+    b0 = hg.info()["device_bytes"]
+    u = p.u0 * 2e4
+    cost, grad = hg.cost_and_grad(u)
+    inf = hg.info()
+    assert inf["fused_fallback"] == 0 and inf["device_bytes"] > b0
+    _check(p, u, cost, grad)
+
+
+def test_three_stage_under_stream_capture_falls_back_when_the_buffers_are_small():
+    """Inside a CUDA-graph capture the schedule cannot be read back: if the block buffers are too small
+    for it, the device-side plan runs the fused backward instead, with the same result."""
+    import torch
+    p = _weak_drift_problem()
+    hg = _hg(p, backward_mode=3, block_steps=1)
+    dev = torch.device("cuda", 0)
+    s = torch.cuda.Stream(dev)
+    cost = torch.zeros((), dtype=torch.float64, device=dev)
+    grad = torch.zeros((p.n_controls, p.n_steps), dtype=torch.float64, device=dev)
+    u_small = torch.tensor(p.u0, dtype=torch.float64, device=dev)
+    with torch.cuda.stream(s):
+        hg.cost_device(u_small, cost, s)
+        hg.grad_device(grad, s)
+    torch.cuda.synchronize()
+    assert hg.info()["fused_fallback"] == 0
+    u_big = p.u0 * 2e4
+    ug = torch.tensor(u_big, dtype=torch.float64, device=dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        hg.cost_device(ug, cost, s)
+        hg.grad_device(grad, s)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert hg.info()["fused_fallback"] == 1
+    _check(p, u_big, float(cost.item()), grad.cpu().numpy())
+
+
 def test_medium_two_transmon_cavity_parity():
     """Two transmons x cavity (the d = 4000 system's structure) at d = 4*4*40 = 640, clustered."""
     from workloads.transmon import _gate_problem, _subspace_two, two_transmon_cavity
@@ -597,21 +689,21 @@ def test_closed_form_golden_values(propagator):
 
 
 def test_c3_full_size_in_the_bench_configuration():
-    """d = 4000, N = 2000 with the partitions bench.py times (forward 16 CTAs per column, two-team
-    backward): equal to the one-team backward within rounding, and sampled gradient entries equal to
-    central differences of the GPU's own cost (schedule unchanged by the perturbation)."""
+    """d = 4000, N = 2000 with the partitions bench.py times (forward 16 CTAs per column, three-stage
+    backward): the same cost as the fused one-team backward with the forward's partition and its
+    gradient within rounding, and sampled gradient entries equal to central differences of the GPU's
+    own cost (schedule unchanged by the perturbation)."""
     p = build_config("c3_gate_d4000")
     hg = _hg(p)
     inf = hg.info()
-    assert inf["backward_mode"] == 2 and inf["cluster_forward"] == 16
+    assert inf["backward_mode"] == 3 and inf["cluster_forward"] == 16
     u = np.array(p.u0)
     cost, grad = hg.cost_and_grad(u)
+    assert hg.info()["fused_fallback"] == 0
     m0, s0, _ = hg.schedule()
-    # the one-team problem gets the backward's team size for its forward sweep as well, so the two
-    # differ by rounding only (bitwise equality at equal partitions is tested above)
-    one_team = _hg(p, cluster=inf["cluster"], backward_mode=1)
+    one_team = _hg(p, cluster=inf["cluster_forward"], backward_mode=1)
     c1, g1 = one_team.cost_and_grad(u)
-    assert abs(c1 - cost) <= 1e-13 * abs(cost)
+    assert c1 == cost
     assert np.linalg.norm(g1 - grad) <= 1e-11 * np.linalg.norm(grad)
     one_team.close()
     h = 1e-5
