@@ -32,9 +32,9 @@ if ROOT not in sys.path:
 
 METRIC = "cost+gradient evals/s & peak HBM: HG kernels vs torch full-AD, 1 GB300"
 DEFAULT_WORKLOAD = "c3_gate_d4000"
-FP64_PEAK_GFLOPS = 1250.0        # GB300 nominal FP64 (non-tensor) rate, all 152 SMs
+FP64_NOMINAL_GFLOPS = 152 * 2 * 2 * 2.07   # 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz (used if the probe fails)
+HBM_FALLBACK_GBS = 6800.0                  # recipe fallback when MEASURED_PEAKS.json is absent
 L2_FLUSH_BYTES = 256 << 20       # > 129 MB L2
-LAUNCHES_PER_EVAL = 5            # k_schedule, k_forward, k_finalize, k_backward(_split), k_grad_reduce
 
 
 def parse_args(argv=None):
@@ -143,25 +143,80 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ algorithmic work model
 
-def backward_flops(schedule_m, schedule_s, nnz: int, nnz_ctrl_entries: int, dim: int, n: int) -> float:
-    """FP64 flops one k_backward launch must do (complex multiply-add = 8 flops).
+def entry_classes(p):
+    """Entries of the union pattern by the real work one product y += B_ij x_j takes per column:
+    the diagonal when every H_ii is real (B_ii imaginary: 2 multiplies), off-diagonal entries whose
+    every H_ij term is real or every one imaginary (B_ij imaginary or real: 2 multiply-adds, 4 flops),
+    the rest (a complex multiply-add, 8 flops).  Returns (n_diag, n_single, n_general, n_ctrl)."""
+    import scipy.sparse as sp
+    ops = [sp.csr_matrix(p.H0)] + [sp.csr_matrix(h) for h in p.Hk]
+    union = abs(ops[0]).astype(bool)
+    for h in ops[1:]:
+        union = union + abs(h).astype(bool)
+    union = union.tocoo()
+    rows, cols = union.row, union.col
+    re_any = np.zeros(rows.size, bool)
+    im_any = np.zeros(rows.size, bool)
+    ctrl = np.zeros(rows.size, bool)
+    for k, h in enumerate(ops):
+        v = np.asarray(h.tocsr()[rows, cols]).ravel()
+        re_any |= v.real != 0
+        im_any |= v.imag != 0
+        if k > 0:
+            ctrl |= v != 0
+    diag = rows == cols
+    diag_real = bool(np.all(~im_any[diag]))
+    n_diag = int(diag.sum()) if diag_real else 0
+    single = (~diag) & (re_any ^ im_any)
+    n_single = int(single.sum())
+    return n_diag, n_single, int(rows.size) - n_diag - n_single, int(ctrl.sum())
 
-    Per substep (s_n of them per step): phase A applies -B to two columns-blocks for m_n terms
-    (psi re-propagation and the Horner costate chain), phase B applies B for m_n - 1 terms and
-    accumulates conj(w_p) x_p on the control entries for m_n terms.  Each Taylor term also
-    scales and accumulates d*n complex numbers (4 flops each).
-    """
+
+def product_flops(cls, dim: int) -> float:
+    """FP64 flops of one Taylor term's product and its row update, per column."""
+    n_diag, n_single, n_general, _ = cls
+    return 2.0 * n_diag + 4.0 * n_single + 8.0 * n_general + 4.0 * dim
+
+
+def forward_flops(schedule_m, schedule_s, cls, dim: int, n: int) -> float:
+    """k_forward: m_n s_n terms per step (Eqs. (eBm equation), (eBmpsi))."""
+    return float(np.sum(np.asarray(schedule_m, float) * np.asarray(schedule_s, float))) * product_flops(cls, dim) * n
+
+
+def costate_flops(schedule_m, schedule_s, cls, dim: int, n: int) -> float:
+    """k_costate (all launches of one evaluation): one product and one Horner update per term."""
+    return forward_flops(schedule_m, schedule_s, cls, dim, n)
+
+
+def gradient_flops(schedule_m, schedule_s, cls, dim: int, n: int) -> float:
+    """k_gradient (all launches of one evaluation): per step m s accumulations conj(w_p[i]) x_p[j] on the
+    control entries (8 flops each) and m s - 1 products with their increment updates."""
+    mu = np.asarray(schedule_m, float) * np.asarray(schedule_s, float)
+    return float(np.sum(mu * 8.0 * cls[3] + (mu - 1.0) * product_flops(cls, dim))) * n
+
+
+def fused_backward_flops(schedule_m, schedule_s, cls, dim: int, n: int) -> float:
+    """The one-team or two-team backward: per substep 2m products (psi chain, Horner chain), m - 1
+    products of the x chain and m accumulations on the control entries."""
     tot = 0.0
     for m, s in zip(schedule_m, schedule_s):
-        m = int(m)
-        s = int(s)
-        spmm_terms = 2 * m + (m - 1)
-        tot += s * (spmm_terms * (8.0 * nnz * n + 4.0 * dim * n) + m * 8.0 * nnz_ctrl_entries * n)
-    return tot
+        m, s = int(m), int(s)
+        tot += s * ((3 * m - 1) * product_flops(cls, dim) + m * 8.0 * cls[3])
+    return tot * n
 
 
-def forward_flops(schedule_m, schedule_s, nnz: int, dim: int, n: int) -> float:
-    return sum(int(s) * int(m) * (8.0 * nnz * n + 4.0 * dim * n) for m, s in zip(schedule_m, schedule_s))
+def measured_peaks():
+    """HBM GB/s and its source: MEASURED_PEAKS.json when the driver wrote one, else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        for key in ("hbm_gbs", "hbm_GBps", "hbm"):
+            if key in d:
+                return float(d[key]), "MEASURED_PEAKS.json"
+    except Exception:
+        pass
+    return HBM_FALLBACK_GBS, "fallback (no MEASURED_PEAKS.json)"
 
 
 def read_traffic(kernel: str, workload: str):
@@ -310,6 +365,12 @@ def run_ours(args):
     info = hg.info()
     sched_m, sched_s, norms = hg.schedule()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    import ctypes
+    fp64_peak = ctypes.c_double(0.0)
+    peak_ok = lib().grape_fp64_fma_rate(local, ctypes.byref(fp64_peak)) == 0 and fp64_peak.value > 0
+    fp64_peak = fp64_peak.value if peak_ok else FP64_NOMINAL_GFLOPS
+    hg.set_kernel_tracing(True)
+    hg.kernel_times()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
@@ -328,6 +389,8 @@ def run_ours(args):
         torch.distributed.barrier()
     clk = clocks.stop()
     hg.sync_status(stream)
+    ktimes = hg.kernel_times()
+    hg.set_kernel_tracing(False)
     step_ms = [ev[i][0].elapsed_time(ev[i][2]) for i in range(args.steps)]
     fwd_ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
     bwd_ms = [ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]
@@ -354,7 +417,6 @@ def run_ours(args):
     cost_h = torch.zeros(1, dtype=torch.float64).pin_memory()
     grad_h = torch.zeros((p.n_controls, p.n_steps), dtype=torch.float64).pin_memory()
     e2e_times = []
-    import ctypes
     for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         flush.zero_()
         torch.cuda.synchronize()
@@ -376,22 +438,52 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return
 
-    # ---- roofline of the dominant kernel (k_backward; FP64-pipe bound)
+    # ---- roofline: every sweep kernel's algorithmic FP64 flops per launch over its live CUDA-event
+    # duration (traced during the timed steps); the dominant kernel (largest summed time) is reported
+    cls = entry_classes(p)
+    mode = info["backward_mode"]
+    total_flops = {"k_forward": forward_flops(sched_m, sched_s, cls, p.dim, p.n_states)}
+    if mode == 3:
+        total_flops["k_costate"] = costate_flops(sched_m, sched_s, cls, p.dim, p.n_states)
+        total_flops["k_gradient"] = gradient_flops(sched_m, sched_s, cls, p.dim, p.n_states)
+    else:
+        total_flops["k_backward"] = fused_backward_flops(sched_m, sched_s, cls, p.dim, p.n_states)
+    kern = {}
+    for name, fl in total_flops.items():
+        t = ktimes[name]
+        if t["launches"] == 0:
+            continue
+        per_launch_ms = t["ms"] / t["launches"]
+        launches_per_eval = t["launches"] / args.steps
+        flops_per_launch = fl / launches_per_eval
+        ach = flops_per_launch / (per_launch_ms * 1e-3) / 1e9
+        kern[name] = {"launches_per_eval": launches_per_eval, "avg_launch_ms": round(per_launch_ms, 4),
+                      "ms_per_eval": round(t["ms"] / args.steps, 2), "flops_per_launch": flops_per_launch,
+                      "achieved": round(ach, 2), "frac": round(ach / fp64_peak, 4)}
+    dom = max(kern, key=lambda k: kern[k]["ms_per_eval"])
     nnz = info["union_nnz"]
-    ctrl_entries = hg_ctrl_entry_count(p)
-    bflops = backward_flops(sched_m, sched_s, nnz, ctrl_entries, p.dim, p.n_states)
-    fflops = forward_flops(sched_m, sched_s, nnz, p.dim, p.n_states)
-    bwd_s = statistics.mean(bwd_ms) / 1e3
-    fwd_s = statistics.mean(fwd_ms) / 1e3
-    achieved = bflops / bwd_s / 1e9
-    traffic = read_traffic("k_backward_split" if info["backward_mode"] == 2 else "k_backward", args.workload)
-    bwd_kernel = "k_backward_split" if info["backward_mode"] == 2 else "k_backward"
-    roofline = {"bound": "alu", "kernel": bwd_kernel, "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS,
-                "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": traffic,
-                "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (no measured FP64 peak in MEASURED_PEAKS)",
-                "flops_per_launch": bflops, "launch_ms": round(bwd_s * 1e3, 3),
-                "forward": {"kernel": "k_forward", "achieved": round(fflops / fwd_s / 1e9, 2), "launch_ms": round(fwd_s * 1e3, 3),
-                            "frac": round(fflops / fwd_s / 1e9 / FP64_PEAK_GFLOPS, 4)}}
+    mu_tot = float(np.sum(sched_m * sched_s))
+    # Sec. 8(d)-style algorithmic bytes: per Taylor term the union pattern's values and indices once,
+    # the input and output blocks once; three passes of terms (forward, costate chain, gradient) plus
+    # the stored states and Horner vectors written and read once
+    term_bytes = nnz * (16 + 4) + (p.dim + 1) * 4 + 2 * p.dim * p.n_states * 16
+    passes = 3 if mode == 3 else 4
+    eval_bytes = passes * mu_tot * term_bytes
+    if mode == 3:
+        eval_bytes += 2 * p.n_steps * p.dim * p.n_states * 16 + 2 * mu_tot * p.dim * p.n_states * 16
+    hbm_peak, hbm_src = measured_peaks()
+    hbm_ach = eval_bytes * value / 1e9
+    roofline = {"bound": "alu", "kernel": dom, "achieved": kern[dom]["achieved"], "peak": round(fp64_peak, 1),
+                "unit": "GFLOP/s", "frac": kern[dom]["frac"], "traffic": read_traffic(dom, args.workload),
+                "peak_source": ("measured: grape_fp64_fma_rate (independent FP64 FMA chains on every SM, CUDA events) "
+                                "on this GPU in this run" if peak_ok else "nominal 152 SMs x 2 FMA/clk x 2 x 2.07 GHz"),
+                "flops_per_launch": kern[dom]["flops_per_launch"], "launch_ms": kern[dom]["avg_launch_ms"],
+                "flop_model": "per Taylor term and column: 8 flops per general entry, 4 per single-phase entry, "
+                              "2 per real-H diagonal entry, 4 per row update; k_gradient adds 8 per control entry",
+                "entry_classes": {"diag": cls[0], "single_phase": cls[1], "general": cls[2], "control": cls[3]},
+                "kernels": kern,
+                "hbm": {"algorithmic_bytes_per_eval": eval_bytes, "achieved_GBps": round(hbm_ach, 1),
+                        "peak_GBps": hbm_peak, "peak_source": hbm_src, "frac": round(hbm_ach / hbm_peak, 4)}}
 
     # ---- torch full-AD comparator (same GPU, same Taylor schedule) for peak HBM
     peak_hbm = {"hg_bytes": int(hg_peak), "hg_problem_bytes": int(info["device_bytes"])}
@@ -447,20 +539,28 @@ def run_ours(args):
     if args.optimize:
         extra["steepest_descent"] = optimize_compare(local)
 
+    # our kernels per evaluation: k_schedule, k_forward, k_finalize, the backward kernels, k_grad_reduce
+    if mode == 3:
+        nb = -(-p.n_steps // max(info["block_steps"], 1))
+        per_eval = 3 + 1 + 2 * nb + 1 + 1          # + k_plan, per block k_costate and k_gradient, gated fallback
+    else:
+        per_eval = 5
+    gpu_launches = per_eval * args.steps
     out = {
         "metric": METRIC, "value": round(value, 6), "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(tmax / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_description(p), "parallelism": f"replicas x{world}",
                    "l2": "flushed before every timed step (256 MB write)", "cluster_ctas_per_column_fwd": info["cluster_forward"],
-                   "cluster_ctas_per_column_bwd": info["cluster"], "backward_teams_per_column": info["backward_mode"],
+                   "cluster_ctas_per_column_bwd": info["cluster"], "backward_mode": info["backward_mode"],
+                   "gradient_team_ctas": info["grad_cluster"], "steps_per_block": info["block_steps"],
                    "ckpt_every": info["ckpt_every"], "total_taylor_terms_per_sweep": int(np.sum(sched_m * sched_s)),
                    "max_norm_A1": round(float(np.max(norms)), 4)},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_value, 6) if e2e_value else None, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "api": "grape_cost_and_grad with pinned host u/cost/grad"},
-        "gpu_launches": LAUNCHES_PER_EVAL * args.steps,
+        "gpu_launches": gpu_launches,
         "clocks": clk,
         "peak_hbm": peak_hbm,
     }

@@ -235,6 +235,25 @@ grape_status grape_sync_status(grape_problem* prob, void* stream);
 /* Problem information (see grape_info). */
 grape_status grape_problem_info(grape_problem* prob, grape_info* info);
 
+/* Kernel tracing (no counterpart in the paper: measurement support).  With tracing enabled, every
+ * evaluation records a pair of CUDA events around each launch of the sweep kernels (on the stream
+ * the kernel runs on; nothing is recorded while a stream is being captured into a CUDA graph), and
+ * grape_kernel_times sums their durations over the evaluations since the last call (which resets
+ * the sums; it waits for the problem's pending work).  Index: 0 = k_forward, 1 = k_costate,
+ * 2 = k_gradient, 3 = the fused or two-team backward kernel. */
+typedef struct {
+  int32_t launches[4];
+  double ms[4];
+} grape_kernel_times_t;
+grape_status grape_set_kernel_tracing(grape_problem* prob, int32_t enable);
+grape_status grape_kernel_times(grape_problem* prob, grape_kernel_times_t* out);
+
+/* Measurement support (no counterpart in the paper): the device's FP64 fused multiply-add rate in
+ * GFLOP/s (2 flops per FMA), from one launch of independent FMA chains on every SM timed with CUDA
+ * events; the sweep kernels are bound by FP64 issue, so this is their roofline's peak.  Allocates
+ * and frees a small buffer; synchronises the device; about 0.1 s. */
+grape_status grape_fp64_fma_rate(int32_t device, double* gflops);
+
 /* Per-step schedule of the last evaluation, copied to host arrays of n_steps entries
  * each (any may be NULL): Taylor order m_n, scaling factor s_n, and ||A_n||_1. */
 grape_status grape_step_schedule(grape_problem* prob, int32_t* m, int32_t* s, double* norm1);

@@ -22,6 +22,7 @@ EXPORTED = [
     "grape_sync_status", "grape_problem_info", "grape_step_schedule", "grape_select_ms", "grape_error_bound",
     "grape_status_string", "grape_last_error", "grape_abi_version", "grape_taylor_step_noalloc",
     "grape_batch_create", "grape_batch_destroy", "grape_batch_cost_and_grad", "grape_optimize",
+    "grape_set_kernel_tracing", "grape_kernel_times", "grape_fp64_fma_rate",
 ]
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -53,6 +54,10 @@ class GrapeInfo(C.Structure):
                 ("max_norm", C.c_double), ("backward_mode", C.c_int32), ("cluster_forward", C.c_int32),
                 ("propagator", C.c_int32), ("grad_cluster", C.c_int32), ("block_steps", C.c_int32),
                 ("fused_fallback", C.c_int32)]
+
+
+class GrapeKernelTimes(C.Structure):
+    _fields_ = [("launches", C.c_int32 * 4), ("ms", C.c_double * 4)]
 
 
 _LIB = None
@@ -100,6 +105,12 @@ def lib(path: str | None = None):
     L.grape_batch_cost_and_grad.restype = C.c_int
     L.grape_optimize.argtypes = [P, P, C.c_int32, C.c_double, P, C.c_int32, P]
     L.grape_optimize.restype = C.c_int
+    L.grape_set_kernel_tracing.argtypes = [P, C.c_int32]
+    L.grape_set_kernel_tracing.restype = C.c_int
+    L.grape_kernel_times.argtypes = [P, C.POINTER(GrapeKernelTimes)]
+    L.grape_kernel_times.restype = C.c_int
+    L.grape_fp64_fma_rate.argtypes = [C.c_int32, C.POINTER(C.c_double)]
+    L.grape_fp64_fma_rate.restype = C.c_int
     L.grape_status_string.argtypes = [C.c_int]
     L.grape_status_string.restype = C.c_char_p
     L.grape_last_error.argtypes = []

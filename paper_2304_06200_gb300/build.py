@@ -17,7 +17,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgrape_hg.so")
-SOURCES = ["grape_kernels.cu", "grape_host.cpp", "grape_bound.cpp", "grape_noalloc.cu", "grape_dense.cu", "grape_eig.cu"]
+SOURCES = ["grape_kernels.cu", "grape_host.cpp", "grape_bound.cpp", "grape_noalloc.cu", "grape_dense.cu", "grape_eig.cu",
+           "grape_probe.cu"]
 HEADERS = ["grape_internal.h", "grape_bound.h", "grape_dense.h", "grape_eig.h", os.path.join("..", "..", "include", "grape_hg.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-I" + os.path.join(ROOT, "include")]

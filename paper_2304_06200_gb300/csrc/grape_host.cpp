@@ -212,6 +212,33 @@ struct grape_problem {
   cudaEvent_t ev_b = nullptr, ev_g[kHbufDepth] = {nullptr, nullptr, nullptr};
   int prio_hi = 0;                       // launch priority of the costate chain
   int64_t scr_g_off = 0;                 // k_gradient's region of d_scratch (double2 units)
+  // kernel tracing: event pairs around each launch (kind 0..3), summed by grape_kernel_times
+  bool tracing = false;
+  std::vector<cudaEvent_t> tr_events;    // pool, two per traced launch
+  std::vector<int> tr_kind;              // kind of traced launch i (events 2i, 2i+1)
+  size_t tr_used = 0;                    // traced launches since the last grape_kernel_times
+  // Record the opening event of a traced launch on st; returns its index or -1.
+  int trace_begin(int kind, cudaStream_t st) {
+    if (!tracing) return -1;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return -1;
+    if (2 * (tr_used + 1) > tr_events.size()) {
+      for (int k = 0; k < 2; ++k) {
+        cudaEvent_t ev = nullptr;
+        if (cudaEventCreate(&ev) != cudaSuccess) return -1;
+        tr_events.push_back(ev);
+      }
+      tr_kind.push_back(0);
+    }
+    const size_t i = tr_used;
+    if (cudaEventRecord(tr_events[2 * i], st) != cudaSuccess) return -1;
+    tr_kind[i] = kind;
+    ++tr_used;
+    return (int)i;
+  }
+  void trace_end(int i, cudaStream_t st) {
+    if (i >= 0) cudaEventRecord(tr_events[2 * (size_t)i + 1], st);
+  }
   // eigendecomposition propagators (App. F)
   bool eig = false;
   grape::EigCtx ectx{};
@@ -265,6 +292,10 @@ struct grape_problem {
       }
   }
   void release() {
+    for (auto e : tr_events) cudaEventDestroy(e);
+    tr_events.clear();
+    tr_kind.clear();
+    tr_used = 0;
     if (ev_b) cudaEventDestroy(ev_b);
     ev_b = nullptr;
     for (auto& e : ev_g) {
@@ -900,25 +931,27 @@ grape_status build(grape_problem* P, const grape_desc* d) {
     else if (mode_req == 0)
       three = ckpt_ok && P->N >= 2 && 2 * P->n * P->fwd.CL <= nsm && state_bytes <= 8.0 * (1 << 30);
   }
-  // k_gradient partition: the smallest team (at most 512 rows per CTA) whose exchange buffers, states,
-  // values, W accumulators and pattern all fit shared memory; else the smallest with W in shared
-  // memory, else the smallest that fits at all (the rest in the CTA's global scratch).
+  // k_gradient partition: the smallest team that fits shared memory at all (its exchange buffers,
+  // states and pattern; values and W accumulators join them when they fit, else they stay in the
+  // CTA's global scratch slice, which the L2 holds).  The gradient kernel is throughput bound: the
+  // fewer CTAs per team, the fewer barriers and remote loads per unit of work (measured at
+  // d = 4000: teams of 2 CTAs beat 4, 8 and 16).  Blocks of steps are long enough that a block's
+  // gradient work covers about twice the SMs the costate chain leaves free.
   if (three) {
-    const int full = 1 | 2 | (cb == 8 ? 4 : 0);
     int pick = 0, pick_in = 0;
-    for (int pass = 0; pass < 3 && !pick; ++pass) {
-      for (int CL = 1; CL <= grape::kMaxCluster && !pick; ++CL) {
-        if (d->grad_cluster > 0 && CL != d->grad_cluster) continue;
-        if (CL > 1 && CL > dim) continue;
-        int R = 0, mnl = 0;
-        if (!rows_entries(CL, &R, &mnl)) continue;
-        const int want = pass == 0 ? full : (pass == 1 ? 2 | (cb == 8 ? 4 : 0) : 0);
-        if (pass == 0 && R > 512 && d->grad_cluster == 0) continue;
+    const int full = 1 | 2 | (cb == 8 ? 4 : 0);
+    for (int CL = 1; CL <= grape::kMaxCluster && !pick; ++CL) {
+      if (d->grad_cluster > 0 && CL != d->grad_cluster) continue;
+      if (CL > 1 && CL > dim) continue;
+      int R = 0, mnl = 0;
+      if (!rows_entries(CL, &R, &mnl)) continue;
+      for (int want : {full, 2 | (cb == 8 ? 4 : 0), 0}) {
         if (grape::make_glayout(R, mnl, want, cb).total > smem_max) continue;
         pick = CL;
         pick_in = want;
         P->grd.R = R;
         P->grd.mnl = mnl;
+        break;
       }
     }
     if (!pick) {
@@ -931,7 +964,7 @@ grape_status build(grape_problem* P, const grape_desc* d) {
       P->grd.smem = grape::make_glayout(P->grd.R, P->grd.mnl, pick_in, cb).total;
       P->grd.threads = threads_for(P->grd.R);
       const int free_sms = std::max(nsm - P->n * P->fwd.CL, P->n * pick);
-      int S = d->block_steps > 0 ? d->block_steps : std::max(1, free_sms / (P->n * pick));
+      const int S = d->block_steps > 0 ? d->block_steps : std::min(32, std::max(1, 2 * free_sms / (P->n * pick)));
       P->steps_per_block = std::min(S, P->N);
     }
   }
@@ -1404,8 +1437,10 @@ grape_status run_forward(grape_problem* P, const double* u, bool u_on_device, cu
     return GRAPE_OK;
   }
   grape::SweepParams p = sweep_params(P, P->fwd);
+  const int tf = P->trace_begin(0, st);
   if ((e = grape::launch_forward(p, P->precision, P->fwd.smem, P->fwd.threads, st)) != cudaSuccess)
     return cuda_fail(e, "launch k_forward");
+  P->trace_end(tf, st);
   grape::FinalizeParams fp{};
   fp.n_parts = P->n * P->fwd.CL;
   fp.n_states = P->n;
@@ -1511,12 +1546,16 @@ grape_status run_backward(grape_problem* P, cudaStream_t st) {
       pc.hbuf = pg.hbuf = P->d_hbuf[slot];
       if (b + D <= nb - 1 && (e = cudaStreamWaitEvent(st, P->ev_g[slot], 0)) != cudaSuccess)
         return cuda_fail(e, "cudaStreamWaitEvent");
+      const int tc = P->trace_begin(1, st);
       if ((e = grape::launch_costate(pc, P->precision, P->fwd.smem, P->fwd.threads, P->prio_hi, st)) != cudaSuccess)
         return cuda_fail(e, "launch k_costate");
+      P->trace_end(tc, st);
       if ((e = cudaEventRecord(P->ev_b, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
       if ((e = cudaStreamWaitEvent(gs, P->ev_b, 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+      const int tg = P->trace_begin(2, gs);
       if ((e = grape::launch_gradient(pg, P->precision, P->grd.smem, P->grd.threads, gs)) != cudaSuccess)
         return cuda_fail(e, "launch k_gradient");
+      P->trace_end(tg, gs);
       if ((e = cudaEventRecord(P->ev_g[slot], gs)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     }
     // join: the last gradient kernel of each stream (blocks 0 .. G-1, slots b % D)
@@ -1536,11 +1575,15 @@ grape_status run_backward(grape_problem* P, cudaStream_t st) {
     p.spin_limit = P->wait_limit;
     if ((e = cudaMemsetAsync(P->d_flags, 0, sizeof(unsigned) * 2 * (size_t)P->n * P->bwd.CL, st)) != cudaSuccess)
       return cuda_fail(e, "cudaMemsetAsync (flags)");
+    const int tb = P->trace_begin(3, st);
     if ((e = grape::launch_backward_split(p, P->precision, P->bwd.smem, P->bwd.threads, st)) != cudaSuccess)
       return cuda_fail(e, "launch k_backward_split");
+    P->trace_end(tb, st);
   } else {
+    const int tb = P->trace_begin(3, st);
     if ((e = grape::launch_backward(p, P->precision, P->bwd.smem, P->bwd.threads, st)) != cudaSuccess)
       return cuda_fail(e, "launch k_backward");
+    P->trace_end(tb, st);
   }
   if (P->K > 0) {
     grape::GradReduceParams gp{};
@@ -1963,6 +2006,31 @@ grape_status grape_problem_info(grape_problem* P, grape_info* info) {
     info->total_terms = t;
     info->max_norm = mx;
   }
+  return GRAPE_OK;
+}
+
+grape_status grape_set_kernel_tracing(grape_problem* P, int32_t enable) {
+  if (!P) return fail(GRAPE_EINVAL, "NULL problem");
+  P->tracing = enable != 0;
+  P->tr_used = 0;
+  return GRAPE_OK;
+}
+
+grape_status grape_kernel_times(grape_problem* P, grape_kernel_times_t* out) {
+  if (!P || !out) return fail(GRAPE_EINVAL, "NULL argument");
+  std::memset(out, 0, sizeof(*out));
+  DeviceGuard guard(P->device);
+  if (!guard.ok) return fail(GRAPE_ECUDA, "cudaSetDevice failed");
+  for (size_t i = 0; i < P->tr_used; ++i) {
+    cudaError_t e = cudaEventSynchronize(P->tr_events[2 * i + 1]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+    float ms = 0.0f;
+    if ((e = cudaEventElapsedTime(&ms, P->tr_events[2 * i], P->tr_events[2 * i + 1])) != cudaSuccess)
+      return cuda_fail(e, "cudaEventElapsedTime");
+    out->launches[P->tr_kind[i]] += 1;
+    out->ms[P->tr_kind[i]] += ms;
+  }
+  P->tr_used = 0;
   return GRAPE_OK;
 }
 

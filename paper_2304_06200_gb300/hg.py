@@ -205,6 +205,18 @@ class GrapeProblem:
         check(self._lib.grape_problem_info(self._h, C.byref(inf)), "grape_problem_info")
         return {f: getattr(inf, f) for f, _ in GrapeInfo._fields_}
 
+    def set_kernel_tracing(self, enable: bool = True):
+        """Record CUDA events around every sweep-kernel launch (measurement support)."""
+        check(self._lib.grape_set_kernel_tracing(self._h, 1 if enable else 0), "grape_set_kernel_tracing")
+
+    def kernel_times(self) -> dict:
+        """Summed event durations (ms) and launch counts per sweep kernel since the last call."""
+        from ._abi import GrapeKernelTimes
+        t = GrapeKernelTimes()
+        check(self._lib.grape_kernel_times(self._h, C.byref(t)), "grape_kernel_times")
+        names = ["k_forward", "k_costate", "k_gradient", "k_backward"]
+        return {nm: {"launches": int(t.launches[i]), "ms": float(t.ms[i])} for i, nm in enumerate(names)}
+
     def schedule(self):
         m = np.zeros(self.N, dtype=np.int32)
         s = np.zeros(self.N, dtype=np.int32)

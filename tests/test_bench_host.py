@@ -59,11 +59,25 @@ def test_work_model_counts():
     import bench
     m = np.array([3, 2])
     s = np.array([1, 2])
-    # forward: sum s m terms, each 8 nnz n + 4 d n flops
-    assert bench.forward_flops(m, s, nnz=10, dim=4, n=2) == (3 + 4) * (8 * 10 * 2 + 4 * 4 * 2)
-    # backward: per substep (3m - 1) sparse products + m W-accumulations on control entries
-    want = 1 * (8 * (160 + 32) + 3 * 8 * 6 * 2) + 2 * (5 * (160 + 32) + 2 * 8 * 6 * 2)
-    assert bench.backward_flops(m, s, nnz=10, nnz_ctrl_entries=6, dim=4, n=2) == want
+    cls = (4, 2, 4, 6)          # diagonal, single-phase, general, control-carrying entries
+    per_term = 2 * 4 + 4 * 2 + 8 * 4 + 4 * 4   # per column: the product and the row update (d = 4)
+    # forward and costate chain: sum s m terms
+    assert bench.forward_flops(m, s, cls, dim=4, n=2) == (3 + 4) * per_term * 2
+    assert bench.costate_flops(m, s, cls, dim=4, n=2) == (3 + 4) * per_term * 2
+    # gradient: m s control accumulations and m s - 1 products per step
+    assert bench.gradient_flops(m, s, cls, dim=4, n=2) == 2 * ((3 * 8 * 6 + 2 * per_term) + (4 * 8 * 6 + 3 * per_term))
+    # fused backward: per substep (3m - 1) products + m control accumulations
+    want = 2 * (1 * (8 * per_term + 3 * 8 * 6) + 2 * (5 * per_term + 2 * 8 * 6))
+    assert bench.fused_backward_flops(m, s, cls, dim=4, n=2) == want
+
+
+def test_entry_classes_of_a_two_level_drive():
+    """H0 = (delta/2) sigma_z (real diagonal), one control sigma_x (real off-diagonal: single phase)."""
+    import bench
+    from workloads import two_level_rabi
+    p = two_level_rabi(3, 0.1, delta=1.0)
+    n_diag, n_single, n_general, n_ctrl = bench.entry_classes(p)
+    assert (n_diag, n_single, n_general, n_ctrl) == (2, 2, 0, 2)
 
 
 def test_single_rank_aggregate_without_collectives():
