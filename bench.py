@@ -64,7 +64,7 @@ def parse_args(argv=None):
                     help="also time the three-transmon, qubit-chain and fluxonium-pair Hamiltonians (FP64, FP32 bulk)")
     ap.add_argument("--optimize", action="store_true",
                     help="also time steepest descent in a CUDA graph against a host-driven loop (c2_gate_d80)")
-    ap.add_argument("--backward-mode", type=int, default=0, help="0 auto, 1 one team per column, 2 two teams")
+    ap.add_argument("--backward-mode", type=int, default=0, help="0 auto, 1 one team per column, 3 three-stage")
     return ap.parse_args(argv)
 
 
@@ -196,7 +196,7 @@ def gradient_flops(schedule_m, schedule_s, cls, dim: int, n: int) -> float:
 
 
 def fused_backward_flops(schedule_m, schedule_s, cls, dim: int, n: int) -> float:
-    """The one-team or two-team backward: per substep 2m products (psi chain, Horner chain), m - 1
+    """The one-team backward: per substep 2m products (psi chain, Horner chain), m - 1
     products of the x chain and m accumulations on the control entries."""
     tot = 0.0
     for m, s in zip(schedule_m, schedule_s):

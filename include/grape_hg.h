@@ -129,8 +129,7 @@ typedef struct {
   grape_free_fn free;
   void* alloc_ctx;
   int32_t backward_mode;       /* 0 = automatic, 1 = one team per column runs both backward
-                                  phases, 2 = two concurrent teams per column (phase A / phase B),
-                                  needs all 2 * n_states teams co-resident, 3 = three-stage: the
+                                  phases (adjoint re-propagation of psi), 3 = three-stage: the
                                   forward stores every state, one team per column runs only the
                                   costate chain and stores its Horner vectors, the gradient terms
                                   of every step are computed independently on the remaining SMs
@@ -144,9 +143,6 @@ typedef struct {
                                   C3 = 1 - 1/(N n^2) sum_{n'=1..N} |sum_h <phi_T^h|psi_n'^h>|^2
                                   (App. A, C3st / C3g; 0 = off)                                 */
   int32_t propagator;          /* grape_propagator (0 = Taylor)                               */
-  int64_t wait_limit;          /* polls (about 0.1 us apart) before a device wait of the two-team
-                                  backward sweep gives up and the call returns GRAPE_ETIMEOUT;
-                                  0 = default (2^24, about two seconds)                        */
   int32_t grad_cluster;        /* three-stage backward: CTAs per (step, column) team of the gradient
                                   kernel, 0 = automatic (the smallest team whose working set fits
                                   shared memory), else 1..16                                   */
@@ -167,8 +163,8 @@ typedef struct {
   int32_t smem_bytes;          /* dynamic shared memory per CTA of the sweep kernels       */
   int64_t total_terms;         /* sum over steps of m_n * s_n for the last evaluation (-1 before) */
   double max_norm;             /* max_n ||A_n||_1 of the last evaluation (-1 before)       */
-  int32_t backward_mode;       /* 1 = one team per column, 2 = two concurrent teams per column,
-                                  3 = three-stage (costate chain + per-step gradient kernels)  */
+  int32_t backward_mode;       /* 1 = one team per column, 3 = three-stage (costate chain +
+                                  per-step gradient kernels)                                   */
   int32_t cluster_forward;     /* CTAs per column team of the forward sweep                */
   int32_t propagator;          /* grape_propagator of the problem                          */
   int32_t grad_cluster;        /* three-stage backward: CTAs per gradient team (0 = not used)  */
@@ -240,7 +236,7 @@ grape_status grape_problem_info(grape_problem* prob, grape_info* info);
  * the kernel runs on; nothing is recorded while a stream is being captured into a CUDA graph), and
  * grape_kernel_times sums their durations over the evaluations since the last call (which resets
  * the sums; it waits for the problem's pending work).  Index: 0 = k_forward, 1 = k_costate,
- * 2 = k_gradient, 3 = the fused or two-team backward kernel. */
+ * 2 = k_gradient, 3 = the fused one-team backward kernel. */
 typedef struct {
   int32_t launches[4];
   double ms[4];
@@ -273,8 +269,8 @@ double grape_error_bound(double x, int32_t m, int32_t s, int32_t sigma, int32_t 
  * gradient) into one CUDA graph whose branches run on n_streams concurrent lanes (0 = 8), members
  * assigned longest first; a launch of the graph then evaluates all members with their kernels
  * running side by side, so that many small column teams fill the GPU.  Members must be distinct
- * problems on one device created with backward_mode = 1 (the two-team sweep waits on its partner
- * team and must not share the GPU with unrelated kernels).  The batch does not own the problems:
+ * problems on one device created with backward_mode = 1 (the three-stage backward sizes its block
+ * buffers from a schedule read that a recording cannot make).  The batch does not own the problems:
  * destroy the batch before them.  This realises the paper's per-instance HG evaluation (Sec. III)
  * for many instances at once; the paper itself treats one instance at a time. */
 typedef struct grape_batch grape_batch;

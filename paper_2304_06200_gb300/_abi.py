@@ -43,7 +43,7 @@ class GrapeDesc(C.Structure):
                 ("tau", C.c_double), ("m_max", C.c_int32), ("ckpt_every", C.c_int32), ("precision", C.c_int32),
                 ("cluster", C.c_int32), ("device", C.c_int32),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p), ("backward_mode", C.c_int32),
-                ("bulk_norm_cap", C.c_double), ("w_tint", C.c_double), ("propagator", C.c_int32), ("wait_limit", C.c_int64),
+                ("bulk_norm_cap", C.c_double), ("w_tint", C.c_double), ("propagator", C.c_int32),
                 ("grad_cluster", C.c_int32), ("block_steps", C.c_int32)]
 
 

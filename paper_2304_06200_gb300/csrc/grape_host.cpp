@@ -147,7 +147,6 @@ struct grape_problem {
   double dt = 0, w_fid = 0, w_forbid = 0, w_amp = 0, tau = 0;
   double b_cap = 0;   // cap on ||B||_1 = ||A||_1 / s in the schedule (0 = the paper's rule unchanged)
   double w_tint = 0;  // weight of the time-integrated infidelity C3
-  long long wait_limit = 1LL << 24;   // polls before a device wait gives up
   int precision = 0, ckpt_every = 0, n_ckpt = 0, m_cap = 0, s_cap = 0, sigma = 0;
   int64_t nnz = 0, n_ctr = 0;
   bool has_omega = false;
@@ -189,12 +188,7 @@ struct grape_problem {
   double* d_grad = nullptr;
   double2* d_scratch = nullptr;
   int* d_err = nullptr;
-  // split backward
-  int bwd_mode = 1;                 // 1 fused, 2 split
-  double2* d_ring = nullptr;
-  int64_t ring_slot = 0;
-  int ring_depth = 2;
-  unsigned* d_flags = nullptr;      // ready[n*CL], done[n*CL]
+  int bwd_mode = 1;                 // 1 fused (one team per column), 3 three-stage
   // launch plans of the forward and the backward sweep
   KPlan fwd, bwd;
   // three-stage backward (bwd_mode 3): k_costate on the forward's partition, k_gradient on grd;
@@ -890,12 +884,7 @@ grape_status build(grape_problem* P, const grape_desc* d) {
     return true;
   };
   int mode_req = d->backward_mode;
-  if (mode_req < 0 || mode_req > 3) return fail(GRAPE_EINVAL, "backward_mode must be 0, 1, 2 or 3");
-  if (mode_req == 3 && d->ckpt_every != 0 && d->ckpt_every != 1)
-    return fail(GRAPE_EINVAL, "backward_mode 3 stores every state: ckpt_every must be 0 or 1");
-  if (d->grad_cluster < 0 || d->grad_cluster > grape::kMaxCluster)
-    return fail(GRAPE_EINVAL, "grad_cluster must be 0 (automatic) or 1..16");
-  if (d->block_steps < 0) return fail(GRAPE_EINVAL, "block_steps must be >= 0");
+
   // forward
   {
     double best = 1e300;
@@ -968,8 +957,7 @@ grape_status build(grape_problem* P, const grape_desc* d) {
       P->steps_per_block = std::min(S, P->N);
     }
   }
-  // backward: one team per column (fused) or two concurrent teams (split) when co-resident; with the
-  // three-stage backward, the fused plan is its fallback
+  // backward: one team per column (fused); with the three-stage backward, the fused plan is its fallback
   if (three) mode_req = 1;
   {
     double best = 1e300;
@@ -980,32 +968,21 @@ grape_status build(grape_problem* P, const grape_desc* d) {
       if (!rows_entries(CL, &R, &mnl)) continue;
       if (!bwd_plan(R, mnl, &bin, &msm, &fsm, &ssm)) continue;
       const int thr = threads_for(R);
-      for (int mode = 1; mode <= 2; ++mode) {
-        if (mode_req != 0 && mode != mode_req) continue;
-        double cost;
-        if (mode == 1) {
-          cost = waves(P->n * CL) * (a_cost * mnl * (3.0 + wf) + b_cost * R * 2.0 + 2.0 * sync_cost(CL));
-        } else {
-          if (grape::split_capacity(P->precision, CL, ssm, thr) < 2 * P->n) continue;
-          cost = std::max(a_cost * mnl * 2.0 + b_cost * R + sync_cost(CL), a_cost * mnl * (1.0 + wf) + sync_cost(CL));
-        }
-        if (cost < best * 0.98) {
-          best = cost;
-          P->bwd_mode = mode;
-          P->bwd.CL = CL;
-          P->bwd.R = R;
-          P->bwd.mnl = mnl;
-          P->bwd.in_smem = bin;
-          P->bwd.m_smem = mode == 1 ? msm : 0;
-          P->bwd.smem = mode == 1 ? fsm : ssm;
-          P->bwd.threads = thr;
-        }
+      (void)ssm;
+      const double cost = waves(P->n * CL) * (a_cost * mnl * (3.0 + wf) + b_cost * R * 2.0 + 2.0 * sync_cost(CL));
+      if (cost < best * 0.98) {
+        best = cost;
+        P->bwd_mode = 1;
+        P->bwd.CL = CL;
+        P->bwd.R = R;
+        P->bwd.mnl = mnl;
+        P->bwd.in_smem = bin;
+        P->bwd.m_smem = msm;
+        P->bwd.smem = fsm;
+        P->bwd.threads = thr;
       }
     }
-    if (P->bwd.CL == 0) {
-      if (mode_req == 2) return fail(GRAPE_EINVAL, "backward_mode 2: the 2 * n_states teams cannot be co-resident");
-      return fail(GRAPE_EINVAL, "problem does not fit the backward sweep's shared memory");
-    }
+    if (P->bwd.CL == 0) return fail(GRAPE_EINVAL, "problem does not fit the backward sweep's shared memory");
   }
   if (three) P->bwd_mode = 3;
   // column encodings (owner CTA, local row, control bit) of both partitions, control slices of the backward one
@@ -1044,7 +1021,7 @@ grape_status build(grape_problem* P, const grape_desc* d) {
     kp->scr_W = kp->mnl;
     kp->scr_Wb = 2 * (int64_t)kp->mnl;
     kp->scr_wslot = 3 * (int64_t)kp->mnl;
-    const int wslots = kp == &P->bwd && P->bwd_mode != 2 ? std::max(0, P->m_cap - kp->m_smem) : 0;
+    const int wslots = kp == &P->bwd ? std::max(0, P->m_cap - kp->m_smem) : 0;
     kp->stride = (3 * (int64_t)kp->mnl + (int64_t)wslots * kp->R + 15) / 16 * 16;
   }
   // ---- checkpoints
@@ -1091,13 +1068,8 @@ grape_status build(grape_problem* P, const grape_desc* d) {
   if ((st = dzeros(P, &P->d_grad, (size_t)std::max(K, 1) * P->N))) return st;
   if ((st = dzeros(P, &P->d_err, 1))) return st;
   if ((st = dzeros(P, &P->d_part_g3, (size_t)parts_f * P->N)) || (st = dzeros(P, &P->d_g3, (size_t)P->N))) return st;
-  if (P->bwd_mode == 2) {
-    P->ring_slot = (int64_t)(1 + P->m_cap) * dim;
-    if ((st = dzeros(P, &P->d_ring, (size_t)P->n * P->ring_depth * P->ring_slot))) return st;
-    if ((st = dzeros(P, &P->d_flags, (size_t)2 * parts_b))) return st;
-  }
   const int64_t scr_f = (int64_t)parts_f * P->fwd.stride;
-  const int64_t scr_b = (int64_t)(P->bwd_mode == 2 ? 2 * P->n * P->bwd.CL : P->n * P->bwd.CL) * P->bwd.stride;
+  const int64_t scr_b = (int64_t)P->n * P->bwd.CL * P->bwd.stride;
   // k_costate (forward partition) and k_gradient run at the same time: disjoint scratch regions
   int64_t scr_g = 0;
   if (three) scr_g = (int64_t)P->steps_per_block * P->n * P->grd.CL * P->grd.stride;
@@ -1285,9 +1257,15 @@ grape_status grape_problem_create(const grape_desc* d, grape_problem** out) {
   if (d->propagator == GRAPE_PROP_EIG && (d->precision != GRAPE_FP64 || d->dim > grape::kEigMaxDim))
     return fail(GRAPE_EINVAL, "GRAPE_PROP_EIG needs GRAPE_FP64 and dim <= 96");
   if (d->cluster < 0 || d->cluster > grape::kMaxCluster) return fail(GRAPE_EINVAL, "cluster must be 0 (automatic) or 1..16");
+  if (d->backward_mode < 0 || d->backward_mode > 3 || d->backward_mode == 2)
+    return fail(GRAPE_EINVAL, "backward_mode must be 0 (automatic), 1 (one team per column) or 3 (three-stage)");
+  if (d->backward_mode == 3 && d->ckpt_every != 0 && d->ckpt_every != 1)
+    return fail(GRAPE_EINVAL, "backward_mode 3 stores every state: ckpt_every must be 0 or 1");
+  if (d->grad_cluster < 0 || d->grad_cluster > grape::kMaxCluster)
+    return fail(GRAPE_EINVAL, "grad_cluster must be 0 (automatic) or 1..16");
+  if (d->block_steps < 0) return fail(GRAPE_EINVAL, "block_steps must be >= 0");
   if (d->n_controls > 0 && !d->Hk) return fail(GRAPE_EINVAL, "Hk is NULL");
   if (d->bulk_norm_cap < 0.0 || !std::isfinite(d->bulk_norm_cap)) return fail(GRAPE_EINVAL, "bulk_norm_cap must be >= 0");
-  if (d->wait_limit < 0) return fail(GRAPE_EINVAL, "wait_limit must be >= 0");
   if (!d->psi0 || !d->target) return fail(GRAPE_EINVAL, "psi0 / target is NULL");
   if ((d->alloc == nullptr) != (d->free == nullptr)) return fail(GRAPE_EINVAL, "alloc and free must both be set or both NULL");
   const double ws[4] = {d->w_fid, d->w_forbid, d->w_amp, d->w_tint};
@@ -1313,7 +1291,6 @@ grape_status grape_problem_create(const grape_desc* d, grape_problem** out) {
   P->w_forbid = d->w_forbid;
   P->w_amp = d->w_amp;
   P->w_tint = d->w_tint;
-  P->wait_limit = d->wait_limit > 0 ? d->wait_limit : (1LL << 24);
   P->tau = d->tau;
   P->precision = d->precision;
   P->m_cap = d->m_max == 0 ? grape::kMaxTaylor : d->m_max;
@@ -1566,19 +1543,6 @@ grape_status run_backward(grape_problem* P, cudaStream_t st) {
     pf.gate_on_flag = 1;
     if ((e = grape::launch_backward(pf, P->precision, P->bwd.smem, P->bwd.threads, st)) != cudaSuccess)
       return cuda_fail(e, "launch k_backward (fallback)");
-  } else if (P->bwd_mode == 2) {
-    p.ring = P->d_ring;
-    p.ring_slot = P->ring_slot;
-    p.ring_depth = P->ring_depth;
-    p.ready = P->d_flags;
-    p.done = P->d_flags + (size_t)P->n * P->bwd.CL;
-    p.spin_limit = P->wait_limit;
-    if ((e = cudaMemsetAsync(P->d_flags, 0, sizeof(unsigned) * 2 * (size_t)P->n * P->bwd.CL, st)) != cudaSuccess)
-      return cuda_fail(e, "cudaMemsetAsync (flags)");
-    const int tb = P->trace_begin(3, st);
-    if ((e = grape::launch_backward_split(p, P->precision, P->bwd.smem, P->bwd.threads, st)) != cudaSuccess)
-      return cuda_fail(e, "launch k_backward_split");
-    P->trace_end(tb, st);
   } else {
     const int tb = P->trace_begin(3, st);
     if ((e = grape::launch_backward(p, P->precision, P->bwd.smem, P->bwd.threads, st)) != cudaSuccess)
@@ -1803,8 +1767,9 @@ grape_status grape_batch_create(grape_problem* const* probs, int32_t count, int3
     if (probs[i]->device != probs[0]->device) return fail(GRAPE_EINVAL, "batch problems must share one device");
     if (probs[i]->dense) return fail(GRAPE_EINVAL, "tensor-core problems are driven from the host and cannot join a batch");
     if (probs[i]->bwd_mode != 1)
-      return fail(GRAPE_EINVAL, "batch members must use backward_mode 1 (two-team sweeps wait on each other and must "
-                                "not share the GPU with concurrent kernels)");
+      return fail(GRAPE_EINVAL, "batch members must use backward_mode 1 (the batch records every member's kernels "
+                                "into one graph; the three-stage backward sizes its buffers from a schedule read "
+                                "that a recording cannot make)");
     for (int j = 0; j < i; ++j)
       if (probs[j] == probs[i]) return fail(GRAPE_EINVAL, "a problem appears twice in the batch");
   }

@@ -73,13 +73,6 @@ struct SweepParams {
   const int* ectr_k;
   const double2* ectr_val;
   int* err;                            // device error word
-  // split backward (team A: psi and Horner chains; team B: x chain, W, gradient), see k_backward_split
-  double2* ring;                       // n_states x ring_depth slots of (1 + m_cap) * dim
-  int64_t ring_slot;                   // complex numbers per slot
-  int ring_depth;
-  unsigned* ready;                     // n_states x CL: substeps published by team A's CTA
-  unsigned* done;                      // n_states x CL: substeps consumed by team B's CTA
-  long long spin_limit;                // polls before a wait gives up (sets the timeout error)
   // three-stage backward: k_costate (costate chain) and k_gradient (per-step gradient) work on the
   // block of steps [n_begin, n_end); k_plan decides once per evaluation whether they run
   int n_begin, n_end;
@@ -205,9 +198,6 @@ __host__ __device__ inline SmemLayout make_glayout(int R, int max_nnz_loc, int i
 cudaError_t launch_schedule(const ScheduleParams& p, cudaStream_t st);
 cudaError_t launch_forward(const SweepParams& p, int precision, int smem_bytes, int threads, cudaStream_t st);
 cudaError_t launch_backward(const SweepParams& p, int precision, int smem_bytes, int threads, cudaStream_t st);
-cudaError_t launch_backward_split(const SweepParams& p, int precision, int smem_bytes, int threads, cudaStream_t st);
-// Largest number of co-resident clusters (or blocks when CL == 1) of the split backward kernel.
-int split_capacity(int precision, int CL, int smem_bytes, int threads);
 cudaError_t launch_plan(const PlanParams& p, cudaStream_t st);
 // priority: launch priority of the costate chain (the critical path), e.g. the device's greatest
 cudaError_t launch_costate(const SweepParams& p, int precision, int smem_bytes, int threads, int priority,

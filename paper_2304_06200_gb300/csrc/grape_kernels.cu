@@ -10,8 +10,8 @@
 // memory (distributed shared memory), and terms are separated by one team
 // barrier (__syncthreads for CL = 1, barrier.cluster otherwise; with one row per
 // thread its arrive and wait are split around the CTA-local entries).  Within a
-// team nothing goes through global memory; the two teams of k_backward_split
-// hand over through a ring of slots in global memory.
+// team nothing goes through global memory.  No kernel waits for another kernel or
+// for a CTA outside its cluster: kernels are ordered by their streams and events.
 //
 // Row layout.  Each row of the union pattern holds its diagonal first (when every
 // H_ii is real), then the entries whose B_ij is imaginary, then those whose B_ij
@@ -22,8 +22,10 @@
 //   k_schedule        ||A_n||_1 = dt max_i sum_j |H_n,ij| and the (m_n, s_n) lookup (Sec. III.B, App. C)
 //   k_forward         psi_n = (e^{B_n}_m)^s psi_{n-1}, C2 sum, C3 overlaps, checkpoints, psi_N, <phi_T|psi_N> partials
 //   k_finalize        g, C1, C2, C3, C_amp, cost
-//   k_backward        adjoint re-propagation of psi and the costate, gradient terms per step (one team per column)
-//   k_backward_split  the same with two concurrent teams per column (phase A / phase B of every substep)
+//   k_costate         the costate chain alone, Horner vectors stored per block of steps (three-stage backward)
+//   k_gradient        per-step gradient terms from the stored states and Horner vectors (three-stage backward)
+//   k_backward        adjoint re-propagation of psi and the costate, gradient terms per step (one team per
+//                     column; the fallback of the three-stage backward)
 //   k_grad_reduce     sum of per-CTA gradient partials + amplitude-penalty gradient
 //   k_sd_update       steepest-descent step u - (eta g) and the iterate's cost (Sec. II, Eq. (4))
 //   k_check_finite    non-finite controls set the device error word
@@ -102,6 +104,24 @@ __device__ __forceinline__ void cluster_arrive() {
 __device__ __forceinline__ void cluster_wait() {
   asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
+
+// Bulk asynchronous copy shared -> global of `bytes` (a multiple of 16, both addresses 16-byte
+// aligned), issued by one thread.  Its writes go through the async proxy: a later release (e.g. the
+// arrive of a cluster barrier) does not wait for them.  The source may be overwritten once
+// bulk_wait_read has confirmed the copy read it.
+__device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_t bytes) {
+  const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(ssrc));
+  asm volatile("fence.proxy.async.shared::cta;\n\t"
+               "cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n\t"
+               "cp.async.bulk.commit_group;\n" ::"l"(gdst), "r"(s), "r"(bytes) : "memory");
+}
+// At most N of this thread's bulk copies may still be reading their sources.
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;\n" ::"n"(N) : "memory");
+}
+// Every bulk copy of this thread has completed (its writes are performed).
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
 
 // The split barrier of the one-row-per-thread term loops.  A team of one CTA needs neither half: the
 // __syncthreads that ends every term already orders each buffer's writes before the next term's
@@ -1130,145 +1150,6 @@ __global__ void __launch_bounds__(512, 1) k_backward(SweepParams p) {
   team_sync<CLUSTER>();
 }
 
-// ------------------------------------------------------------------ backward sweep, two teams per column
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* a) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_release(unsigned* a, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
-}
-
-// Thread 0 polls until *flag >= target (wrap-safe), at most `limit` polls.
-__device__ __forceinline__ int wait_geq(const unsigned* flag, unsigned target, long long limit) {
-  for (long long it = 0; it < limit; ++it) {
-    if ((int)(ld_acquire(flag) - target) >= 0) return 1;
-    __nanosleep(128);
-  }
-  return 0;
-}
-
-// Team-uniform AND of one flag per CTA: every CTA of the team takes the same decision, so no CTA
-// leaves a loop that its cluster peers continue (which would strand them at a cluster barrier).
-// Alternating slots make one barrier sufficient.
-template <bool CLUSTER>
-__device__ __forceinline__ int team_all(int mine, int* s_flags, unsigned t, int CL) {
-  int* f = s_flags + (t & 1);
-  if (threadIdx.x == 0) *f = mine;
-  team_sync<CLUSTER>();
-  int all = 1;
-  if constexpr (CLUSTER) {
-    cg::cluster_group cl = cg::this_cluster();
-    for (int r = 0; r < CL; ++r) all &= *cl.map_shared_rank(f, r);
-  } else {
-    all = *f;
-  }
-  return all;
-}
-
-// The backward sweep with its two phases on two teams per column that run concurrently: team A
-// (role 0) runs phase A and publishes, per substep, psi^(l) and the Horner vectors w_p into a ring
-// slot in global memory; team B (role 1) runs phase B one substep behind and computes the per-step
-// gradient partials.  A's CTA r hands rows [r0, r1) to B's CTA r through release/acquire flags
-// (one pair per CTA), so a substep costs no extra team barrier.  Every wait is bounded; a wait that
-// gives up sets the timeout error and both teams leave uniformly.  The arithmetic per row is the
-// same as in k_backward, so the results are identical.
-template <typename T, bool CLUSTER>
-__global__ void __launch_bounds__(512, 1) k_backward_split(SweepParams p) {
-  using C2 = cx<T>;
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double red[32];
-  __shared__ double s_u[kMaxControls];
-  __shared__ XTab<T> tab[6];
-  __shared__ int s_flags[2];
-  const int part = blockIdx.x;
-  const int team = part / p.CL, rank = part % p.CL;
-  const int col = team >> 1, role = team & 1;
-  Team<T, CLUSTER> tm;
-  team_init<T, CLUSTER>(tm, smem, tab, p, part, rank);
-  const Carve<T>& c = tm.c;
-  const int64_t col0 = (int64_t)col * p.dim + tm.r0;
-  const int dim = p.dim, r0 = tm.r0;
-  const int64_t slot_c2 = p.ring_slot;                  // bulk-type elements per ring slot
-  C2* ring_col = reinterpret_cast<C2*>(p.ring) + (int64_t)col * p.ring_depth * slot_c2;
-  unsigned* ready = p.ready + col * p.CL + rank;
-  unsigned* done = p.done + col * p.CL + rank;
-  const double c2w = (p.omega && p.w_forbid != 0.0) ? p.w_forbid / ((double)p.N * p.n_states) : 0.0;
-  unsigned t = 0;
-  bool alive = true;
-  if (role == 0) {
-    costate_init(p, c.psi, c.chi, col0, r0, tm.nrows, c2w);
-    team_sync<CLUSTER>();
-    for (int n = p.N - 1; n >= 0 && alive; --n) {
-      const int m = p.ms_m[n], s = p.ms_s[n];
-      if (s <= 0 || m <= 0) continue;
-      load_controls(p, n, s_u);
-      __syncthreads();
-      assemble<T>(p, c.vals, tm.e0, tm.nnz_loc, p.dt / s, s_u);
-      __syncthreads();
-      for (int l = s - 1; l >= 0; --l) {
-        C2* rs = ring_col + (int64_t)(t % (unsigned)p.ring_depth) * slot_c2;
-        if (t >= (unsigned)p.ring_depth) {
-          int ok = 1;
-          if (threadIdx.x == 0) ok = wait_geq(done, t + 1 - (unsigned)p.ring_depth, p.spin_limit);
-          if (!team_all<CLUSTER>(ok, s_flags, t, p.CL)) {
-            if (threadIdx.x == 0) set_error(p.err, kErrTimeout);
-            alive = false;
-            break;
-          }
-        }
-        phase_a<T, CLUSTER>(tm, m, [&](int pp, int i, C2 w) { rs[(int64_t)(1 + pp) * dim + r0 + i] = w; });
-        for (int i = threadIdx.x; i < tm.nrows; i += blockDim.x) rs[r0 + i] = from_d2<T>(c.psi[i]);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          __threadfence();
-          st_release(ready, t + 1);
-        }
-        ++t;
-      }
-      if (!alive) break;
-      __syncthreads();
-      step_end(p, c.psi, c.chi, n, col, r0, tm.nrows, c2w);
-      __syncthreads();
-    }
-  } else {
-    const int partB = col * p.CL + rank;
-    team_sync<CLUSTER>();
-    for (int n = p.N - 1; n >= 0 && alive; --n) {
-      const int m = p.ms_m[n], s = p.ms_s[n];
-      if (s <= 0 || m <= 0) continue;
-      load_controls(p, n, s_u);
-      __syncthreads();
-      assemble<T>(p, c.vals, tm.e0, tm.nnz_loc, p.dt / s, s_u);
-      zero_w(p, c.W, c.Wb, tm.nnz_loc, sizeof(C2) == 8);
-      __syncthreads();
-      for (int l = s - 1; l >= 0; --l) {
-        const C2* rs = ring_col + (int64_t)(t % (unsigned)p.ring_depth) * slot_c2;
-        int ok = 1;
-        if (threadIdx.x == 0) ok = wait_geq(ready, t + 1, p.spin_limit);
-        if (!team_all<CLUSTER>(ok, s_flags, t, p.CL)) {
-          if (threadIdx.x == 0) set_error(p.err, kErrTimeout);
-          alive = false;
-          break;
-        }
-        for (int i = threadIdx.x; i < tm.nrows; i += blockDim.x) tm.X(4)[i] = __ldcg(rs + r0 + i);
-        phase_b<T, CLUSTER>(tm, m, [&](int pp, int i) -> C2 { return __ldcg(rs + (int64_t)(1 + pp) * dim + r0 + i); });
-        __syncthreads();
-        if (threadIdx.x == 0) st_release(done, t + 1);
-        ++t;
-      }
-      if (!alive) break;
-      __syncthreads();
-      grad_partials(p, c.W, rank, partB, n, s, tm.e0, red);
-      __syncthreads();
-    }
-  }
-  team_sync<CLUSTER>();
-}
-
 // ------------------------------------------------------------------ three-stage backward
 //
 // The backward sweep split by role.  Its only sequential part is the costate chain: for every step
@@ -1408,16 +1289,17 @@ __global__ void __launch_bounds__(512, 1) k_costate(SweepParams p) {
     for (int l = s - 1; l >= 0; --l) {
       C2* const hl = hb + (toff + (int64_t)l * m) * hstride + col0;   // w_p of substep l: hl[p * hstride + i]
       const double fm = c_inv_fact[m];
-      for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
-        const C2 w = from_d2<T>(cscale(chi[i], fm));
-        X0[i] = w;
-        hl[(int64_t)(m - 1) * hstride + i] = w;
-      }
       if constexpr (sizeof(C2) == 16) {
         if (split_rows) {
           // Same split cluster barrier as the forward sweep: term q reads w_{m-q} from buffer
-          // (q - 1) & 1 and writes w_{m-1-q} to buffer q & 1.
+          // (q - 1) & 1 and writes w_{m-1-q} to buffer q & 1.  Thread 0 copies each buffer's rows
+          // to the Horner block with one bulk asynchronous copy once the term has written it; a
+          // buffer is rewritten two terms later, after thread 0 has waited (before its arrive) for
+          // all but its latest copy to finish reading.
+          const uint32_t rbytes = (uint32_t)nrows * 16u;
+          for (int i = threadIdx.x; i < nrows; i += blockDim.x) X0[i] = from_d2<T>(cscale(chi[i], fm));
           __syncthreads();
+          if (threadIdx.x == 0 && rbytes) bulk_store(hl + (int64_t)(m - 1) * hstride, X0, rbytes);
           split_arrive<CLUSTER>();
           const int i = threadIdx.x;
           for (int q = 1; q <= m; ++q) {
@@ -1447,16 +1329,23 @@ __global__ void __launch_bounds__(512, 1) k_costate(SweepParams p) {
             }
             if (q < m) {
               __syncthreads();
+              if (threadIdx.x == 0 && rbytes) {
+                bulk_store(hl + (int64_t)(m - 1 - q) * hstride, X0 + dst * R, rbytes);
+                bulk_wait_read<1>();   // the copy of the other buffer has read it
+              }
               split_arrive<CLUSTER>();
-              // the global copy of w_{m-1-q} is issued after the arrive: the arrive's release then does
-              // not wait for it (only the next term's does, by when it has long completed)
-              if (i < nrows) hl[(int64_t)(m - 1 - q) * hstride + i] = y;
             } else {
+              if (threadIdx.x == 0) bulk_wait_read<0>();   // the next substep rewrites buffer 0
               team_sync<CLUSTER>();
             }
           }
           continue;
         }
+      }
+      for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+        const C2 w = from_d2<T>(cscale(chi[i], fm));
+        X0[i] = w;
+        hl[(int64_t)(m - 1) * hstride + i] = w;
       }
       team_sync<CLUSTER>();
       for (int q = 1; q <= m; ++q) {
@@ -1505,6 +1394,7 @@ __global__ void __launch_bounds__(512, 1) k_costate(SweepParams p) {
     }
   }
   for (int i = threadIdx.x; i < nrows; i += blockDim.x) p.chi_io[col0 + i] = chi[i];
+  if (threadIdx.x == 0) bulk_wait_all();   // the Horner block is complete before the kernel ends
   team_sync<CLUSTER>();   // no CTA leaves while a team member may still read its shared memory
 }
 
@@ -1897,89 +1787,6 @@ cudaError_t launch_backward(const SweepParams& p, int precision, int smem_bytes,
   }
   if (p.CL > 1) return launch_sweep(k_backward<double, true>, p, smem_bytes, threads, st);
   return launch_sweep(k_backward<double, false>, p, smem_bytes, threads, st);
-}
-
-template <typename KernelT>
-static cudaError_t launch_split(KernelT kern, const SweepParams& p, int smem_bytes, int threads, cudaStream_t st) {
-  cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-  if (r != cudaSuccess) return r;
-  if (p.CL > 8) {
-    r = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (r != cudaSuccess) return r;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(2 * p.n_states * p.CL);
-  cfg.blockDim = dim3(threads);
-  cfg.dynamicSmemBytes = smem_bytes;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[2];
-  int na = 0;
-  attr[na].id = cudaLaunchAttributeCooperative;   // both teams of a column must be co-resident
-  attr[na].val.cooperative = 1;
-  ++na;
-  if (p.CL > 1) {
-    attr[na].id = cudaLaunchAttributeClusterDimension;
-    attr[na].val.clusterDim.x = p.CL;
-    attr[na].val.clusterDim.y = 1;
-    attr[na].val.clusterDim.z = 1;
-    ++na;
-  }
-  cfg.attrs = attr;
-  cfg.numAttrs = na;
-  r = cudaLaunchKernelEx(&cfg, kern, p);
-  if (r != cudaSuccess) return r;
-  return cudaGetLastError();
-}
-
-cudaError_t launch_backward_split(const SweepParams& p, int precision, int smem_bytes, int threads, cudaStream_t st) {
-  cudaError_t e = ensure_constants();
-  if (e != cudaSuccess) return e;
-  if (precision == 1) {
-    if (p.CL > 1) return launch_split(k_backward_split<float, true>, p, smem_bytes, threads, st);
-    return launch_split(k_backward_split<float, false>, p, smem_bytes, threads, st);
-  }
-  if (p.CL > 1) return launch_split(k_backward_split<double, true>, p, smem_bytes, threads, st);
-  return launch_split(k_backward_split<double, false>, p, smem_bytes, threads, st);
-}
-
-template <typename KernelT>
-static int capacity_of(KernelT kern, int CL, int smem_bytes, int threads) {
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) != cudaSuccess) return 0;
-  if (CL > 1) {
-    if (CL > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) return 0;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(CL);
-    cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = smem_bytes;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) return 0;
-    return n;
-  }
-  int per_sm = 0, dev = 0, nsm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem_bytes) != cudaSuccess) return 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  return per_sm * nsm;
-}
-
-int split_capacity(int precision, int CL, int smem_bytes, int threads) {
-  cudaGetLastError();
-  int r;
-  if (precision == 1)
-    r = CL > 1 ? capacity_of(k_backward_split<float, true>, CL, smem_bytes, threads)
-               : capacity_of(k_backward_split<float, false>, CL, smem_bytes, threads);
-  else
-    r = CL > 1 ? capacity_of(k_backward_split<double, true>, CL, smem_bytes, threads)
-               : capacity_of(k_backward_split<double, false>, CL, smem_bytes, threads);
-  cudaGetLastError();
-  return r;
 }
 
 cudaError_t launch_plan(const PlanParams& p, cudaStream_t st) {

@@ -74,7 +74,7 @@ class GrapeProblem:
     def __init__(self, problem, precision: str = "fp64", ckpt_every: int = 0, cluster: int = 0, device: int = 0,
                  tau: float | None = None, m_max: int = 0, torch_allocator: bool = True, n_steps: int | None = None,
                  backward_mode: int = 0, bulk_norm_cap: float = 0.0, propagator: str = "taylor",
-                 wait_limit: int = 0, grad_cluster: int = 0, block_steps: int = 0):
+                 grad_cluster: int = 0, block_steps: int = 0):
         L = lib()
         self._lib = L
         self.dim = int(problem.dim)
@@ -129,7 +129,6 @@ class GrapeProblem:
         d.bulk_norm_cap = float(bulk_norm_cap)
         d.w_tint = float(getattr(problem, "w_tint", 0.0))
         d.propagator = PROPAGATORS[propagator]
-        d.wait_limit = int(wait_limit)
         d.grad_cluster = int(grad_cluster)
         d.block_steps = int(block_steps)
         handle = C.c_void_p()

@@ -108,11 +108,24 @@ def test_create_rejects_bad_propagator_choices(L):
     assert not h.value
 
 
-def test_create_rejects_a_negative_wait_limit(L):
+@pytest.mark.parametrize("field,value,word", [("backward_mode", 2, b"backward_mode"), ("backward_mode", 4, b"backward_mode"),
+                                             ("grad_cluster", 17, b"grad_cluster"), ("block_steps", -1, b"block_steps")])
+def test_create_rejects_bad_backward_options(L, field, value, word):
     from paper_2304_06200_gb300._abi import GrapeDesc
     h = C.c_void_p()
     d = GrapeDesc()
     d.dim, d.n_steps, d.n_states, d.dt, d.tau = 4, 3, 1, 0.1, 1e-8
-    d.wait_limit = -1
+    setattr(d, field, value)
     assert L.grape_problem_create(C.byref(d), C.byref(h)) == 1
-    assert b"wait_limit" in L.grape_last_error()
+    assert word in L.grape_last_error()
+    assert not h.value
+
+
+def test_three_stage_needs_every_state_stored(L):
+    from paper_2304_06200_gb300._abi import GrapeDesc
+    h = C.c_void_p()
+    d = GrapeDesc()
+    d.dim, d.n_steps, d.n_states, d.dt, d.tau = 4, 3, 1, 0.1, 1e-8
+    d.backward_mode, d.ckpt_every = 3, 5
+    assert L.grape_problem_create(C.byref(d), C.byref(h)) == 1
+    assert b"ckpt_every" in L.grape_last_error()

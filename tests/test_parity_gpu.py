@@ -161,8 +161,8 @@ def _single_phase_entries(p, seed, diag_imag=0.0):
     return q, [sum(1 for v in kind.values() if v == c) for c in range(3)]
 
 
-@pytest.mark.parametrize("cluster,mode,diag_imag", [(4, 1, 0.0), (4, 2, 0.0), (8, 2, 0.0), (16, 1, 0.0),
-                                                    (4, 2, 1e-14)])
+@pytest.mark.parametrize("cluster,mode,diag_imag", [(4, 1, 0.0), (4, 3, 0.0), (8, 3, 0.0), (16, 1, 0.0),
+                                                    (4, 3, 1e-14)])
 def test_single_phase_entries_in_cluster_sweeps(cluster, mode, diag_imag):
     """Real, imaginary and general H_ij in the same rows (and a diagonal that is not exactly real):
     the one-row-per-thread cluster sweeps that apply the single-phase entries with two multiplies
@@ -191,24 +191,6 @@ def test_team_sizes_agree(cluster):
     hg = _hg(p, cluster=cluster)
     cost, grad = hg.cost_and_grad(u)
     _check(p, u, cost, grad, ref=ref)
-
-
-@pytest.mark.parametrize("name,N,cluster,drive", [("c2_gate_d80", 60, 0, 10.0), ("c2_gate_d80", 30, 4, 20.0),
-                                                 ("c1_state_transfer_d30", 40, 16, 5.0),
-                                                 ("c2_gate_d80", 25, 12, 10.0), ("c1_state_transfer_d30", 20, 7, 3.0)])
-def test_split_and_fused_backward_agree_bitwise(name, N, cluster, drive):
-    """Two concurrent teams per column (phase A / phase B) give exactly the one-team result."""
-    p = build_config(name, n_steps=N)
-    u = p.u0 * drive
-    fused = _hg(p, cluster=cluster, backward_mode=1)
-    split = _hg(p, cluster=cluster, backward_mode=2)
-    assert fused.info()["backward_mode"] == 1 and split.info()["backward_mode"] == 2
-    c1, g1 = fused.cost_and_grad(u)
-    c2, g2 = split.cost_and_grad(u)
-    assert c1 == c2
-    assert np.array_equal(g1, g2)
-    c3, g3 = split.cost_and_grad(u)          # the ring flags restart at zero every launch
-    assert c3 == c2 and np.array_equal(g3, g2)
 
 
 @pytest.mark.parametrize("name,N,cluster,gcl,steps,drive,prec", [
@@ -389,16 +371,6 @@ def test_fp32_bulk_parity_random(dim, K, n, N, cluster):
     _check(p, p.u0, cost, grad, cost_rtol=FP32_RTOL, grad_rtol=FP32_RTOL)
 
 
-def test_fp32_bulk_split_and_fused_agree_bitwise():
-    p = build_config("c2_gate_d80", n_steps=40)
-    u = p.u0 * 10
-    a = _hg(p, precision="fp32_bulk", backward_mode=1).cost_and_grad(u)
-    b = _hg(p, precision="fp32_bulk", backward_mode=2).cost_and_grad(u)
-    assert a[0] == b[0] and np.array_equal(a[1], b[1])
-
-
-# ---------------------------------------------------------------- batches (one CUDA-graph launch for many problems)
-
 def _small_batch(precision):
     from paper_2304_06200_gb300 import GrapeProblem
     from workloads.transmon import _gate_problem, _subspace_one, transmon_cavity
@@ -434,12 +406,14 @@ def test_batch_graph_matches_individual_evaluations(precision):
     batch.close()
 
 
-def test_batch_rejects_two_team_members():
+def test_batch_rejects_three_stage_members_and_removed_modes():
     from paper_2304_06200_gb300 import GrapeBatch, GrapeError
     p = build_config("c1_state_transfer_d30", n_steps=10)
-    hg = _hg(p, backward_mode=2)
+    hg = _hg(p, backward_mode=3)
     with pytest.raises(GrapeError):
         GrapeBatch([hg])
+    with pytest.raises(GrapeError):      # the two-team mode 2 no longer exists
+        _hg(p, backward_mode=2)
 
 
 def test_autotune_returns_a_correct_problem():
@@ -715,22 +689,6 @@ def test_c3_full_size_in_the_bench_configuration():
         cm = hg.cost(um)
         fd = (cp - cm) / (2 * h)
         assert abs(fd - grad[k, n]) <= 1e-6 * np.abs(grad).max(), (k, n, fd, grad[k, n])
-
-
-def test_bounded_wait_gives_up_with_a_status():
-    """Failure detection without a GPU fault: with a one-poll wait limit the two-team backward's
-    first wait for its partner runs out; both teams leave uniformly, the call returns
-    GRAPE_ETIMEOUT, and the device stays usable."""
-    from paper_2304_06200_gb300 import GrapeError
-    p = build_config("c2_gate_d80", n_steps=30)
-    impatient = _hg(p, backward_mode=2, wait_limit=1)
-    assert impatient.info()["backward_mode"] == 2
-    with pytest.raises(GrapeError) as ei:
-        impatient.cost_and_grad(p.u0)
-    assert ei.value.name == "GRAPE_ETIMEOUT"
-    impatient.close()
-    c, g = _hg(p, backward_mode=2).cost_and_grad(p.u0)
-    _check(p, p.u0, c, g)
 
 
 def test_allocation_failure_is_reported():
