@@ -68,7 +68,11 @@ typedef enum { GRAPE_CSR = 0, GRAPE_DENSE = 1 } grape_format;
  * step norms are FP64 in every mode. */
 typedef enum {
   GRAPE_FP64 = 0,        /* complex128 throughout                                        */
-  GRAPE_FP32_BULK = 1,   /* Taylor increments in complex64, states/costates kept FP64     */
+  GRAPE_FP32_BULK = 1,   /* compensated FP32 bulk: every Taylor term, product and Horner vector
+                            is a pair of complex64 numbers hi + lo, accumulated with error-free
+                            FP32 transformations (TwoProduct by FMA, TwoSum), about 2^-48
+                            relative per operation; states, costates, W and reductions FP64.
+                            Scheduled by the FP64 rule (u = 2^-53); errors are measured.       */
   GRAPE_TC_FP16 = 2,     /* dense operator: every Taylor product is a real-split GEMM on the
                             tensor cores (FP16 hi/lo operands, FP32 accumulation); states,
                             costates and reductions FP64.  Needs dim % 128 == 0, n_states <= 16. */
@@ -136,9 +140,9 @@ typedef struct {
                                   (needs ckpt_every 0 or 1; memory N * dim * n_states * 16 bytes
                                   for the states plus two blocks of Horner vectors)            */
   double bulk_norm_cap;        /* > 0: the (m, s) rule only considers s >= ||A||_1 / cap, i.e.
-                                  ||B||_1 <= cap, which bounds the largest Taylor term (reduces
-                                  FP32-bulk rounding); 0 = default (2.0 for GRAPE_FP32_BULK, no
-                                  cap for GRAPE_FP64, i.e. the paper's rule unchanged)            */
+                                  ||B||_1 <= cap, which bounds the largest Taylor term; 0 = default
+                                  (2.0 for the tensor-core modes, no cap for GRAPE_FP64 and
+                                  GRAPE_FP32_BULK, i.e. the paper's rule unchanged)             */
   double w_tint;               /* weight alpha_4 of the time-integrated infidelity
                                   C3 = 1 - 1/(N n^2) sum_{n'=1..N} |sum_h <phi_T^h|psi_n'^h>|^2
                                   (App. A, C3st / C3g; 0 = off)                                 */
@@ -256,7 +260,8 @@ grape_status grape_step_schedule(grape_problem* prob, int32_t* m, int32_t* s, do
 
 /* The paper's rule on the host (Sec. III.B; App. C Eq. (overallupperbound)): the smallest
  * s, then the smallest m <= m_max, with E_A(m, s) <= tau for ||A||_1 = x and sigma' = sigma,
- * unit roundoff 2^-53 (precision GRAPE_FP64) or 2^-24 (GRAPE_FP32_BULK).
+ * unit roundoff 2^-53 (precision GRAPE_FP64) or 2^-24 (precision 1: the bound for plain FP32
+ * terms; GRAPE_FP32_BULK problems themselves are scheduled with 2^-53).
  * GRAPE_ETOL if no pair with s <= s_max qualifies.  Pure host computation. */
 grape_status grape_select_ms(double x, double tau, int32_t sigma, int32_t precision, int32_t m_max,
                              int32_t s_max, int32_t* m, int32_t* s);

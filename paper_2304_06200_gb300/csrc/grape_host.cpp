@@ -205,7 +205,8 @@ struct grape_problem {
   cudaStream_t g_stream[kGradStreams] = {nullptr, nullptr};   // k_gradient launches
   cudaEvent_t ev_b = nullptr, ev_g[kHbufDepth] = {nullptr, nullptr, nullptr};
   int prio_hi = 0;                       // launch priority of the costate chain
-  int64_t scr_g_off = 0;                 // k_gradient's region of d_scratch (double2 units)
+  int64_t scr_g_off = 0;                 // k_gradient's regions of d_scratch (double2 units), one of
+  int64_t scr_g_size = 0;                // scr_g_size per gradient stream
   // kernel tracing: event pairs around each launch (kind 0..3), summed by grape_kernel_times
   bool tracing = false;
   std::vector<cudaEvent_t> tr_events;    // pool, two per traced launch
@@ -844,10 +845,13 @@ grape_status build(grape_problem* P, const grape_desc* d) {
   // (barrier + first remote loads) across a cluster; launches wider than the GPU run in waves.
   const int dev = P->device;
   const int nsm = sm_count(dev);
-  const int cb = P->precision == GRAPE_FP32_BULK ? 8 : 16;   // bytes of one bulk complex number
+  const int cb = 16;                                          // bytes of one bulk complex number
+  const bool stg = P->precision == GRAPE_FP32_BULK;           // compensated FP32 bulk: staged W
   const int smem_max = grape::max_dynamic_smem(dev) - 2048;   // static shared memory of the kernels
-  const double a_cost = cb == 16 ? 4.0 / 1.7 : 4.0 / 100.0;   // clocks per complex multiply-add per SM
-  const double b_cost = 2.0 / 1.7;
+  // clocks per complex multiply-add per SM: FP64 4 FMAs (the model's constant from the sweeps' own
+  // measured rate); the compensated FP32 one about 48 FP32 operations at 128 lanes/clk
+  const double a_cost = stg ? 48.0 / 128.0 : 4.0 / 1.7;
+  const double b_cost = stg ? 24.0 / 128.0 : 2.0 / 1.7;
   int64_t nnz_ctrl = 0;
   for (int64_t e = 0; e < nnz; ++e) nnz_ctrl += ectr_ptr[e + 1] > ectr_ptr[e] ? 1 : 0;
   const double wf = nnz > 0 ? (double)nnz_ctrl / (double)nnz : 0.0;
@@ -869,17 +873,17 @@ grape_status build(grape_problem* P, const grape_desc* d) {
   auto waves = [&](int ctas) { return std::ceil((double)ctas / nsm); };
   // backward shared-memory plan for (R, mnl): which optional buffers fit, Horner slots kept in smem
   auto bwd_plan = [&](int R, int mnl, int* bin_out, int* msm_out, int* fused_smem, int* split_smem) -> bool {
-    if (grape::make_layout(true, R, mnl, 0, 0, cb).total > smem_max) return false;
+    if (grape::make_layout(true, R, mnl, 0, 0, cb, stg).total > smem_max) return false;
     int bin = 0;
-    if (grape::make_layout(true, R, mnl, 1, 0, cb).total <= smem_max) bin = 1;
-    if (grape::make_layout(true, R, mnl, bin | 2, 0, cb).total <= smem_max) bin |= 2;
-    if (cb == 8 && grape::make_layout(true, R, mnl, bin | 4, 0, cb).total <= smem_max) bin |= 4;
-    const int base = grape::make_layout(true, R, mnl, bin, 0, cb).total;
+    if (grape::make_layout(true, R, mnl, 1, 0, cb, stg).total <= smem_max) bin = 1;
+    if (grape::make_layout(true, R, mnl, bin | 2, 0, cb, stg).total <= smem_max) bin |= 2;
+    if (stg && grape::make_layout(true, R, mnl, bin | 4, 0, cb, stg).total <= smem_max) bin |= 4;
+    const int base = grape::make_layout(true, R, mnl, bin, 0, cb, stg).total;
     int msm = (int)std::min<int64_t>(P->m_cap, (smem_max - base - 16) / std::max<int64_t>((int64_t)R * cb, 1));
     msm = std::max(msm, 0);
     *bin_out = bin;
     *msm_out = msm;
-    *fused_smem = grape::make_layout(true, R, mnl, bin, msm, cb).total;
+    *fused_smem = grape::make_layout(true, R, mnl, bin, msm, cb, stg).total;
     *split_smem = base;
     return true;
   };
@@ -893,7 +897,7 @@ grape_status build(grape_problem* P, const grape_desc* d) {
       if (CL > 1 && CL > dim) continue;
       int R = 0, mnl = 0;
       if (!rows_entries(CL, &R, &mnl)) continue;
-      if (grape::make_layout(false, R, mnl, 0, 0, cb).total > smem_max) continue;
+      if (grape::make_layout(false, R, mnl, 0, 0, cb, stg).total > smem_max) continue;
       const double cost = waves(P->n * CL) * (a_cost * mnl + b_cost * R + sync_cost(CL));
       if (cost < best * 0.98) {
         best = cost;
@@ -904,9 +908,9 @@ grape_status build(grape_problem* P, const grape_desc* d) {
     }
     if (P->fwd.CL == 0) return fail(GRAPE_EINVAL, "problem does not fit the forward sweep's shared memory");
     const int R = P->fwd.R, mnl = P->fwd.mnl;
-    P->fwd.in_smem = grape::make_layout(false, R, mnl, 1, 0, cb).total <= smem_max ? 1 : 0;
+    P->fwd.in_smem = grape::make_layout(false, R, mnl, 1, 0, cb, stg).total <= smem_max ? 1 : 0;
     P->fwd.m_smem = 0;
-    P->fwd.smem = grape::make_layout(false, R, mnl, P->fwd.in_smem, 0, cb).total;
+    P->fwd.smem = grape::make_layout(false, R, mnl, P->fwd.in_smem, 0, cb, stg).total;
     P->fwd.threads = threads_for(R);
   }
   // Three-stage backward: the costate chain runs on the forward's partition (n * CL_f SMs); it pays
@@ -928,14 +932,14 @@ grape_status build(grape_problem* P, const grape_desc* d) {
   // gradient work covers about twice the SMs the costate chain leaves free.
   if (three) {
     int pick = 0, pick_in = 0;
-    const int full = 1 | 2 | (cb == 8 ? 4 : 0);
+    const int full = 1 | 2 | (stg ? 4 : 0);
     for (int CL = 1; CL <= grape::kMaxCluster && !pick; ++CL) {
       if (d->grad_cluster > 0 && CL != d->grad_cluster) continue;
       if (CL > 1 && CL > dim) continue;
       int R = 0, mnl = 0;
       if (!rows_entries(CL, &R, &mnl)) continue;
-      for (int want : {full, 2 | (cb == 8 ? 4 : 0), 0}) {
-        if (grape::make_glayout(R, mnl, want, cb).total > smem_max) continue;
+      for (int want : {full, 2 | (stg ? 4 : 0), 0}) {
+        if (grape::make_glayout(R, mnl, want, cb, stg).total > smem_max) continue;
         pick = CL;
         pick_in = want;
         P->grd.R = R;
@@ -950,7 +954,7 @@ grape_status build(grape_problem* P, const grape_desc* d) {
       P->grd.CL = pick;
       P->grd.in_smem = pick_in;
       P->grd.m_smem = 0;
-      P->grd.smem = grape::make_glayout(P->grd.R, P->grd.mnl, pick_in, cb).total;
+      P->grd.smem = grape::make_glayout(P->grd.R, P->grd.mnl, pick_in, cb, stg).total;
       P->grd.threads = threads_for(P->grd.R);
       const int free_sms = std::max(nsm - P->n * P->fwd.CL, P->n * pick);
       const int S = d->block_steps > 0 ? d->block_steps : std::min(32, std::max(1, 2 * free_sms / (P->n * pick)));
@@ -1070,11 +1074,14 @@ grape_status build(grape_problem* P, const grape_desc* d) {
   if ((st = dzeros(P, &P->d_part_g3, (size_t)parts_f * P->N)) || (st = dzeros(P, &P->d_g3, (size_t)P->N))) return st;
   const int64_t scr_f = (int64_t)parts_f * P->fwd.stride;
   const int64_t scr_b = (int64_t)P->n * P->bwd.CL * P->bwd.stride;
-  // k_costate (forward partition) and k_gradient run at the same time: disjoint scratch regions
+  // k_costate (forward partition) and the k_gradient launches of the gradient streams run at the
+  // same time: disjoint scratch regions, one per gradient stream
   int64_t scr_g = 0;
   if (three) scr_g = (int64_t)P->steps_per_block * P->n * P->grd.CL * P->grd.stride;
   P->scr_g_off = scr_f;
-  if ((st = dzeros(P, &P->d_scratch, (size_t)std::max(scr_f + scr_g, scr_b)))) return st;
+  P->scr_g_size = scr_g;
+  const int64_t scr_three = scr_f + grape_problem::kGradStreams * scr_g;
+  if ((st = dzeros(P, &P->d_scratch, (size_t)std::max(scr_three, scr_b)))) return st;
   if (three) {
     // Block buffers of Horner vectors, first sized for the schedule of 1.25 times the drift's norm (at
     // least 2 m_cap terms per step).  Outside stream capture every evaluation reads its schedule back
@@ -1294,7 +1301,8 @@ grape_status grape_problem_create(const grape_desc* d, grape_problem** out) {
   P->tau = d->tau;
   P->precision = d->precision;
   P->m_cap = d->m_max == 0 ? grape::kMaxTaylor : d->m_max;
-  P->b_cap = d->bulk_norm_cap > 0.0 ? d->bulk_norm_cap : (d->precision != GRAPE_FP64 ? 2.0 : 0.0);
+  const bool tc = d->precision == GRAPE_TC_FP16 || d->precision == GRAPE_TC_BF16;
+  P->b_cap = d->bulk_norm_cap > 0.0 ? d->bulk_norm_cap : (tc ? 2.0 : 0.0);
   P->alloc_fn = d->alloc;
   P->free_fn = d->free;
   P->alloc_ctx = d->alloc_ctx;
@@ -1481,7 +1489,7 @@ grape_status run_backward(grape_problem* P, cudaStream_t st) {
           P->opt_exec = nullptr;
         }
         const int64_t terms = need + need / 4;
-        const size_t cbytes = P->precision == GRAPE_FP32_BULK ? 8 : 16;
+        const size_t cbytes = 16;   // one bulk complex (double2, or float4 for the compensated bulk)
         const size_t hb = (size_t)terms * (size_t)P->dim * P->n * cbytes;
         for (auto& h : P->d_hbuf) {
           P->dfree(h);
@@ -1510,7 +1518,7 @@ grape_status run_backward(grape_problem* P, cudaStream_t st) {
     pc.hbuf_terms = P->hbuf_terms;
     grape::SweepParams pg = sweep_params(P, P->grd);
     pg.cslice = P->d_cslice_g;
-    pg.scratch = P->d_scratch + P->scr_g_off;
+    double2* const scr_g0 = P->d_scratch + P->scr_g_off;
     pg.plan_flag = P->d_plan_flag;
     pg.hbuf_terms = P->hbuf_terms;
     const int S = P->steps_per_block, nb = (P->N + S - 1) / S;
@@ -1518,6 +1526,7 @@ grape_status run_backward(grape_problem* P, cudaStream_t st) {
     for (int b = nb - 1; b >= 0; --b) {
       const int slot = b % D;
       cudaStream_t gs = P->g_stream[b % G];
+      pg.scratch = scr_g0 + (int64_t)(b % G) * P->scr_g_size;   // concurrent launches never share scratch
       pc.n_begin = pg.n_begin = b * S;
       pc.n_end = pg.n_end = std::min(P->N, (b + 1) * S);
       pc.hbuf = pg.hbuf = P->d_hbuf[slot];

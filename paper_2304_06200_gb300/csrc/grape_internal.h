@@ -107,7 +107,7 @@ struct ScheduleParams {
   const double* table;                 // s_cap x m_cap breakpoints X[s-1][m-1] (largest feasible x), < 0 = never
   const double* table_smax;            // s_cap: max over m of X
   int m_cap, s_cap;
-  double b_cap;                        // > 0: only pairs with ||B||_1 = x / s <= b_cap (FP32-bulk schedule)
+  double b_cap;                        // > 0: only pairs with ||B||_1 = x / s <= b_cap
   int* ms_m;
   int* ms_s;
   double* norm1;
@@ -151,10 +151,11 @@ struct SmemLayout {
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
-// in_smem bit 0: vals, bit 1: W, bit 2: Wb (FP32-bulk staging of W); m_smem = Horner slots kept in
-// shared memory; cplx_bytes = 16 (FP64 bulk) or 8 (FP32 bulk).
+// in_smem bit 0: vals, bit 1: W, bit 2: Wb (per-substep compensated staging of W, staged = true for the
+// compensated FP32 bulk, 16 bytes per entry); m_smem = Horner slots kept in
+// shared memory; cplx_bytes = 16 (one bulk complex: double2, or float4 for the compensated FP32 bulk).
 __host__ __device__ inline SmemLayout make_layout(bool backward, int R, int max_nnz_loc, int in_smem, int m_smem,
-                                                  int cplx_bytes) {
+                                                  int cplx_bytes, bool staged) {
   SmemLayout L;
   const int nchains = backward ? 3 : 1;
   int off = 0;
@@ -166,7 +167,7 @@ __host__ __device__ inline SmemLayout make_layout(bool backward, int R, int max_
   L.vals = -1; L.W = -1; L.Wb = -1; L.wslot = -1;
   if (in_smem & 1) { L.vals = off; off += align16(max_nnz_loc * cplx_bytes); }
   if (backward && (in_smem & 2)) { L.W = off; off += align16(max_nnz_loc * 16); }
-  if (backward && cplx_bytes == 8 && (in_smem & 4)) { L.Wb = off; off += align16(max_nnz_loc * 8); }
+  if (backward && staged && (in_smem & 4)) { L.Wb = off; off += align16(max_nnz_loc * 16); }
   if (backward && m_smem > 0) { L.wslot = off; off += align16(m_smem * R * cplx_bytes); }
   L.lrow = off; off += align16((R + 1) * 4);
   L.lcol = off; off += align16(max_nnz_loc * 4);
@@ -175,9 +176,9 @@ __host__ __device__ inline SmemLayout make_layout(bool backward, int R, int max_
 }
 
 // Layout of k_gradient (byte offsets): the x chain's two exchange buffers, psi^(l), the increment,
-// then vals (in_smem bit 0) and W (bit 1, FP64 accumulators per local entry) and, for the FP32
-// bulk, the FP32 staging of W (bit 2), then the local pattern.
-__host__ __device__ inline SmemLayout make_glayout(int R, int max_nnz_loc, int in_smem, int cplx_bytes) {
+// then vals (in_smem bit 0) and W (bit 1, FP64 accumulators per local entry) and, for the compensated FP32
+// bulk, the compensated staging of W (bit 2, 16 bytes per entry), then the local pattern.
+__host__ __device__ inline SmemLayout make_glayout(int R, int max_nnz_loc, int in_smem, int cplx_bytes, bool staged) {
   SmemLayout L;
   int off = 0;
   L.xbuf = off; off += align16(2 * R * cplx_bytes);
@@ -187,7 +188,7 @@ __host__ __device__ inline SmemLayout make_glayout(int R, int max_nnz_loc, int i
   L.vals = -1; L.W = -1; L.Wb = -1; L.wslot = -1;
   if (in_smem & 1) { L.vals = off; off += align16(max_nnz_loc * cplx_bytes); }
   if (in_smem & 2) { L.W = off; off += align16(max_nnz_loc * 16); }
-  if (cplx_bytes == 8 && (in_smem & 4)) { L.Wb = off; off += align16(max_nnz_loc * 8); }
+  if (staged && (in_smem & 4)) { L.Wb = off; off += align16(max_nnz_loc * 16); }
   L.lrow = off; off += align16((R + 1) * 4);
   L.lcol = off; off += align16(max_nnz_loc * 4);
   L.total = off;

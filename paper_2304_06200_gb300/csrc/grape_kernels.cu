@@ -37,10 +37,12 @@ namespace cg = cooperative_groups;
 
 namespace grape {
 
-// 1/q, 1/q! and (-1)^q / q! for q = 0..kMaxTaylor
+// 1/q, 1/q! and (-1)^q / q! for q = 0..kMaxTaylor; 1/q as a pair of floats (hi, lo), hi + lo = 1/q to
+// about 2^-48 (the compensated FP32 bulk)
 __constant__ double c_inv_int[kMaxTaylor + 2];
 __constant__ double c_inv_fact[kMaxTaylor + 2];
 __constant__ double c_sgn_fact[kMaxTaylor + 2];
+__constant__ float2 c_dw_inv[kMaxTaylor + 2];
 
 static bool g_constants_ready[64] = {false};
 
@@ -57,7 +59,14 @@ static cudaError_t ensure_constants() {
     inv_fact[q] = inv_fact[q - 1] / q;
   }
   for (int q = 0; q < kMaxTaylor + 2; ++q) sgn_fact[q] = (q & 1) ? -inv_fact[q] : inv_fact[q];
-  e = cudaMemcpyToSymbol(c_inv_int, inv_int, sizeof(inv_int));
+  float2 dw_inv[kMaxTaylor + 2];
+  dw_inv[0] = make_float2(0.0f, 0.0f);
+  for (int q = 1; q < kMaxTaylor + 2; ++q) {
+    const float hi = (float)inv_int[q];
+    dw_inv[q] = make_float2(hi, (float)(inv_int[q] - (double)hi));
+  }
+  e = cudaMemcpyToSymbol(c_dw_inv, dw_inv, sizeof(dw_inv));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_inv_int, inv_int, sizeof(inv_int));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_inv_fact, inv_fact, sizeof(inv_fact));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_sgn_fact, sgn_fact, sizeof(sgn_fact));
   if (e == cudaSuccess && dev >= 0 && dev < 64) g_constants_ready[dev] = true;
@@ -220,26 +229,22 @@ __global__ void __launch_bounds__(256) k_schedule(ScheduleParams p) {
 
 // ------------------------------------------------------------------ sweep helpers
 
-// Bulk (Taylor-term) arithmetic type: double for the FP64 path, float for the FP32-bulk path.
-// States (psi, chi), their increments, the W accumulators and every reduction stay FP64.
+// Bulk (Taylor-term) arithmetic type: double for the FP64 path, dw for the compensated FP32 bulk.
+// States (psi, chi), the W accumulators and every reduction stay FP64.
+struct dw {};   // tag: a real number as an unevaluated pair of floats hi + lo
 template <typename T> struct CxT;
 template <> struct CxT<double> { using t = double2; };
-template <> struct CxT<float> { using t = float2; };
+template <> struct CxT<dw> { using t = float4; };   // {hi.re, hi.im, lo.re, lo.im}
 template <typename T> using cx = typename CxT<T>::t;
+template <typename T> constexpr bool kF64 = sizeof(cx<T>) == 16 && !__is_same(T, dw);
 
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double2 to_d2(const double2 v) { return v; }
-__device__ __forceinline__ double2 to_d2(const float2 v) { return make_double2(v.x, v.y); }
 template <typename T> __device__ __forceinline__ cx<T> from_d2(const double2 v);
 template <> __device__ __forceinline__ double2 from_d2<double>(const double2 v) { return v; }
-template <> __device__ __forceinline__ float2 from_d2<float>(const double2 v) { return make_float2((float)v.x, (float)v.y); }
-template <typename T> __device__ __forceinline__ cx<T> make_cx(T x, T y);
-template <> __device__ __forceinline__ double2 make_cx<double>(double x, double y) { return make_double2(x, y); }
-template <> __device__ __forceinline__ float2 make_cx<float>(float x, float y) { return make_float2(x, y); }
 template <typename C2> __device__ __forceinline__ C2 czero();
 template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
-template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.0f, 0.0f); }
+template <> __device__ __forceinline__ float4 czero<float4>() { return make_float4(0.0f, 0.0f, 0.0f, 0.0f); }
 
 template <typename C2>
 __device__ __forceinline__ void cmacT(C2& acc, const C2 a, const C2 b) {  // acc += a b
@@ -257,12 +262,99 @@ __device__ __forceinline__ void cmac_conjT(C2& acc, const C2 a, const C2 b) {  /
   acc.y = fmaT(-a.y, b.x, acc.y);
 }
 
+// ------------------------------------------------------------------ compensated FP32 (double-word) arithmetic
+//
+// A real bulk number is an unevaluated pair of floats hi + lo (|lo| about 2^-24 |hi| at most once
+// normalised), a complex one float4 {hi.re, hi.im, lo.re, lo.im}.  Row sums accumulate in a DwAcc:
+// per component a running float sum s and a float compensation c, the compensated dot product of
+// Ogita, Rump and Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005): each
+// product a b of pairs is the float product p = ah bh with its exact error fma(ah, bh, -p) plus the
+// cross terms ah bl + al bh; p joins s by Knuth's TwoSum, whose exact addition error joins c with
+// the product's error.  A sum is normalised once, by Dekker's Fast2Sum.  The float operations are
+// the correctly rounded intrinsics, which the compiler does not contract into FMAs (TwoSum relies
+// on each sum being rounded on its own).  The result carries about 2^-48 relative error per
+// operation on the magnitudes involved, against 2^-53 for FP64, at FP32 instruction rates.
+struct DwAcc {
+  float sr, si, cr, ci;
+};
+__device__ __forceinline__ DwAcc acc_zero() { return DwAcc{0.0f, 0.0f, 0.0f, 0.0f}; }
+
+// (s, c) += p + e, p a float, e its small companion
+__device__ __forceinline__ void acc_add(float& s, float& c, float p, float e) {
+  const float t = __fadd_rn(s, p);
+  const float z = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+  c = __fadd_rn(c, __fadd_rn(err, e));
+  s = t;
+}
+// (s, c) += (ah + al)(bh + bl)
+__device__ __forceinline__ void acc_mul(float& s, float& c, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  acc_add(s, c, p, e);
+}
+__device__ __forceinline__ void cmacT(DwAcc& a, const float4 v, const float4 x) {   // a += v x
+  acc_mul(a.sr, a.cr, v.x, v.z, x.x, x.z);
+  acc_mul(a.sr, a.cr, -v.y, -v.w, x.y, x.w);
+  acc_mul(a.si, a.ci, v.x, v.z, x.y, x.w);
+  acc_mul(a.si, a.ci, v.y, v.w, x.x, x.z);
+}
+__device__ __forceinline__ void cmac_conjT(DwAcc& a, const float4 v, const float4 x) {   // a += conj(v) x
+  acc_mul(a.sr, a.cr, v.x, v.z, x.x, x.z);
+  acc_mul(a.sr, a.cr, v.y, v.w, x.y, x.w);
+  acc_mul(a.si, a.ci, v.x, v.z, x.y, x.w);
+  acc_mul(a.si, a.ci, -v.y, -v.w, x.x, x.z);
+}
+// the normalised pair of each component (Fast2Sum)
+__device__ __forceinline__ float4 dw_norm(const DwAcc& a) {
+  const float hr = __fadd_rn(a.sr, a.cr), hi = __fadd_rn(a.si, a.ci);
+  return make_float4(hr, hi, __fsub_rn(a.cr, __fsub_rn(hr, a.sr)), __fsub_rn(a.ci, __fsub_rn(hi, a.si)));
+}
+// x f for a complex pair x and a real pair f
+__device__ __forceinline__ float4 dw_scale(const float4 x, const float2 f) {
+  DwAcc a = acc_zero();
+  acc_mul(a.sr, a.cr, x.x, x.z, f.x, f.y);
+  acc_mul(a.si, a.ci, x.y, x.w, f.x, f.y);
+  return dw_norm(a);
+}
+// a - b for complex pairs
+__device__ __forceinline__ float4 dw_sub(const float4 a, const float4 b) {
+  DwAcc r{a.x, a.y, a.z, a.w};
+  acc_add(r.sr, r.cr, -b.x, -b.z);
+  acc_add(r.si, r.ci, -b.y, -b.w);
+  return dw_norm(r);
+}
+// acc += x for a complex pair x
+__device__ __forceinline__ void acc_add4(DwAcc& a, const float4 x) {
+  acc_add(a.sr, a.cr, x.x, x.z);
+  acc_add(a.si, a.ci, x.y, x.w);
+}
+template <> __device__ __forceinline__ float4 from_d2<dw>(const double2 v) {
+  const float hr = __double2float_rn(v.x), hi = __double2float_rn(v.y);
+  return make_float4(hr, hi, __double2float_rn(v.x - (double)hr), __double2float_rn(v.y - (double)hi));
+}
+__device__ __forceinline__ double2 to_d2(const float4 v) {
+  return make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+}
+__device__ __forceinline__ double2 to_d2(const DwAcc& a) {
+  return make_double2((double)a.sr + (double)a.cr, (double)a.si + (double)a.ci);
+}
+// accumulator type of a bulk row sum
+template <typename T> struct AccT { using t = cx<T>; };
+template <> struct AccT<dw> { using t = DwAcc; };
+template <typename T> using acc_t = typename AccT<T>::t;
+template <typename T> __device__ __forceinline__ acc_t<T> acc0();
+template <> __device__ __forceinline__ double2 acc0<double>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ DwAcc acc0<dw>() { return acc_zero(); }
+// the bulk value of a row sum
+__device__ __forceinline__ double2 finish(const double2 a) { return a; }
+__device__ __forceinline__ float4 finish(const DwAcc& a) { return dw_norm(a); }
+
 // One Horner step in bulk precision: chi/(p+1)! - yw (for FP64 in one fused rounding).
 __device__ __forceinline__ double2 horner(const double2 ch, double f, const double2 yw) {
   return make_double2(fma(ch.x, f, -yw.x), fma(ch.y, f, -yw.y));
-}
-__device__ __forceinline__ float2 horner(const double2 ch, double f, const float2 yw) {
-  return make_float2((float)(ch.x * f) - yw.x, (float)(ch.y * f) - yw.y);
 }
 
 // B_ii x with B_ii = (0, b) imaginary (H_ii real): two multiplies.  As the first term of a row sum it
@@ -286,7 +378,7 @@ struct Carve {
   double2* inc;
   cx<T>* vals;
   double2* W;         // FP64 accumulators of conj(w_p) x_p per local entry
-  float2* Wb;         // FP32-bulk path: per-substep staging of W in bulk precision
+  DwAcc* Wb;          // compensated FP32 bulk: per-substep compensated staging of W
   cx<T>* wsm;         // Horner slots in shared memory (first m_smem)
   cx<T>* wgl;         // Horner slots in global scratch (slots >= m_smem)
   int* lrow;
@@ -295,7 +387,7 @@ struct Carve {
 
 template <typename T>
 __device__ __forceinline__ Carve<T> carve(unsigned char* smem, const SweepParams& p, bool backward, int part) {
-  const SmemLayout L = make_layout(backward, p.R, p.max_nnz_loc, p.in_smem, p.m_smem, (int)sizeof(cx<T>));
+  const SmemLayout L = make_layout(backward, p.R, p.max_nnz_loc, p.in_smem, p.m_smem, (int)sizeof(cx<T>), !kF64<T>);
   double2* scr = p.scratch + (int64_t)part * p.scratch_stride;
   Carve<T> c;
   c.xb = reinterpret_cast<cx<T>*>(smem + L.xbuf);
@@ -304,7 +396,7 @@ __device__ __forceinline__ Carve<T> carve(unsigned char* smem, const SweepParams
   c.inc = reinterpret_cast<double2*>(smem + L.inc);
   c.vals = L.vals >= 0 ? reinterpret_cast<cx<T>*>(smem + L.vals) : reinterpret_cast<cx<T>*>(scr + p.scr_vals);
   c.W = L.W >= 0 ? reinterpret_cast<double2*>(smem + L.W) : scr + p.scr_W;
-  c.Wb = L.Wb >= 0 ? reinterpret_cast<float2*>(smem + L.Wb) : reinterpret_cast<float2*>(scr + p.scr_Wb);
+  c.Wb = L.Wb >= 0 ? reinterpret_cast<DwAcc*>(smem + L.Wb) : reinterpret_cast<DwAcc*>(scr + p.scr_Wb);
   c.wsm = L.wslot >= 0 ? reinterpret_cast<cx<T>*>(smem + L.wslot) : nullptr;
   c.wgl = reinterpret_cast<cx<T>*>(scr + p.scr_wslot);
   c.lrow = reinterpret_cast<int*>(smem + L.lrow);
@@ -364,32 +456,34 @@ __device__ __forceinline__ cx<T> xload(const cx<T>* local, const XTab<T>& tab, u
 }
 
 
-// Row products on the local pattern.  FP64: one accumulator per chain (the FP64 pipe is the bound,
-// so no extra instructions).  FP32 (latency bound): entries two at a time, both loads (a remote
-// row costs a distributed-shared-memory round trip) issued before the two multiply-adds, which go
-// to two accumulators.  The trip count is exact either way: no padded multiply-adds.
+// Row products on the local pattern, returned as the row sum's bulk value.  FP64: one accumulator per
+// chain (the FP64 pipe is the bound, so no extra instructions).  Compensated FP32 (latency bound):
+// entries two at a time, both loads (a remote row costs a distributed-shared-memory round trip)
+// issued before the two multiply-adds, which go to two accumulators.  The trip count is exact
+// either way: no padded multiply-adds.
 template <typename T, bool CLUSTER>
 __device__ __forceinline__ cx<T> row_mv(const cx<T>* __restrict__ vals, const uint32_t* __restrict__ lcol, int ea,
                                         int eb, const cx<T>* xs, const XTab<T>& tab) {
   using C2 = cx<T>;
-  if constexpr (sizeof(C2) == 16) {
+  if constexpr (kF64<T>) {
     C2 y = czero<C2>();
     for (int e = ea; e < eb; ++e) cmacT(y, vals[e], xload<T, CLUSTER>(xs, tab, lcol[e]));
     return y;
+  } else {
+    DwAcc y0 = acc_zero(), y1 = acc_zero();
+    int e = ea;
+    for (; e + 2 <= eb; e += 2) {
+      const C2 v0 = vals[e], v1 = vals[e + 1];
+      const C2 x0 = xload<T, CLUSTER>(xs, tab, lcol[e]);
+      const C2 x1 = xload<T, CLUSTER>(xs, tab, lcol[e + 1]);
+      cmacT(y0, v0, x0);
+      cmacT(y1, v1, x1);
+    }
+    if (e < eb) cmacT(y0, vals[e], xload<T, CLUSTER>(xs, tab, lcol[e]));
+    acc_add(y0.sr, y0.cr, y1.sr, y1.cr);
+    acc_add(y0.si, y0.ci, y1.si, y1.ci);
+    return dw_norm(y0);
   }
-  C2 y0 = czero<C2>(), y1 = czero<C2>();
-  int e = ea;
-  for (; e + 2 <= eb; e += 2) {
-    const C2 v0 = vals[e], v1 = vals[e + 1];
-    const C2 x0 = xload<T, CLUSTER>(xs, tab, lcol[e]);
-    const C2 x1 = xload<T, CLUSTER>(xs, tab, lcol[e + 1]);
-    cmacT(y0, v0, x0);
-    cmacT(y1, v1, x1);
-  }
-  if (e < eb) cmacT(y0, vals[e], xload<T, CLUSTER>(xs, tab, lcol[e]));
-  y0.x += y1.x;
-  y0.y += y1.y;
-  return y0;
 }
 
 // Two chains through the same matrix row: ya = row . xa, yw = row . xw.
@@ -398,7 +492,7 @@ __device__ __forceinline__ void row_mv2(const cx<T>* __restrict__ vals, const ui
                                         const cx<T>* xa, const XTab<T>& ta, const cx<T>* xw, const XTab<T>& tw,
                                         cx<T>& ya, cx<T>& yw) {
   using C2 = cx<T>;
-  if constexpr (sizeof(C2) == 16) {
+  if constexpr (kF64<T>) {
     C2 a = czero<C2>(), w = czero<C2>();
     for (int e = ea; e < eb; ++e) {
       const uint32_t enc = lcol[e];
@@ -408,28 +502,19 @@ __device__ __forceinline__ void row_mv2(const cx<T>* __restrict__ vals, const ui
     }
     ya = a;
     yw = w;
-    return;
+  } else {
+    DwAcc a = acc_zero(), w = acc_zero();
+    for (int e = ea; e < eb; ++e) {
+      const uint32_t enc = lcol[e];
+      const C2 v = vals[e];
+      const C2 x0 = xload<T, CLUSTER>(xa, ta, enc);
+      const C2 x1 = xload<T, CLUSTER>(xw, tw, enc);
+      cmacT(a, v, x0);
+      cmacT(w, v, x1);
+    }
+    ya = dw_norm(a);
+    yw = dw_norm(w);
   }
-  C2 a0 = czero<C2>(), a1 = czero<C2>(), w0 = czero<C2>(), w1 = czero<C2>();
-  int e = ea;
-  for (; e + 2 <= eb; e += 2) {
-    const uint32_t c0 = lcol[e], c1 = lcol[e + 1];
-    const C2 v0 = vals[e], v1 = vals[e + 1];
-    const C2 xa0 = xload<T, CLUSTER>(xa, ta, c0), xa1 = xload<T, CLUSTER>(xa, ta, c1);
-    const C2 xw0 = xload<T, CLUSTER>(xw, tw, c0), xw1 = xload<T, CLUSTER>(xw, tw, c1);
-    cmacT(a0, v0, xa0);
-    cmacT(w0, v0, xw0);
-    cmacT(a1, v1, xa1);
-    cmacT(w1, v1, xw1);
-  }
-  if (e < eb) {
-    const uint32_t c0 = lcol[e];
-    const C2 v0 = vals[e];
-    cmacT(a0, v0, xload<T, CLUSTER>(xa, ta, c0));
-    cmacT(w0, v0, xload<T, CLUSTER>(xw, tw, c0));
-  }
-  ya = make_cx<T>(a0.x + a1.x, a0.y + a1.y);
-  yw = make_cx<T>(w0.x + w1.x, w0.y + w1.y);
 }
 
 __device__ __forceinline__ void sweep_setup(const SweepParams& p, int* lrow, uint32_t* lcol, int r0, int nrows,
@@ -521,9 +606,9 @@ __global__ void __launch_bounds__(512, 1) k_forward(SweepParams p) {
     for (int l = 0; l < s; ++l) {
       for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
         X0[i] = from_d2<T>(c.psi[i]);
-        c.inc[i] = make_double2(0.0, 0.0);
+        c.inc[i] = make_double2(0.0, 0.0);   // the compensated bulk keeps a DwAcc in the same 16 bytes
       }
-      if constexpr (sizeof(C2) == 16) {
+      if constexpr (kF64<T>) {
         if (split_rows) {
           // Each term: the entries whose column lies in this CTA's rows are summed between the
           // arrive and the wait of the previous term's cluster barrier; the remote ones after it.
@@ -586,33 +671,31 @@ __global__ void __launch_bounds__(512, 1) k_forward(SweepParams p) {
       team_sync<CLUSTER>();
       for (int q = 1; q <= m; ++q) {
         const int src = (q - 1) & 1, dst = q & 1;
-        const T iq = (T)c_inv_int[q];
         const double fq = c_inv_fact[q];
         const C2* xs = X0 + src * R;
         C2* xd = X0 + dst * R;
         for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
           C2 y = row_mv<T, CLUSTER>(c.vals, c.lcol, c.lrow[i], c.lrow[i + 1], xs, tab[src]);
-          double2 a = c.inc[i];
-          if constexpr (sizeof(C2) == 16) {   // B^q c unscaled; the sum takes 1/q!
+          if constexpr (kF64<T>) {   // B^q c unscaled; the sum takes 1/q!
+            double2 a = c.inc[i];
             xd[i] = y;
-            const double2 yd = to_d2(y);
-            a.x = fma(yd.x, fq, a.x);
-            a.y = fma(yd.y, fq, a.y);
-          } else {
-            y.x *= iq;
-            y.y *= iq;
+            a.x = fma(y.x, fq, a.x);
+            a.y = fma(y.y, fq, a.y);
+            c.inc[i] = a;
+          } else {                   // scaled terms b_q = (B b_{q-1}) / q, summed compensated
+            y = dw_scale(y, c_dw_inv[q]);
             xd[i] = y;
-            const double2 yd = to_d2(y);
-            a.x += yd.x;
-            a.y += yd.y;
+            DwAcc* a = reinterpret_cast<DwAcc*>(c.inc) + i;
+            acc_add4(*a, y);
           }
-          c.inc[i] = a;
         }
         team_sync<CLUSTER>();
       }
       for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
         double2 v = c.psi[i];
-        const double2 a = c.inc[i];
+        double2 a;
+        if constexpr (kF64<T>) a = c.inc[i];
+        else a = to_d2(reinterpret_cast<const DwAcc*>(c.inc)[i]);
         v.x += a.x;
         v.y += a.y;
         c.psi[i] = v;
@@ -694,9 +777,13 @@ __device__ __forceinline__ void costate_init(const SweepParams& p, double2* psi,
   }
 }
 
-// Phase A of one substep.  wout(p, i, w) stores Horner vector w_p of local row i.  The psi chain
-// psi^(l) = P(-B) psi^(l+1) keeps its FP64 terms unscaled (B^q psi^(l+1)) and sums them with the
-// weights (-1)^q / q!; FP32 terms are scaled by -1/q at every step.
+// Phase A of one substep.  wout(p, i, w) stores the Horner vector of index p of local row i.  The
+// psi chain psi^(l) = P(-B) psi^(l+1) keeps its FP64 terms unscaled (B^q psi^(l+1)) and sums them
+// with the weights (-1)^q / q!; compensated FP32 terms are scaled by -1/q at every step.  FP64
+// stores w_p; the compensated bulk runs the scaled recursion w'_{m-1} = chi,
+// w'_p = chi - (B w'_{p+1}) / (p+2), w'_p = (p+1)! w_p (magnitudes stay near |chi| instead of
+// falling like 1/p!), and stores h_p = w'_p / (p+1), which pairs with the scaled x chain
+// b_p = B^p psi / p! exactly as w_p pairs with B^p psi: conj(w_p) B^p psi = conj(h_p) b_p.
 template <typename T, bool CLUSTER, typename WOut>
 __device__ __forceinline__ void phase_a(Team<T, CLUSTER>& tm, int m, WOut wout) {
   using C2 = cx<T>;
@@ -705,11 +792,17 @@ __device__ __forceinline__ void phase_a(Team<T, CLUSTER>& tm, int m, WOut wout) 
   for (int i = threadIdx.x; i < tm.nrows; i += blockDim.x) {
     tm.X(0)[i] = from_d2<T>(c.psi[i]);
     c.inc[i] = make_double2(0.0, 0.0);
-    const C2 w0 = from_d2<T>(cscale(c.chi[i], fm));
-    tm.X(2)[i] = w0;
-    wout(m - 1, i, w0);
+    if constexpr (kF64<T>) {
+      const C2 w0 = from_d2<T>(cscale(c.chi[i], fm));
+      tm.X(2)[i] = w0;
+      wout(m - 1, i, w0);
+    } else {
+      const C2 w0 = from_d2<T>(c.chi[i]);
+      tm.X(2)[i] = w0;
+      wout(m - 1, i, dw_scale(w0, c_dw_inv[m]));
+    }
   }
-  if constexpr (sizeof(C2) == 16) {
+  if constexpr (kF64<T>) {
     if (tm.one_row) {
       // Split cluster barrier.  Term q: the first l1 local entries of the row (reading this CTA's
       // rows of X_{q-1}) before wait(q-1), the other entries after it; X_q is written, the barrier
@@ -799,57 +892,65 @@ __device__ __forceinline__ void phase_a(Team<T, CLUSTER>& tm, int m, WOut wout) 
   team_sync<CLUSTER>();
   for (int q = 1; q <= m; ++q) {
     const int src = (q - 1) & 1, dst = q & 1;
-    const T iq = (T)c_inv_int[q];
     const double fq = c_inv_fact[m - q];
     for (int i = threadIdx.x; i < tm.nrows; i += blockDim.x) {
       C2 ya, yw;
       row_mv2<T, CLUSTER>(c.vals, c.lcol, c.lrow[i], c.lrow[i + 1], tm.X(src), tm.tab[src], tm.X(2 + src),
                           tm.tab[2 + src], ya, yw);
-      double2 a = c.inc[i];
-      if constexpr (sizeof(C2) == 16) {              // FP64: B^q psi unscaled, the sum takes (-1)^q / q!
+      const double2 ch = c.chi[i];
+      if constexpr (kF64<T>) {                       // FP64: B^q psi unscaled, the sum takes (-1)^q / q!
+        double2 a = c.inc[i];
         tm.X(dst)[i] = ya;
         const double sq = c_sgn_fact[q];
         a.x = fma(ya.x, sq, a.x);
         a.y = fma(ya.y, sq, a.y);
+        c.inc[i] = a;
+        if (q < m) {
+          const C2 w = horner(ch, fq, yw);           // chi/(p+1)! + (-B) w_{p+1}
+          tm.X(2 + dst)[i] = w;
+          wout(m - 1 - q, i, w);
+        } else {
+          c.chi[i] = make_double2(fma(ch.x, fq, -yw.x), fma(ch.y, fq, -yw.y));   // chi^(l) = w_{-1}
+        }
       } else {
-        ya.x *= -iq;                                 // (-B) a_{q-1} / q
-        ya.y *= -iq;
+        ya = dw_scale(ya, c_dw_inv[q]);              // a_q = ((-B) a_{q-1}) / q
+        ya = make_float4(-ya.x, -ya.y, -ya.z, -ya.w);
         tm.X(dst)[i] = ya;
-        const double2 yad = to_d2(ya);
-        a.x += yad.x;
-        a.y += yad.y;
-      }
-      c.inc[i] = a;
-      const double2 ch = c.chi[i];
-      if (q < m) {
-        const C2 w = horner(ch, fq, yw);             // chi/(p+1)! + (-B) w_{p+1}
-        tm.X(2 + dst)[i] = w;
-        wout(m - 1 - q, i, w);
-      } else {
-        const double2 ywd = to_d2(yw);
-        c.chi[i] = make_double2(fma(ch.x, fq, -ywd.x), fma(ch.y, fq, -ywd.y));   // chi^(l) = w_{-1}
+        acc_add4(reinterpret_cast<DwAcc*>(c.inc)[i], ya);
+        if (q < m) {                                 // w'_p = chi - (B w'_{p+1}) / (p+2), p = m-1-q
+          const C2 w = dw_sub(from_d2<T>(ch), dw_scale(yw, c_dw_inv[m - q + 1]));
+          tm.X(2 + dst)[i] = w;
+          wout(m - 1 - q, i, dw_scale(w, c_dw_inv[m - q]));
+        } else {
+          const double2 yd = to_d2(yw);              // chi^(l) = w'_{-1} = chi - B w'_0
+          c.chi[i] = make_double2(ch.x - yd.x, ch.y - yd.y);
+        }
       }
     }
     team_sync<CLUSTER>();
   }
   for (int i = threadIdx.x; i < tm.nrows; i += blockDim.x) {
     double2 v = c.psi[i];
-    const double2 a = c.inc[i];
+    double2 a;
+    if constexpr (kF64<T>) a = c.inc[i];
+    else a = to_d2(reinterpret_cast<const DwAcc*>(c.inc)[i]);
     v.x += a.x;
     v.y += a.y;
     c.psi[i] = v;                                  // psi^(l)
   }
 }
 
-// Phase B of one substep.  X[4] must hold psi^(l) (own rows) on entry; win(p, i) returns w_p of row i.
+// Phase B of one substep.  X[4] must hold psi^(l) (own rows) on entry; win(p, i) returns the Horner
+// vector of index p of row i (w_p, or h_p for the compensated bulk, whose x chain is scaled:
+// b_{p+1} = (B b_p) / (p+1)).
 template <typename T, bool CLUSTER, typename WIn>
 __device__ __forceinline__ void phase_b(Team<T, CLUSTER>& tm, int m, WIn win) {
   using C2 = cx<T>;
-  constexpr bool kStage = sizeof(C2) == 8;      // FP32 bulk: stage W per substep in float
+  constexpr bool kStage = !kF64<T>;             // compensated bulk: stage W per substep
   const Carve<T>& c = tm.c;
   // With one row per thread, w_{p+1} is fetched while term p runs (it may come from L2).
   const bool one_row = tm.nrows <= (int)blockDim.x;
-  if constexpr (sizeof(C2) == 16) {
+  if constexpr (kF64<T>) {
     if (tm.one_row) {
       // Split cluster barrier as in phase A: the first l1 local entries before the wait, the rest
       // after it.  The last term writes nothing that others read, so it ends after its wait.
@@ -938,9 +1039,9 @@ __device__ __forceinline__ void phase_b(Team<T, CLUSTER>& tm, int m, WIn win) {
       } else {
         wp = win(pp, i);
       }
-      C2 y0 = czero<C2>(), y1 = czero<C2>();
       const int ea = c.lrow[i], eb = c.lrow[i + 1];
-      if constexpr (sizeof(C2) == 16) {   // FP64: one accumulator, exact loop
+      if constexpr (kF64<T>) {   // FP64: one accumulator, exact loop
+        C2 y0 = czero<C2>();
         for (int e = ea; e < eb; ++e) {
           const uint32_t enc = c.lcol[e];
           const C2 x = xload<T, CLUSTER>(xs, tm.tab[4 + src], enc);
@@ -952,59 +1053,53 @@ __device__ __forceinline__ void phase_b(Team<T, CLUSTER>& tm, int m, WIn win) {
           }
         }
         if (more) tm.X(4 + dst)[i] = y0;
-        continue;
-      }
-      auto wacc = [&](int e, const C2 x) {
-        if constexpr (kStage) {
-          float2 acc = c.Wb[e];
-          cmac_conjT(acc, wp, x);
-          c.Wb[e] = acc;
-        } else {
-          double2 acc = c.W[e];
-          cmac_conjT(acc, wp, x);
-          c.W[e] = acc;
+      } else {
+        DwAcc y0 = acc_zero(), y1 = acc_zero();
+        int e = ea;
+        for (; e + 2 <= eb; e += 2) {
+          const uint32_t c0 = c.lcol[e], c1 = c.lcol[e + 1];
+          const C2 x0 = xload<T, CLUSTER>(xs, tm.tab[4 + src], c0);
+          const C2 x1 = xload<T, CLUSTER>(xs, tm.tab[4 + src], c1);
+          if (more) {
+            cmacT(y0, c.vals[e], x0);
+            cmacT(y1, c.vals[e + 1], x1);
+          }
+          if (c0 & kCtrlBit) cmac_conjT(c.Wb[e], wp, x0);
+          if (c1 & kCtrlBit) cmac_conjT(c.Wb[e + 1], wp, x1);
         }
-      };
-      int e = ea;
-      for (; e + 2 <= eb; e += 2) {
-        const uint32_t c0 = c.lcol[e], c1 = c.lcol[e + 1];
-        const C2 x0 = xload<T, CLUSTER>(xs, tm.tab[4 + src], c0);
-        const C2 x1 = xload<T, CLUSTER>(xs, tm.tab[4 + src], c1);
+        if (e < eb) {
+          const uint32_t c0 = c.lcol[e];
+          const C2 x0 = xload<T, CLUSTER>(xs, tm.tab[4 + src], c0);
+          if (more) cmacT(y0, c.vals[e], x0);
+          if (c0 & kCtrlBit) cmac_conjT(c.Wb[e], wp, x0);
+        }
         if (more) {
-          cmacT(y0, c.vals[e], x0);
-          cmacT(y1, c.vals[e + 1], x1);
+          acc_add(y0.sr, y0.cr, y1.sr, y1.cr);
+          acc_add(y0.si, y0.ci, y1.si, y1.ci);
+          tm.X(4 + dst)[i] = dw_scale(dw_norm(y0), c_dw_inv[pp + 1]);
         }
-        if (c0 & kCtrlBit) wacc(e, x0);
-        if (c1 & kCtrlBit) wacc(e + 1, x1);
       }
-      if (e < eb) {
-        const uint32_t c0 = c.lcol[e];
-        const C2 x0 = xload<T, CLUSTER>(xs, tm.tab[4 + src], c0);
-        if (more) cmacT(y0, c.vals[e], x0);
-        if (c0 & kCtrlBit) wacc(e, x0);
-      }
-      if (more) tm.X(4 + dst)[i] = make_cx<T>(y0.x + y1.x, y0.y + y1.y);
     }
     if (more) team_sync<CLUSTER>();
   }
-  if constexpr (kStage) {   // fold the substep's FP32 sums into the FP64 accumulators (same thread owns the row)
+  if constexpr (kStage) {   // fold the substep's compensated sums into the FP64 accumulators (row owner)
     for (int i = threadIdx.x; i < tm.nrows; i += blockDim.x)
       for (int e = c.lrow[i]; e < c.lrow[i + 1]; ++e)
         if (c.lcol[e] & kCtrlBit) {
-          const float2 b = c.Wb[e];
+          const double2 b = to_d2(c.Wb[e]);
           double2 a = c.W[e];
           a.x += b.x;
           a.y += b.y;
           c.W[e] = a;
-          c.Wb[e] = make_float2(0.0f, 0.0f);
+          c.Wb[e] = acc_zero();
         }
   }
 }
 
-__device__ __forceinline__ void zero_w(const SweepParams& p, double2* W, float2* Wb, int nnz_loc, bool staged) {
+__device__ __forceinline__ void zero_w(const SweepParams& p, double2* W, DwAcc* Wb, int nnz_loc, bool staged) {
   for (int e = threadIdx.x; e < nnz_loc; e += blockDim.x) {
     W[e] = make_double2(0.0, 0.0);
-    if (staged) Wb[e] = make_float2(0.0f, 0.0f);
+    if (staged) Wb[e] = acc_zero();
   }
 }
 
@@ -1080,7 +1175,7 @@ __device__ __forceinline__ void team_init(Team<T, CLUSTER>& tm, unsigned char* s
       for (int b = 0; b < 6; ++b) tab[b].ptr[threadIdx.x] = cl.map_shared_rank(tm.X(b), threadIdx.x);
   }
   sweep_setup(p, tm.c.lrow, tm.c.lcol, tm.r0, tm.nrows, tm.e0, tm.nnz_loc);
-  tm.one_row = sizeof(cx<T>) == 16 && tm.nrows <= (int)blockDim.x;
+  tm.one_row = kF64<T> && tm.nrows <= (int)blockDim.x;
   tm.ea = tm.eb = tm.la = tm.l1 = tm.c0 = tm.ci = 0;
   tm.ed = -1;
   __syncthreads();   // the local pattern
@@ -1135,7 +1230,7 @@ __global__ void __launch_bounds__(512, 1) k_backward(SweepParams p) {
     load_controls(p, n, s_u);
     __syncthreads();
     assemble<T>(p, c.vals, tm.e0, tm.nnz_loc, p.dt / s, s_u);
-    zero_w(p, c.W, c.Wb, tm.nnz_loc, sizeof(C2) == 8);
+    zero_w(p, c.W, c.Wb, tm.nnz_loc, !kF64<T>);
     __syncthreads();
     for (int l = s - 1; l >= 0; --l) {
       phase_a<T, CLUSTER>(tm, m, [&](int pp, int i, C2 w) { *slot(pp, i) = w; });
@@ -1289,7 +1384,7 @@ __global__ void __launch_bounds__(512, 1) k_costate(SweepParams p) {
     for (int l = s - 1; l >= 0; --l) {
       C2* const hl = hb + (toff + (int64_t)l * m) * hstride + col0;   // w_p of substep l: hl[p * hstride + i]
       const double fm = c_inv_fact[m];
-      if constexpr (sizeof(C2) == 16) {
+      if constexpr (kF64<T>) {
         if (split_rows) {
           // Same split cluster barrier as the forward sweep: term q reads w_{m-q} from buffer
           // (q - 1) & 1 and writes w_{m-1-q} to buffer q & 1.  Thread 0 copies each buffer's rows
@@ -1342,10 +1437,21 @@ __global__ void __launch_bounds__(512, 1) k_costate(SweepParams p) {
           continue;
         }
       }
+      // Generic loop.  The compensated bulk runs the scaled recursion w'_{m-1} = chi,
+      // w'_p = chi - (B w'_{p+1}) / (p+2) and stores h_p = w'_p / (p+1) (see phase_a); its copy of
+      // chi as a pair of floats lives in the (otherwise unused) increment rows.
+      C2* const chi_b = reinterpret_cast<C2*>(c.inc);
       for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
-        const C2 w = from_d2<T>(cscale(chi[i], fm));
-        X0[i] = w;
-        hl[(int64_t)(m - 1) * hstride + i] = w;
+        if constexpr (kF64<T>) {
+          const C2 w = from_d2<T>(cscale(chi[i], fm));
+          X0[i] = w;
+          hl[(int64_t)(m - 1) * hstride + i] = w;
+        } else {
+          const C2 w = from_d2<T>(chi[i]);
+          chi_b[i] = w;
+          X0[i] = w;
+          hl[(int64_t)(m - 1) * hstride + i] = dw_scale(w, c_dw_inv[m]);
+        }
       }
       team_sync<CLUSTER>();
       for (int q = 1; q <= m; ++q) {
@@ -1354,9 +1460,15 @@ __global__ void __launch_bounds__(512, 1) k_costate(SweepParams p) {
           const C2 y = row_mv<T, CLUSTER>(c.vals, c.lcol, c.lrow[i], c.lrow[i + 1], X0 + src * R, tab[src]);
           const double2 ch = chi[i];
           if (q < m) {
-            const C2 w = horner(ch, c_inv_fact[m - q], y);
-            X0[dst * R + i] = w;
-            hl[(int64_t)(m - 1 - q) * hstride + i] = w;
+            if constexpr (kF64<T>) {
+              const C2 w = horner(ch, c_inv_fact[m - q], y);
+              X0[dst * R + i] = w;
+              hl[(int64_t)(m - 1 - q) * hstride + i] = w;
+            } else {
+              const C2 w = dw_sub(chi_b[i], dw_scale(y, c_dw_inv[m - q + 1]));
+              X0[dst * R + i] = w;
+              hl[(int64_t)(m - 1 - q) * hstride + i] = dw_scale(w, c_dw_inv[m - q]);
+            }
           } else {
             const double2 yd = to_d2(y);
             chi[i] = make_double2(fma(ch.x, c_inv_fact[0], -yd.x), fma(ch.y, c_inv_fact[0], -yd.y));
@@ -1406,7 +1518,7 @@ __global__ void __launch_bounds__(512, 1) k_costate(SweepParams p) {
 template <typename T, bool CLUSTER>
 __global__ void __launch_bounds__(512, 1) k_gradient(SweepParams p) {
   using C2 = cx<T>;
-  constexpr bool kStage = sizeof(C2) == 8;   // FP32 bulk: W staged per substep in float
+  constexpr bool kStage = !kF64<T>;   // compensated bulk: W staged per substep
   if (*p.plan_flag != 0) return;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32];
@@ -1419,14 +1531,14 @@ __global__ void __launch_bounds__(512, 1) k_gradient(SweepParams p) {
   const int r0 = min(rank * p.R, p.dim), r1 = min(r0 + p.R, p.dim), nrows = r1 - r0;
   const int64_t e0 = p.rowptr[r0];
   const int nnz_loc = (int)(p.rowptr[r1] - e0);
-  const SmemLayout L = make_glayout(p.R, p.max_nnz_loc, p.in_smem, (int)sizeof(C2));
+  const SmemLayout L = make_glayout(p.R, p.max_nnz_loc, p.in_smem, (int)sizeof(C2), kStage);
   double2* const scr = p.scratch + (int64_t)part * p.scratch_stride;
   C2* const X0 = reinterpret_cast<C2*>(smem + L.xbuf);
   double2* const psi = reinterpret_cast<double2*>(smem + L.psi);
   double2* const inc = reinterpret_cast<double2*>(smem + L.inc);
   C2* const vals = L.vals >= 0 ? reinterpret_cast<C2*>(smem + L.vals) : reinterpret_cast<C2*>(scr + p.scr_vals);
   double2* const W = L.W >= 0 ? reinterpret_cast<double2*>(smem + L.W) : scr + p.scr_W;
-  float2* const Wb = L.Wb >= 0 ? reinterpret_cast<float2*>(smem + L.Wb) : reinterpret_cast<float2*>(scr + p.scr_Wb);
+  DwAcc* const Wb = L.Wb >= 0 ? reinterpret_cast<DwAcc*>(smem + L.Wb) : reinterpret_cast<DwAcc*>(scr + p.scr_Wb);
   int* const lrow = reinterpret_cast<int*>(smem + L.lrow);
   uint32_t* const lcol = reinterpret_cast<uint32_t*>(smem + L.lcol);
   const int R = p.R;
@@ -1448,11 +1560,11 @@ __global__ void __launch_bounds__(512, 1) k_gradient(SweepParams p) {
   for (int i = threadIdx.x; i < nrows; i += blockDim.x) psi[i] = st[i];
   for (int e = threadIdx.x; e < nnz_loc; e += blockDim.x) {
     W[e] = make_double2(0.0, 0.0);
-    if (kStage) Wb[e] = make_float2(0.0f, 0.0f);
+    if (kStage) Wb[e] = acc_zero();
   }
   __syncthreads();
   assemble<T>(p, vals, e0, nnz_loc, p.dt / s, s_u);
-  const bool one_row = sizeof(C2) == 16 && nrows <= (int)blockDim.x;
+  const bool one_row = kF64<T> && nrows <= (int)blockDim.x;
   int ea = 0, eb = 0, la = 0, l1 = 0, ed = -1, c0 = 0, ci = 0;
   {
     int nloc = 1 << 30;
@@ -1484,7 +1596,7 @@ __global__ void __launch_bounds__(512, 1) k_gradient(SweepParams p) {
       inc[i] = make_double2(0.0, 0.0);
     }
     bool split_done = false;
-    if constexpr (sizeof(C2) == 16) {
+    if constexpr (kF64<T>) {
      if (one_row) {
       split_done = true;
       // Split cluster barrier (as in the fused sweep's phase B): term p sums the first l1 local
@@ -1569,67 +1681,91 @@ __global__ void __launch_bounds__(512, 1) k_gradient(SweepParams p) {
         const C2* xs = X0 + src * R;
         for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
           const C2 wp = __ldcg(hl + (int64_t)pp * hstride + i);
-          C2 y0 = czero<C2>(), y1 = czero<C2>();
           const int ra = lrow[i], rb = lrow[i + 1];
-          auto wacc = [&](int e, const C2 x) {
-            if constexpr (kStage) {
-              float2 acc = Wb[e];
-              cmac_conjT(acc, wp, x);
-              Wb[e] = acc;
-            } else {
+          if constexpr (kF64<T>) {
+            C2 y0 = czero<C2>(), y1 = czero<C2>();
+            auto wacc = [&](int e, const C2 x) {
               double2 acc = W[e];
               cmac_conjT(acc, wp, x);
               W[e] = acc;
+            };
+            int e = ra;
+            for (; e + 2 <= rb; e += 2) {
+              const uint32_t q0 = lcol[e], q1 = lcol[e + 1];
+              const C2 x0 = xload<T, CLUSTER>(xs, tab[src], q0);
+              const C2 x1 = xload<T, CLUSTER>(xs, tab[src], q1);
+              if (more) {
+                cmacT(y0, vals[e], x0);
+                cmacT(y1, vals[e + 1], x1);
+              }
+              if (q0 & kCtrlBit) wacc(e, x0);
+              if (q1 & kCtrlBit) wacc(e + 1, x1);
             }
-          };
-          int e = ra;
-          for (; e + 2 <= rb; e += 2) {
-            const uint32_t q0 = lcol[e], q1 = lcol[e + 1];
-            const C2 x0 = xload<T, CLUSTER>(xs, tab[src], q0);
-            const C2 x1 = xload<T, CLUSTER>(xs, tab[src], q1);
+            if (e < rb) {
+              const uint32_t q0 = lcol[e];
+              const C2 x0 = xload<T, CLUSTER>(xs, tab[src], q0);
+              if (more) cmacT(y0, vals[e], x0);
+              if (q0 & kCtrlBit) wacc(e, x0);
+            }
             if (more) {
-              cmacT(y0, vals[e], x0);
-              cmacT(y1, vals[e + 1], x1);
+              const C2 y = make_double2(y0.x + y1.x, y0.y + y1.y);
+              if (pp < m - 1) X0[dst * R + i] = y;
+              double2 a = inc[i];
+              const double f = c_inv_fact[pp + 1];
+              a.x = fma(y.x, f, a.x);
+              a.y = fma(y.y, f, a.y);
+              inc[i] = a;
             }
-            if (q0 & kCtrlBit) wacc(e, x0);
-            if (q1 & kCtrlBit) wacc(e + 1, x1);
-          }
-          if (e < rb) {
-            const uint32_t q0 = lcol[e];
-            const C2 x0 = xload<T, CLUSTER>(xs, tab[src], q0);
-            if (more) cmacT(y0, vals[e], x0);
-            if (q0 & kCtrlBit) wacc(e, x0);
-          }
-          if (more) {
-            const C2 y = make_cx<T>(y0.x + y1.x, y0.y + y1.y);
-            if (pp < m - 1) X0[dst * R + i] = y;
-            const double2 yd = to_d2(y);
-            double2 a = inc[i];
-            const double f = c_inv_fact[pp + 1];
-            a.x = fma(yd.x, f, a.x);
-            a.y = fma(yd.y, f, a.y);
-            inc[i] = a;
+          } else {   // scaled x chain b_{p+1} = (B b_p) / (p+1), W += conj(h_p) b_p compensated
+            DwAcc y0 = acc_zero(), y1 = acc_zero();
+            int e = ra;
+            for (; e + 2 <= rb; e += 2) {
+              const uint32_t q0 = lcol[e], q1 = lcol[e + 1];
+              const C2 x0 = xload<T, CLUSTER>(xs, tab[src], q0);
+              const C2 x1 = xload<T, CLUSTER>(xs, tab[src], q1);
+              if (more) {
+                cmacT(y0, vals[e], x0);
+                cmacT(y1, vals[e + 1], x1);
+              }
+              if (q0 & kCtrlBit) cmac_conjT(Wb[e], wp, x0);
+              if (q1 & kCtrlBit) cmac_conjT(Wb[e + 1], wp, x1);
+            }
+            if (e < rb) {
+              const uint32_t q0 = lcol[e];
+              const C2 x0 = xload<T, CLUSTER>(xs, tab[src], q0);
+              if (more) cmacT(y0, vals[e], x0);
+              if (q0 & kCtrlBit) cmac_conjT(Wb[e], wp, x0);
+            }
+            if (more) {
+              acc_add(y0.sr, y0.cr, y1.sr, y1.cr);
+              acc_add(y0.si, y0.ci, y1.si, y1.ci);
+              const C2 y = dw_scale(dw_norm(y0), c_dw_inv[pp + 1]);
+              if (pp < m - 1) X0[dst * R + i] = y;
+              acc_add4(reinterpret_cast<DwAcc*>(inc)[i], y);
+            }
           }
         }
         team_sync<CLUSTER>();
       }
-      if constexpr (kStage) {   // fold the substep's FP32 sums into the FP64 accumulators (row owner)
+      if constexpr (kStage) {   // fold the substep's compensated sums into the FP64 accumulators (row owner)
         for (int i = threadIdx.x; i < nrows; i += blockDim.x)
           for (int e = lrow[i]; e < lrow[i + 1]; ++e)
             if (lcol[e] & kCtrlBit) {
-              const float2 b = Wb[e];
+              const double2 b = to_d2(Wb[e]);
               double2 a = W[e];
               a.x += b.x;
               a.y += b.y;
               W[e] = a;
-              Wb[e] = make_float2(0.0f, 0.0f);
+              Wb[e] = acc_zero();
             }
       }
     }
     if (!last)
       for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
         double2 v = psi[i];
-        const double2 a = inc[i];
+        double2 a;
+        if constexpr (kF64<T>) a = inc[i];
+        else a = to_d2(reinterpret_cast<const DwAcc*>(inc)[i]);
         v.x += a.x;
         v.y += a.y;
         psi[i] = v;   // psi^(l+1)
@@ -1773,8 +1909,8 @@ static cudaError_t launch_sweep(KernelT kern, const SweepParams& p, int smem_byt
 
 cudaError_t launch_forward(const SweepParams& p, int precision, int smem_bytes, int threads, cudaStream_t st) {
   if (precision == 1) {
-    if (p.CL > 1) return launch_sweep(k_forward<float, true>, p, smem_bytes, threads, st);
-    return launch_sweep(k_forward<float, false>, p, smem_bytes, threads, st);
+    if (p.CL > 1) return launch_sweep(k_forward<dw, true>, p, smem_bytes, threads, st);
+    return launch_sweep(k_forward<dw, false>, p, smem_bytes, threads, st);
   }
   if (p.CL > 1) return launch_sweep(k_forward<double, true>, p, smem_bytes, threads, st);
   return launch_sweep(k_forward<double, false>, p, smem_bytes, threads, st);
@@ -1782,8 +1918,8 @@ cudaError_t launch_forward(const SweepParams& p, int precision, int smem_bytes, 
 
 cudaError_t launch_backward(const SweepParams& p, int precision, int smem_bytes, int threads, cudaStream_t st) {
   if (precision == 1) {
-    if (p.CL > 1) return launch_sweep(k_backward<float, true>, p, smem_bytes, threads, st);
-    return launch_sweep(k_backward<float, false>, p, smem_bytes, threads, st);
+    if (p.CL > 1) return launch_sweep(k_backward<dw, true>, p, smem_bytes, threads, st);
+    return launch_sweep(k_backward<dw, false>, p, smem_bytes, threads, st);
   }
   if (p.CL > 1) return launch_sweep(k_backward<double, true>, p, smem_bytes, threads, st);
   return launch_sweep(k_backward<double, false>, p, smem_bytes, threads, st);
@@ -1835,8 +1971,8 @@ cudaError_t launch_costate(const SweepParams& p, int precision, int smem_bytes, 
                            cudaStream_t st) {
   const int blocks = p.n_states * p.CL;
   if (precision == 1) {
-    if (p.CL > 1) return launch_role(k_costate<float, true>, p, blocks, smem_bytes, threads, priority, true, st);
-    return launch_role(k_costate<float, false>, p, blocks, smem_bytes, threads, priority, true, st);
+    if (p.CL > 1) return launch_role(k_costate<dw, true>, p, blocks, smem_bytes, threads, priority, true, st);
+    return launch_role(k_costate<dw, false>, p, blocks, smem_bytes, threads, priority, true, st);
   }
   if (p.CL > 1) return launch_role(k_costate<double, true>, p, blocks, smem_bytes, threads, priority, true, st);
   return launch_role(k_costate<double, false>, p, blocks, smem_bytes, threads, priority, true, st);
@@ -1846,8 +1982,8 @@ cudaError_t launch_gradient(const SweepParams& p, int precision, int smem_bytes,
   const int blocks = (p.n_end - p.n_begin) * p.n_states * p.CL;
   if (blocks <= 0) return cudaSuccess;
   if (precision == 1) {
-    if (p.CL > 1) return launch_role(k_gradient<float, true>, p, blocks, smem_bytes, threads, 0, false, st);
-    return launch_role(k_gradient<float, false>, p, blocks, smem_bytes, threads, 0, false, st);
+    if (p.CL > 1) return launch_role(k_gradient<dw, true>, p, blocks, smem_bytes, threads, 0, false, st);
+    return launch_role(k_gradient<dw, false>, p, blocks, smem_bytes, threads, 0, false, st);
   }
   if (p.CL > 1) return launch_role(k_gradient<double, true>, p, blocks, smem_bytes, threads, 0, false, st);
   return launch_role(k_gradient<double, false>, p, blocks, smem_bytes, threads, 0, false, st);

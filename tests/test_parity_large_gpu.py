@@ -81,3 +81,36 @@ def test_fp64_c4_reduced_n_against_the_exact_reference():
     cost, grad = hg.cost_and_grad(p.u0)
     ce, ge = _errors(cost, grad, ref_cost, ref_grad)
     assert ce <= COST_RTOL and ge <= GRAD_RTOL, (ce, ge)
+
+
+def test_fp32_bulk_full_size_against_the_exact_reference():
+    """The compensated FP32 bulk at d = 4000, N = 2000 (three-stage backward: its costate chain is
+    fast, so consecutive gradient blocks run side by side on the two gradient streams)."""
+    p = build_config("c3_gate_d4000")
+    ref_cost, ref_grad = _golden("c3_gate_d4000_full_exact.txt")
+    hg = _hg(p, precision="fp32_bulk")
+    assert hg.info()["backward_mode"] == 3
+    cost, grad = hg.cost_and_grad(p.u0)
+    ce, ge = _errors(cost, grad, ref_cost, ref_grad)
+    print(f"c3 full size, compensated FP32 bulk vs exact exponential: cost {ce:.2e}, gradient {ge:.2e}")
+    assert ce <= FP32_RTOL and ge <= FP32_RTOL, (ce, ge)
+
+
+def test_repeated_device_pointer_evaluations_at_full_size():
+    """Evaluations through device pointers, back to back on one stream (as the benchmark runs them),
+    the first one growing the Horner block buffers: every one equals the exact reference."""
+    import torch
+    p = build_config("c3_gate_d4000")
+    ref_cost, ref_grad = _golden("c3_gate_d4000_full_exact.txt")
+    hg = _hg(p)
+    dev = torch.device("cuda", 0)
+    u = torch.tensor(p.u0, dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        cost = torch.zeros((), dtype=torch.float64, device=dev)
+        grad = torch.zeros((p.n_controls, p.n_steps), dtype=torch.float64, device=dev)
+        hg.cost_device(u, cost, st)
+        hg.grad_device(grad, st)
+        torch.cuda.synchronize()
+        ce, ge = _errors(float(cost.item()), grad.cpu().numpy(), ref_cost, ref_grad)
+        assert ce <= COST_RTOL and ge <= GRAD_RTOL, (ce, ge)
