@@ -240,10 +240,11 @@ grape_status grape_problem_info(grape_problem* prob, grape_info* info);
  * the kernel runs on; nothing is recorded while a stream is being captured into a CUDA graph), and
  * grape_kernel_times sums their durations over the evaluations since the last call (which resets
  * the sums; it waits for the problem's pending work).  Index: 0 = k_forward, 1 = k_costate,
- * 2 = k_gradient, 3 = the fused one-team backward kernel. */
+ * 2 = k_gradient, 3 = the fused one-team backward kernel, 4 = the forward launches that recompute
+ * a segment's states (three-stage backward with checkpoints more than one step apart). */
 typedef struct {
-  int32_t launches[4];
-  double ms[4];
+  int32_t launches[5];
+  double ms[5];
 } grape_kernel_times_t;
 grape_status grape_set_kernel_tracing(grape_problem* prob, int32_t enable);
 grape_status grape_kernel_times(grape_problem* prob, grape_kernel_times_t* out);

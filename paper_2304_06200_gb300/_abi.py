@@ -57,7 +57,7 @@ class GrapeInfo(C.Structure):
 
 
 class GrapeKernelTimes(C.Structure):
-    _fields_ = [("launches", C.c_int32 * 4), ("ms", C.c_double * 4)]
+    _fields_ = [("launches", C.c_int32 * 5), ("ms", C.c_double * 5)]
 
 
 _LIB = None

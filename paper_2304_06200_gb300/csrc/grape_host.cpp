@@ -200,6 +200,8 @@ struct grape_problem {
   static constexpr int kGradStreams = 2; // k_gradient launches alternate between these streams
   void* d_hbuf[kHbufDepth] = {nullptr, nullptr, nullptr};
   double2* d_chi_io = nullptr;           // costate between k_costate launches
+  double2* d_seg = nullptr;              // two segments of recomputed states (checkpoints M > 1 apart)
+  cudaEvent_t ev_seg[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [slot][gradient stream]
   int* d_plan_flag = nullptr;            // set by k_plan: 1 = the fused fallback runs
   int* d_cslice_g = nullptr;             // control slices of the gradient partition
   cudaStream_t g_stream[kGradStreams] = {nullptr, nullptr};   // k_gradient launches
@@ -293,6 +295,11 @@ struct grape_problem {
     tr_used = 0;
     if (ev_b) cudaEventDestroy(ev_b);
     ev_b = nullptr;
+    for (auto& row : ev_seg)
+      for (auto& e : row) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+      }
     for (auto& e : ev_g) {
       if (e) cudaEventDestroy(e);
       e = nullptr;
@@ -899,7 +906,9 @@ grape_status build(grape_problem* P, const grape_desc* d) {
       if (!rows_entries(CL, &R, &mnl)) continue;
       if (grape::make_layout(false, R, mnl, 0, 0, cb, stg).total > smem_max) continue;
       const double cost = waves(P->n * CL) * (a_cost * mnl + b_cost * R + sync_cost(CL));
-      if (cost < best * 0.98) {
+      // FP64: a larger team must win by 2% (its barriers cost more than the model says); the
+      // compensated bulk is latency bound and measured fastest with the largest team that fits
+      if (cost < best * (stg ? 1.0 : 0.98)) {
         best = cost;
         P->fwd.CL = CL;
         P->fwd.R = R;
@@ -916,13 +925,18 @@ grape_status build(grape_problem* P, const grape_desc* d) {
   // Three-stage backward: the costate chain runs on the forward's partition (n * CL_f SMs); it pays
   // when at least half of the GPU is left for the gradient kernel, and the states of every step
   // (N * dim * n * 16 bytes) are stored.  Automatic choice: at most 8 GiB of states.
+  // Its checkpoint spacing M: every state (M = 1) when they fit 8 GiB, else M = 50, whose segments
+  // are recomputed (2 M states held) before the costate chain enters them; an explicit M > 1 asks
+  // for that recompute.
   bool three = false;
+  int three_M = 1;
   {
     const double state_bytes = (double)P->N * (double)dim * P->n * 16.0;
-    const bool ckpt_ok = d->ckpt_every == 0 || d->ckpt_every == 1;
     if (mode_req == 3) three = true;
     else if (mode_req == 0)
-      three = ckpt_ok && P->N >= 2 && 2 * P->n * P->fwd.CL <= nsm && state_bytes <= 8.0 * (1 << 30);
+      three = d->ckpt_every >= 0 && P->N >= 2 && 2 * P->n * P->fwd.CL <= nsm;
+    if (three) three_M = d->ckpt_every > 0 ? d->ckpt_every : (state_bytes <= 8.0 * (1 << 30) ? 1 : 50);
+    three_M = std::max(1, std::min(three_M, P->N));
   }
   // k_gradient partition: the smallest team that fits shared memory at all (its exchange buffers,
   // states and pattern; values and W accumulators join them when they fit, else they stay in the
@@ -933,20 +947,24 @@ grape_status build(grape_problem* P, const grape_desc* d) {
   if (three) {
     int pick = 0, pick_in = 0;
     const int full = 1 | 2 | (stg ? 4 : 0);
-    for (int CL = 1; CL <= grape::kMaxCluster && !pick; ++CL) {
-      if (d->grad_cluster > 0 && CL != d->grad_cluster) continue;
-      if (CL > 1 && CL > dim) continue;
-      int R = 0, mnl = 0;
-      if (!rows_entries(CL, &R, &mnl)) continue;
-      for (int want : {full, 2 | (stg ? 4 : 0), 0}) {
-        if (grape::make_glayout(R, mnl, want, cb, stg).total > smem_max) continue;
-        pick = CL;
-        pick_in = want;
-        P->grd.R = R;
-        P->grd.mnl = mnl;
-        break;
+    // The compensated bulk's accumulations are cheap enough that W and value traffic to global
+    // scratch would dominate: it first looks for the smallest team that holds everything.
+    for (int pass = stg ? 0 : 1; pass < 2 && !pick; ++pass)
+      for (int CL = 1; CL <= grape::kMaxCluster && !pick; ++CL) {
+        if (d->grad_cluster > 0 && CL != d->grad_cluster) continue;
+        if (CL > 1 && CL > dim) continue;
+        int R = 0, mnl = 0;
+        if (!rows_entries(CL, &R, &mnl)) continue;
+        for (int want : {full, 2 | (stg ? 4 : 0), 0}) {
+          if (pass == 0 && want != full) break;
+          if (grape::make_glayout(R, mnl, want, cb, stg).total > smem_max) continue;
+          pick = CL;
+          pick_in = want;
+          P->grd.R = R;
+          P->grd.mnl = mnl;
+          break;
+        }
       }
-    }
     if (!pick) {
       if (mode_req == 3) return fail(GRAPE_EINVAL, "backward_mode 3: the gradient kernel does not fit shared memory");
       three = false;
@@ -957,8 +975,14 @@ grape_status build(grape_problem* P, const grape_desc* d) {
       P->grd.smem = grape::make_glayout(P->grd.R, P->grd.mnl, pick_in, cb, stg).total;
       P->grd.threads = threads_for(P->grd.R);
       const int free_sms = std::max(nsm - P->n * P->fwd.CL, P->n * pick);
-      const int S = d->block_steps > 0 ? d->block_steps : std::min(32, std::max(1, 2 * free_sms / (P->n * pick)));
-      P->steps_per_block = std::min(S, P->N);
+      int S = d->block_steps > 0 ? d->block_steps : std::min(32, std::max(1, 2 * free_sms / (P->n * pick)));
+      S = std::min(S, P->N);
+      // with recomputed segments, blocks must not straddle them: the largest divisor of M not above S
+      if (three_M > 1) {
+        S = std::min(S, three_M);
+        while (three_M % S) --S;
+      }
+      P->steps_per_block = S;
     }
   }
   // backward: one team per column (fused); with the three-stage backward, the fused plan is its fallback
@@ -1030,7 +1054,8 @@ grape_status build(grape_problem* P, const grape_desc* d) {
   }
   // ---- checkpoints
   int M = d->ckpt_every;
-  if (M == 0) M = three ? 1 : std::min(50, P->N);
+  if (M == 0) M = three ? three_M : std::min(50, P->N);
+  if (three) M = three_M;
   if (M < 0) M = 0;
   P->ckpt_every = M;
   P->n_ckpt = M > 0 ? (P->N - 1) / M : 0;
@@ -1115,6 +1140,7 @@ grape_status build(grape_problem* P, const grape_desc* d) {
     if ((st = upload(P, &P->d_cslice_g, cslice_g.data(), cslice_g.size()))) return st;
     if ((st = dzeros(P, &P->d_chi_io, blk))) return st;
     if ((st = dzeros(P, &P->d_plan_flag, 1))) return st;
+    if (M > 1 && (st = dzeros(P, &P->d_seg, (size_t)2 * M * blk))) return st;
     int lo = 0, hi = 0;
     cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetStreamPriorityRange");
@@ -1127,6 +1153,10 @@ grape_status build(grape_problem* P, const grape_desc* d) {
     for (auto& ev : P->ev_g)
       if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
         return cuda_fail(e, "cudaEventCreateWithFlags");
+    for (auto& row : P->ev_seg)
+      for (auto& ev : row)
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+          return cuda_fail(e, "cudaEventCreateWithFlags");
   }
   return GRAPE_OK;
 }
@@ -1266,8 +1296,8 @@ grape_status grape_problem_create(const grape_desc* d, grape_problem** out) {
   if (d->cluster < 0 || d->cluster > grape::kMaxCluster) return fail(GRAPE_EINVAL, "cluster must be 0 (automatic) or 1..16");
   if (d->backward_mode < 0 || d->backward_mode > 3 || d->backward_mode == 2)
     return fail(GRAPE_EINVAL, "backward_mode must be 0 (automatic), 1 (one team per column) or 3 (three-stage)");
-  if (d->backward_mode == 3 && d->ckpt_every != 0 && d->ckpt_every != 1)
-    return fail(GRAPE_EINVAL, "backward_mode 3 stores every state: ckpt_every must be 0 or 1");
+  if (d->backward_mode == 3 && d->ckpt_every < 0)
+    return fail(GRAPE_EINVAL, "backward_mode 3 needs checkpoints: ckpt_every must be >= 0");
   if (d->grad_cluster < 0 || d->grad_cluster > grape::kMaxCluster)
     return fail(GRAPE_EINVAL, "grad_cluster must be 0 (automatic) or 1..16");
   if (d->block_steps < 0) return fail(GRAPE_EINVAL, "block_steps must be >= 0");
@@ -1523,9 +1553,39 @@ grape_status run_backward(grape_problem* P, cudaStream_t st) {
     pg.hbuf_terms = P->hbuf_terms;
     const int S = P->steps_per_block, nb = (P->N + S - 1) / S;
     constexpr int D = grape_problem::kHbufDepth, G = grape_problem::kGradStreams;
+    // Checkpoints M > 1 apart: before the costate chain enters segment j = [j M, (j+1) M), a
+    // forward launch recomputes the segment's states from its checkpoint into slot j % 2 of the
+    // segment buffer, once the gradient kernels of segment j + 2 (the slot's previous user) are done.
+    const int Mseg = P->ckpt_every;
+    const bool segs = Mseg > 1;
+    const int last_seg = segs ? (P->N - 1) / Mseg : 0;
+    if (segs) {
+      pc.seg = pg.seg = P->d_seg;
+      pc.seg_M = pg.seg_M = Mseg;
+    }
+    int cur_seg = -1;
     for (int b = nb - 1; b >= 0; --b) {
       const int slot = b % D;
       cudaStream_t gs = P->g_stream[b % G];
+      const int jseg = segs ? (b * S) / Mseg : 0;
+      if (segs && jseg != cur_seg) {
+        if (jseg + 2 <= last_seg)
+          for (int g = 0; g < G; ++g)
+            if ((e = cudaStreamWaitEvent(st, P->ev_seg[jseg & 1][g], 0)) != cudaSuccess)
+              return cuda_fail(e, "cudaStreamWaitEvent");
+        grape::SweepParams pr = sweep_params(P, P->fwd);
+        pr.recompute = 1;
+        pr.seg = P->d_seg;
+        pr.seg_M = Mseg;
+        pr.n_begin = jseg * Mseg;
+        pr.n_end = std::min((jseg + 1) * Mseg, P->N) - 1;
+        pr.rec_src = jseg == 0 ? P->d_psi0 : P->d_ckpt + (size_t)(jseg - 1) * P->n * P->dim;
+        const int tr = P->trace_begin(4, st);
+        if ((e = grape::launch_forward(pr, P->precision, P->fwd.smem, P->fwd.threads, st)) != cudaSuccess)
+          return cuda_fail(e, "launch k_forward (segment recompute)");
+        P->trace_end(tr, st);
+        cur_seg = jseg;
+      }
       pg.scratch = scr_g0 + (int64_t)(b % G) * P->scr_g_size;   // concurrent launches never share scratch
       pc.n_begin = pg.n_begin = b * S;
       pc.n_end = pg.n_end = std::min(P->N, (b + 1) * S);
@@ -1543,6 +1603,10 @@ grape_status run_backward(grape_problem* P, cudaStream_t st) {
         return cuda_fail(e, "launch k_gradient");
       P->trace_end(tg, gs);
       if ((e = cudaEventRecord(P->ev_g[slot], gs)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+      if (segs && b * S == jseg * Mseg)   // the segment's last block: mark its gradient work on each stream
+        for (int g = 0; g < G; ++g)
+          if ((e = cudaEventRecord(P->ev_seg[jseg & 1][g], P->g_stream[g])) != cudaSuccess)
+            return cuda_fail(e, "cudaEventRecord");
     }
     // join: the last gradient kernel of each stream (blocks 0 .. G-1, slots b % D)
     for (int b = 0; b < std::min(G, nb); ++b)

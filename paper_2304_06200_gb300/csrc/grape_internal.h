@@ -81,6 +81,13 @@ struct SweepParams {
   int64_t hbuf_terms;                  // capacity of hbuf in terms
   const int* plan_flag;                // 0: the three-stage kernels run; 1: the fused k_backward runs instead
   int gate_on_flag;                    // k_backward: 1 = run only when *plan_flag != 0 (the fallback)
+  // segment recompute (three-stage backward, checkpoints every seg_M > 1 steps): states psi_n of the
+  // segment [j M, (j+1) M) live in slot j % 2 of seg (2 x seg_M x n x dim); k_forward with
+  // recompute = 1 runs steps [n_begin, n_end) from rec_src (psi_{n_begin}) and fills the slot
+  double2* seg;
+  int seg_M;
+  int recompute;
+  const double2* rec_src;
 };
 
 // Block plan of the three-stage backward: per block of S steps the Horner vectors of every term must

@@ -326,6 +326,16 @@ __device__ __forceinline__ float4 dw_sub(const float4 a, const float4 b) {
   acc_add(r.si, r.ci, -b.y, -b.w);
   return dw_norm(r);
 }
+// a += (0, b) x: B_ij imaginary (H_ij real), b = the imaginary pair (v.y, v.w) of the stored value
+__device__ __forceinline__ void dw_mac_imag(DwAcc& a, const float4 v, const float4 x) {
+  acc_mul(a.sr, a.cr, -v.y, -v.w, x.y, x.w);
+  acc_mul(a.si, a.ci, v.y, v.w, x.x, x.z);
+}
+// a += (b, 0) x: B_ij real (H_ij imaginary), b = the real pair (v.x, v.z)
+__device__ __forceinline__ void dw_mac_real(DwAcc& a, const float4 v, const float4 x) {
+  acc_mul(a.sr, a.cr, v.x, v.z, x.x, x.z);
+  acc_mul(a.si, a.ci, v.x, v.z, x.y, x.w);
+}
 // acc += x for a complex pair x
 __device__ __forceinline__ void acc_add4(DwAcc& a, const float4 x) {
   acc_add(a.sr, a.cr, x.x, x.z);
@@ -440,6 +450,12 @@ __device__ __forceinline__ void row_segments(const uint32_t* lcol, int ea, int e
   *ci = e;
   while (e < eb && (lcol[e] & kRealBBit)) ++e;
   *cr = e;
+}
+
+// psi_n of column col in the segment buffer (slot (n / seg_M) % 2, position n % seg_M).
+__device__ __forceinline__ double2* seg_state(const SweepParams& p, int n, int col) {
+  const int pos = ((n / p.seg_M) & 1) * p.seg_M + n % p.seg_M;
+  return p.seg + ((int64_t)pos * p.n_states + col) * p.dim;
 }
 
 __device__ __forceinline__ void load_controls(const SweepParams& p, int n, double* s_u) {
@@ -575,7 +591,15 @@ __global__ void __launch_bounds__(512, 1) k_forward(SweepParams p) {
   }
   sweep_setup(p, c.lrow, c.lcol, r0, nrows, e0, nnz_loc);
   const int64_t col0 = (int64_t)team * p.dim + r0;
-  for (int i = threadIdx.x; i < nrows; i += blockDim.x) c.psi[i] = p.psi0[col0 + i];
+  // Segment recompute: steps [n_begin, n_end) from the segment's first state rec_src, every state of
+  // the segment written to its slot of the segment buffer; no cost partials, checkpoints or psi_N.
+  const bool rec = p.recompute != 0;
+  const double2* const src0 = rec ? p.rec_src : p.psi0;
+  for (int i = threadIdx.x; i < nrows; i += blockDim.x) c.psi[i] = src0[col0 + i];
+  if (rec) {
+    double2* const sg = seg_state(p, p.n_begin, team) + r0;
+    for (int i = threadIdx.x; i < nrows; i += blockDim.x) sg[i] = c.psi[i];
+  }
   double c2acc = 0.0;
   const bool split_rows = nrows <= (int)blockDim.x;   // one row per thread: split-barrier term loop
   // The thread's row: a diagonal stored first (ed), the single-phase entries [c0, ci) (imaginary B_ij)
@@ -596,7 +620,7 @@ __global__ void __launch_bounds__(512, 1) k_forward(SweepParams p) {
     while (lb < eb && ((c.lcol[lb] >> kOwnerShift) & 0xFFu) == (uint32_t)rank) ++lb;
   }
   team_sync<CLUSTER>();
-  for (int n = 0; n < p.N; ++n) {
+  for (int n = rec ? p.n_begin : 0; n < (rec ? p.n_end : p.N); ++n) {
     const int m = p.ms_m[n], s = p.ms_s[n];
     if (s <= 0 || m <= 0) continue;   // flagged by k_schedule; uniform over the team
     load_controls(p, n, s_u);
@@ -667,6 +691,51 @@ __global__ void __launch_bounds__(512, 1) k_forward(SweepParams p) {
           }
           continue;
         }
+      } else {
+        if (split_rows) {
+          // The compensated bulk's term loop with the same split cluster barrier: scaled terms
+          // b_q = (B b_{q-1}) / q, their sum kept in a register accumulator of the thread's row.
+          __syncthreads();
+          split_arrive<CLUSTER>();
+          const int i = threadIdx.x;
+          DwAcc incr = acc_zero();
+          for (int q = 1; q <= m; ++q) {
+            const int src = (q - 1) & 1, dst = q & 1;
+            const C2* xs = X0 + src * R;
+            DwAcc y = acc_zero();
+            if (i < nrows) {
+              if (ed >= 0) dw_mac_imag(y, c.vals[ed], xs[i]);
+              for (int e = la; e < lb; ++e) cmacT(y, c.vals[e], xs[c.lcol[e] & kLocalMask]);
+            }
+            split_wait<CLUSTER>();
+            if (i < nrows) {
+              for (int e = c0; e < ci; ++e) dw_mac_imag(y, c.vals[e], xload<T, CLUSTER>(xs, tab[src], c.lcol[e]));
+              for (int e = ci; e < ea; ++e) dw_mac_real(y, c.vals[e], xload<T, CLUSTER>(xs, tab[src], c.lcol[e]));
+              const int nl = la - ea, nr = nl + (eb - lb);
+              for (int k = 0; k < nr; ++k) {
+                const int e = k < nl ? ea + k : lb + (k - nl);
+                cmacT(y, c.vals[e], xload<T, CLUSTER>(xs, tab[src], c.lcol[e]));
+              }
+              const C2 b = dw_scale(dw_norm(y), c_dw_inv[q]);
+              X0[dst * R + i] = b;
+              acc_add4(incr, b);
+            }
+            if (q < m) {
+              __syncthreads();
+              split_arrive<CLUSTER>();
+            } else {
+              team_sync<CLUSTER>();
+            }
+          }
+          if (i < nrows) {
+            const double2 a = to_d2(incr);
+            double2 v = c.psi[i];
+            v.x += a.x;
+            v.y += a.y;
+            c.psi[i] = v;
+          }
+          continue;
+        }
       }
       team_sync<CLUSTER>();
       for (int q = 1; q <= m; ++q) {
@@ -702,6 +771,11 @@ __global__ void __launch_bounds__(512, 1) k_forward(SweepParams p) {
       }
     }
     // psi now holds psi_{n+1}
+    if (rec) {
+      double2* const sg = seg_state(p, n + 1, team) + r0;
+      for (int i = threadIdx.x; i < nrows; i += blockDim.x) sg[i] = c.psi[i];
+      continue;
+    }
     if (p.omega) {
       for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
         const double2 v = c.psi[i];
@@ -723,18 +797,20 @@ __global__ void __launch_bounds__(512, 1) k_forward(SweepParams p) {
       }
     }
   }
-  double2 gl = make_double2(0.0, 0.0);
-  for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
-    const double2 v = c.psi[i];
-    p.psiN[col0 + i] = v;
-    cmac_conj(gl, p.target[col0 + i], v);
-  }
-  const double gx = block_sum(gl.x, red);
-  const double gy = block_sum(gl.y, red);
-  const double c2 = block_sum(c2acc, red);
-  if (threadIdx.x == 0) {
-    p.part_g[part] = make_double2(gx, gy);
-    p.part_c2[part] = c2;
+  if (!rec) {
+    double2 gl = make_double2(0.0, 0.0);
+    for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+      const double2 v = c.psi[i];
+      p.psiN[col0 + i] = v;
+      cmac_conj(gl, p.target[col0 + i], v);
+    }
+    const double gx = block_sum(gl.x, red);
+    const double gy = block_sum(gl.y, red);
+    const double c2 = block_sum(c2acc, red);
+    if (threadIdx.x == 0) {
+      p.part_g[part] = make_double2(gx, gy);
+      p.part_c2[part] = c2;
+    }
   }
   team_sync<CLUSTER>();   // no CTA leaves while a team member may still read its shared memory
 }
@@ -1262,9 +1338,10 @@ __global__ void __launch_bounds__(512, 1) k_backward(SweepParams p) {
 // a second stream after an event; the block buffers alternate, and k_costate(b - 2) waits for
 // k_gradient(b).  No kernel waits for another one on the device.
 
-// psi_n, the input state of step n: psi_0, else the state the forward stored after step n - 1 (every
-// step is stored when the three-stage backward runs).
+// psi_n, the input state of step n: from the segment buffer when checkpoints are M > 1 steps apart
+// (the segment was recomputed), else psi_0 or the state the forward stored after step n - 1.
 __device__ __forceinline__ const double2* step_state(const SweepParams& p, int n, int col) {
+  if (p.seg) return seg_state(p, n, col);
   return n == 0 ? p.psi0 + (int64_t)col * p.dim : p.ckpt + ((int64_t)(n - 1) * p.n_states + col) * p.dim;
 }
 
@@ -1436,10 +1513,65 @@ __global__ void __launch_bounds__(512, 1) k_costate(SweepParams p) {
           }
           continue;
         }
+      } else {
+        if (split_rows) {
+          // The compensated bulk's Horner chain with the split cluster barrier: the scaled recursion
+          // w'_{m-1} = chi, w'_p = chi - (B w'_{p+1}) / (p+2); the w'_p go to the Horner block by the
+          // same bulk copies as in FP64 (k_gradient applies the 1/(p+1)); chi's pair in a register.
+          const int i = threadIdx.x;
+          const uint32_t rbytes = (uint32_t)nrows * 16u;
+          C2 chb = czero<C2>();
+          if (i < nrows) {
+            chb = from_d2<T>(chi[i]);
+            X0[i] = chb;
+          }
+          __syncthreads();
+          if (threadIdx.x == 0 && rbytes) bulk_store(hl + (int64_t)(m - 1) * hstride, X0, rbytes);
+          split_arrive<CLUSTER>();
+          for (int q = 1; q <= m; ++q) {
+            const int src = (q - 1) & 1, dst = q & 1;
+            const C2* xs = X0 + src * R;
+            DwAcc y = acc_zero();
+            if (i < nrows) {
+              if (ed >= 0) dw_mac_imag(y, c.vals[ed], xs[i]);
+              for (int e = la; e < lb; ++e) cmacT(y, c.vals[e], xs[c.lcol[e] & kLocalMask]);
+            }
+            split_wait<CLUSTER>();
+            if (i < nrows) {
+              for (int e = c0; e < ci; ++e) dw_mac_imag(y, c.vals[e], xload<T, CLUSTER>(xs, tab[src], c.lcol[e]));
+              for (int e = ci; e < ea; ++e) dw_mac_real(y, c.vals[e], xload<T, CLUSTER>(xs, tab[src], c.lcol[e]));
+              const int nl = la - ea, nr = nl + (eb - lb);
+              for (int k = 0; k < nr; ++k) {
+                const int e = k < nl ? ea + k : lb + (k - nl);
+                cmacT(y, c.vals[e], xload<T, CLUSTER>(xs, tab[src], c.lcol[e]));
+              }
+              if (q < m) {
+                X0[dst * R + i] = dw_sub(chb, dw_scale(dw_norm(y), c_dw_inv[m - q + 1]));
+              } else {
+                const double2 yd = to_d2(y);   // chi^(l) = w'_{-1} = chi - B w'_0
+                const double2 ch = chi[i];
+                chi[i] = make_double2(ch.x - yd.x, ch.y - yd.y);
+              }
+            }
+            if (q < m) {
+              __syncthreads();
+              if (threadIdx.x == 0 && rbytes) {
+                bulk_store(hl + (int64_t)(m - 1 - q) * hstride, X0 + dst * R, rbytes);
+                bulk_wait_read<1>();
+              }
+              split_arrive<CLUSTER>();
+            } else {
+              if (threadIdx.x == 0) bulk_wait_read<0>();
+              team_sync<CLUSTER>();
+            }
+          }
+          continue;
+        }
       }
       // Generic loop.  The compensated bulk runs the scaled recursion w'_{m-1} = chi,
-      // w'_p = chi - (B w'_{p+1}) / (p+2) and stores h_p = w'_p / (p+1) (see phase_a); its copy of
-      // chi as a pair of floats lives in the (otherwise unused) increment rows.
+      // w'_p = chi - (B w'_{p+1}) / (p+2) and stores w'_p (k_gradient pairs w'_p / (p+1) with the
+      // scaled x chain, see phase_a); its copy of chi as a pair of floats lives in the (otherwise
+      // unused) increment rows.
       C2* const chi_b = reinterpret_cast<C2*>(c.inc);
       for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
         if constexpr (kF64<T>) {
@@ -1450,7 +1582,7 @@ __global__ void __launch_bounds__(512, 1) k_costate(SweepParams p) {
           const C2 w = from_d2<T>(chi[i]);
           chi_b[i] = w;
           X0[i] = w;
-          hl[(int64_t)(m - 1) * hstride + i] = dw_scale(w, c_dw_inv[m]);
+          hl[(int64_t)(m - 1) * hstride + i] = w;
         }
       }
       team_sync<CLUSTER>();
@@ -1467,7 +1599,7 @@ __global__ void __launch_bounds__(512, 1) k_costate(SweepParams p) {
             } else {
               const C2 w = dw_sub(chi_b[i], dw_scale(y, c_dw_inv[m - q + 1]));
               X0[dst * R + i] = w;
-              hl[(int64_t)(m - 1 - q) * hstride + i] = dw_scale(w, c_dw_inv[m - q]);
+              hl[(int64_t)(m - 1 - q) * hstride + i] = w;
             }
           } else {
             const double2 yd = to_d2(y);
@@ -1680,7 +1812,8 @@ __global__ void __launch_bounds__(512, 1) k_gradient(SweepParams p) {
         const bool more = pp < m - 1 || !last;
         const C2* xs = X0 + src * R;
         for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
-          const C2 wp = __ldcg(hl + (int64_t)pp * hstride + i);
+          C2 wp = __ldcg(hl + (int64_t)pp * hstride + i);
+          if constexpr (!kF64<T>) wp = dw_scale(wp, c_dw_inv[pp + 1]);   // h_p = w'_p / (p+1)
           const int ra = lrow[i], rb = lrow[i + 1];
           if constexpr (kF64<T>) {
             C2 y0 = czero<C2>(), y1 = czero<C2>();

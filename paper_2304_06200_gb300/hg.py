@@ -213,7 +213,7 @@ class GrapeProblem:
         from ._abi import GrapeKernelTimes
         t = GrapeKernelTimes()
         check(self._lib.grape_kernel_times(self._h, C.byref(t)), "grape_kernel_times")
-        names = ["k_forward", "k_costate", "k_gradient", "k_backward"]
+        names = ["k_forward", "k_costate", "k_gradient", "k_backward", "k_forward_recompute"]
         return {nm: {"launches": int(t.launches[i]), "ms": float(t.ms[i])} for i, nm in enumerate(names)}
 
     def schedule(self):

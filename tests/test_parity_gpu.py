@@ -237,6 +237,34 @@ def test_three_stage_random_ragged_problems(dim, K, n, N, cluster, gcl, steps):
     _check(p, p.u0, cost, grad)
 
 
+@pytest.mark.parametrize("name,N,M,steps,prec", [
+    ("c2_gate_d80", 60, 10, 0, "fp64"), ("c2_gate_d80", 61, 7, 3, "fp64"), ("c1_state_transfer_d30", 45, 50, 4, "fp64"),
+    ("c2_gate_d80", 40, 8, 8, "fp32_bulk"), ("c2_gate_d80", 33, 2, 1, "fp64"),
+])
+def test_three_stage_with_recomputed_segments(name, N, M, steps, prec):
+    """Checkpoints M > 1 steps apart: each segment's states are recomputed before the costate chain
+    enters it (blocks never straddle segments; a ragged last segment).  Against the oracle, and the
+    states held are two segments instead of all N."""
+    p = build_config(name, n_steps=N)
+    u = p.u0 * 10.0
+    hg = _hg(p, backward_mode=3, ckpt_every=M, block_steps=steps, precision=prec)
+    inf = hg.info()
+    M = min(M, N)
+    assert inf["backward_mode"] == 3 and inf["ckpt_every"] == M and M % inf["block_steps"] == 0
+    cost, grad = hg.cost_and_grad(u)
+    assert hg.info()["fused_fallback"] == 0
+    tol = (COST_RTOL, GRAD_RTOL) if prec == "fp64" else (FP32_RTOL, FP32_RTOL)
+    _check(p, u, cost, grad, *tol)
+    c2, g2 = hg.cost_and_grad(u)
+    assert c2 == cost and np.array_equal(g2, grad)
+    kt = None
+    hg.set_kernel_tracing(True)
+    hg.kernel_times()
+    hg.cost_and_grad(u)
+    kt = hg.kernel_times()
+    assert kt["k_forward_recompute"]["launches"] == -(-N // M)
+
+
 def _weak_drift_problem():
     p = random_problem(40, 2, 2, 6, seed=77)
     p.H0 = p.H0 * 1e-3
