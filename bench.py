@@ -611,7 +611,7 @@ def secondary_run(name: str, precision: str, local: int, ref=None, n_steps=None,
     info = hg.info()
     out = {"workload": workload_description(p), "precision": precision, "evals_per_s": round(1e3 / ms, 4),
            "ms_per_eval": round(ms, 3), "cluster_fwd": info["cluster_forward"], "cluster_bwd": info["cluster"],
-           "backward_teams_per_column": info["backward_mode"]}
+           "backward_mode": info["backward_mode"], "gradient_team_ctas": info["grad_cluster"]}
     if ref is not None:
         c_ref, g_ref = ref
         g = grad.cpu().numpy()
@@ -637,7 +637,10 @@ def _timed_eval(hg, u, cost, grad, reps=1):
 
 
 def checkpoint_sweep(name, local, n_steps=None):
-    """Checkpoint spacing M in {50, 200, 1000}: evals/s and peak HBM of the HG evaluation."""
+    """Checkpoint spacing M: evals/s and peak HBM of the evaluation.  Three-stage backward with every
+    state stored (M = 1) and with segments of M in {50, 200, 1000} recomputed from checkpoints (also
+    with short blocks, the least memory), and the fused backward that re-propagates between
+    checkpoints M apart (Sec. III.C; Table I's memory column)."""
     import torch
     from paper_2304_06200_gb300 import GrapeProblem
     from workloads import build_config
@@ -645,18 +648,21 @@ def checkpoint_sweep(name, local, n_steps=None):
     p = build_config(name, n_steps=n_steps)
     dev = torch.device("cuda", local)
     out = []
-    for M in (50, 200, 1000):
+    cases = [(3, 1, 0), (3, 50, 0), (3, 200, 0), (3, 1000, 0), (3, 200, 4), (1, 50, 0), (1, 200, 0), (1, 1000, 0)]
+    for mode, M, steps in cases:
         torch.cuda.synchronize()
         torch.cuda.reset_peak_memory_stats(dev)
         m0 = torch.cuda.memory_allocated(dev)
-        hg = GrapeProblem(p, device=local, ckpt_every=M)
+        hg = GrapeProblem(p, device=local, ckpt_every=M, backward_mode=mode, block_steps=steps)
         u = torch.tensor(p.u0, dtype=torch.float64, device=dev)
         cost = torch.zeros((), dtype=torch.float64, device=dev)
         grad = torch.zeros_like(u)
         ms = _timed_eval(hg, u, cost, grad)
         peak = torch.cuda.max_memory_allocated(dev) - m0
-        out.append({"M": M, "evals_per_s": round(1e3 / ms, 4), "peak_bytes": int(peak), "cost": float(cost.item()),
-                    "grad_norm": float(torch.linalg.norm(grad).item())})
+        inf = hg.info()
+        out.append({"backward_mode": inf["backward_mode"], "M": inf["ckpt_every"], "steps_per_block": inf["block_steps"],
+                    "evals_per_s": round(1e3 / ms, 4), "peak_bytes": int(peak), "problem_bytes": int(inf["device_bytes"]),
+                    "cost": float(cost.item()), "grad_norm": float(torch.linalg.norm(grad).item())})
         hg.close()
         del u, cost, grad
     return out
@@ -687,7 +693,7 @@ def families_compare(local, n_steps=500):
             ms = _timed_eval(hg, u, cost, grad, reps=3)
             inf = hg.info()
             r = {"evals_per_s": round(1e3 / ms, 3), "ms_per_eval": round(ms, 2), "cluster_fwd": inf["cluster_forward"],
-                 "cluster_bwd": inf["cluster"], "backward_teams_per_column": inf["backward_mode"],
+                 "cluster_bwd": inf["cluster"], "backward_mode": inf["backward_mode"],
                  "taylor_terms_per_sweep": inf["total_terms"], "union_nnz": inf["union_nnz"]}
             g = grad.cpu().numpy()
             if ref is None:
@@ -767,7 +773,7 @@ def c4_compare(local):
         ms = _timed_eval(hg, u, cost, grad)
         inf = hg.info()
         r = {"evals_per_s": round(1e3 / ms, 5), "ms_per_eval": round(ms, 1), "cluster_fwd": inf["cluster_forward"],
-             "cluster_bwd": inf["cluster"], "backward_teams_per_column": inf["backward_mode"],
+             "cluster_bwd": inf["cluster"], "backward_mode": inf["backward_mode"],
              "taylor_terms_per_sweep": inf["total_terms"], "device_bytes": inf["device_bytes"]}
         g = grad.cpu().numpy()
         if ref is None:

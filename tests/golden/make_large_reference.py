@@ -11,6 +11,8 @@ Every value comes from ``oracle/`` alone (nothing from the CUDA path):
   oracle above before writing anything.
 * ``c4_gate_d16000_n3_exact.txt``  two transmons x cavity (1000 levels), d = 16,000, 16 states,
   first 3 steps: ``oracle.sparse_reference.cost_and_grad``.
+* ``dense_gue_q11_n2_dense.txt``   11-qubit register with a dense GUE drift (every H_ij non-zero),
+  d = 2048, 16 states, first 2 steps: ``oracle.cost_and_grad``.
 
 Each file: comment lines, then ``cost``, ``C1``, ``C2``, ``C_amp``, then the K x N gradient, one
 row per control.  Run:  python tests/golden/make_large_reference.py [--workers 8]
@@ -46,12 +48,12 @@ def write(name, problem, res, how):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workers", type=int, default=os.cpu_count() or 1)
-    ap.add_argument("--only", default="", help="comma list of: c3n3, c3full, c4n3")
+    ap.add_argument("--only", default="", help="comma list of: c3n3, c3full, c4n3, dense2")
     args = ap.parse_args()
     only = set(filter(None, args.only.split(",")))
     from oracle import cost_and_grad as dense_cost_and_grad
     from oracle import sparse_reference
-    from workloads import build_config
+    from workloads import build_config, dense_register_gate
 
     if not only or "c3n3" in only or "c3full" in only:
         p3 = build_config("c3_gate_d4000", n_steps=3)
@@ -80,6 +82,13 @@ def main():
         print(f"sparse reference, d = 16000, N = 3: {time.time() - t:.0f} s")
         write("c4_gate_d16000_n3_exact.txt", p4, res,
               "oracle.sparse_reference.cost_and_grad (expm_multiply actions, auxiliary block-matrix derivative)")
+    if not only or "dense2" in only:
+        pd = dense_register_gate(n_steps=2)
+        t = time.time()
+        res = dense_cost_and_grad(pd, pd.u0)
+        print(f"dense oracle, d = 2048 dense drift, N = 2: {time.time() - t:.0f} s")
+        write("dense_gue_q11_n2_dense.txt", pd, res,
+              "oracle.cost_and_grad (dense eigh propagators, App. F divided differences)")
 
 
 if __name__ == "__main__":

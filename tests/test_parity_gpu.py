@@ -505,7 +505,7 @@ def test_time_integrated_infidelity_parity(name, N, drive):
     u = p.u0 * drive
     ref = oracle_cost_and_grad(p, u)
     assert ref.parts["C3"] > 0.1
-    for mode in (1, 2):
+    for mode in (1, 3):
         hg = _hg(p, backward_mode=mode)
         cost, grad = hg.cost_and_grad(u)
         _check(p, u, cost, grad, ref=ref)

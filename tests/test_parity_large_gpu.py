@@ -114,3 +114,32 @@ def test_repeated_device_pointer_evaluations_at_full_size():
         torch.cuda.synchronize()
         ce, ge = _errors(float(cost.item()), grad.cpu().numpy(), ref_cost, ref_grad)
         assert ce <= COST_RTOL and ge <= GRAD_RTOL, (ce, ge)
+
+
+# FP16 hi/lo pairs carry 22 significant bits, BF16 pairs 16: the tensor-core modes' bounds
+TC_FP16_RTOL = 1e-5
+TC_BF16_RTOL = 1e-3
+
+
+@pytest.mark.parametrize("precision,tol", [("tc_fp16", TC_FP16_RTOL), ("tc_bf16", TC_BF16_RTOL)])
+def test_tensor_core_dense_drift_d2048_against_the_dense_oracle(precision, tol):
+    """A drift with every matrix element non-zero (GUE, 11 qubits, d = 2048, 16 states), first 2 steps
+    against the dense-eigh oracle: the workload the tensor-core products exist for (Sec. V, dense H)."""
+    from workloads import dense_register_gate
+    p = dense_register_gate(n_steps=2)
+    ref_cost, ref_grad = _golden("dense_gue_q11_n2_dense.txt")
+    hg = _hg(p, precision=precision)
+    cost, grad = hg.cost_and_grad(p.u0)
+    ce, ge = _errors(cost, grad, ref_cost, ref_grad)
+    print(f"dense GUE d = 2048, {precision}: cost {ce:.2e}, gradient {ge:.2e}")
+    assert ce <= tol and ge <= tol, (ce, ge)
+
+
+def test_dense_drift_is_refused_by_the_sparse_kernels():
+    """The sparse sweeps keep a team's pattern in shared memory: a dense d = 2048 drift does not fit
+    and is refused at creation (no launch), which is why the tensor-core path carries dense H."""
+    from paper_2304_06200_gb300 import GrapeError
+    from workloads import dense_register_gate
+    p = dense_register_gate(n_steps=2)
+    with pytest.raises(GrapeError):
+        _hg(p, precision="fp64")

@@ -35,3 +35,4 @@ from .families import (  # noqa: F401
     fluxonium_pair,
     fluxonium_problem,
 )
+from .dense import dense_register_gate, gue_drift, qubit0_drives  # noqa: F401
