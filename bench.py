@@ -801,50 +801,72 @@ def dense_problem_d2048(n_steps):
 
 
 def dense_compare(local, n_steps):
-    """Dense d = 2048 on tcgen05 (FP16 hi/lo, FP32 accumulation) against the FP64 kernels on the same problem."""
+    """Tensor-core dense path (tcgen05, FP16/BF16 hi/lo operand pairs, FP32 accumulation) at d = 2048,
+    16 states: on a drift with every element non-zero (GUE, 11 qubits; the sparse kernels refuse it),
+    and on the transmon-cavity Hamiltonian stored dense (against the FP64 sparse kernels)."""
     import torch
-    from paper_2304_06200_gb300 import GrapeProblem
+    from paper_2304_06200_gb300 import GrapeError, GrapeProblem
+    from workloads import dense_register_gate
 
-    p = dense_problem_d2048(n_steps)
     dev = torch.device("cuda", local)
-    res = {"workload": workload_description(p) + ", H stored dense"}
-    ref = None
-    for prec in ("fp64", "tc_fp16", "tc_bf16"):
-        hg = GrapeProblem(p, device=local, precision=prec)
-        u = torch.tensor(p.u0, dtype=torch.float64, device=dev)
-        cost = torch.zeros((), dtype=torch.float64, device=dev)
-        grad = torch.zeros_like(u)
-        hg.cost_device(u, cost)
-        hg.grad_device(grad)
-        torch.cuda.synchronize()
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        e[0].record()
-        hg.cost_device(u, cost)
-        e[1].record()
-        hg.grad_device(grad)
-        e[2].record()
-        torch.cuda.synchronize()
-        hg.sync_status()
-        inf = hg.info()
-        fwd_ms, bwd_ms = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
-        r = {"ms_per_eval": round(fwd_ms + bwd_ms, 2), "fwd_ms": round(fwd_ms, 2), "bwd_ms": round(bwd_ms, 2),
-             "taylor_terms_per_sweep": inf["total_terms"]}
-        g = grad.cpu().numpy()
-        if ref is None:
-            ref = (float(cost.item()), g)
-        else:
-            r["cost_rel_diff_vs_fp64"] = abs(float(cost.item()) - ref[0]) / abs(ref[0])
-            r["grad_rel_diff_vs_fp64"] = float(np.linalg.norm(g - ref[1]) / np.linalg.norm(ref[1]))
-            # tensor work actually issued per forward product: 2 operators x 3 hi/lo products x 2 d^2 N_real
-            nreal = ((2 * p.n_states + 15) // 16) * 16
-            flops = inf["total_terms"] * 2 * 3 * 2.0 * p.dim * p.dim * nreal
-            r["forward_tensor_tflops"] = round(flops / (fwd_ms / 1e3) / 1e12, 2)
-            r["forward_us_per_term"] = round(fwd_ms * 1e3 / inf["total_terms"], 2)
-            r["operator_bytes_per_term"] = 4 * p.dim * p.dim * 2
-            r["forward_l2_gbs"] = round(r["operator_bytes_per_term"] * inf["total_terms"] / (fwd_ms / 1e3) / 1e9, 1)
-        res[prec] = r
-        hg.close()
-    return res
+    bf16_peak, bf16_src = 1900.0, "fallback 1.9 PFLOP/s (no MEASURED_PEAKS.json)"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            bf16_peak, bf16_src = float(json.load(fh)["bf16_tflops"]), "measured"
+    except Exception:
+        pass
+    out = {}
+    for key, p in (("gue_dense_drift", dense_register_gate(n_steps=n_steps)),
+                   ("transmon_stored_dense", dense_problem_d2048(n_steps))):
+        res = {"workload": workload_description(p) + ", H stored dense"}
+        ref = None
+        for prec in ("fp64", "tc_fp16", "tc_bf16"):
+            try:
+                hg = GrapeProblem(p, device=local, precision=prec)
+            except GrapeError as exc:
+                res[prec] = {"unsupported": str(exc).split(": ", 1)[-1][:160]}
+                continue
+            u = torch.tensor(p.u0, dtype=torch.float64, device=dev)
+            cost = torch.zeros((), dtype=torch.float64, device=dev)
+            grad = torch.zeros_like(u)
+            hg.cost_device(u, cost)
+            hg.grad_device(grad)
+            torch.cuda.synchronize()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
+            hg.cost_device(u, cost)
+            e[1].record()
+            hg.grad_device(grad)
+            e[2].record()
+            torch.cuda.synchronize()
+            hg.sync_status()
+            inf = hg.info()
+            fwd_ms, bwd_ms = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+            r = {"ms_per_eval": round(fwd_ms + bwd_ms, 2), "fwd_ms": round(fwd_ms, 2), "bwd_ms": round(bwd_ms, 2),
+                 "taylor_terms_per_sweep": inf["total_terms"]}
+            g = grad.cpu().numpy()
+            if ref is None:
+                ref = (prec, float(cost.item()), g)
+            else:
+                r[f"cost_rel_diff_vs_{ref[0]}"] = abs(float(cost.item()) - ref[1]) / abs(ref[1])
+                r[f"grad_rel_diff_vs_{ref[0]}"] = float(np.linalg.norm(g - ref[2]) / np.linalg.norm(ref[2]))
+            if prec.startswith("tc"):
+                # tensor work issued per forward product: 2 operators x 3 hi/lo products x 2 d^2 N_real;
+                # the complex product itself is 8 d^2 n flops
+                nreal = ((2 * p.n_states + 15) // 16) * 16
+                issued = inf["total_terms"] * 2 * 3 * 2.0 * p.dim * p.dim * nreal
+                alg = inf["total_terms"] * 8.0 * p.dim * p.dim * p.n_states
+                r["forward_issued_tensor_tflops"] = round(issued / (fwd_ms / 1e3) / 1e12, 2)
+                r["forward_algorithmic_tflops"] = round(alg / (fwd_ms / 1e3) / 1e12, 2)
+                r["forward_issued_frac_of_bf16_peak"] = round(issued / (fwd_ms / 1e3) / 1e12 / bf16_peak, 4)
+                r["bf16_peak"] = bf16_src
+                r["forward_us_per_term"] = round(fwd_ms * 1e3 / inf["total_terms"], 2)
+                r["operator_bytes_per_term"] = 4 * p.dim * p.dim * 2
+                r["forward_l2_gbs"] = round(r["operator_bytes_per_term"] * inf["total_terms"] / (fwd_ms / 1e3) / 1e9, 1)
+            res[prec] = r
+            hg.close()
+        out[key] = res
+    return out
 
 
 def _timed_fwd_bwd(hg, p, u0, dev, reps=3):
@@ -909,7 +931,9 @@ def eig_compare(local):
 
 
 def batch_compare(local, tune=False):
-    """64 uneven instances: one graph launch (FP32 bulk) against the same 64 one at a time (plain FP64)."""
+    """64 uneven instances in one graph launch (FP32 bulk): the work queue (single-CTA members in two
+    persistent launches, the rest on lanes) and the lanes-only recording, against the same 64 one
+    at a time in plain FP64."""
     import numpy as np
     import torch
     from paper_2304_06200_gb300 import GrapeBatch, GrapeProblem, autotune
@@ -927,51 +951,64 @@ def batch_compare(local, tune=False):
             tune_report.append({"name": p.name, "cluster": rep["cluster"], "m_max": rep["m_max"],
                                 "ckpt_every": rep["ckpt_every"]})
         else:
-            hg = GrapeProblem(p, device=local, precision="fp32_bulk", backward_mode=1)
+            hg = GrapeProblem(p, device=local, precision="fp32_bulk")
         members.append(hg)
-    batch = GrapeBatch(members, n_streams=16)
-    setup_s = time.perf_counter() - t0
+    create_s = time.perf_counter() - t0
     us = [torch.tensor(p.u0, dtype=torch.float64, device=dev) for p in insts]
-    grads = [torch.zeros_like(u) for u in us]
-    costs = torch.zeros(len(insts), dtype=torch.float64, device=dev)
-    batch.cost_and_grad_device(us, costs, grads)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    reps = 3
-    e0.record()
-    for _ in range(reps):
+    res = {"instances": len(insts)}
+    outs = {}
+    for name, qc in (("queue", 0), ("lanes_only", -1)):
+        t1 = time.perf_counter()
+        batch = GrapeBatch(members, n_streams=16, queue_ctas=qc)
+        build_s = time.perf_counter() - t1
+        grads = [torch.zeros_like(u) for u in us]
+        costs = torch.zeros(len(insts), dtype=torch.float64, device=dev)
         batch.cost_and_grad_device(us, costs, grads)
-    e1.record()
-    torch.cuda.synchronize()
-    for m in members:
-        m.sync_status()
-    batch_ms = e0.elapsed_time(e1) / reps
-    cb = costs.cpu().numpy()
-    gb = [g.cpu().numpy() for g in grads]
-    batch.close()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record()
+        for _ in range(reps):
+            batch.cost_and_grad_device(us, costs, grads)
+        e1.record()
+        torch.cuda.synchronize()
+        for m in members:
+            m.sync_status()
+        ms = e0.elapsed_time(e1) / reps
+        outs[name] = (costs.cpu().numpy(), [g.cpu().numpy() for g in grads])
+        res[name] = {"ms_per_eval_of_all": round(ms, 2), "evals_per_s": round(len(insts) * 1e3 / ms, 3),
+                     "record_s": round(build_s, 1), **batch.info()}
+        batch.close()
     for m in members:
         m.close()
     # the same 64, one at a time, plain FP64 kernels
     seq_ms = 0.0
-    cerr, gerr = 0.0, 0.0
+    err = {k: [0.0, 0.0] for k in outs}
     for i, p in enumerate(insts):
         hg = GrapeProblem(p, device=local, precision="fp64")
         cost = torch.zeros((), dtype=torch.float64, device=dev)
-        ms = _timed_eval(hg, us[i], cost, grads[i])
+        g64 = torch.zeros_like(us[i])
+        ms = _timed_eval(hg, us[i], cost, g64)
         seq_ms += ms
         c = float(cost.item())
-        g = grads[i].cpu().numpy()
-        cerr = max(cerr, abs(cb[i] - c) / abs(c))
-        gerr = max(gerr, float(np.linalg.norm(gb[i] - g) / np.linalg.norm(g)))
+        g = g64.cpu().numpy()
+        for k, (cb, gb) in outs.items():
+            err[k][0] = max(err[k][0], abs(cb[i] - c) / abs(c))
+            err[k][1] = max(err[k][1], float(np.linalg.norm(gb[i] - g) / np.linalg.norm(g)))
         hg.close()
+    for k in outs:
+        res[k]["max_cost_rel_diff_vs_fp64"] = err[k][0]
+        res[k]["max_grad_rel_diff_vs_fp64"] = err[k][1]
     dims = sorted({p.dim for p in insts})
-    return {"instances": len(insts), "dims": dims, "counts": {d: sum(p.dim == d for p in insts) for d in dims},
-            "batch_ms_per_eval_of_all": round(batch_ms, 2), "batch_evals_per_s": round(len(insts) * 1e3 / batch_ms, 3),
-            "sequential_fp64_ms": round(seq_ms, 1), "sequential_fp64_evals_per_s": round(len(insts) * 1e3 / seq_ms, 3),
-            "speedup": round(seq_ms / batch_ms, 2), "max_cost_rel_diff_vs_fp64": cerr,
-            "max_grad_rel_diff_vs_fp64": gerr, "setup_s": round(setup_s, 1), "autotuned": tune,
-            "tune": tune_report[:8]}
+    res.update({"dims": dims, "counts": {d: sum(p.dim == d for p in insts) for d in dims},
+                "sequential_fp64_ms": round(seq_ms, 1),
+                "sequential_fp64_evals_per_s": round(len(insts) * 1e3 / seq_ms, 3),
+                "speedup_queue_over_sequential_fp64": round(seq_ms / res["queue"]["ms_per_eval_of_all"], 2),
+                "speedup_queue_over_lanes_only": round(res["lanes_only"]["ms_per_eval_of_all"]
+                                                       / res["queue"]["ms_per_eval_of_all"], 3),
+                "create_s": round(create_s, 1), "autotuned": tune, "tune": tune_report[:8]})
+    return res
 
 
 # ------------------------------------------------------------------ reference arm (CPU oracle)

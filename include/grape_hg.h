@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define GRAPE_ABI_VERSION 4
+#define GRAPE_ABI_VERSION 5
 
 typedef struct grape_problem grape_problem;
 
@@ -271,16 +271,41 @@ grape_status grape_select_ms(double x, double tau, int32_t sigma, int32_t precis
 double grape_error_bound(double x, int32_t m, int32_t s, int32_t sigma, int32_t precision);
 
 /* ---- Batches: many independent problems evaluated by one CUDA-graph launch.
- * grape_batch_create records, once, every member's evaluation (forward sweep, cost, backward sweep,
- * gradient) into one CUDA graph whose branches run on n_streams concurrent lanes (0 = 8), members
- * assigned longest first; a launch of the graph then evaluates all members with their kernels
- * running side by side, so that many small column teams fill the GPU.  Members must be distinct
- * problems on one device created with backward_mode = 1 (the three-stage backward sizes its block
- * buffers from a schedule read that a recording cannot make).  The batch does not own the problems:
- * destroy the batch before them.  This realises the paper's per-instance HG evaluation (Sec. III)
- * for many instances at once; the paper itself treats one instance at a time. */
+ * The paper evaluates one instance at a time (Sec. III); a batch evaluates many uneven instances
+ * together so that their small column teams fill the GPU.  grape_batch_create records, once, one
+ * CUDA graph that evaluates every member (forward sweep, cost, backward sweep, gradient):
+ *   - Work queue: members whose column teams are single CTAs in the forward and the fused backward
+ *     sweep (grape_info: cluster_forward == 1 and cluster == 1; FP64 or GRAPE_FP32_BULK) become
+ *     (member, column) items, ordered longest first by Taylor terms x union entries.  One launch
+ *     computes all their (m, s) schedules; then ONE persistent kernel per sweep direction runs
+ *     queue_ctas CTAs that take items from an atomic counter until none is left.  The CTA that
+ *     completes a member's last column reduces that member's partials (cost after the forward,
+ *     gradient after the backward), so no CTA waits for another.  Queued members of the
+ *     three-stage kind run their fused backward there.
+ *   - Lanes: every other member's own launches (cluster teams, three-stage backward) on n_streams
+ *     concurrent graph branches (0 = 8), assigned longest first; the queue shares lane 0.
+ * queue_ctas: 0 = automatic (the queue's share of the batch's work times the SMs times the
+ * kernel's CTAs per SM), > 0 = that many CTAs, < 0 = no queue (every member on the lanes).
+ * u_warm: NULL, or per member NULL or HOST controls (K_i x N_i) of the warm evaluation that runs
+ * before the recording (zero controls otherwise).  Three-stage members size their block buffers
+ * for that evaluation's schedule, with 25% headroom; while a batch exists these buffers are not
+ * replaced, and an evaluation whose schedule needs more runs that member's fused backward instead
+ * (same result, slower).
+ * Members must be distinct problems on one device and not tensor-core problems.  The batch does
+ * not own the problems: destroy the batch before them.  The members' own cost and gradient
+ * buffers are not updated by batch evaluations of queued members. */
 typedef struct grape_batch grape_batch;
-grape_status grape_batch_create(grape_problem* const* probs, int32_t count, int32_t n_streams, grape_batch** out);
+typedef struct {
+  int32_t members;       /* problems in the batch */
+  int32_t queued;        /* problems evaluated by the work-queue kernels */
+  int32_t queue_items;   /* (member, column) items */
+  int32_t queue_ctas;    /* CTAs of the largest work-queue launch (0: no queue) */
+  int32_t lanes;         /* graph branches */
+  int32_t lane_members;  /* problems evaluated by their own launches on the lanes */
+} grape_batch_info_t;
+grape_status grape_batch_create(grape_problem* const* probs, int32_t count, int32_t n_streams, int32_t queue_ctas,
+                                const double* const* u_warm, grape_batch** out);
+grape_status grape_batch_info(const grape_batch* batch, grape_batch_info_t* out);
 void grape_batch_destroy(grape_batch* batch);
 /* u[i]: member i's controls (K_i x N_i), costs[count], grads[i] (K_i x N_i, the array may be NULL or
  * hold NULLs).  on_device selects host or device pointers as in grape_cost_and_grad. */

@@ -21,7 +21,7 @@ EXPORTED = [
     "grape_problem_create", "grape_problem_destroy", "grape_cost_and_grad", "grape_cost", "grape_grad",
     "grape_sync_status", "grape_problem_info", "grape_step_schedule", "grape_select_ms", "grape_error_bound",
     "grape_status_string", "grape_last_error", "grape_abi_version", "grape_taylor_step_noalloc",
-    "grape_batch_create", "grape_batch_destroy", "grape_batch_cost_and_grad", "grape_optimize",
+    "grape_batch_create", "grape_batch_destroy", "grape_batch_cost_and_grad", "grape_batch_info", "grape_optimize",
     "grape_set_kernel_tracing", "grape_kernel_times", "grape_fp64_fma_rate",
 ]
 
@@ -54,6 +54,11 @@ class GrapeInfo(C.Structure):
                 ("max_norm", C.c_double), ("backward_mode", C.c_int32), ("cluster_forward", C.c_int32),
                 ("propagator", C.c_int32), ("grad_cluster", C.c_int32), ("block_steps", C.c_int32),
                 ("fused_fallback", C.c_int32)]
+
+
+class GrapeBatchInfo(C.Structure):
+    _fields_ = [("members", C.c_int32), ("queued", C.c_int32), ("queue_items", C.c_int32), ("queue_ctas", C.c_int32),
+                ("lanes", C.c_int32), ("lane_members", C.c_int32)]
 
 
 class GrapeKernelTimes(C.Structure):
@@ -97,8 +102,10 @@ def lib(path: str | None = None):
     L.grape_error_bound.restype = C.c_double
     L.grape_taylor_step_noalloc.argtypes = [C.c_int64, C.c_int64, C.c_int32, P, P, P, C.c_double, C.c_int32, C.c_int32, P, P, P]
     L.grape_taylor_step_noalloc.restype = C.c_int
-    L.grape_batch_create.argtypes = [C.POINTER(P), C.c_int32, C.c_int32, C.POINTER(P)]
+    L.grape_batch_create.argtypes = [C.POINTER(P), C.c_int32, C.c_int32, C.c_int32, C.POINTER(P), C.POINTER(P)]
     L.grape_batch_create.restype = C.c_int
+    L.grape_batch_info.argtypes = [P, C.POINTER(GrapeBatchInfo)]
+    L.grape_batch_info.restype = C.c_int
     L.grape_batch_destroy.argtypes = [P]
     L.grape_batch_destroy.restype = None
     L.grape_batch_cost_and_grad.argtypes = [P, C.POINTER(P), P, C.POINTER(P), C.c_int32, P]

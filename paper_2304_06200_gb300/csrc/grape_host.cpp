@@ -261,6 +261,7 @@ struct grape_problem {
   bool forward_done = false;
   bool evaluated = false;
   cudaStream_t last_stream = nullptr;
+  int batch_refs = 0;               // batches whose recorded graph refers to this problem's buffers
 
   void* dalloc(size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -1365,39 +1366,7 @@ void grape_problem_destroy(grape_problem* P) {
 
 namespace {
 
-// Forward sweep (Fig. 1(a)) without host synchronisation; the cost stays on the device.
-grape_status run_forward(grape_problem* P, const double* u, bool u_on_device, cudaStream_t st) {
-  const size_t ubytes = (size_t)P->K * P->N * sizeof(double);
-  cudaError_t e = cudaSuccess;
-  if (ubytes && u != P->d_u)
-    e = cudaMemcpyAsync(P->d_u, u, ubytes, u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync (u)");
-  if (P->eig) {
-    if ((e = grape::check_nonfinite_u(P->d_u, (int64_t)P->K * P->N, P->d_err, st)) != cudaSuccess)
-      return cuda_fail(e, "launch k_check_finite");
-    if ((e = eig_forward_all(P, st)) != cudaSuccess) return cuda_fail(e, "eigendecomposition forward sweep");
-    grape::FinalizeParams fp{};
-    fp.n_parts = P->n * P->ectx.sweep_cl;
-    fp.n_states = P->n;
-    fp.N = P->N;
-    fp.K = P->K;
-    fp.w_fid = P->w_fid;
-    fp.w_forbid = P->w_forbid;
-    fp.w_amp = P->w_amp;
-    fp.w_tint = P->w_tint;
-    fp.part_g3 = P->w_tint != 0.0 ? P->d_part_g3 : nullptr;
-    fp.g3_out = P->d_g3;
-    fp.part_g = P->d_part_g;
-    fp.part_c2 = P->d_part_c2;
-    fp.u = P->d_u;
-    fp.g_out = P->d_g;
-    fp.cost_out = P->d_cost;
-    fp.parts_out = P->d_parts;
-    if ((e = grape::launch_finalize(fp, st)) != cudaSuccess) return cuda_fail(e, "launch k_finalize");
-    P->forward_done = true;
-    P->evaluated = true;
-    return GRAPE_OK;
-  }
+grape::ScheduleParams schedule_params(const grape_problem* P) {
   grape::ScheduleParams sp{};
   sp.dim = (int)P->dim;
   sp.K = P->K;
@@ -1418,46 +1387,13 @@ grape_status run_forward(grape_problem* P, const double* u, bool u_on_device, cu
   sp.norm1 = P->d_norm1;
   sp.err = P->d_err;
   sp.b_cap = P->b_cap;
-  if ((e = grape::launch_schedule(sp, st)) != cudaSuccess) return cuda_fail(e, "launch k_schedule");
-  if (P->dense) {
-    // the host drives one tensor-core product per Taylor term: it needs the schedule
-    if ((e = cudaMemcpyAsync(P->m_host.data(), P->d_ms_m, P->N * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(P->s_host.data(), P->d_ms_s, P->N * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(st)) != cudaSuccess)
-      return cuda_fail(e, "schedule download");
-    e = run_recorded(P, &P->fwd_exec, &P->fwd_sched, st, [&](cudaStream_t cs) {
-      return grape::dense_forward(P->dctx, P->m_host.data(), P->s_host.data(), cs);
-    });
-    if (e != cudaSuccess) return cuda_fail(e, "dense forward sweep");
-    grape::FinalizeParams fp{};
-    fp.n_parts = 1;
-    fp.n_states = P->n;
-    fp.N = P->N;
-    fp.K = P->K;
-    fp.w_fid = P->w_fid;
-    fp.w_forbid = P->w_forbid;
-    fp.w_amp = P->w_amp;
-    fp.w_tint = P->w_tint;
-    fp.part_g3 = P->w_tint != 0.0 ? P->d_part_g3 : nullptr;
-    fp.g3_out = P->d_g3;
-    fp.part_g = P->d_part_g;
-    fp.part_c2 = P->d_part_c2;
-    fp.u = P->d_u;
-    fp.g_out = P->d_g;
-    fp.cost_out = P->d_cost;
-    fp.parts_out = P->d_parts;
-    if ((e = grape::launch_finalize(fp, st)) != cudaSuccess) return cuda_fail(e, "launch k_finalize");
-    P->forward_done = true;
-    P->evaluated = true;
-    return GRAPE_OK;
-  }
-  grape::SweepParams p = sweep_params(P, P->fwd);
-  const int tf = P->trace_begin(0, st);
-  if ((e = grape::launch_forward(p, P->precision, P->fwd.smem, P->fwd.threads, st)) != cudaSuccess)
-    return cuda_fail(e, "launch k_forward");
-  P->trace_end(tf, st);
+  return sp;
+}
+
+// The cost from the forward sweep's n_parts partials (Sec. II composite cost).
+grape::FinalizeParams finalize_params(const grape_problem* P, int n_parts) {
   grape::FinalizeParams fp{};
-  fp.n_parts = P->n * P->fwd.CL;
+  fp.n_parts = n_parts;
   fp.n_states = P->n;
   fp.N = P->N;
   fp.K = P->K;
@@ -1473,6 +1409,63 @@ grape_status run_forward(grape_problem* P, const double* u, bool u_on_device, cu
   fp.g_out = P->d_g;
   fp.cost_out = P->d_cost;
   fp.parts_out = P->d_parts;
+  return fp;
+}
+
+// dC/du_kn from the backward sweep's n_parts partials plus the amplitude term 2 w_amp u_kn / N (App. A).
+grape::GradReduceParams grad_reduce_params(const grape_problem* P, int n_parts) {
+  grape::GradReduceParams gp{};
+  gp.n_parts = n_parts;
+  gp.N = P->N;
+  gp.K = P->K;
+  gp.w_amp = P->w_amp;
+  gp.part_grad = P->d_part_grad;
+  gp.u = P->d_u;
+  gp.grad = P->d_grad;
+  return gp;
+}
+
+// Forward sweep (Fig. 1(a)) without host synchronisation; the cost stays on the device.
+grape_status run_forward(grape_problem* P, const double* u, bool u_on_device, cudaStream_t st) {
+  const size_t ubytes = (size_t)P->K * P->N * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  if (ubytes && u != P->d_u)
+    e = cudaMemcpyAsync(P->d_u, u, ubytes, u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync (u)");
+  if (P->eig) {
+    if ((e = grape::check_nonfinite_u(P->d_u, (int64_t)P->K * P->N, P->d_err, st)) != cudaSuccess)
+      return cuda_fail(e, "launch k_check_finite");
+    if ((e = eig_forward_all(P, st)) != cudaSuccess) return cuda_fail(e, "eigendecomposition forward sweep");
+    const grape::FinalizeParams fp = finalize_params(P, P->n * P->ectx.sweep_cl);
+    if ((e = grape::launch_finalize(fp, st)) != cudaSuccess) return cuda_fail(e, "launch k_finalize");
+    P->forward_done = true;
+    P->evaluated = true;
+    return GRAPE_OK;
+  }
+  const grape::ScheduleParams sp = schedule_params(P);
+  if ((e = grape::launch_schedule(sp, st)) != cudaSuccess) return cuda_fail(e, "launch k_schedule");
+  if (P->dense) {
+    // the host drives one tensor-core product per Taylor term: it needs the schedule
+    if ((e = cudaMemcpyAsync(P->m_host.data(), P->d_ms_m, P->N * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(P->s_host.data(), P->d_ms_s, P->N * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      return cuda_fail(e, "schedule download");
+    e = run_recorded(P, &P->fwd_exec, &P->fwd_sched, st, [&](cudaStream_t cs) {
+      return grape::dense_forward(P->dctx, P->m_host.data(), P->s_host.data(), cs);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "dense forward sweep");
+    const grape::FinalizeParams fp = finalize_params(P, 1);
+    if ((e = grape::launch_finalize(fp, st)) != cudaSuccess) return cuda_fail(e, "launch k_finalize");
+    P->forward_done = true;
+    P->evaluated = true;
+    return GRAPE_OK;
+  }
+  grape::SweepParams p = sweep_params(P, P->fwd);
+  const int tf = P->trace_begin(0, st);
+  if ((e = grape::launch_forward(p, P->precision, P->fwd.smem, P->fwd.threads, st)) != cudaSuccess)
+    return cuda_fail(e, "launch k_forward");
+  P->trace_end(tf, st);
+  const grape::FinalizeParams fp = finalize_params(P, P->n * P->fwd.CL);
   if ((e = grape::launch_finalize(fp, st)) != cudaSuccess) return cuda_fail(e, "launch k_finalize");
   P->forward_done = true;
   P->evaluated = true;
@@ -1513,7 +1506,9 @@ grape_status run_backward(grape_problem* P, cudaStream_t st) {
           if (P->m_host[n] > 0 && P->s_host[n] > 0) t += (int64_t)P->m_host[n] * P->s_host[n];
         need = std::max(need, t);
       }
-      if (need > P->hbuf_terms) {   // nothing runs on the device: the stream was just synchronised
+      // A recorded batch refers to the current buffers: they are not replaced while one exists (k_plan
+      // then selects the fused backward for a schedule that does not fit).
+      if (need > P->hbuf_terms && P->batch_refs == 0) {   // the stream was just synchronised
         if (P->opt_exec) {            // a recorded optimizer iteration refers to the old buffers
           cudaGraphExecDestroy(P->opt_exec);
           P->opt_exec = nullptr;
@@ -1623,19 +1618,12 @@ grape_status run_backward(grape_problem* P, cudaStream_t st) {
     P->trace_end(tb, st);
   }
   if (P->K > 0) {
-    grape::GradReduceParams gp{};
-    gp.n_parts = (P->dense || P->eig) ? 1 : P->n * P->bwd.CL;
+    grape::GradReduceParams gp = grad_reduce_params(P, (P->dense || P->eig) ? 1 : P->n * P->bwd.CL);
     if (!P->dense && !P->eig && P->bwd_mode == 3) {
       gp.n_parts = P->n * P->grd.CL;
       gp.n_parts_alt = P->n * P->bwd.CL;
       gp.plan_flag = P->d_plan_flag;
     }
-    gp.N = P->N;
-    gp.K = P->K;
-    gp.w_amp = P->w_amp;
-    gp.part_grad = P->d_part_grad;
-    gp.u = P->d_u;
-    gp.grad = P->d_grad;
     if ((e = grape::launch_grad_reduce(gp, st)) != cudaSuccess) return cuda_fail(e, "launch k_grad_reduce");
   }
   return GRAPE_OK;
@@ -1713,14 +1701,30 @@ struct grape_batch {
   double* d_u = nullptr;
   double* d_cost = nullptr;
   double* d_grad = nullptr;
-  std::vector<void*> owned;                 // cudaMalloc'ed staging buffers
+  std::vector<void*> owned;                 // cudaMalloc'ed staging and queue buffers
   cudaStream_t origin = nullptr;
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> events;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  std::vector<int> order;                   // longest first
-  std::vector<int> lane;                    // stream of each problem
+  std::vector<int> order;                   // lane members, longest first
+  std::vector<int> lane;                    // stream of each lane member
+  std::vector<char> queued;                 // member runs in the work queue
+  // Work queue, one per bulk precision among the queued members: k_schedule_batch, then one
+  // persistent k_queue launch per sweep direction over (member, column) items, longest first.
+  struct Queue {
+    int precision = 0;
+    std::vector<int> members;               // batch indices
+    int n_items = 0, max_n = 1;
+    int threads_f = 64, threads_b = 64, smem_f = 0, smem_b = 0, ctas_f = 1, ctas_b = 1;
+    grape::ScheduleParams* d_sched = nullptr;
+    grape::QueueParams qf{}, qb{};
+    int* d_counters = nullptr;              // head_f, head_b, done_f[Q], done_b[Q]
+    size_t counter_bytes = 0;
+  };
+  std::vector<Queue> queues;
+  int n_queued = 0, n_items = 0, queue_ctas = 0;
+  bool refs_taken = false;
   void release() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -1728,6 +1732,10 @@ struct grape_batch {
     for (auto s : streams) cudaStreamDestroy(s);
     if (origin) cudaStreamDestroy(origin);
     for (void* p : owned) cudaFree(p);
+    if (refs_taken)
+      for (grape_problem* P : probs) --P->batch_refs;
+    refs_taken = false;
+    probs.clear();
     exec = nullptr;
     graph = nullptr;
     events.clear();
@@ -1739,9 +1747,28 @@ struct grape_batch {
 
 namespace {
 
-grape_status batch_build(grape_batch* B, int n_streams) {
+template <typename T>
+grape_status batch_upload(grape_batch* B, const std::vector<T>& host, T** dev) {
+  void* ptr = nullptr;
+  cudaError_t e = cudaMalloc(&ptr, std::max<size_t>(host.size(), 1) * sizeof(T));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (batch queue)");
+  B->owned.push_back(ptr);
+  *dev = static_cast<T*>(ptr);
+  if (!host.empty() && (e = cudaMemcpy(ptr, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemcpy (batch queue)");
+  return GRAPE_OK;
+}
+
+// A member's column teams are single CTAs in the forward and the fused backward sweep: its columns
+// can be items of the work queue (members of the three-stage kind run their fused backward there).
+bool queue_eligible(const grape_problem* P) {
+  return !P->dense && !P->eig && P->fwd.CL == 1 && P->bwd.CL == 1 && (P->precision == 0 || P->precision == 1);
+}
+
+grape_status batch_build(grape_batch* B, int n_streams, int queue_ctas, const double* const* u_warm) {
   cudaError_t e;
   const int count = B->count;
+  const int nsm = sm_count(B->device);
   // staging buffers (fixed addresses referenced by the graph)
   B->u_off.resize(count);
   B->g_off.resize(count);
@@ -1761,32 +1788,16 @@ grape_status batch_build(grape_batch* B, int n_streams) {
     *dst[k] = static_cast<double*>(ptr);
     if ((e = cudaMemset(ptr, 0, bytes[k])) != cudaSuccess) return cuda_fail(e, "cudaMemset (batch staging)");
   }
-  // longest-first order, greedy assignment to the least loaded stream
-  std::vector<double> work(count);
-  for (int i = 0; i < count; ++i) {
-    const grape_problem* P = B->probs[i];
-    work[i] = (double)P->N * (double)P->nnz * (double)P->n;
-  }
-  B->order.resize(count);
-  std::iota(B->order.begin(), B->order.end(), 0);
-  std::stable_sort(B->order.begin(), B->order.end(), [&](int a, int b) { return work[a] > work[b]; });
-  n_streams = std::max(1, std::min(n_streams, count));
-  std::vector<double> load(n_streams, 0.0);
-  B->lane.assign(count, 0);
-  for (int i : B->order) {
-    const int j = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-    B->lane[i] = j;
-    load[j] += work[i];
-  }
   if ((e = cudaStreamCreateWithFlags(&B->origin, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
-  B->streams.resize(n_streams);
-  for (auto& s : B->streams)
-    if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
-  B->events.resize(n_streams + 1);
-  for (auto& ev : B->events)
-    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
-  // one warm evaluation per problem outside the capture (first launches set kernel attributes and
-  // constants, which are not stream work)
+  // one warm evaluation per problem outside the capture, at the caller's controls (else zero):
+  // first launches set kernel attributes and constants (not stream work), and three-stage members
+  // size their block buffers for this schedule
+  for (int i = 0; i < count; ++i) {
+    const size_t ub = (size_t)B->probs[i]->K * B->probs[i]->N * sizeof(double);
+    if (u_warm && u_warm[i] && ub &&
+        (e = cudaMemcpy(B->d_u + B->u_off[i], u_warm[i], ub, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return cuda_fail(e, "cudaMemcpy (warm controls)");
+  }
   for (int i = 0; i < count; ++i) {
     grape_problem* P = B->probs[i];
     grape_status s = run_forward(P, B->d_u + B->u_off[i], true, B->origin);
@@ -1794,26 +1805,181 @@ grape_status batch_build(grape_batch* B, int n_streams) {
     if ((s = run_backward(P, B->origin))) return s;
   }
   if ((e = cudaStreamSynchronize(B->origin)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-  for (int i = 0; i < count; ++i) cudaMemset(B->probs[i]->d_err, 0, sizeof(int));
-  // capture: fork onto the lanes, every problem's sequence on its lane, join back
+  // work estimate of every member: Taylor terms of its sweep x union entries x columns
+  std::vector<double> work(count), col_work(count);
+  for (int i = 0; i < count; ++i) {
+    grape_problem* P = B->probs[i];
+    cudaMemset(P->d_err, 0, sizeof(int));
+    std::vector<int> m(P->N), sv(P->N);
+    if ((e = cudaMemcpy(m.data(), P->d_ms_m, P->N * sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (e = cudaMemcpy(sv.data(), P->d_ms_s, P->N * sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(e, "schedule download");
+    double terms = 0.0;
+    for (int n = 0; n < P->N; ++n) terms += (double)std::max(m[n], 0) * std::max(sv[n], 0);
+    col_work[i] = std::max(terms, 1.0) * (double)P->nnz;
+    work[i] = col_work[i] * P->n;
+  }
+  // queue membership (queue_ctas < 0: none) and the queues, one per bulk precision
+  B->queued.assign(count, 0);
+  double w_queue = 0.0, w_all = 0.0;
+  for (int i = 0; i < count; ++i) {
+    w_all += work[i];
+    if (queue_ctas >= 0 && queue_eligible(B->probs[i])) {
+      B->queued[i] = 1;
+      w_queue += work[i];
+    }
+  }
+  for (int prec = 0; prec < 2; ++prec) {
+    grape_batch::Queue q;
+    q.precision = prec;
+    for (int i = 0; i < count; ++i)
+      if (B->queued[i] && B->probs[i]->precision == prec) q.members.push_back(i);
+    if (!q.members.empty()) B->queues.push_back(std::move(q));
+  }
+  for (auto& q : B->queues) {
+    const int Q = (int)q.members.size();
+    std::vector<grape::ScheduleParams> sched(Q);
+    std::vector<grape::SweepParams> fwd(Q), bwd(Q);
+    std::vector<grape::FinalizeParams> fin(Q);
+    std::vector<grape::GradReduceParams> red(Q);
+    std::vector<int2> items;
+    std::vector<double> item_cost;
+    double wq = 0.0;
+    for (int j = 0; j < Q; ++j) {
+      const int i = q.members[j];
+      grape_problem* P = B->probs[i];
+      double* u = B->d_u + B->u_off[i];
+      sched[j] = schedule_params(P);
+      sched[j].u = u;
+      fwd[j] = sweep_params(P, P->fwd);
+      fwd[j].u = u;
+      bwd[j] = sweep_params(P, P->bwd);
+      bwd[j].u = u;
+      fin[j] = finalize_params(P, P->n);
+      fin[j].u = u;
+      fin[j].cost_out = B->d_cost + i;
+      red[j] = grad_reduce_params(P, P->n);
+      red[j].u = u;
+      red[j].grad = B->d_grad + B->g_off[i];
+      q.max_n = std::max(q.max_n, P->N);
+      q.threads_f = std::max(q.threads_f, P->fwd.threads);
+      q.threads_b = std::max(q.threads_b, P->bwd.threads);
+      q.smem_f = std::max(q.smem_f, P->fwd.smem);
+      q.smem_b = std::max(q.smem_b, P->bwd.smem);
+      for (int c = 0; c < P->n; ++c) {
+        items.push_back(make_int2(j, c));
+        item_cost.push_back(col_work[i]);
+      }
+      wq += work[i];
+    }
+    // longest first
+    std::vector<int> idx(items.size());
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return item_cost[a] > item_cost[b]; });
+    std::vector<int2> sorted(items.size());
+    for (size_t k = 0; k < idx.size(); ++k) sorted[k] = items[idx[k]];
+    q.n_items = (int)sorted.size();
+    // CTAs: the queue's share of the work (the rest runs on the lanes) at the kernel's occupancy,
+    // or the caller's count; never more than items
+    const int occ_f = std::max(1, grape::queue_ctas_per_sm(q.precision, false, q.threads_f, q.smem_f));
+    const int occ_b = std::max(1, grape::queue_ctas_per_sm(q.precision, true, q.threads_b, q.smem_b));
+    const double share = w_all > 0.0 ? wq / w_all : 1.0;
+    auto pick = [&](int occ) {
+      int c = queue_ctas > 0 ? queue_ctas : (int)std::lround(share * nsm * occ);
+      return std::max(1, std::min(c, q.n_items));
+    };
+    q.ctas_f = pick(occ_f);
+    q.ctas_b = pick(occ_b);
+    grape::SweepParams* d_fwd = nullptr;
+    grape::SweepParams* d_bwd = nullptr;
+    grape::FinalizeParams* d_fin = nullptr;
+    grape::GradReduceParams* d_red = nullptr;
+    int2* d_items = nullptr;
+    grape_status st;
+    if ((st = batch_upload(B, sched, &q.d_sched)) || (st = batch_upload(B, fwd, &d_fwd)) ||
+        (st = batch_upload(B, bwd, &d_bwd)) || (st = batch_upload(B, fin, &d_fin)) ||
+        (st = batch_upload(B, red, &d_red)) || (st = batch_upload(B, sorted, &d_items)))
+      return st;
+    std::vector<int> counters(2 + 2 * Q, 0);
+    if ((st = batch_upload(B, counters, &q.d_counters))) return st;
+    q.counter_bytes = counters.size() * sizeof(int);
+    q.qf.sweep = d_fwd;
+    q.qf.fin = d_fin;
+    q.qf.items = d_items;
+    q.qf.n_items = q.n_items;
+    q.qf.head = q.d_counters;
+    q.qf.done = q.d_counters + 2;
+    q.qb.sweep = d_bwd;
+    q.qb.red = d_red;
+    q.qb.items = d_items;
+    q.qb.n_items = q.n_items;
+    q.qb.head = q.d_counters + 1;
+    q.qb.done = q.d_counters + 2 + Q;
+    B->n_queued += Q;
+    B->n_items += q.n_items;
+    B->queue_ctas = std::max(B->queue_ctas, std::max(q.ctas_f, q.ctas_b));
+  }
+  // the other members: longest first, greedy assignment to the least loaded lane; lane 0 also
+  // carries the queues
+  for (int i = 0; i < count; ++i)
+    if (!B->queued[i]) B->order.push_back(i);
+  std::stable_sort(B->order.begin(), B->order.end(), [&](int a, int b) { return work[a] > work[b]; });
+  n_streams = std::max(1, std::min(n_streams, (int)B->order.size() + (B->queues.empty() ? 0 : 1)));
+  std::vector<double> load(n_streams, 0.0);
+  if (!B->queues.empty()) load[0] = w_queue;
+  B->lane.assign(count, 0);
+  for (int i : B->order) {
+    const int j = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    B->lane[i] = j;
+    load[j] += work[i];
+  }
+  B->streams.resize(n_streams);
+  for (auto& s : B->streams)
+    if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+  B->events.resize(n_streams + 1);
+  for (auto& ev : B->events)
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+  // capture: fork onto the lanes, the queues on lane 0, every other member's sequence on its lane,
+  // join back
   if ((e = cudaStreamBeginCapture(B->origin, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
     return cuda_fail(e, "cudaStreamBeginCapture");
   grape_status st = GRAPE_OK;
   cudaEventRecord(B->events[n_streams], B->origin);
   for (auto s : B->streams) cudaStreamWaitEvent(s, B->events[n_streams], 0);
-  for (int i : B->order) {
-    grape_problem* P = B->probs[i];
-    cudaStream_t s = B->streams[B->lane[i]];
-    if ((st = run_forward(P, B->d_u + B->u_off[i], true, s))) break;
-    if ((st = run_backward(P, s))) break;
-    if ((e = cudaMemcpyAsync(B->d_cost + i, P->d_cost, sizeof(double), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
-      st = cuda_fail(e, "cudaMemcpyAsync (batch cost)");
+  for (auto& q : B->queues) {
+    cudaStream_t s = B->streams[0];
+    if ((e = cudaMemsetAsync(q.d_counters, 0, q.counter_bytes, s)) != cudaSuccess) {
+      st = cuda_fail(e, "cudaMemsetAsync (queue counters)");
       break;
     }
-    if (P->K > 0 && (e = cudaMemcpyAsync(B->d_grad + B->g_off[i], P->d_grad, (size_t)P->K * P->N * sizeof(double),
-                                         cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
-      st = cuda_fail(e, "cudaMemcpyAsync (batch grad)");
+    if ((e = grape::launch_schedule_batch(q.d_sched, (int)q.members.size(), q.max_n, s)) != cudaSuccess) {
+      st = cuda_fail(e, "launch k_schedule_batch");
       break;
+    }
+    if ((e = grape::launch_queue(q.qf, q.precision, false, q.ctas_f, q.threads_f, q.smem_f, s)) != cudaSuccess) {
+      st = cuda_fail(e, "launch k_queue (forward)");
+      break;
+    }
+    if ((e = grape::launch_queue(q.qb, q.precision, true, q.ctas_b, q.threads_b, q.smem_b, s)) != cudaSuccess) {
+      st = cuda_fail(e, "launch k_queue (backward)");
+      break;
+    }
+  }
+  if (!st) {
+    for (int i : B->order) {
+      grape_problem* P = B->probs[i];
+      cudaStream_t s = B->streams[B->lane[i]];
+      if ((st = run_forward(P, B->d_u + B->u_off[i], true, s))) break;
+      if ((st = run_backward(P, s))) break;
+      if ((e = cudaMemcpyAsync(B->d_cost + i, P->d_cost, sizeof(double), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
+        st = cuda_fail(e, "cudaMemcpyAsync (batch cost)");
+        break;
+      }
+      if (P->K > 0 && (e = cudaMemcpyAsync(B->d_grad + B->g_off[i], P->d_grad, (size_t)P->K * P->N * sizeof(double),
+                                           cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
+        st = cuda_fail(e, "cudaMemcpyAsync (batch grad)");
+        break;
+      }
     }
   }
   for (int j = 0; j < n_streams; ++j) {
@@ -1831,7 +1997,8 @@ grape_status batch_build(grape_batch* B, int n_streams) {
 
 extern "C" {
 
-grape_status grape_batch_create(grape_problem* const* probs, int32_t count, int32_t n_streams, grape_batch** out) {
+grape_status grape_batch_create(grape_problem* const* probs, int32_t count, int32_t n_streams, int32_t queue_ctas,
+                                const double* const* u_warm, grape_batch** out) {
   if (!out) return fail(GRAPE_EINVAL, "out is NULL");
   *out = nullptr;
   if (!probs || count < 1) return fail(GRAPE_EINVAL, "need at least one problem");
@@ -1839,10 +2006,6 @@ grape_status grape_batch_create(grape_problem* const* probs, int32_t count, int3
     if (!probs[i]) return fail(GRAPE_EINVAL, "NULL problem in batch");
     if (probs[i]->device != probs[0]->device) return fail(GRAPE_EINVAL, "batch problems must share one device");
     if (probs[i]->dense) return fail(GRAPE_EINVAL, "tensor-core problems are driven from the host and cannot join a batch");
-    if (probs[i]->bwd_mode != 1)
-      return fail(GRAPE_EINVAL, "batch members must use backward_mode 1 (the batch records every member's kernels "
-                                "into one graph; the three-stage backward sizes its buffers from a schedule read "
-                                "that a recording cannot make)");
     for (int j = 0; j < i; ++j)
       if (probs[j] == probs[i]) return fail(GRAPE_EINVAL, "a problem appears twice in the batch");
   }
@@ -1855,11 +2018,16 @@ grape_status grape_batch_create(grape_problem* const* probs, int32_t count, int3
   B->probs.assign(probs, probs + count);
   grape_status st;
   try {
-    st = batch_build(B, n_streams <= 0 ? 8 : n_streams);
+    st = batch_build(B, n_streams <= 0 ? 8 : n_streams, queue_ctas, u_warm);
   } catch (...) {
     st = fail(GRAPE_ENOMEM, "host allocation failed");
   }
+  if (!st) {   // the recording refers to the members' block buffers from now on
+    for (grape_problem* P : B->probs) ++P->batch_refs;
+    B->refs_taken = true;
+  }
   if (st) {
+    cudaDeviceSynchronize();
     B->release();
     delete B;
     return st;
@@ -1874,6 +2042,17 @@ void grape_batch_destroy(grape_batch* B) {
   cudaDeviceSynchronize();
   B->release();
   delete B;
+}
+
+grape_status grape_batch_info(const grape_batch* B, grape_batch_info_t* out) {
+  if (!B || !out) return fail(GRAPE_EINVAL, "NULL argument");
+  out->members = B->count;
+  out->queued = B->n_queued;
+  out->queue_items = B->n_items;
+  out->queue_ctas = B->queue_ctas;
+  out->lanes = (int32_t)B->streams.size();
+  out->lane_members = (int32_t)B->order.size();
+  return GRAPE_OK;
 }
 
 grape_status grape_batch_cost_and_grad(grape_batch* B, const double* const* u, double* costs, double* const* grads,

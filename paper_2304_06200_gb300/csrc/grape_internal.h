@@ -144,6 +144,18 @@ struct GradReduceParams {
   double* grad;                        // K x N row-major
 };
 
+// Batch work queue (k_queue): (problem, column) items, longest first, over problems whose column
+// teams are single CTAs.  head and done[] start at zero for every launch.
+struct QueueParams {
+  const SweepParams* sweep;            // per problem: its forward or fused-backward sweep (CL = 1)
+  const FinalizeParams* fin;           // forward queue: per problem, run by the CTA finishing its last column
+  const GradReduceParams* red;         // backward queue: the same for the gradient reduction
+  const int2* items;                   // (problem, column)
+  int n_items;
+  int* head;                           // next item to take
+  int* done;                           // per problem: columns finished
+};
+
 // Dynamic shared-memory layout of the sweep kernels (byte offsets).  Exchange buffers,
 // per-row states and the local pattern always live in shared memory; the drift-plus-control
 // values (vals), the per-entry gradient accumulators (W) and the first m_smem Horner slots
@@ -214,6 +226,12 @@ cudaError_t launch_gradient(const SweepParams& p, int precision, int smem_bytes,
 cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t st);
 cudaError_t launch_grad_reduce(const GradReduceParams& p, cudaStream_t st);
 cudaError_t check_nonfinite_u(const double* u, int64_t count, int* err, cudaStream_t st);
+// Batch: the schedules of `count` problems (device array ps, max_n = their largest N) in one launch,
+// and the persistent work-queue sweeps (precision 0 FP64, 1 compensated FP32 bulk).
+cudaError_t launch_schedule_batch(const ScheduleParams* ps, int count, int max_n, cudaStream_t st);
+int queue_ctas_per_sm(int precision, bool backward, int threads, int smem_bytes);
+cudaError_t launch_queue(const QueueParams& q, int precision, bool backward, int ctas, int threads, int smem_bytes,
+                         cudaStream_t st);
 cudaError_t launch_sd_update(double* u, const double* grad, int64_t count, double eta, const double* cost, double* costs,
                              int* counter, int max_count, cudaStream_t st);
 int max_dynamic_smem(int device);

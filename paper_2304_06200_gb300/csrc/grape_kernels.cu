@@ -178,10 +178,11 @@ __device__ __forceinline__ void set_error(int* err, int code) { atomicCAS(err, 0
 
 // One block per step (grid-strided).  ||A_n||_1 = dt * max_i sum_j |H_n,ij| on the union pattern
 // (the 1-norm equals the infinity norm for Hermitian H, footnote to Eq. (norm inequality)).
-__global__ void __launch_bounds__(256) k_schedule(ScheduleParams p) {
+// The (m, s) of steps b, b + nb, b + 2 nb, ... of one problem.
+__device__ __forceinline__ void schedule_body(const ScheduleParams& p, const int b, const int nb) {
   __shared__ double red[32];
   __shared__ double s_u[kMaxControls];
-  for (int n = blockIdx.x; n < p.N; n += gridDim.x) {
+  for (int n = b; n < p.N; n += nb) {
     __syncthreads();
     if (threadIdx.x < p.K) s_u[threadIdx.x] = p.u[(int64_t)threadIdx.x * p.N + n];
     __syncthreads();
@@ -225,6 +226,22 @@ __global__ void __launch_bounds__(256) k_schedule(ScheduleParams p) {
       p.norm1[n] = x;
     }
   }
+}
+
+__global__ void __launch_bounds__(256) k_schedule(const __grid_constant__ ScheduleParams p) {
+  schedule_body(p, blockIdx.x, gridDim.x);
+}
+
+// Schedules of many problems in one launch: problem blockIdx.y, its steps over blockIdx.x.
+__global__ void __launch_bounds__(256) k_schedule_batch(const ScheduleParams* __restrict__ ps) {
+  __shared__ ScheduleParams sp;
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(ps + blockIdx.y);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&sp);
+    for (int i = threadIdx.x; i < (int)(sizeof(ScheduleParams) / 4); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  schedule_body(sp, blockIdx.x, gridDim.x);
 }
 
 // ------------------------------------------------------------------ sweep helpers
@@ -567,14 +584,15 @@ struct Team {
 // FP64 terms are kept unscaled, x_j = B^j c_{l-1} = j! b_j, and the sum takes x_j / j! in one fused
 // multiply-add (one FP64 operation per component fewer than scaling every term by 1/j); FP32 terms
 // keep the 1/j scaling, which bounds their range.
+// The sweep of CTA `part` (team part / CL, rank part % CL); k_forward runs it for blockIdx.x, the
+// batch work queue (k_queue) for one (problem, column) item at a time.
 template <typename T, bool CLUSTER>
-__global__ void __launch_bounds__(512, 1) k_forward(SweepParams p) {
+__device__ __forceinline__ void forward_body(const SweepParams& p, const int part) {
   using C2 = cx<T>;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32];
   __shared__ double s_u[kMaxControls];
   __shared__ XTab<T> tab[2];
-  const int part = blockIdx.x;
   const int team = part / p.CL, rank = part % p.CL;
   const int r0 = min(rank * p.R, p.dim), r1 = min(r0 + p.R, p.dim), nrows = r1 - r0;
   const int64_t e0 = p.rowptr[r0];
@@ -813,6 +831,11 @@ __global__ void __launch_bounds__(512, 1) k_forward(SweepParams p) {
     }
   }
   team_sync<CLUSTER>();   // no CTA leaves while a team member may still read its shared memory
+}
+
+template <typename T, bool CLUSTER>
+__global__ void __launch_bounds__(512, 1) k_forward(const __grid_constant__ SweepParams p) {
+  forward_body<T, CLUSTER>(p, blockIdx.x);
 }
 
 // ------------------------------------------------------------------ backward sweep: shared pieces
@@ -1280,14 +1303,12 @@ __device__ __forceinline__ void team_init(Team<T, CLUSTER>& tm, unsigned char* s
 // ------------------------------------------------------------------ backward sweep, one team per column
 
 template <typename T, bool CLUSTER>
-__global__ void __launch_bounds__(512, 1) k_backward(SweepParams p) {
+__device__ __forceinline__ void backward_body(const SweepParams& p, const int part) {
   using C2 = cx<T>;
-  if (p.gate_on_flag && *p.plan_flag == 0) return;   // the three-stage backward ran (uniform over the grid)
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32];
   __shared__ double s_u[kMaxControls];
   __shared__ XTab<T> tab[6];
-  const int part = blockIdx.x;
   const int col = part / p.CL, rank = part % p.CL;
   Team<T, CLUSTER> tm;
   team_init<T, CLUSTER>(tm, smem, tab, p, part, rank);
@@ -1319,6 +1340,12 @@ __global__ void __launch_bounds__(512, 1) k_backward(SweepParams p) {
     __syncthreads();
   }
   team_sync<CLUSTER>();
+}
+
+template <typename T, bool CLUSTER>
+__global__ void __launch_bounds__(512, 1) k_backward(const __grid_constant__ SweepParams p) {
+  if (p.gate_on_flag && *p.plan_flag == 0) return;   // the three-stage backward ran (uniform over the grid)
+  backward_body<T, CLUSTER>(p, blockIdx.x);
 }
 
 // ------------------------------------------------------------------ three-stage backward
@@ -1911,13 +1938,16 @@ __global__ void __launch_bounds__(512, 1) k_gradient(SweepParams p) {
 
 // ------------------------------------------------------------------ finalize (one block)
 
-__global__ void __launch_bounds__(256) k_finalize(FinalizeParams p) {
+// The partials are read through L2 (__ldcg): in the batch work queue they were written by other
+// CTAs of the same launch, whose writes this SM's L1 need not hold.
+__device__ __forceinline__ void finalize_body(const FinalizeParams& p) {
   __shared__ double red[32];
   double gx = 0.0, gy = 0.0, c2 = 0.0, a2 = 0.0;
   for (int i = threadIdx.x; i < p.n_parts; i += blockDim.x) {
-    gx += p.part_g[i].x;
-    gy += p.part_g[i].y;
-    c2 += p.part_c2[i];
+    const double2 g = __ldcg(p.part_g + i);
+    gx += g.x;
+    gy += g.y;
+    c2 += __ldcg(p.part_c2 + i);
   }
   for (int64_t i = threadIdx.x; i < (int64_t)p.K * p.N; i += blockDim.x) a2 = fma(p.u[i], p.u[i], a2);
   double g3sq = 0.0;
@@ -1925,7 +1955,7 @@ __global__ void __launch_bounds__(256) k_finalize(FinalizeParams p) {
     for (int n = threadIdx.x; n < p.N; n += blockDim.x) {
       double sx = 0.0, sy = 0.0;
       for (int i = 0; i < p.n_parts; ++i) {
-        const double2 v = p.part_g3[(int64_t)i * p.N + n];
+        const double2 v = __ldcg(p.part_g3 + (int64_t)i * p.N + n);
         sx += v.x;
         sy += v.y;
       }
@@ -1956,16 +1986,62 @@ __global__ void __launch_bounds__(256) k_finalize(FinalizeParams p) {
   }
 }
 
+__global__ void __launch_bounds__(256) k_finalize(const __grid_constant__ FinalizeParams p) { finalize_body(p); }
+
 // ------------------------------------------------------------------ gradient reduce
 
-__global__ void k_grad_reduce(GradReduceParams p) {
+__device__ __forceinline__ void grad_reduce_body(const GradReduceParams& p, const int64_t first, const int64_t stride) {
   const int64_t total = (int64_t)p.K * p.N;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t idx = first; idx < total; idx += stride) {
     const int k = (int)(idx / p.N), n = (int)(idx % p.N);
     const int n_parts = (p.plan_flag && *p.plan_flag != 0) ? p.n_parts_alt : p.n_parts;
     double acc = 0.0;
-    for (int part = 0; part < n_parts; ++part) acc += p.part_grad[((int64_t)part * p.N + n) * p.K + k];
+    for (int part = 0; part < n_parts; ++part) acc += __ldcg(p.part_grad + ((int64_t)part * p.N + n) * p.K + k);
     p.grad[idx] = acc + p.w_amp * 2.0 * p.u[idx] / (double)p.N;
+  }
+}
+
+__global__ void k_grad_reduce(const __grid_constant__ GradReduceParams p) {
+  grad_reduce_body(p, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+}
+
+// ------------------------------------------------------------------ batch work queue
+//
+// Many independent problems whose column teams are single CTAs: one persistent launch per sweep
+// direction takes (problem, column) items from a queue ordered longest first.  A CTA runs the whole
+// sweep of its item, then counts the item done for its problem; the CTA that completes a problem's
+// last column also reduces that problem's partials (the finalize after the forward sweep, the
+// gradient reduction after the backward sweep), so no CTA ever waits for another one.
+template <typename T, bool BACKWARD>
+__global__ void __launch_bounds__(512, 1) k_queue(const __grid_constant__ QueueParams q) {
+  __shared__ SweepParams sp;
+  __shared__ int s_item, s_last;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(q.head, 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= q.n_items) break;   // uniform over the CTA
+    const int2 w = q.items[it];
+    {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(q.sweep + w.x);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&sp);
+      for (int i = threadIdx.x; i < (int)(sizeof(SweepParams) / 4); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    if constexpr (BACKWARD) backward_body<T, false>(sp, w.y);
+    else forward_body<T, false>(sp, w.y);
+    __threadfence();   // this CTA's partials before the count that publishes them
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_last = atomicAdd(q.done + w.x, 1) == sp.n_states - 1;
+      __threadfence();
+    }
+    __syncthreads();
+    if (s_last) {
+      if constexpr (BACKWARD) grad_reduce_body(q.red[w.x], threadIdx.x, blockDim.x);
+      else finalize_body(q.fin[w.x]);
+    }
+    __syncthreads();   // s_item, s_last and sp are rewritten by the next item
   }
 }
 
@@ -2133,6 +2209,45 @@ cudaError_t launch_grad_reduce(const GradReduceParams& p, cudaStream_t st) {
   if (grid < 1) grid = 1;
   if (grid > 4096) grid = 4096;
   k_grad_reduce<<<grid, 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_schedule_batch(const ScheduleParams* ps, int count, int max_n, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  int gx = 2432 / count;
+  if (gx > max_n) gx = max_n;
+  if (gx < 1) gx = 1;
+  k_schedule_batch<<<dim3(gx, count), 256, 0, st>>>(ps);
+  return cudaGetLastError();
+}
+
+using QueueKernel = void (*)(QueueParams);
+static QueueKernel queue_kernel(int precision, bool backward) {
+  if (precision == 1) return backward ? k_queue<dw, true> : k_queue<dw, false>;
+  return backward ? k_queue<double, true> : k_queue<double, false>;
+}
+
+static cudaError_t queue_attrs(QueueKernel kern, int smem_bytes) {
+  cudaError_t e = ensure_constants();
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+}
+
+int queue_ctas_per_sm(int precision, bool backward, int threads, int smem_bytes) {
+  QueueKernel kern = queue_kernel(precision, backward);
+  if (queue_attrs(kern, smem_bytes) != cudaSuccess) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem_bytes) != cudaSuccess) return 0;
+  return n;
+}
+
+cudaError_t launch_queue(const QueueParams& q, int precision, bool backward, int ctas, int threads, int smem_bytes,
+                         cudaStream_t st) {
+  if (q.n_items <= 0) return cudaSuccess;
+  QueueKernel kern = queue_kernel(precision, backward);
+  cudaError_t e = queue_attrs(kern, smem_bytes);
+  if (e != cudaSuccess) return e;
+  kern<<<ctas, threads, smem_bytes, st>>>(q);
   return cudaGetLastError();
 }
 

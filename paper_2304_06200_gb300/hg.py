@@ -13,7 +13,7 @@ import ctypes as C
 import numpy as np
 
 from . import _abi
-from ._abi import GrapeDesc, GrapeInfo, GrapeOp, check, lib
+from ._abi import GrapeBatchInfo, GrapeDesc, GrapeInfo, GrapeOp, check, lib
 
 PRECISIONS = {"fp64": _abi.GRAPE_FP64, "fp32_bulk": _abi.GRAPE_FP32_BULK, "tc_fp16": _abi.GRAPE_TC_FP16,
               "tc_bf16": _abi.GRAPE_TC_BF16}
@@ -82,6 +82,8 @@ class GrapeProblem:
         self.N = int(problem.n_steps if n_steps is None else n_steps)
         self.n = int(np.asarray(problem.psi0).shape[1])
         self.device = int(device)
+        u0 = getattr(problem, "u0", None)   # the workload's seeded controls, when it has them (K x N)
+        self.u0 = None if u0 is None or np.shape(u0) != (self.K, self.N) else np.ascontiguousarray(u0, dtype=np.float64)
         self._keep = []
         ops = [_csr_arrays(problem.H0, self.dim)] + [_csr_arrays(h, self.dim) for h in problem.Hk]
         self._keep.append(ops)
@@ -238,18 +240,30 @@ class GrapeProblem:
 class GrapeBatch:
     """Many independent problems evaluated by one CUDA-graph launch (``grape_batch_create``).
 
-    The members must be ``GrapeProblem`` objects created with ``backward_mode=1``; the batch keeps
-    references to them so they outlive it.
+    Members with single-CTA column teams run in the persistent work-queue kernels, the others on
+    graph lanes.  ``queue_ctas``: 0 automatic, > 0 that many CTAs, < 0 no queue.  ``u_warm``: the
+    controls of the warm evaluation before the recording (default: each member's workload ``u0``
+    when it has one).  The batch keeps references to the members so they outlive it.
     """
 
-    def __init__(self, problems, n_streams: int = 8):
+    def __init__(self, problems, n_streams: int = 8, queue_ctas: int = 0, u_warm=None):
         L = lib()
         self._lib = L
         self.problems = list(problems)
         handles = (C.c_void_p * len(self.problems))(*[p._h.value for p in self.problems])
+        if u_warm is None:
+            u_warm = [p.u0 for p in self.problems]
+        self._u_warm = [None if u is None else np.ascontiguousarray(u, dtype=np.float64) for u in u_warm]
+        warm = (C.c_void_p * len(self.problems))(*[0 if u is None else u.ctypes.data for u in self._u_warm])
         h = C.c_void_p()
-        check(L.grape_batch_create(handles, len(self.problems), int(n_streams), C.byref(h)), "grape_batch_create")
+        check(L.grape_batch_create(handles, len(self.problems), int(n_streams), int(queue_ctas), warm, C.byref(h)),
+              "grape_batch_create")
         self._h = h
+
+    def info(self) -> dict:
+        out = GrapeBatchInfo()
+        check(self._lib.grape_batch_info(self._h, C.byref(out)), "grape_batch_info")
+        return {name: getattr(out, name) for name, _ in GrapeBatchInfo._fields_}
 
     def cost_and_grad(self, us):
         """Host arrays: list of (K_i, N_i) controls -> (costs array, list of gradients)."""

@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol(L):
     assert sorted(EXPORTED) == declared
     for name in declared:
         assert hasattr(L, name), name
-    assert L.grape_abi_version() == 4
+    assert L.grape_abi_version() == 5
 
 
 def test_status_strings(L):

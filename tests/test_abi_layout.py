@@ -13,7 +13,7 @@ from paper_2304_06200_gb300 import _abi
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 STRUCTS = [("grape_op", _abi.GrapeOp), ("grape_desc", _abi.GrapeDesc), ("grape_info", _abi.GrapeInfo),
-           ("grape_kernel_times_t", _abi.GrapeKernelTimes)]
+           ("grape_kernel_times_t", _abi.GrapeKernelTimes), ("grape_batch_info_t", _abi.GrapeBatchInfo)]
 ENUMS = ["GRAPE_CSR", "GRAPE_DENSE", "GRAPE_FP64", "GRAPE_FP32_BULK", "GRAPE_TC_FP16", "GRAPE_TC_BF16",
          "GRAPE_PROP_TAYLOR", "GRAPE_PROP_EIG"]
 

@@ -417,29 +417,98 @@ def _small_batch(precision):
     return raw, probs
 
 
+def _single_cta_teams(hg):
+    inf = hg.info()
+    return inf["cluster_forward"] == 1 and inf["cluster"] == 1
+
+
+def _batch_rtol(precision):
+    return (COST_RTOL, GRAD_RTOL) if precision == "fp64" else (FP32_RTOL, FP32_RTOL)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
-def test_batch_graph_matches_individual_evaluations(precision):
+@pytest.mark.parametrize("queue_ctas", [0, 2, -1])
+def test_batch_matches_individual_evaluations_and_the_oracle(precision, queue_ctas):
+    """Every member of the batch (work queue: automatic or 2 CTAs; or lanes only) against its own
+    evaluation and against the oracle, over repeated launches of the recorded graph."""
     from paper_2304_06200_gb300 import GrapeBatch
     raw, probs = _small_batch(precision)
     singles = [hg.cost_and_grad(p.u0) for p, hg in zip(raw, probs)]
-    batch = GrapeBatch(probs, n_streams=3)
+    batch = GrapeBatch(probs, n_streams=3, queue_ctas=queue_ctas)
+    inf = batch.info()
+    single = [p for p, hg in zip(raw, probs) if _single_cta_teams(hg)]
+    if queue_ctas < 0:
+        assert inf["queued"] == 0 and inf["lane_members"] == len(raw)
+    else:
+        assert len(single) >= 4
+        assert inf["queued"] == len(single) and inf["lane_members"] == len(raw) - len(single)
+        assert inf["queue_items"] == sum(p.n_states for p in single)
+        assert inf["queue_ctas"] == 2 if queue_ctas == 2 else inf["queue_ctas"] >= 1
+    crt, grt = _batch_rtol(precision)
     for _ in range(2):                                # the graph is launched repeatedly
         costs, grads = batch.cost_and_grad([p.u0 for p in raw])
         for (c, g), cb, gb in zip(singles, costs, grads):
-            assert c == cb
-            assert np.array_equal(g, gb)
-    if precision == "fp64":                           # and the batch is right, not just consistent
-        for p, cb, gb in zip(raw[:2], costs[:2], grads[:2]):
-            _check(p, p.u0, cb, gb)
+            if queue_ctas < 0:                        # the members' own launches: the same bits
+                assert c == cb and np.array_equal(g, gb)
+            else:                                     # one CTA per column at the queue's block size
+                assert abs(cb - c) <= 1e-12 * abs(c)
+                assert np.linalg.norm(gb - g) <= 1e-11 * np.linalg.norm(g)
+    for p, cb, gb in zip(raw, costs, grads):          # every member is right, not just consistent
+        _check(p, p.u0, cb, gb, cost_rtol=crt, grad_rtol=grt)
     batch.close()
 
 
-def test_batch_rejects_three_stage_members_and_removed_modes():
-    from paper_2304_06200_gb300 import GrapeBatch, GrapeError
+@pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
+def test_batch_mixes_the_queue_with_cluster_and_three_stage_members(precision):
+    """Queued single-CTA members beside lane members: a clustered fused-backward member and a clustered
+    three-stage member (block buffers sized by the warm evaluation), every one against the oracle."""
+    from paper_2304_06200_gb300 import GrapeBatch, GrapeProblem
+    raw, probs = _small_batch(precision)
+    big = random_problem(600, 3, 3, 12, seed=6161, band=4, density=0.004)
+    big.u0 = big.u0 * 3
+    tri = build_config("c2_gate_d80", n_steps=40)
+    tri.u0 = tri.u0 * 10
+    raw += [big, tri]
+    probs += [GrapeProblem(big, precision=precision, cluster=4, backward_mode=1),
+              GrapeProblem(tri, precision=precision, cluster=2, backward_mode=3)]
+    assert probs[-1].info()["backward_mode"] == 3
+    batch = GrapeBatch(probs, n_streams=3)
+    inf = batch.info()
+    queued = sum(_single_cta_teams(hg) for hg in probs)
+    assert queued >= 4 and not _single_cta_teams(probs[-1]) and not _single_cta_teams(probs[-2])
+    assert inf["queued"] == queued and inf["lane_members"] == len(raw) - queued
+    costs, grads = batch.cost_and_grad([p.u0 for p in raw])
+    crt, grt = _batch_rtol(precision)
+    for p, cb, gb in zip(raw, costs, grads):
+        _check(p, p.u0, cb, gb, cost_rtol=crt, grad_rtol=grt)
+    batch.close()
+
+
+def test_batch_keeps_three_stage_buffers_and_falls_back_on_the_device():
+    """While a batch exists a member's block buffers are not replaced (the recording refers to them):
+    controls needing more Taylor terms than the warm evaluation's run the fused backward on the device,
+    with the same result; after the batch is gone the buffers grow again."""
+    from paper_2304_06200_gb300 import GrapeBatch
+    p = _weak_drift_problem()
+    hg = _hg(p, backward_mode=3, block_steps=1, cluster=2)
+    batch = GrapeBatch([hg], u_warm=[p.u0])
+    u_big = p.u0 * 2e4
+    costs, grads = batch.cost_and_grad([u_big])
+    assert hg.info()["fused_fallback"] == 1
+    _check(p, u_big, costs[0], grads[0])
+    b0 = hg.info()["device_bytes"]
+    cost, grad = hg.cost_and_grad(u_big)             # the member alone: buffers kept, fallback again
+    assert hg.info()["fused_fallback"] == 1 and hg.info()["device_bytes"] == b0
+    _check(p, u_big, cost, grad)
+    batch.close()
+    cost, grad = hg.cost_and_grad(u_big)             # no batch left: the buffers grow
+    assert hg.info()["fused_fallback"] == 0 and hg.info()["device_bytes"] > b0
+    _check(p, u_big, cost, grad)
+
+
+def test_removed_backward_mode_is_rejected():
+    from paper_2304_06200_gb300 import GrapeError
     p = build_config("c1_state_transfer_d30", n_steps=10)
-    hg = _hg(p, backward_mode=3)
-    with pytest.raises(GrapeError):
-        GrapeBatch([hg])
     with pytest.raises(GrapeError):      # the two-team mode 2 no longer exists
         _hg(p, backward_mode=2)
 
@@ -743,7 +812,8 @@ def test_allocation_failure_is_reported():
 
 def test_batch_with_eigendecomposition_members():
     """A batch mixing Taylor and eigendecomposition members (the latter forking their step chunks
-    onto their own streams inside the recorded graph): equal to the individual evaluations."""
+    onto their own streams inside the recorded graph, the Taylor member in the work queue): the
+    eigendecomposition members equal their individual evaluations bit for bit, all match the oracle."""
     from paper_2304_06200_gb300 import GrapeBatch
     raw = [build_config("c1_state_transfer_d30", n_steps=300), build_config("c2_gate_d80", n_steps=70),
            random_problem(48, 2, 3, 20, seed=5151, density=0.5)]
@@ -752,10 +822,18 @@ def test_batch_with_eigendecomposition_members():
     batch = GrapeBatch(probs, n_streams=2)
     for _ in range(2):
         costs, grads = batch.cost_and_grad([p.u0 for p in raw])
-        for (c, g), cb, gb in zip(singles, costs, grads):
-            assert c == cb
-            assert np.array_equal(g, gb)
-    _check(raw[0], raw[0].u0, costs[0], grads[0], cost_rtol=EIG_COST_RTOL, grad_rtol=EIG_GRAD_RTOL)
+        for i, ((c, g), cb, gb) in enumerate(zip(singles, costs, grads)):
+            if i == 1:                                # queued Taylor member: the queue's block size
+                assert abs(cb - c) <= 1e-12 * abs(c)
+                assert np.linalg.norm(gb - g) <= 1e-11 * np.linalg.norm(g)
+            else:
+                assert c == cb
+                assert np.array_equal(g, gb)
+    for i, p in enumerate(raw):
+        if i == 1:
+            _check(p, p.u0, costs[i], grads[i])
+        else:
+            _check(p, p.u0, costs[i], grads[i], cost_rtol=EIG_COST_RTOL, grad_rtol=EIG_GRAD_RTOL)
     batch.close()
 
 
