@@ -1810,6 +1810,11 @@ grape_status batch_build(grape_batch* B, int n_streams, int queue_ctas, const do
   for (int i = 0; i < count; ++i) {
     grape_problem* P = B->probs[i];
     cudaMemset(P->d_err, 0, sizeof(int));
+    if (P->eig) {   // one dense d x d product per step and column
+      col_work[i] = (double)P->N * (double)P->dim * (double)P->dim;
+      work[i] = col_work[i] * P->n;
+      continue;
+    }
     std::vector<int> m(P->N), sv(P->N);
     if ((e = cudaMemcpy(m.data(), P->d_ms_m, P->N * sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess ||
         (e = cudaMemcpy(sv.data(), P->d_ms_s, P->N * sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
