@@ -954,12 +954,16 @@ def batch_compare(local, tune=False):
             hg = GrapeProblem(p, device=local, precision="fp32_bulk")
         members.append(hg)
     create_s = time.perf_counter() - t0
+    # throughput variant: the d = 4000 members with teams of 8 CTAs (fewer barriers per unit of work;
+    # in a batch the SMs are shared, so per-SM efficiency counts more than one member's latency)
+    members_cl8 = [GrapeProblem(p, device=local, precision="fp32_bulk", cluster=8) if p.dim >= 4000 else hg
+                   for p, hg in zip(insts, members)]
     us = [torch.tensor(p.u0, dtype=torch.float64, device=dev) for p in insts]
     res = {"instances": len(insts)}
     outs = {}
-    for name, qc in (("queue", 0), ("lanes_only", -1)):
+    for name, qc, mem in (("queue", 0, members), ("lanes_only", -1, members), ("queue_big_teams_of_8", 0, members_cl8)):
         t1 = time.perf_counter()
-        batch = GrapeBatch(members, n_streams=16, queue_ctas=qc)
+        batch = GrapeBatch(mem, n_streams=16, queue_ctas=qc)
         build_s = time.perf_counter() - t1
         grads = [torch.zeros_like(u) for u in us]
         costs = torch.zeros(len(insts), dtype=torch.float64, device=dev)
@@ -980,7 +984,7 @@ def batch_compare(local, tune=False):
         res[name] = {"ms_per_eval_of_all": round(ms, 2), "evals_per_s": round(len(insts) * 1e3 / ms, 3),
                      "record_s": round(build_s, 1), **batch.info()}
         batch.close()
-    for m in members:
+    for m in set(members) | set(members_cl8):
         m.close()
     # the same 64, one at a time, plain FP64 kernels
     seq_ms = 0.0
@@ -1007,6 +1011,8 @@ def batch_compare(local, tune=False):
                 "speedup_queue_over_sequential_fp64": round(seq_ms / res["queue"]["ms_per_eval_of_all"], 2),
                 "speedup_queue_over_lanes_only": round(res["lanes_only"]["ms_per_eval_of_all"]
                                                        / res["queue"]["ms_per_eval_of_all"], 3),
+                "speedup_teams_of_8_over_queue": round(res["queue"]["ms_per_eval_of_all"]
+                                                       / res["queue_big_teams_of_8"]["ms_per_eval_of_all"], 3),
                 "create_s": round(create_s, 1), "autotuned": tune, "tune": tune_report[:8]})
     return res
 
