@@ -684,7 +684,7 @@ static cudaError_t apply(const DenseCtx& c, int ncols, float alpha, float2* y, c
   a.d = c.d;
   a.ncols = ncols;
   a.nreal = ((2 * ncols + 15) / 16) * 16;
-  a.alpha = (float)(alpha / c.op_scale);   // exact: op_scale is a power of two
+  a.alpha = alpha;
   a.bf16 = c.bf16;
   a.err = c.err;
   const int smem = dense_apply_smem(a.nreal);
@@ -757,7 +757,7 @@ cudaError_t dense_forward(const DenseCtx& c, const int* m_host, const int* s_hos
     const int m = m_host[step], s = s_host[step];
     if (m <= 0 || s <= 0) continue;
     SPLIT_LAUNCH(k_dense_assemble, std::min(d, 2048), 256, st, c.rowptr, c.ucol, c.h0v, c.ectr_ptr, c.ectr_k, c.ectr_val,
-                                                       c.u, c.N, step, c.op_scale * c.dt / s, d, c.brh, c.brl, c.bih, c.bil);
+                                                       c.u, c.N, step, c.dt / s, d, c.brh, c.brl, c.bih, c.bil);
     DCHK(cudaGetLastError());
     for (int l = 0; l < s; ++l) {
       int xsel = 0;
@@ -806,7 +806,7 @@ cudaError_t dense_backward(const DenseCtx& c, const int* m_host, const int* s_ho
     const int m = m_host[step], s = s_host[step];
     if (m <= 0 || s <= 0) continue;
     SPLIT_LAUNCH(k_dense_assemble, std::min(d, 2048), 256, st, c.rowptr, c.ucol, c.h0v, c.ectr_ptr, c.ectr_k, c.ectr_val,
-                                                       c.u, c.N, step, c.op_scale * c.dt / s, d, c.brh, c.brl, c.bih, c.bil);
+                                                       c.u, c.N, step, c.dt / s, d, c.brh, c.brl, c.bih, c.bil);
     DCHK(cudaGetLastError());
     DCHK(cudaMemsetAsync(c.W, 0, (size_t)std::max(c.nce, 1) * sizeof(double2), st));
     for (int l = s - 1; l >= 0; --l) {

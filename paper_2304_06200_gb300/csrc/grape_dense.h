@@ -15,10 +15,6 @@ struct DenseCtx {
   int x_rows;               // rows allocated in xh / xl (>= 4 n, >= 64, a multiple of 16)
   int bf16;                 // operand pairs are bf16 (GRAPE_TC_BF16), else fp16 (GRAPE_TC_FP16)
   double dt, w_fid, w_forbid, w_tint;
-  // The operator is stored as op_scale B (a power of two, exact in every format) so that its largest
-  // entries sit near 1, where the FP16 low parts are normal numbers; products are scaled back by
-  // 1 / op_scale in the FP32 epilogue.
-  double op_scale;
   int ckpt_every, n_ckpt;
   double inv_fact[62];
   // operator of the current step (FP16 hi/lo of Br and Bi, d x d row-major) and work blocks

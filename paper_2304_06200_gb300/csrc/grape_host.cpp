@@ -393,15 +393,6 @@ grape_status build_dense(grape_problem* P, const grape_desc* d, const std::vecto
   c.ksplit = 1;   // chosen below, after the kernel attributes are set
   c.bf16 = P->precision == GRAPE_TC_BF16 ? 1 : 0;
   c.dt = P->dt;
-  {
-    // op_scale = 2^e with dt * max |H_s entry| * 2^e in (1/2, 1]; e in [0, 13]: the schedule caps
-    // ||B||_1 at 2 in the tensor-core modes, so every stored entry stays below 2^14 (FP16 max 65504)
-    double hmax = 0.0;
-    for (const double2& v : h0v) hmax = std::max(hmax, std::hypot(v.x, v.y));
-    int e = 0;
-    while (e < 13 && hmax * P->dt * std::ldexp(1.0, e + 1) <= 1.0) ++e;
-    c.op_scale = std::ldexp(1.0, e);
-  }
   c.w_fid = P->w_fid;
   c.w_forbid = P->w_forbid;
   c.ckpt_every = P->ckpt_every;
