@@ -416,18 +416,23 @@ def run_ours(args):
     u_h = torch.tensor(p.u0, dtype=torch.float64).pin_memory()
     cost_h = torch.zeros(1, dtype=torch.float64).pin_memory()
     grad_h = torch.zeros((p.n_controls, p.n_steps), dtype=torch.float64).pin_memory()
-    e2e_times = []
+    e2e_times, e2e_dev = [], []
     for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         flush.zero_()
         torch.cuda.synchronize()
+        e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
+        e_a.record(stream)
         st = hg._lib.grape_cost_and_grad(hg._h, ctypes.c_void_p(u_h.data_ptr()), ctypes.c_void_p(cost_h.data_ptr()),
                                          ctypes.c_void_p(grad_h.data_ptr()), 0, None)
+        e_b.record(stream)
         t1 = time.perf_counter()
         if st != 0:
             raise RuntimeError(f"grape_cost_and_grad failed with status {st}")
+        torch.cuda.synchronize()
         if i > 0:
             e2e_times.append(t1 - t0)
+            e2e_dev.append(e_a.elapsed_time(e_b) / 1e3)
     e2e_local = sum(e2e_times)
     e2e_value = aggregate(e2e_local, len(e2e_times), world, rmax, rsum)[0] if e2e_times else None
     h2d = p.n_controls * p.n_steps * 8
@@ -559,7 +564,8 @@ def run_ours(args):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_value, 6) if e2e_value else None, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "api": "grape_cost_and_grad with pinned host u/cost/grad"},
+                "api": "grape_cost_and_grad with pinned host u/cost/grad",
+                "samples_s": [round(t, 4) for t in e2e_times], "event_samples_s": [round(t, 4) for t in e2e_dev]},
         "gpu_launches": gpu_launches,
         "clocks": clk,
         "peak_hbm": peak_hbm,

@@ -31,6 +31,8 @@
 //   k_check_finite    non-finite controls set the device error word
 #include "grape_internal.h"
 
+#include <algorithm>
+
 #include <cooperative_groups.h>
 
 namespace cg = cooperative_groups;
@@ -176,9 +178,55 @@ __device__ __forceinline__ void set_error(int* err, int code) { atomicCAS(err, 0
 
 // ------------------------------------------------------------------ schedule: norm and (m, s)
 
-// One block per step (grid-strided).  ||A_n||_1 = dt * max_i sum_j |H_n,ij| on the union pattern
-// (the 1-norm equals the infinity norm for Hermitian H, footnote to Eq. (norm inequality)).
-// The (m, s) of steps b, b + nb, b + 2 nb, ... of one problem.
+// ||A_n||_1 = dt * max_i sum_j |H_n,ij| on the union pattern (the 1-norm equals the infinity norm
+// for Hermitian H, footnote to Eq. (norm inequality)).  rows_max: the largest row sum of H_n over
+// rows [r0, r1) (valid in thread 0; +inf marks a non-finite sum), the controls of step n in s_u.
+__device__ __forceinline__ double rows_max(const ScheduleParams& p, const double* s_u, int r0, int r1, double* red) {
+  double rmax = 0.0;
+  bool bad = false;
+  for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    double rs = 0.0;
+    for (int64_t e = p.rowptr[i]; e < p.rowptr[i + 1]; ++e) {
+      double2 v = p.h0v[e];
+      for (int c = p.ectr_ptr[e]; c < p.ectr_ptr[e + 1]; ++c) {
+        const double uk = s_u[p.ectr_k[c]];
+        const double2 hv = p.ectr_val[c];
+        v.x = fma(uk, hv.x, v.x);
+        v.y = fma(uk, hv.y, v.y);
+      }
+      rs += sqrt(v.x * v.x + v.y * v.y);
+    }
+    if (!(rs <= 1e300)) bad = true;   // NaN or inf
+    rmax = fmax(rmax, rs);
+  }
+  if (bad) rmax = __longlong_as_double(0x7ff0000000000000LL);
+  return block_max(rmax, red);
+}
+
+// The paper's rule for step n from its largest row sum mx: the smallest s, then the smallest m, with
+// E_A(m, s) <= tau (the host's breakpoint table); stores (m, s) and ||A_n||_1.
+__device__ __forceinline__ void pick_ms(const ScheduleParams& p, int n, double mx) {
+  const double x = p.dt * mx;
+  int m = 0, s = 0;
+  if (!(x <= 1e300)) {
+    set_error(p.err, kErrNonFinite);
+  } else {
+    int s0 = 1;
+    if (p.b_cap > 0.0) s0 = min(max(1, (int)ceil(x / p.b_cap)), p.s_cap);
+    for (int si = s0; si <= p.s_cap && s == 0; ++si) {
+      if (p.table_smax[si - 1] >= x) {
+        for (int mi = 1; mi <= p.m_cap; ++mi)
+          if (p.table[(int64_t)(si - 1) * p.m_cap + (mi - 1)] >= x) { m = mi; s = si; break; }
+      }
+    }
+    if (s == 0) set_error(p.err, kErrTol);
+  }
+  p.ms_m[n] = m;
+  p.ms_s[n] = s;
+  p.norm1[n] = x;
+}
+
+// The (m, s) of steps b, b + nb, b + 2 nb, ... of one problem, one block per step.
 __device__ __forceinline__ void schedule_body(const ScheduleParams& p, const int b, const int nb) {
   __shared__ double red[32];
   __shared__ double s_u[kMaxControls];
@@ -186,46 +234,32 @@ __device__ __forceinline__ void schedule_body(const ScheduleParams& p, const int
     __syncthreads();
     if (threadIdx.x < p.K) s_u[threadIdx.x] = p.u[(int64_t)threadIdx.x * p.N + n];
     __syncthreads();
-    double rmax = 0.0;
-    bool bad = false;
-    for (int i = threadIdx.x; i < p.dim; i += blockDim.x) {
-      double rs = 0.0;
-      for (int64_t e = p.rowptr[i]; e < p.rowptr[i + 1]; ++e) {
-        double2 v = p.h0v[e];
-        for (int c = p.ectr_ptr[e]; c < p.ectr_ptr[e + 1]; ++c) {
-          const double uk = s_u[p.ectr_k[c]];
-          const double2 hv = p.ectr_val[c];
-          v.x = fma(uk, hv.x, v.x);
-          v.y = fma(uk, hv.y, v.y);
-        }
-        rs += sqrt(v.x * v.x + v.y * v.y);
-      }
-      if (!(rs <= 1e300)) bad = true;   // NaN or inf
-      rmax = fmax(rmax, rs);
-    }
-    if (bad) rmax = __longlong_as_double(0x7ff0000000000000LL);   // +inf marks a non-finite step
-    const double mx = block_max(rmax, red);
-    if (threadIdx.x == 0) {
-      const double x = p.dt * mx;
-      int m = 0, s = 0;
-      if (!(x <= 1e300)) {
-        set_error(p.err, kErrNonFinite);
-      } else {
-        int s0 = 1;
-        if (p.b_cap > 0.0) s0 = min(max(1, (int)ceil(x / p.b_cap)), p.s_cap);
-        for (int si = s0; si <= p.s_cap && s == 0; ++si) {
-          if (p.table_smax[si - 1] >= x) {
-            for (int mi = 1; mi <= p.m_cap; ++mi)
-              if (p.table[(int64_t)(si - 1) * p.m_cap + (mi - 1)] >= x) { m = mi; s = si; break; }
-          }
-        }
-        if (s == 0) set_error(p.err, kErrTol);
-      }
-      p.ms_m[n] = m;
-      p.ms_s[n] = s;
-      p.norm1[n] = x;
-    }
+    const double mx = rows_max(p, s_u, 0, p.dim, red);
+    if (threadIdx.x == 0) pick_ms(p, n, mx);
   }
+}
+
+// Few steps with many entries each (a dense H): the rows of a step are split over blockIdx.y chunks;
+// each block maxes its chunk's largest row sum into norm1[n] as FP64 bits (non-negative doubles order
+// like their bit patterns; norm1 zeroed before), then k_schedule_pick applies the rule per step.
+// The maximum does not depend on the order, so the schedule is the one-block-per-step kernel's.
+__global__ void __launch_bounds__(256) k_schedule_rows(const __grid_constant__ ScheduleParams p, int rows_per) {
+  __shared__ double red[32];
+  __shared__ double s_u[kMaxControls];
+  const int r0 = blockIdx.y * rows_per, r1 = min(p.dim, r0 + rows_per);
+  for (int n = blockIdx.x; n < p.N; n += gridDim.x) {
+    __syncthreads();
+    if (threadIdx.x < p.K) s_u[threadIdx.x] = p.u[(int64_t)threadIdx.x * p.N + n];
+    __syncthreads();
+    const double mx = rows_max(p, s_u, r0, r1, red);
+    if (threadIdx.x == 0)
+      atomicMax(reinterpret_cast<unsigned long long*>(p.norm1) + n, (unsigned long long)__double_as_longlong(mx));
+  }
+}
+
+__global__ void k_schedule_pick(const __grid_constant__ ScheduleParams p) {
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < p.N; n += gridDim.x * blockDim.x)
+    pick_ms(p, n, p.norm1[n]);
 }
 
 __global__ void __launch_bounds__(256) k_schedule(const __grid_constant__ ScheduleParams p) {
@@ -2082,8 +2116,21 @@ int max_dynamic_smem(int device) {
 }
 
 cudaError_t launch_schedule(const ScheduleParams& p, cudaStream_t st) {
-  const int grid = p.N < 1216 ? p.N : 1216;
-  k_schedule<<<grid, 256, 0, st>>>(p);
+  // blocks: one per step up to 1216; with fewer steps than that, rows are split into chunks of at
+  // least 64 so that about 2432 blocks share the work
+  int chunks = p.N >= 1216 ? 1 : std::min(std::max(1, p.dim / 64), std::max(1, 2432 / std::max(p.N, 1)));
+  if (chunks <= 1) {
+    const int grid = p.N < 1216 ? p.N : 1216;
+    k_schedule<<<grid, 256, 0, st>>>(p);
+    return cudaGetLastError();
+  }
+  const int rows_per = (p.dim + chunks - 1) / chunks;
+  chunks = (p.dim + rows_per - 1) / rows_per;
+  cudaError_t e = cudaMemsetAsync(p.norm1, 0, (size_t)p.N * sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  k_schedule_rows<<<dim3(p.N, chunks), 256, 0, st>>>(p, rows_per);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_schedule_pick<<<(p.N + 127) / 128, 128, 0, st>>>(p);
   return cudaGetLastError();
 }
 
