@@ -523,82 +523,6 @@ __device__ __forceinline__ cx<T> xload(const cx<T>* local, const XTab<T>& tab, u
 }
 
 
-// The remote part of one FP64 row product after the cluster wait: the single-phase entries [c0, ci)
-// (imaginary B_ij) and [ci, ea) (real B_ij), then the general entries on both sides of the local
-// run [la, lb), in that order.  The operands of the first kRemotePre entries are loaded together
-// (their distributed-shared-memory round trips overlap instead of following one another), then
-// applied in the same order as one at a time, so the sum is the same bit for bit.
-constexpr int kRemotePre = 6;
-template <bool CLUSTER>
-__device__ __forceinline__ void remote_terms_f64(double2& y, const double2* __restrict__ vals,
-                                                 const uint32_t* __restrict__ lcol, int c0, int ci, int ea, int la,
-                                                 int lb, int eb, const double2* xs, const XTab<double>& tab) {
-  const int n_im = ci - c0, n_sp = ea - c0, nl = la - ea;
-  const int tot = n_sp + nl + (eb - lb);
-  auto ent = [&](int k) { return k < n_sp ? c0 + k : (k - n_sp < nl ? ea + (k - n_sp) : lb + (k - n_sp - nl)); };
-  auto apply = [&](int k, int e, const double2 x) {
-    if (k < n_im) mac_imag(y, vals[e].y, x);
-    else if (k < n_sp) mac_real(y, vals[e].x, x);
-    else cmacT(y, vals[e], x);
-  };
-  if constexpr (CLUSTER) {
-    double2 xr[kRemotePre];
-#pragma unroll
-    for (int k = 0; k < kRemotePre; ++k)
-      if (k < tot) xr[k] = xload<double, CLUSTER>(xs, tab, lcol[ent(k)]);
-#pragma unroll
-    for (int k = 0; k < kRemotePre; ++k)
-      if (k < tot) apply(k, ent(k), xr[k]);
-    for (int k = kRemotePre; k < tot; ++k) {
-      const int e = ent(k);
-      apply(k, e, xload<double, CLUSTER>(xs, tab, lcol[e]));
-    }
-  } else {   // a one-CTA team reads its own shared memory: nothing to overlap, one loop per segment
-    for (int e = c0; e < ci; ++e) mac_imag(y, vals[e].y, xs[lcol[e] & kLocalMask]);
-    for (int e = ci; e < ea; ++e) mac_real(y, vals[e].x, xs[lcol[e] & kLocalMask]);
-    for (int k = 0; k < tot - n_sp; ++k) {
-      const int e = k < nl ? ea + k : lb + (k - nl);
-      cmacT(y, vals[e], xs[lcol[e] & kLocalMask]);
-    }
-  }
-}
-
-// The same for the compensated bulk: remote operands of the first kRemotePre entries loaded together,
-// then accumulated in the usual order.
-template <bool CLUSTER>
-__device__ __forceinline__ void remote_terms_dw(DwAcc& y, const float4* __restrict__ vals,
-                                                const uint32_t* __restrict__ lcol, int c0, int ci, int ea, int la,
-                                                int lb, int eb, const float4* xs, const XTab<dw>& tab) {
-  const int n_im = ci - c0, n_sp = ea - c0, nl = la - ea;
-  const int tot = n_sp + nl + (eb - lb);
-  auto ent = [&](int k) { return k < n_sp ? c0 + k : (k - n_sp < nl ? ea + (k - n_sp) : lb + (k - n_sp - nl)); };
-  auto apply = [&](int k, int e, const float4 x) {
-    if (k < n_im) dw_mac_imag(y, vals[e], x);
-    else if (k < n_sp) dw_mac_real(y, vals[e], x);
-    else cmacT(y, vals[e], x);
-  };
-  if constexpr (CLUSTER) {
-    float4 xr[kRemotePre];
-#pragma unroll
-    for (int k = 0; k < kRemotePre; ++k)
-      if (k < tot) xr[k] = xload<dw, CLUSTER>(xs, tab, lcol[ent(k)]);
-#pragma unroll
-    for (int k = 0; k < kRemotePre; ++k)
-      if (k < tot) apply(k, ent(k), xr[k]);
-    for (int k = kRemotePre; k < tot; ++k) {
-      const int e = ent(k);
-      apply(k, e, xload<dw, CLUSTER>(xs, tab, lcol[e]));
-    }
-  } else {
-    for (int e = c0; e < ci; ++e) dw_mac_imag(y, vals[e], xs[lcol[e] & kLocalMask]);
-    for (int e = ci; e < ea; ++e) dw_mac_real(y, vals[e], xs[lcol[e] & kLocalMask]);
-    for (int k = 0; k < tot - n_sp; ++k) {
-      const int e = k < nl ? ea + k : lb + (k - nl);
-      cmacT(y, vals[e], xs[lcol[e] & kLocalMask]);
-    }
-  }
-}
-
 // Row products on the local pattern, returned as the row sum's bulk value.  FP64: one accumulator per
 // chain (the FP64 pipe is the bound, so no extra instructions).  Compensated FP32 (latency bound):
 // entries two at a time, both loads (a remote row costs a distributed-shared-memory round trip)
@@ -780,9 +704,22 @@ __device__ __forceinline__ void forward_body(const SweepParams& p, const int par
             }
             split_wait<CLUSTER>();
             if (i < nrows) {
-              // one pass over the remote entries on both sides of the local run, so that a warp
+              for (int e = c0; e < ci; ++e) {
+                const uint32_t enc = c.lcol[e];
+                mac_imag(y, c.vals[e].y, xload<T, CLUSTER>(xs, tab[src], enc));
+              }
+              for (int e = ci; e < ea; ++e) {
+                const uint32_t enc = c.lcol[e];
+                mac_real(y, c.vals[e].x, xload<T, CLUSTER>(xs, tab[src], enc));
+              }
+              // one loop over the remote entries on both sides of the local run, so that a warp
               // pays for its longest remote list once
-              remote_terms_f64<CLUSTER>(y, c.vals, c.lcol, c0, ci, ea, la, lb, eb, xs, tab[src]);
+              const int nl = la - ea, nr = nl + (eb - lb);
+              for (int k = 0; k < nr; ++k) {
+                const int e = k < nl ? ea + k : lb + (k - nl);
+                const uint32_t enc = c.lcol[e];
+                cmacT(y, c.vals[e], xload<T, CLUSTER>(xs, tab[src], enc));
+              }
               X0[dst * R + i] = y;   // B^q c (unscaled)
               double2 a = c.inc[i];
               const double fq = c_inv_fact[q];
@@ -824,7 +761,13 @@ __device__ __forceinline__ void forward_body(const SweepParams& p, const int par
             }
             split_wait<CLUSTER>();
             if (i < nrows) {
-              remote_terms_dw<CLUSTER>(y, c.vals, c.lcol, c0, ci, ea, la, lb, eb, xs, tab[src]);
+              for (int e = c0; e < ci; ++e) dw_mac_imag(y, c.vals[e], xload<T, CLUSTER>(xs, tab[src], c.lcol[e]));
+              for (int e = ci; e < ea; ++e) dw_mac_real(y, c.vals[e], xload<T, CLUSTER>(xs, tab[src], c.lcol[e]));
+              const int nl = la - ea, nr = nl + (eb - lb);
+              for (int k = 0; k < nr; ++k) {
+                const int e = k < nl ? ea + k : lb + (k - nl);
+                cmacT(y, c.vals[e], xload<T, CLUSTER>(xs, tab[src], c.lcol[e]));
+              }
               const C2 b = dw_scale(dw_norm(y), c_dw_inv[q]);
               X0[dst * R + i] = b;
               acc_add4(incr, b);
@@ -1602,7 +1545,13 @@ __global__ void __launch_bounds__(512, 1) k_costate(SweepParams p) {
             }
             split_wait<CLUSTER>();
             if (i < nrows) {
-              remote_terms_f64<CLUSTER>(y, c.vals, c.lcol, c0, ci, ea, la, lb, eb, xs, tab[src]);
+              for (int e = c0; e < ci; ++e) mac_imag(y, c.vals[e].y, xload<T, CLUSTER>(xs, tab[src], c.lcol[e]));
+              for (int e = ci; e < ea; ++e) mac_real(y, c.vals[e].x, xload<T, CLUSTER>(xs, tab[src], c.lcol[e]));
+              const int nl = la - ea, nr = nl + (eb - lb);
+              for (int k = 0; k < nr; ++k) {
+                const int e = k < nl ? ea + k : lb + (k - nl);
+                cmacT(y, c.vals[e], xload<T, CLUSTER>(xs, tab[src], c.lcol[e]));
+              }
               const double2 ch = chi[i];
               if (q < m) {
                 y = horner(ch, c_inv_fact[m - q], y);   // w_{m-1-q} = chi/(m-q)! + (-B) w_{m-q}
@@ -1650,7 +1599,13 @@ __global__ void __launch_bounds__(512, 1) k_costate(SweepParams p) {
             }
             split_wait<CLUSTER>();
             if (i < nrows) {
-              remote_terms_dw<CLUSTER>(y, c.vals, c.lcol, c0, ci, ea, la, lb, eb, xs, tab[src]);
+              for (int e = c0; e < ci; ++e) dw_mac_imag(y, c.vals[e], xload<T, CLUSTER>(xs, tab[src], c.lcol[e]));
+              for (int e = ci; e < ea; ++e) dw_mac_real(y, c.vals[e], xload<T, CLUSTER>(xs, tab[src], c.lcol[e]));
+              const int nl = la - ea, nr = nl + (eb - lb);
+              for (int k = 0; k < nr; ++k) {
+                const int e = k < nl ? ea + k : lb + (k - nl);
+                cmacT(y, c.vals[e], xload<T, CLUSTER>(xs, tab[src], c.lcol[e]));
+              }
               if (q < m) {
                 X0[dst * R + i] = dw_sub(chb, dw_scale(dw_norm(y), c_dw_inv[m - q + 1]));
               } else {
