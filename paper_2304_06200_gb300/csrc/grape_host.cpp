@@ -206,6 +206,10 @@ struct grape_problem {
   int* d_cslice_g = nullptr;             // control slices of the gradient partition
   cudaStream_t g_stream[kGradStreams] = {nullptr, nullptr};   // k_gradient launches
   cudaEvent_t ev_b = nullptr, ev_g[kHbufDepth] = {nullptr, nullptr, nullptr};
+  // A timing event recorded behind every costate launch.  Measured at d = 4000: with it the chain's
+  // next launch is not held back behind the gradient kernels (1.96 s per evaluation, against 2.41 s
+  // without it or with an event created without timing); nothing reads its timestamp.
+  cudaEvent_t ev_ct = nullptr;
   int prio_hi = 0;                       // launch priority of the costate chain
   int64_t scr_g_off = 0;                 // k_gradient's regions of d_scratch (double2 units), one of
   int64_t scr_g_size = 0;                // scr_g_size per gradient stream
@@ -296,6 +300,8 @@ struct grape_problem {
     tr_used = 0;
     if (ev_b) cudaEventDestroy(ev_b);
     ev_b = nullptr;
+    if (ev_ct) cudaEventDestroy(ev_ct);
+    ev_ct = nullptr;
     for (auto& row : ev_seg)
       for (auto& e : row) {
         if (e) cudaEventDestroy(e);
@@ -1151,6 +1157,7 @@ grape_status build(grape_problem* P, const grape_desc* d) {
         return cuda_fail(e, "cudaStreamCreateWithPriority");
     if ((e = cudaEventCreateWithFlags(&P->ev_b, cudaEventDisableTiming)) != cudaSuccess)
       return cuda_fail(e, "cudaEventCreateWithFlags");
+    if ((e = cudaEventCreate(&P->ev_ct)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
     for (auto& ev : P->ev_g)
       if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
         return cuda_fail(e, "cudaEventCreateWithFlags");
@@ -1591,6 +1598,7 @@ grape_status run_backward(grape_problem* P, cudaStream_t st) {
       if ((e = grape::launch_costate(pc, P->precision, P->fwd.smem, P->fwd.threads, P->prio_hi, st)) != cudaSuccess)
         return cuda_fail(e, "launch k_costate");
       P->trace_end(tc, st);
+      if ((e = cudaEventRecord(P->ev_ct, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
       if ((e = cudaEventRecord(P->ev_b, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
       if ((e = cudaStreamWaitEvent(gs, P->ev_b, 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
       const int tg = P->trace_begin(2, gs);
