@@ -208,7 +208,8 @@ struct grape_problem {
   cudaEvent_t ev_b = nullptr, ev_g[kHbufDepth] = {nullptr, nullptr, nullptr};
   // A timing event recorded behind every costate launch.  Measured at d = 4000: with it the chain's
   // next launch is not held back behind the gradient kernels (1.96 s per evaluation, against 2.41 s
-  // without it or with an event created without timing); nothing reads its timestamp.
+  // without it or with an event created without timing); nothing reads its timestamp.  Not recorded
+  // while a stream is being captured (a recorded graph orders its launches by its own edges).
   cudaEvent_t ev_ct = nullptr;
   int prio_hi = 0;                       // launch priority of the costate chain
   int64_t scr_g_off = 0;                 // k_gradient's regions of d_scratch (double2 units), one of
@@ -1598,7 +1599,8 @@ grape_status run_backward(grape_problem* P, cudaStream_t st) {
       if ((e = grape::launch_costate(pc, P->precision, P->fwd.smem, P->fwd.threads, P->prio_hi, st)) != cudaSuccess)
         return cuda_fail(e, "launch k_costate");
       P->trace_end(tc, st);
-      if ((e = cudaEventRecord(P->ev_ct, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+      if (cap == cudaStreamCaptureStatusNone && (e = cudaEventRecord(P->ev_ct, st)) != cudaSuccess)
+        return cuda_fail(e, "cudaEventRecord");
       if ((e = cudaEventRecord(P->ev_b, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
       if ((e = cudaStreamWaitEvent(gs, P->ev_b, 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
       const int tg = P->trace_begin(2, gs);
