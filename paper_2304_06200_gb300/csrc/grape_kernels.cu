@@ -126,6 +126,10 @@ __device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_
                "cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n\t"
                "cp.async.bulk.commit_group;\n" ::"l"(gdst), "r"(s), "r"(bytes) : "memory");
 }
+// Each thread orders its own shared-memory writes before later async-proxy reads of them: every
+// thread that wrote a bulk copy's source runs this before the barrier after which one thread
+// issues the copy.
+__device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 // At most N of this thread's bulk copies may still be reading their sources.
 template <int N>
 __device__ __forceinline__ void bulk_wait_read() {
@@ -1531,6 +1535,7 @@ __global__ void __launch_bounds__(512, 1) k_costate(SweepParams p) {
           // all but its latest copy to finish reading.
           const uint32_t rbytes = (uint32_t)nrows * 16u;
           for (int i = threadIdx.x; i < nrows; i += blockDim.x) X0[i] = from_d2<T>(cscale(chi[i], fm));
+          async_proxy_fence();
           __syncthreads();
           if (threadIdx.x == 0 && rbytes) bulk_store(hl + (int64_t)(m - 1) * hstride, X0, rbytes);
           split_arrive<CLUSTER>();
@@ -1561,6 +1566,7 @@ __global__ void __launch_bounds__(512, 1) k_costate(SweepParams p) {
               }
             }
             if (q < m) {
+              async_proxy_fence();
               __syncthreads();
               if (threadIdx.x == 0 && rbytes) {
                 bulk_store(hl + (int64_t)(m - 1 - q) * hstride, X0 + dst * R, rbytes);
@@ -1586,6 +1592,7 @@ __global__ void __launch_bounds__(512, 1) k_costate(SweepParams p) {
             chb = from_d2<T>(chi[i]);
             X0[i] = chb;
           }
+          async_proxy_fence();
           __syncthreads();
           if (threadIdx.x == 0 && rbytes) bulk_store(hl + (int64_t)(m - 1) * hstride, X0, rbytes);
           split_arrive<CLUSTER>();
@@ -1615,6 +1622,7 @@ __global__ void __launch_bounds__(512, 1) k_costate(SweepParams p) {
               }
             }
             if (q < m) {
+              async_proxy_fence();
               __syncthreads();
               if (threadIdx.x == 0 && rbytes) {
                 bulk_store(hl + (int64_t)(m - 1 - q) * hstride, X0 + dst * R, rbytes);
