@@ -132,13 +132,17 @@ typedef struct {
   grape_alloc_fn alloc;        /* optional device allocator (see above)                   */
   grape_free_fn free;
   void* alloc_ctx;
-  int32_t backward_mode;       /* 0 = automatic, 1 = one team per column runs both backward
-                                  phases (adjoint re-propagation of psi), 3 = three-stage: the
-                                  forward stores every state, one team per column runs only the
-                                  costate chain and stores its Horner vectors, the gradient terms
-                                  of every step are computed independently on the remaining SMs
-                                  (needs ckpt_every 0 or 1; memory N * dim * n_states * 16 bytes
-                                  for the states plus two blocks of Horner vectors)            */
+  int32_t backward_mode;       /* 0 = automatic (three-stage when ckpt_every >= 0 and N >= 2,
+                                  else 1), 1 = one team per column runs both backward phases
+                                  (adjoint re-propagation of psi between checkpoints), 3 =
+                                  three-stage: the forward stores every state (ckpt_every 0 or 1;
+                                  N * dim * n_states * 16 bytes; automatic up to 8 GiB) or every
+                                  M-th one (ckpt_every = M > 1, or automatically M = 50 above
+                                  8 GiB; two segments of M states are recomputed from them), one
+                                  team per column runs only the costate chain and stores its
+                                  Horner vectors in three rotating block buffers, and the gradient
+                                  terms of every step of a block are computed independently on
+                                  the remaining SMs                                          */
   double bulk_norm_cap;        /* > 0: the (m, s) rule only considers s >= ||A||_1 / cap, i.e.
                                   ||B||_1 <= cap, which bounds the largest Taylor term; 0 = default
                                   (2.0 for the tensor-core modes, no cap for GRAPE_FP64 and
