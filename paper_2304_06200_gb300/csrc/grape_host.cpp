@@ -864,8 +864,11 @@ grape_status build(grape_problem* P, const grape_desc* d) {
   const bool stg = P->precision == GRAPE_FP32_BULK;           // compensated FP32 bulk: staged W
   const int smem_max = grape::max_dynamic_smem(dev) - 2048;   // static shared memory of the kernels
   // clocks per complex multiply-add per SM: FP64 4 FMAs (the model's constant from the sweeps' own
-  // measured rate); the compensated FP32 one about 48 FP32 operations at 128 lanes/clk
-  const double a_cost = stg ? 48.0 / 128.0 : 4.0 / 1.7;
+  // measured rate); the compensated FP32 one about 48 FP32 operations, whose dependent chains keep
+  // the FP32 pipe less than half busy: 105/128 clk, fitted to the three-transmon d = 512 forward
+  // (one CTA per column: 2.55 us per term measured against 1.5 us predicted at 48/128; teams of 16,
+  // barrier-dominated, matched either way)
+  const double a_cost = stg ? 105.0 / 128.0 : 4.0 / 1.7;
   const double b_cost = stg ? 24.0 / 128.0 : 2.0 / 1.7;
   int64_t nnz_ctrl = 0;
   for (int64_t e = 0; e < nnz; ++e) nnz_ctrl += ectr_ptr[e + 1] > ectr_ptr[e] ? 1 : 0;
