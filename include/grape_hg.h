@@ -288,8 +288,9 @@ double grape_error_bound(double x, int32_t m, int32_t s, int32_t sigma, int32_t 
  *     three-stage kind run their fused backward there.
  *   - Lanes: every other member's own launches (cluster teams, three-stage backward) on n_streams
  *     concurrent graph branches (0 = 8), assigned longest first; the queue shares lane 0.
- * queue_ctas: 0 = automatic (the queue's share of the batch's work times the SMs times the
- * kernel's CTAs per SM), > 0 = that many CTAs, < 0 = no queue (every member on the lanes).
+ * queue_ctas: 0 = automatic (from the members' timed warm evaluations: the count that balances
+ * the queue's CTA-time on its CTAs against the lane members' SM-time on the SMs left), > 0 = that
+ * many CTAs, < 0 = no queue (every member on the lanes).
  * u_warm: NULL, or per member NULL or HOST controls (K_i x N_i) of the warm evaluation that runs
  * before the recording (zero controls otherwise).  Three-stage members size their block buffers
  * for that evaluation's schedule, with 25% headroom; while a batch exists these buffers are not

@@ -1813,11 +1813,29 @@ grape_status batch_build(grape_batch* B, int n_streams, int queue_ctas, const do
         (e = cudaMemcpy(B->d_u + B->u_off[i], u_warm[i], ub, cudaMemcpyHostToDevice)) != cudaSuccess)
       return cuda_fail(e, "cudaMemcpy (warm controls)");
   }
-  for (int i = 0; i < count; ++i) {
-    grape_problem* P = B->probs[i];
-    grape_status s = run_forward(P, B->d_u + B->u_off[i], true, B->origin);
+  // each warm evaluation is timed on its own (the split between the work queue and the lanes below)
+  std::vector<double> t_warm(count, 0.0);
+  {
+    cudaEvent_t wa = nullptr, wb = nullptr;
+    if ((e = cudaEventCreate(&wa)) != cudaSuccess || (e = cudaEventCreate(&wb)) != cudaSuccess) {
+      if (wa) cudaEventDestroy(wa);
+      return cuda_fail(e, "cudaEventCreate");
+    }
+    grape_status s = GRAPE_OK;
+    for (int i = 0; i < count && !s; ++i) {
+      grape_problem* P = B->probs[i];
+      cudaEventRecord(wa, B->origin);
+      if ((s = run_forward(P, B->d_u + B->u_off[i], true, B->origin))) break;
+      if ((s = run_backward(P, B->origin))) break;
+      cudaEventRecord(wb, B->origin);
+      float ms = 0.0f;
+      if ((e = cudaEventSynchronize(wb)) != cudaSuccess || (e = cudaEventElapsedTime(&ms, wa, wb)) != cudaSuccess)
+        s = cuda_fail(e, "timing a warm evaluation");
+      t_warm[i] = ms;
+    }
+    cudaEventDestroy(wa);
+    cudaEventDestroy(wb);
     if (s) return s;
-    if ((s = run_backward(P, B->origin))) return s;
   }
   if ((e = cudaStreamSynchronize(B->origin)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
   // work estimate of every member: Taylor terms of its sweep x union entries x columns
@@ -1841,9 +1859,8 @@ grape_status batch_build(grape_batch* B, int n_streams, int queue_ctas, const do
   }
   // queue membership (queue_ctas < 0: none) and the queues, one per bulk precision
   B->queued.assign(count, 0);
-  double w_queue = 0.0, w_all = 0.0;
+  double w_queue = 0.0;
   for (int i = 0; i < count; ++i) {
-    w_all += work[i];
     if (queue_ctas >= 0 && queue_eligible(B->probs[i])) {
       B->queued[i] = 1;
       w_queue += work[i];
@@ -1864,7 +1881,6 @@ grape_status batch_build(grape_batch* B, int n_streams, int queue_ctas, const do
     std::vector<grape::GradReduceParams> red(Q);
     std::vector<int2> items;
     std::vector<double> item_cost;
-    double wq = 0.0;
     for (int j = 0; j < Q; ++j) {
       const int i = q.members[j];
       grape_problem* P = B->probs[i];
@@ -1890,7 +1906,6 @@ grape_status batch_build(grape_batch* B, int n_streams, int queue_ctas, const do
         items.push_back(make_int2(j, c));
         item_cost.push_back(col_work[i]);
       }
-      wq += work[i];
     }
     // longest first
     std::vector<int> idx(items.size());
@@ -1903,10 +1918,33 @@ grape_status batch_build(grape_batch* B, int n_streams, int queue_ctas, const do
     // or the caller's count; never more than items
     const int occ_f = std::max(1, grape::queue_ctas_per_sm(q.precision, false, q.threads_f, q.smem_f));
     const int occ_b = std::max(1, grape::queue_ctas_per_sm(q.precision, true, q.threads_b, q.smem_b));
-    const double share = w_all > 0.0 ? wq / w_all : 1.0;
+    // Automatic count: each queued member alone kept its n columns' CTAs busy for its warm time, so
+    // the queue holds sum(n_i t_i) CTA-ms of work; the lane members held about t_i x the SMs their
+    // teams occupy (twice the chain's for the three-stage backward).  The count balances the
+    // queue's time on c CTAs against the lanes' time on the SMs the queue leaves.
+    double q_cta_ms = 0.0, lane_sm_ms = 0.0;
+    for (int i : q.members) q_cta_ms += (double)B->probs[i]->n * t_warm[i];
+    for (int i = 0; i < count; ++i) {
+      if (B->queued[i]) continue;
+      const grape_problem* P = B->probs[i];
+      const int team = P->eig ? 8 : std::max(P->fwd.CL, P->bwd.CL);
+      const int sms = std::min(nsm, P->n * team * (P->bwd_mode == 3 ? 2 : 1));
+      lane_sm_ms += t_warm[i] * sms;
+    }
     auto pick = [&](int occ) {
-      int c = queue_ctas > 0 ? queue_ctas : (int)std::lround(share * nsm * occ);
-      return std::max(1, std::min(c, q.n_items));
+      const int c_max = std::max(1, std::min(q.n_items, nsm * occ));
+      if (queue_ctas > 0) return std::max(1, std::min(queue_ctas, q.n_items));
+      if (lane_sm_ms <= 0.0) return c_max;
+      int best_c = 1;
+      double best_t = 1e300;
+      for (int c = 1; c <= c_max; ++c) {
+        const double t = std::max(q_cta_ms / c, lane_sm_ms / std::max(1.0, nsm - (double)c / occ));
+        if (t < best_t) {
+          best_t = t;
+          best_c = c;
+        }
+      }
+      return best_c;
     };
     q.ctas_f = pick(occ_f);
     q.ctas_b = pick(occ_b);
