@@ -1918,10 +1918,12 @@ grape_status batch_build(grape_batch* B, int n_streams, int queue_ctas, const do
     // or the caller's count; never more than items
     const int occ_f = std::max(1, grape::queue_ctas_per_sm(q.precision, false, q.threads_f, q.smem_f));
     const int occ_b = std::max(1, grape::queue_ctas_per_sm(q.precision, true, q.threads_b, q.smem_b));
-    // Automatic count: each queued member alone kept its n columns' CTAs busy for its warm time, so
-    // the queue holds sum(n_i t_i) CTA-ms of work; the lane members held about t_i x the SMs their
-    // teams occupy (twice the chain's for the three-stage backward).  The count balances the
-    // queue's time on c CTAs against the lanes' time on the SMs the queue leaves.
+    // Automatic count: each queued member alone kept its n columns' CTAs busy for its warm time t, so
+    // the queue holds sum(n_i t_i) CTA-ms of work; a lane member held about t x the SMs its teams
+    // occupy.  Where the queued members carry under 5% of that, the lanes alone overlap them with the
+    // large members and the queue is left out (measured on the 64-instance mix: 6.3 s on lanes
+    // against 8.3-19.7 s with queues of 1-4 CTAs); otherwise the queue gets as many CTAs as it has
+    // items, up to the whole GPU, and releases them as it drains.
     double q_cta_ms = 0.0, lane_sm_ms = 0.0;
     for (int i : q.members) q_cta_ms += (double)B->probs[i]->n * t_warm[i];
     for (int i = 0; i < count; ++i) {
@@ -1931,21 +1933,16 @@ grape_status batch_build(grape_batch* B, int n_streams, int queue_ctas, const do
       const int sms = std::min(nsm, P->n * team * (P->bwd_mode == 3 ? 2 : 1));
       lane_sm_ms += t_warm[i] * sms;
     }
+    const bool to_lanes = queue_ctas == 0 && q_cta_ms < 0.05 * lane_sm_ms;
     auto pick = [&](int occ) {
-      const int c_max = std::max(1, std::min(q.n_items, nsm * occ));
       if (queue_ctas > 0) return std::max(1, std::min(queue_ctas, q.n_items));
-      if (lane_sm_ms <= 0.0) return c_max;
-      int best_c = 1;
-      double best_t = 1e300;
-      for (int c = 1; c <= c_max; ++c) {
-        const double t = std::max(q_cta_ms / c, lane_sm_ms / std::max(1.0, nsm - (double)c / occ));
-        if (t < best_t) {
-          best_t = t;
-          best_c = c;
-        }
-      }
-      return best_c;
+      return std::max(1, std::min(q.n_items, nsm * occ));
     };
+    if (to_lanes) {
+      for (int i : q.members) B->queued[i] = 0;
+      q.members.clear();
+      continue;
+    }
     q.ctas_f = pick(occ_f);
     q.ctas_b = pick(occ_b);
     grape::SweepParams* d_fwd = nullptr;
@@ -1979,6 +1976,12 @@ grape_status batch_build(grape_batch* B, int n_streams, int queue_ctas, const do
   }
   // the other members: longest first, greedy assignment to the least loaded lane; lane 0 also
   // carries the queues
+  B->queues.erase(std::remove_if(B->queues.begin(), B->queues.end(),
+                                 [](const grape_batch::Queue& q) { return q.members.empty(); }),
+                  B->queues.end());
+  w_queue = 0.0;
+  for (int i = 0; i < count; ++i)
+    if (B->queued[i]) w_queue += work[i];
   for (int i = 0; i < count; ++i)
     if (!B->queued[i]) B->order.push_back(i);
   std::stable_sort(B->order.begin(), B->order.end(), [&](int a, int b) { return work[a] > work[b]; });

@@ -472,7 +472,7 @@ def test_batch_mixes_the_queue_with_cluster_and_three_stage_members(precision):
     probs += [GrapeProblem(big, precision=precision, cluster=4, backward_mode=1),
               GrapeProblem(tri, precision=precision, cluster=2, backward_mode=3)]
     assert probs[-1].info()["backward_mode"] == 3
-    batch = GrapeBatch(probs, n_streams=3)
+    batch = GrapeBatch(probs, n_streams=3, queue_ctas=8)   # the queue forced beside the lanes
     inf = batch.info()
     queued = sum(_single_cta_teams(hg) for hg in probs)
     assert queued >= 4 and not _single_cta_teams(probs[-1]) and not _single_cta_teams(probs[-2])
