@@ -92,3 +92,23 @@ def test_oracle_matches_fullad_on_each_family(build):
     c, g = cost_and_grad_fullad(p, u)
     assert abs(r.cost - c) <= 1e-12 * abs(c)
     assert np.linalg.norm(r.grad - g) <= 1e-10 * np.linalg.norm(g)
+
+
+def test_dense_register_is_dense_hermitian_with_the_stated_norm():
+    """The d = 2048 register's drift: Hermitian, every element non-zero, matrix 1-norm 2 pi x 0.5 rad/ns;
+    the controls are sigma_x, sigma_y on qubit 0 (Hermitian, unitary, anticommuting); 16 orthonormal
+    states and a target in their span (a unitary on the subspace)."""
+    from workloads import dense_register_gate
+    p = dense_register_gate(n_steps=2)
+    H0 = p.H0.toarray()
+    assert p.dim == 2048 and p.H0.nnz == 2048 * 2048
+    assert np.allclose(H0, H0.conj().T, atol=0, rtol=0)
+    assert np.isclose(np.max(np.sum(np.abs(H0), axis=0)), 2 * np.pi * 0.5, rtol=1e-12)
+    X, Y = (h.toarray() for h in p.Hk)
+    for h in (X, Y):
+        assert np.array_equal(h, h.conj().T) and np.allclose(h @ h, np.eye(p.dim))
+    assert np.allclose(X @ Y + Y @ X, 0)
+    assert np.allclose(X[0, 1], 1) and np.allclose(Y[1, 0], 1j)   # qubit 0 = the lowest index bit
+    assert np.allclose(p.psi0.conj().T @ p.psi0, np.eye(16))
+    ov = p.psi0.conj().T @ p.target
+    assert np.allclose(ov.conj().T @ ov, np.eye(16))
